@@ -1,0 +1,307 @@
+"""Pins for the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test names the passage it follows.  None of them re-types the oracle's
+quadrant formula: the local update is checked against eq. Eik_discr itself
+(evaluated exactly in rational arithmetic), whole solutions against closed
+forms, the paper's printed errors, invariants of the discretisation
+(Remark discr_properties) and brute force.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1110_6220_gb300 import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def solve_all(orc, I):
+    U1 = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+    U2 = orc.fsm(I.F, I.h, I.si, I.sj, I.sq)
+    return U1, U2
+
+
+def _g(U, a, b):
+    """h^2 times the left side of eq. Eik_discr at a node whose smaller
+    x-neighbour is a and smaller y-neighbour is b, evaluated exactly."""
+    U, a, b = Fraction(U), Fraction(a), Fraction(b)
+    return max(U - a, 0) ** 2 + max(U - b, 0) ** 2
+
+
+# ---------------------------------------------------------------- local update
+
+
+def test_local_update_solves_eik_discr_exactly(orc):
+    """eq. Eik_discr: the update U is the root of
+    max(U-min(UW,UE),0)^2 + max(U-min(US,UN),0)^2 = (h/F)^2;
+    the left side is increasing in U, so bracketing the exact root by the
+    doubles 4 ulps below and above the returned U pins U to the rounding
+    error of evaluating a square root and three sums (a few ulps)."""
+    rng = np.random.default_rng(7)
+    cases = 0
+    for _ in range(4000):
+        f = float(rng.uniform(1e-4, 1.0))
+        base = float(rng.uniform(0, 3))
+        vals = base + rng.uniform(0, 1.5 * f, size=4) * (rng.random(4) < 0.8)
+        vals[rng.random(4) < 0.15] = np.inf
+        ue, uw, un, us = (float(v) for v in vals)
+        U = orc.node_update(ue, uw, un, us, f)
+        a, b = min(ue, uw), min(un, us)
+        if math.isinf(a) and math.isinf(b):
+            assert math.isinf(U)
+            continue
+        assert U > min(a, b)
+        lo, hi = U, U
+        for _ in range(4):
+            lo, hi = np.nextafter(lo, -np.inf), np.nextafter(hi, np.inf)
+        a_ = a if not math.isinf(a) else 1e300
+        b_ = b if not math.isinf(b) else 1e300
+        f2 = Fraction(f) ** 2
+        assert _g(lo, a_, b_) <= f2 <= _g(hi, a_, b_), (ue, uw, un, us, f, U)
+        cases += 1
+    assert cases > 3000
+
+
+def test_local_update_special_values(orc):
+    inf = math.inf
+    assert math.isinf(orc.node_update(inf, inf, inf, inf, 0.1))
+    assert math.isinf(orc.node_update(0.0, 0.0, 0.0, 0.0, inf))  # obstacle
+    # one finite neighbour: one-sided update, eq. one_sided_update
+    assert orc.node_update(inf, 0.25, inf, inf, 0.5) == 0.75
+    # equal neighbours in x and y: (2a + sqrt(2 f^2)) / 2 = a + f / sqrt(2)
+    assert abs(orc.node_update(1.0, 5.0, 1.0, 9.0, 0.5) - (1.0 + 0.5 / math.sqrt(2))) < 4e-16
+    # |a-b| >= f: only the smaller one-sided update is consistent
+    assert orc.node_update(0.0, inf, 2.0, inf, 1.0) == 1.0
+
+
+# ---------------------------------------------------------------- closed forms
+
+
+def test_corner_source_closed_form(orc):
+    """F == 1, source at a corner: axis nodes are exactly k*h (one-sided
+    updates along the axis, eq. one_sided_update); the diagonal neighbour is
+    h(1 + sqrt(2)/2) from the two-sided update with a = b = h."""
+    n, h = 9, 0.125
+    F = np.ones((n, n))
+    U = orc.fmm(F, h, [0], [0], [0.0])
+    for k in range(n):
+        assert U[0, k] == k * h and U[k, 0] == k * h
+    assert abs(U[1, 1] - h * (1 + math.sqrt(2) / 2)) <= 2 ** -52 * U[1, 1]
+
+
+@pytest.mark.parametrize("ny", [1, 2])
+def test_one_dimensional_reduction(orc, ny):
+    """A 1-D strip (ny = 1, or ny = 2 with an obstacle row) has no two-sided
+    updates, so U_i = min over sources of q_s + the sum of h/F over the nodes
+    from the source (exclusive) to i (inclusive): a path-graph shortest path."""
+    rng = np.random.default_rng(3)
+    n = 200
+    h = 1.0 / (n - 1)
+    F = np.ones((ny, n))
+    F[0] = rng.uniform(0.5, 2.0, size=n)
+    if ny == 2:
+        F[1] = 0.0
+    src = [17, 120]
+    q = [0.3, 0.0]
+    U = orc.fmm(F, h, src, [0, 0], q)
+    f = h / F[0]
+    best = np.full(n, np.inf)
+    for s, qs in zip(src, q):
+        right = qs + np.concatenate([[0.0], np.cumsum(f[s + 1:])])
+        left = qs + np.concatenate([[0.0], np.cumsum(f[:s][::-1])])[::-1]
+        cand = np.full(n, np.inf)
+        cand[s:] = right
+        cand[:s + 1] = np.minimum(cand[:s + 1], left)
+        best = np.minimum(best, cand)
+    assert np.allclose(U[0], best, rtol=1e-14, atol=0)
+    if ny == 2:
+        assert np.isinf(U[1]).all()
+
+
+def test_distance_function_converges_first_order(orc):
+    """F == 1, point source: the viscosity solution is the distance to the
+    centre (Sec. 5.3).  The upwind scheme is first order with the usual
+    point-source log factor: halving h divides the max error by 1.6 - 2.1,
+    and the discrete solution never undershoots the distance."""
+    prev = None
+    for n in (65, 129, 257, 513, 1025):
+        I = W.const_point(n)
+        U = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+        x = np.arange(n) * I.h
+        D = np.hypot(x[None, :] - 0.5, x[:, None] - 0.5)
+        err = np.abs(U - D).max()
+        assert (U >= D - 1e-15).all()
+        if prev is not None:
+            assert 1.6 <= prev / err <= 2.1, (n, prev / err)
+        prev = err
+
+
+@pytest.mark.slow
+def test_paper_printed_errors(orc):
+    """Tab. const and Tab. sinu_1 print the L_inf error of the 1408 x 1408
+    solution against Fast Marching on an h/4 grid (Sec. 5).  Reading the grid
+    as 1408 intervals (h = 1/1408) the oracle reproduces both to 0.5%."""
+    with open(os.path.join(GOLD, "paper_errors.json")) as fh:
+        gold = json.load(fh)
+    for case in gold["cases"]:
+        n = case["n"]
+        mk = getattr(W, case["workload"])
+        I = mk(n)
+        J = mk(4 * (n - 1) + 1)
+        U = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+        V = orc.fmm(J.F, J.h, J.si, J.sj, J.sq)[::4, ::4]
+        linf = np.abs(U - V).max()
+        assert abs(linf / case["Linf"] - 1) < 5e-3, (case["name"], linf)
+        l1 = np.abs(U - V).mean()
+        assert abs(l1 / case["L1"] - 1) < 0.1, (case["name"], l1)
+
+
+def test_fsm_sweep_count_constant_speed(orc):
+    """Tab. const: FSM needs 5 sweeps for F == 1 with a centre source (one per
+    quadrant plus the final sweep that changes nothing)."""
+    I = W.const_point(257)
+    _, ns = orc.fsm(I.F, I.h, I.si, I.sj, I.sq, return_sweeps=True)
+    assert ns == 5
+
+
+# ---------------------------------------------------------------- whole solver
+
+
+def test_fmm_fsm_jacobi_agree_on_tiny_grids(orc):
+    """FMM, FSM and Jacobi value iteration from +inf solve the same system
+    (Sec. 3.3: all produce the same numerical solution); Jacobi terminates
+    because the dependency digraph is acyclic (Sec. 3.2)."""
+    rng = np.random.default_rng(11)
+    for _ in range(300):
+        I = W.tiny_random(rng)
+        U1, U2 = solve_all(orc, I)
+        U3 = orc.jacobi(I.F, I.h, I.si, I.sj, I.sq)
+        fin = np.isfinite(U1)
+        assert (fin == np.isfinite(U2)).all() and (fin == np.isfinite(U3)).all()
+        scale = max(1.0, np.abs(U1[fin]).max())
+        assert np.abs(U1[fin] - U2[fin]).max() <= 1e-13 * scale
+        assert np.abs(U1[fin] - U3[fin]).max() <= 1e-13 * scale
+
+
+def _eik_discr_residual(I, U):
+    """Relative defect of eq. Eik_discr at every non-source finite node."""
+    ny, nx = U.shape
+    P = np.full((ny + 2, nx + 2), np.inf)
+    P[1:-1, 1:-1] = U
+    a = np.minimum(P[1:-1, :-2], P[1:-1, 2:])
+    b = np.minimum(P[:-2, 1:-1], P[2:, 1:-1])
+    f = np.where(I.F > 0, I.h / np.where(I.F > 0, I.F, 1), np.inf)
+    with np.errstate(invalid="ignore"):
+        lhs = np.maximum(U - a, 0) ** 2 + np.maximum(U - b, 0) ** 2
+    src = np.zeros_like(U, dtype=bool)
+    src[I.sj, I.si] = True
+    m = np.isfinite(U) & ~src
+    return np.abs(lhs[m] - f[m] ** 2) / f[m] ** 2
+
+
+def test_solution_satisfies_eik_discr(orc):
+    """The computed grid function satisfies eq. Eik_discr at every non-source
+    node (up to rounding), for smooth, checkerboard and random speeds."""
+    rng = np.random.default_rng(5)
+    insts = [W.sin_point(129), W.const_point(65)]
+    I = W.checker_maze(257, seed=2, n_walls=6)
+    insts.append(I)
+    insts += [W.tiny_random(rng) for _ in range(50)]
+    for I in insts:
+        U = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+        r = _eik_discr_residual(I, U)
+        # relative defect of a squared equation; ulp(U)/f amplification
+        if r.size:
+            assert r.max() < 1e-9, (I.name, r.max())
+        TV = orc.apply_T(I.F, I.h, I.si, I.sj, I.sq, U)
+        fin = np.isfinite(U)
+        assert (np.isfinite(TV) == fin).all()
+        assert np.all(np.abs(TV[fin] - U[fin]) <= 4 * np.spacing(np.abs(U[fin]) + 1e-300))
+
+
+def test_unreachable_and_obstacles(orc):
+    """F = 0 nodes stay +inf unless they are sources; a region walled off by
+    obstacles stays +inf; with no source everything is +inf."""
+    n = 20
+    F = np.ones((n, n))
+    F[:, 10] = 0.0
+    U = orc.fmm(F, 0.05, [3], [4], [0.0])
+    assert np.isinf(U[:, 10:]).all() and np.isfinite(U[:, :10]).all()
+    U = orc.fmm(F, 0.05, [10], [4], [0.5])  # a source on an obstacle
+    assert U[4, 10] == 0.5 and np.isfinite(U[4, 9]) and np.isfinite(U[4, 11])
+    U = orc.fmm(F, 0.05, [], [], [])
+    assert np.isinf(U).all()
+
+
+def test_duplicate_sources_keep_min(orc):
+    F = np.ones((6, 7))
+    U = orc.fmm(F, 0.2, [2, 2], [3, 3], [0.5, 0.1])
+    assert U[3, 2] == 0.1
+
+
+def test_d4_symmetry(orc):
+    """A centred source with a D4-symmetric speed gives a D4-symmetric
+    solution (the scheme treats the four directions alike)."""
+    n = 65
+    c = (n - 1) // 2
+    d = np.arange(n) - c
+    r2 = (d[None, :] ** 2 + d[:, None] ** 2).astype(np.float64) / (n - 1) ** 2
+    F = 1.0 + 0.5 * np.cos(3.0 * np.pi * r2)
+    for solve in (orc.fmm, orc.fsm):
+        U = solve(F, 1.0 / (n - 1), [c], [c], [0.0])
+        for V in (U.T, U[::-1, :], U[:, ::-1]):
+            assert np.abs(U - V).max() <= 2e-16 * U.max()
+
+
+def test_scaling_and_shift(orc):
+    """F -> cF gives U -> U/c (q = 0), and q -> q + s gives U -> U + s
+    (eq. Eik_discr is invariant under both)."""
+    rng = np.random.default_rng(9)
+    for _ in range(40):
+        I = W.tiny_random(rng)
+        q0 = np.zeros_like(I.sq)
+        U = orc.fmm(I.F, I.h, I.si, I.sj, q0)
+        fin = np.isfinite(U)
+        for c in (2.0, 0.5, 3.0):
+            Uc = orc.fmm(c * I.F, I.h, I.si, I.sj, q0)
+            assert (np.isfinite(Uc) == fin).all()
+            assert np.allclose(Uc[fin], U[fin] / c, rtol=1e-13, atol=1e-300)
+        Us = orc.fmm(I.F, I.h, I.si, I.sj, q0 + 0.75)
+        assert np.allclose(Us[fin], U[fin] + 0.75, rtol=1e-13, atol=0)
+
+
+def test_monotonicity(orc):
+    """Remark discr_properties (monotone scheme): a faster speed field or an
+    extra source never raises the solution."""
+    rng = np.random.default_rng(13)
+    for _ in range(40):
+        I = W.tiny_random(rng)
+        U = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+        G = I.F * rng.uniform(1.0, 1.5, size=I.F.shape)
+        G[(I.F == 0) & (rng.random(I.F.shape) < 0.5)] = 1.0  # open some obstacles
+        U2 = orc.fmm(G, I.h, I.si, I.sj, I.sq)
+        assert (U2 <= U * (1 + 1e-14)).all()
+        k = int(rng.integers(0, I.nx * I.ny))
+        U3 = orc.fmm(I.F, I.h, np.append(I.si, k % I.nx), np.append(I.sj, k // I.nx),
+                     np.append(I.sq, 0.05))
+        assert (U3 <= U * (1 + 1e-14)).all()
+
+
+def test_causality(orc):
+    """Remark discr_properties (causal scheme): every finite non-source node
+    has a neighbour with a strictly smaller value."""
+    rng = np.random.default_rng(17)
+    for I in [W.tiny_random(rng) for _ in range(60)] + [W.sin_point(65)]:
+        U = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+        ny, nx = U.shape
+        P = np.full((ny + 2, nx + 2), np.inf)
+        P[1:-1, 1:-1] = U
+        m = np.minimum.reduce([P[1:-1, :-2], P[1:-1, 2:], P[:-2, 1:-1], P[2:, 1:-1]])
+        src = np.zeros_like(U, dtype=bool)
+        src[I.sj, I.si] = True
+        fin = np.isfinite(U) & ~src
+        assert (m[fin] < U[fin]).all()
