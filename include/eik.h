@@ -1,0 +1,137 @@
+/*
+ * eik.h -- C ABI of the GB300-native two-scale Eikonal solver.
+ *
+ * Problem (Chacon & Vladimirsky, "Fast two-scale methods for Eikonal
+ * equations", Sec. 1 eq. Eikonal and Sec. 3): find U on an nx x ny Cartesian
+ * grid with spacing h such that, at every node that is not a source, the
+ * first-order upwind discretisation of |grad u| F = 1 holds (Sec. 3,
+ * eq. Eik_discr):
+ *
+ *   max(U - min(U_W, U_E), 0)^2 + max(U - min(U_S, U_N), 0)^2 = (h / F)^2,
+ *
+ * with U = q on the source set Q.  Neighbours outside the grid count as
+ * +infinity (the exit-set form of Sec. 3: q = +inf on the boundary outside
+ * Q).  F = 0 marks an obstacle: such a node stays +inf unless it is a source.
+ *
+ * Method: the heap-cell idea of Sec. 4.2 (Alg. generic_LC_cells with the cell
+ * values of eq. cell_value and the directional flags of Remark
+ * HCM_preferred_sweeps), recast for the GPU -- k x k cells are released from
+ * a device-side queue in buckets of cell value instead of one at a time, and
+ * each released cell is swept to convergence in shared memory.  By Theorem
+ * convergence the result is the exact solution of eq. Eik_discr for any
+ * removal order.
+ *
+ * Layout of every grid array passed in or out: row-major, x fastest, node
+ * (i, j) at index j*nx + i, x_i = i*h, y_j = j*h.
+ *
+ * Pointers: every data pointer (F, sources, U) may be a host pointer or a
+ * CUDA device pointer; the library detects which.  Host buffers are copied
+ * through the plan's workspace; pinned host memory makes those copies faster.
+ * The caller owns all buffers; they must stay valid until the call that uses
+ * them has returned (eik_solve, eik_solve_batch) or until eik_poll reports
+ * EIK_OK (eik_submit).
+ *
+ * Errors: every function returns an eik status code (0 = EIK_OK, negative =
+ * error); nothing aborts, throws or traps across this boundary.  Device-side
+ * waits are bounded by a deadline after which the solve stops with
+ * EIK_ETIMEDOUT and the CUDA context stays usable.
+ *
+ * Threading: an eik_plan may be used by one thread at a time; different plans
+ * are independent.  A server (eik_server) is thread-safe.
+ */
+#ifndef EIK_H
+#define EIK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+enum {
+    EIK_OK = 0,
+    EIK_EINVAL = -1,         /* malformed argument (see each function) */
+    EIK_ENOMEM = -2,         /* device or host allocation failed */
+    EIK_EBUSY = -3,          /* admission refused: over the memory budget or no slot */
+    EIK_EAGAIN = -4,         /* eik_poll: request not finished yet */
+    EIK_ETIMEDOUT = -5,      /* device deadline expired; result incomplete */
+    EIK_ENOTCONVERGED = -6,  /* sweep cap hit, or the FP32+refinement
+                                certificate did not reach the tolerance */
+    EIK_ECUDA = -7           /* a CUDA runtime call failed */
+};
+
+/* Precision modes.  EIK_FP64: every local update in FP64.  EIK_FP32_REFINE:
+ * cell solves in FP32 with the cancellation-free quadratic, then an FP64
+ * refinement pass seeded by the FP32 result, then an FP64 residual check
+ * whose bound (eik_stats.err_bound) certifies the tolerance. */
+enum { EIK_FP64 = 0, EIK_FP32_REFINE = 1 };
+
+/* Problem-shape description (Sec. 3 problem statement plus the method's
+ * cell size).  All fields are read at eik_plan_create. */
+typedef struct {
+    int32_t nx, ny;        /* grid nodes per side, each >= 2 */
+    double h;              /* grid spacing, > 0 */
+    int32_t cell_k;        /* cell side k in nodes: 4, 8, 16, 32 or 64; 0 = choose */
+    double bucket_width;   /* width of a bucket of cell values; <= 0: k * min(h/F) */
+    int32_t precision;     /* EIK_FP64 or EIK_FP32_REFINE */
+    double tol;            /* FP32_REFINE: certified max error / max|u|; <= 0: 1e-5 */
+    int64_t deadline_ns;   /* device wall-clock limit per solve; <= 0: 20 s */
+} eik_plan_desc;
+
+/* One problem instance (Sec. 3: speed F, exit set Q with values q). */
+typedef struct {
+    const double* F;        /* nx*ny speeds, F >= 0 and finite; 0 = obstacle */
+    const int32_t* src_ij;  /* 2*nsrc ints: (i, j) of each source node */
+    const double* src_q;    /* nsrc source values q, finite; duplicates keep the min */
+    int32_t nsrc;           /* number of sources, >= 0 (0: U is +inf everywhere) */
+    double* U;              /* out: nx*ny values; +inf = unreachable */
+} eik_instance;
+
+/* Per-solve report.  Counters follow the paper's cost accounting (Sec. 5):
+ * avhr = cell removals / cells (AvHR), avs = sweeps / cells (AvS). */
+typedef struct {
+    double ms;              /* device time from inputs resident to result ready */
+    double mpts_per_s;      /* nx*ny / ms / 1000 */
+    double updates_per_pt;  /* local updates evaluated / (nx*ny) */
+    double avhr;            /* cell visits / number of cells */
+    double avs;             /* cell sweeps / number of cells */
+    double max_residual;    /* FP64 max |V - T(V)| over finite non-source nodes */
+    double err_bound;       /* certified max |V - U| / max|U| (FP32_REFINE); 0 for FP64 */
+    double bucket_width;    /* bucket width used */
+    int64_t cell_visits;    /* total cell removals (all passes) */
+    int64_t rounds;         /* grid-wide rounds (barrier-separated bucket releases) */
+    int64_t buckets;        /* bucket advances (threshold moves) */
+    int32_t cell_k;         /* cell size used */
+    int32_t status;         /* EIK_OK or the error of this solve */
+} eik_stats;
+
+typedef struct eik_plan_s* eik_plan;
+
+/* Human-readable name of a status code.  Never NULL. */
+const char* eik_strerror(int code);
+
+/* Create a plan for one grid shape: validates *d (EIK_EINVAL for nx or ny <
+ * 2, h <= 0, a cell_k outside {0,4,8,16,32,64}, an unknown precision), and
+ * allocates the device workspace (EIK_ENOMEM on failure).  cuda_stream is a
+ * cudaStream_t on which all of the plan's work is queued; NULL makes the plan
+ * create its own non-blocking stream.  On success *out owns the workspace. */
+int eik_plan_create(eik_plan* out, const eik_plan_desc* d, void* cuda_stream);
+
+/* Release a plan and its device workspace.  NULL is ignored. */
+void eik_plan_destroy(eik_plan p);
+
+/* Bytes of device workspace a plan for *d would hold (0 if *d is invalid). */
+size_t eik_plan_workspace_bytes(const eik_plan_desc* d);
+
+/* Solve one instance on the plan's grid shape; blocks until U is written.
+ * EIK_EINVAL: NULL pointers, nsrc < 0, a source outside the grid or with a
+ * non-finite q, an F value that is negative, NaN or infinite.  st may be NULL. */
+int eik_solve(eik_plan p, const eik_instance* in, eik_stats* st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EIK_H */

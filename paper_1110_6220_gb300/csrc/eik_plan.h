@@ -1,0 +1,86 @@
+// eik_plan.h -- host-side structures shared by the single-solve, batch and
+// serving entry points.  Internal: not part of the C ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "eik_common.cuh"
+
+namespace eik {
+
+// Padded device layout of one instance (see SolveParams in eik_common.cuh).
+struct Layout {
+    int nx, ny, k;
+    int cxn, cyn, J;
+    int nxp, nyp;
+    int upitch, urows;  // U arrays: urows x upitch elements
+    int fpitch, frows;  // f arrays: frows x fpitch elements
+};
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+// Device workspace of one instance.
+struct Workspace {
+    Layout L;
+    bool fp32;
+    double* U64;
+    double* f64;
+    float* U32;
+    float* f32;
+    double* Fstage;  // device copy of a host F
+    unsigned long long* cval;
+    int* qflag;
+    int* dirmask;
+    int* visits;
+    unsigned char* has_src;
+    int* lists;
+    Ctl* ctl;          // [0] FP32 pass, [1] FP64 pass (or the only pass)
+    ResidualOut* res;  // follows ctl[1]
+    CUtensorMap tmU64, tmF64, tmU32, tmF32;
+};
+
+struct HostSources {
+    std::vector<int> node;                     // unique source nodes, j*nx + i
+    std::vector<double> q;                     // min q per node
+    std::vector<int> cell;                     // cells that hold sources
+    std::vector<unsigned long long> cell_key;  // key(max q) per such cell
+    double q_min = 0.0;
+};
+
+struct SrcDev {
+    DevBuf buf;
+};
+
+bool desc_valid(const eik_plan_desc* d);
+int default_k(const eik_plan_desc* d);
+Layout make_layout(int nx, int ny, int k);
+size_t layout_bytes(const Layout& L, bool fp32);
+int workspace_alloc(Workspace* w, const Layout& L, bool fp32, cudaStream_t st);
+void workspace_free(Workspace* w);
+int prepare_sources(const Layout& L, const eik_instance* in, HostSources* hs);
+bool is_device_ptr(const void* p);
+int grow_staging(DevBuf* b, size_t bytes);
+int enqueue_solve(Workspace* w, const eik_plan_desc* d, const double* Fdev, const HostSources& hs,
+                  SrcDev* sd, int num_sms, cudaStream_t st);
+void finish_stats(const Layout& L, const eik_plan_desc* d, const Ctl* c32, const Ctl* c64,
+                  const ResidualOut* r, double q_min, bool fp32, double ms, eik_stats* st);
+
+}  // namespace eik
+
+struct eik_plan_s {
+    eik_plan_desc d;
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    eik::Workspace ws{};
+    eik::SrcDev src;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    void* host_ctl = nullptr;  // pinned copy of ctl[2] + residual
+};
