@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark of the two-scale Eikonal solver (one JSON line on rank 0).
+
+A step is one complete solve through the C ABI of the 1025 x 1025 grid with
+speed F = 1 + 0.5 sin(20 pi x) sin(20 pi y) and a point source at the centre
+(the paper's Tab. sinu_1 example at the single-GPU size): FP32 cell solves,
+the FP64 refinement pass and the FP64 residual certificate (precision
+"fp32ref", the default), or the plain FP64 solve (--precision fp64).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own replica on its own GPU (the single
+grid does not shard without an exchange step; instances are independent), so
+scaling is weak and value = total points solved by all ranks / max rank time.
+--impl reference times the CPU FP64 oracle (Fast Marching) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "converged Mpts/s at max|err| vs FP64 oracle"
+UNIT = "Mpts/s"
+N_GRID = 1025
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32ref", "fp64"], default="fp32ref")
+    ap.add_argument("--k", type=int, default=0, help="cell size (0: the tuned default)")
+    ap.add_argument("--bucket-width", type=float, default=0.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload():
+    from paper_1110_6220_gb300 import workloads as W
+    return W.sin_point(N_GRID, omega=20.0, amp=0.5)
+
+
+def config_dict(args, k, precision):
+    return {"workload": f"single solve, {N_GRID}x{N_GRID} grid on [0,1]^2, "
+                        "F=1+0.5 sin(20 pi x) sin(20 pi y), point source at centre",
+            "grid": N_GRID, "precision": precision, "cell_k": k,
+            "bucket_width": "auto (k * min h/F)" if args.bucket_width <= 0 else args.bucket_width,
+            "parallelism": "replicas (one independent grid per GPU)",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ------------------------------------------------------------------ CPU side
+def cpu_baseline(I, seconds):
+    """The oracle FMM, as it stands, on one host core: whole solves of the
+    same grid until `seconds` have passed (at least one)."""
+    import oracle
+    oracle.build()
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.fmm(I.F, I.h, I.si, I.sj, I.sq)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": n * I.npts / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} full {I.nx}x{I.ny} solves with the FP64 Fast Marching oracle "
+                      f"(binary heap), 1 thread, {el:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    I = workload()
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.fmm(I.F, I.h, I.si, I.sj, I.sq)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.fmm(I.F, I.h, I.si, I.sj, I.sq)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps * I.npts / tot / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args, 0, "fp64 (CPU oracle)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full {I.nx}x{I.ny} FMM solves, 1 thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU side
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows]
+        smax = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].strip().lower() == "active"})
+        busy = [s for s in sm if s > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "of fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1110_6220_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, k):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = t.get(f"{kernel}/k{k}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the solver has no CPU path)")
+    torch.cuda.set_device(local)
+    from paper_1110_6220_gb300 import build
+    build.build()
+    from paper_1110_6220_gb300 import eik
+
+    I = workload()
+    prec = eik.EIK_FP32_REFINE if args.precision == "fp32ref" else eik.EIK_FP64
+    k = args.k or 8
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", local)
+    F = torch.from_numpy(I.F).to(dev)
+    src = torch.from_numpy(I.src_ij).to(dev)
+    q = torch.from_numpy(I.sq).to(dev)
+    U = torch.empty_like(F)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    plan = eik.Plan(I.nx, I.ny, I.h, k, prec, bucket_width=args.bucket_width, stream=stream)
+
+    def step():
+        rc, st = plan.solve(F, src, q, U)
+        if rc:
+            raise RuntimeError(f"eik_solve: {eik.eik_strerror(rc)}")
+        return st
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stats = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            stats.append(step())
+            e1.record(stream)
+        torch.cuda.synchronize()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        dist.barrier()
+    value = world * args.steps * I.npts / (tot_ms / 1e3) / 1e6
+
+    # ---- end to end through the public API with host (pinned) buffers
+    Fh = torch.from_numpy(I.F).pin_memory()
+    srch = torch.from_numpy(I.src_ij).pin_memory()
+    qh = torch.from_numpy(I.sq).pin_memory()
+    Uh = torch.empty(I.F.shape, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        plan.solve(Fh, srch, qh, Uh)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rc, _ = plan.solve(Fh, srch, qh, Uh)
+        b.record(stream)
+        b.synchronize()
+        if rc:
+            raise RuntimeError(f"eik_solve (host buffers): {eik.eik_strerror(rc)}")
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_tot = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_tot], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_tot = float(t.item())
+    e2e_value = world * args.steps * I.npts / (e2e_tot / 1e3) / 1e6
+
+    if rank == 0:
+        Ug = U.cpu().numpy()
+        import oracle
+        V = oracle.fmm(I.F, I.h, I.si, I.sj, I.sq)
+        fin = np.isfinite(V)
+        rel_err = float(np.abs(Ug[fin] - V[fin]).max() / np.abs(V[fin]).max())
+        same_inf = bool((np.isfinite(Ug) == fin).all())
+
+        # ---- roofline of the dominant kernel (the longer persistent pass)
+        p32 = statistics.mean(s.pass_ms[0] for s in stats)
+        p64 = statistics.mean(s.pass_ms[1] for s in stats)
+        if p32 > p64:
+            kname, kms, bpp = "k_solve<float>", p32, 12.0 * (1 + 4.0 / k)
+        else:
+            kname, kms, bpp = "k_solve<double>", p64, 24.0 * (1 + 4.0 / k)
+        peak, peak_src = measured_hbm()
+        achieved = bpp * I.npts / (kms / 1e3) / 1e9
+        traffic = ncu_traffic(kname, k)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                "kernel": kname, "kernel_ms": kms,
+                "algorithmic_bytes_per_pt": bpp}
+        s0 = stats[-1]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if prec else "f64", "data": "synthetic",
+                "config": config_dict(args, k, args.precision),
+                "max_rel_err": rel_err, "inf_pattern_exact": same_inf,
+                "err_bound": s0.err_bound, "status": eik.eik_strerror(s0.status),
+                "roofline": roof,
+                "e2e": {"value": e2e_value, "unit": UNIT,
+                        "h2d_bytes_per_step": int(I.F.nbytes + I.src_ij.nbytes + I.sq.nbytes),
+                        "d2h_bytes_per_step": int(I.F.nbytes)},
+                "gpu_launches": int(sum(s.launches for s in stats)),
+                "clocks": clk.summary(),
+                "solver": {"avhr": s0.avhr, "avs": s0.avs, "updates_per_pt": s0.updates_per_pt,
+                           "rounds": s0.rounds, "buckets": s0.buckets,
+                           "pass_ms": [p32, p64], "solve_ms_device": statistics.mean(s.ms for s in stats),
+                           "paper_hcm_k8_1408": {"avhr": 1.117, "avs": 4.350,
+                                                 "cite": "Tab. sinu_1, HCM 176x176 cells"}}}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(I, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

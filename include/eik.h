@@ -103,6 +103,9 @@ typedef struct {
     int64_t cell_visits;    /* total cell removals (all passes) */
     int64_t rounds;         /* grid-wide rounds (barrier-separated bucket releases) */
     int64_t buckets;        /* bucket advances (threshold moves) */
+    double pass_ms[2];      /* device time of the persistent FP32 pass [0] and FP64 pass [1]
+                               (CUDA events on the plan's stream; 0 if not run) */
+    int32_t launches;       /* kernels this solve launched */
     int32_t cell_k;         /* cell size used */
     int32_t status;         /* EIK_OK or the error of this solve */
 } eik_stats;

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <limits>
@@ -63,19 +64,20 @@ Layout make_layout(int nx, int ny, int k) {
     // room for the FP32 box (k+4 wide from column cx*k) and a multiple of 16 B rows
     L.upitch = round_up(L.nxp + 4, 32);
     L.urows = L.nyp + 2;
-    L.fpitch = round_up(L.nxp, 32);
-    L.frows = L.nyp;
+    // f shares U's layout (ring included) so that its TMA box carries the halo
+    L.fpitch = L.upitch;
+    L.frows = L.urows;
     return L;
 }
 
 size_t layout_bytes(const Layout& L, bool fp32) {
     size_t b = 0;
     const size_t un = (size_t)L.upitch * L.urows, fn = (size_t)L.fpitch * L.frows;
-    b += un * 8 + fn * 8;                  // U64, f64
-    if (fp32) b += un * 4 + fn * 4;        // U32, f32
-    b += (size_t)L.nx * L.ny * 8;          // staging for host F
-    b += (size_t)L.J * (8 + 4 + 4 + 4 + 1);  // cval, qflag, dirmask, visits, has_src
-    b += (size_t)5 * L.J * 4;              // lists
+    if (fp32) b += un * (4 + 8) + fn * (4 + 8);  // U32, Udf, f32, fdf
+    else b += un * 8 + fn * 8;                   // U64, f64
+    b += (size_t)L.nx * L.ny * 8;                // staging for host F / output
+    b += (size_t)L.J * (8 + 4 + 4 + 1);          // cval, qflag, visits, has_src
+    b += (size_t)5 * L.J * 4;                    // lists
     b += 2 * sizeof(Ctl) + sizeof(ResidualOut);
     return b;
 }
@@ -124,19 +126,22 @@ static void* dalloc(size_t bytes, int* err) {
 
 int workspace_alloc(Workspace* w, const Layout& L, bool fp32, cudaStream_t st) {
     int err = 0;
+    std::memset((void*)w, 0, sizeof(*w));
     w->L = L;
     w->fp32 = fp32;
     const size_t un = (size_t)L.upitch * L.urows, fn = (size_t)L.fpitch * L.frows;
-    w->U64 = (double*)dalloc(un * 8, &err);
-    w->f64 = (double*)dalloc(fn * 8, &err);
     if (fp32) {
         w->U32 = (float*)dalloc(un * 4, &err);
         w->f32 = (float*)dalloc(fn * 4, &err);
+        w->Udf = (float2*)dalloc(un * 8, &err);
+        w->fdf = (float2*)dalloc(fn * 8, &err);
+    } else {
+        w->U64 = (double*)dalloc(un * 8, &err);
+        w->f64 = (double*)dalloc(fn * 8, &err);
     }
     w->Fstage = (double*)dalloc((size_t)L.nx * L.ny * 8, &err);
     w->cval = (unsigned long long*)dalloc((size_t)L.J * 8, &err);
     w->qflag = (int*)dalloc((size_t)L.J * 4, &err);
-    w->dirmask = (int*)dalloc((size_t)L.J * 4, &err);
     w->visits = (int*)dalloc((size_t)L.J * 4, &err);
     w->has_src = (unsigned char*)dalloc((size_t)L.J, &err);
     w->lists = (int*)dalloc((size_t)5 * L.J * 4, &err);
@@ -147,25 +152,36 @@ int workspace_alloc(Workspace* w, const Layout& L, bool fp32, cudaStream_t st) {
     }
     w->res = (ResidualOut*)(w->ctl + 2);
     // the +inf ring (and padding columns) never change after this fill
-    const double INF = std::numeric_limits<double>::infinity();
-    if (launch_fill(w->U64, un, INF, st) != cudaSuccess) err = EIK_ECUDA;
-    if (fp32 && launch_fill32(w->U32, un, std::numeric_limits<float>::infinity(), st) != cudaSuccess)
+    if (w->U64 && launch_fill(w->U64, un, std::numeric_limits<double>::infinity(), st) != cudaSuccess)
         err = EIK_ECUDA;
+    if (w->U32 && launch_fill32(w->U32, un, std::numeric_limits<float>::infinity(), st) != cudaSuccess)
+        err = EIK_ECUDA;
+    if (w->Udf && launch_fill_df(w->Udf, un, st) != cudaSuccess) err = EIK_ECUDA;
+    // f's ring: +inf (obstacles) forever
+    if (w->f64 && launch_fill(w->f64, fn, std::numeric_limits<double>::infinity(), st) != cudaSuccess)
+        err = EIK_ECUDA;
+    if (w->f32 && launch_fill32(w->f32, fn, std::numeric_limits<float>::infinity(), st) != cudaSuccess)
+        err = EIK_ECUDA;
+    if (w->fdf && launch_fill_df(w->fdf, fn, st) != cudaSuccess) err = EIK_ECUDA;
     const int K = L.k;
-    // U: width = pitch so that the FP32 box (k+4 wide) never leaves the array
-    if (!make_map(&w->tmU64, w->U64, true, L.upitch, L.urows, L.upitch, K + 2, K + 2)) err = EIK_ECUDA;
-    if (!make_map(&w->tmF64, w->f64, true, L.fpitch, L.frows, L.fpitch, K, K)) err = EIK_ECUDA;
+    // U maps span the whole pitch, so a box (k+2 or k+4 wide) never leaves the
+    // array; 8-byte values (doubles or float pairs) move as FLOAT64 elements
     if (fp32) {
         if (!make_map(&w->tmU32, w->U32, false, L.upitch, L.urows, L.upitch, K + 4, K + 2)) err = EIK_ECUDA;
-        if (!make_map(&w->tmF32, w->f32, false, L.fpitch, L.frows, L.fpitch, K, K)) err = EIK_ECUDA;
+        if (!make_map(&w->tmF32, w->f32, false, L.fpitch, L.frows, L.fpitch, K + 4, K + 2)) err = EIK_ECUDA;
+        if (!make_map(&w->tmUdf, w->Udf, true, L.upitch, L.urows, L.upitch, K + 2, K + 2)) err = EIK_ECUDA;
+        if (!make_map(&w->tmFdf, w->fdf, true, L.fpitch, L.frows, L.fpitch, K + 2, K + 2)) err = EIK_ECUDA;
+    } else {
+        if (!make_map(&w->tmU64, w->U64, true, L.upitch, L.urows, L.upitch, K + 2, K + 2)) err = EIK_ECUDA;
+        if (!make_map(&w->tmF64, w->f64, true, L.fpitch, L.frows, L.fpitch, K + 2, K + 2)) err = EIK_ECUDA;
     }
     if (err) workspace_free(w);
     return err;
 }
 
 void workspace_free(Workspace* w) {
-    void* ptrs[] = {w->U64, w->f64, w->U32, w->f32, w->Fstage, w->cval, w->qflag,
-                    w->dirmask, w->visits, w->has_src, w->lists, w->ctl};
+    void* ptrs[] = {w->U64, w->f64, w->U32, w->f32, w->Udf, w->fdf, w->Fstage,
+                    w->cval, w->qflag, w->visits, w->has_src, w->lists, w->ctl};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     std::memset((void*)w, 0, sizeof(*w));
@@ -203,6 +219,8 @@ int prepare_sources(const Layout& L, const eik_instance* in, HostSources* hs) {
         hs->q.push_back(s[e].second);
         hs->q_min = std::min(hs->q_min, s[e].second);
     }
+    // the device works on q - q_min >= 0 (see the solver: ordered bit patterns)
+    for (double& v : hs->q) v -= hs->q_min;
     // cell value of a source cell: max q over its sources (Sec. 4.2, HCM item 1)
     std::vector<std::pair<int, double>> cq;
     for (size_t e = 0; e < hs->node.size(); ++e) {
@@ -245,10 +263,35 @@ int grow_staging(DevBuf* b, size_t bytes) {
 }
 
 // ---------------------------------------------------------------- one solve
+// EIK_PROFILE=1 (debugging aid): kernels accumulate per-phase clock cycles and
+// each solve prints them to stderr.
+int profiling() {
+    static int on = -1;
+    if (on < 0) {
+        const char* e = std::getenv("EIK_PROFILE");
+        on = (e && e[0] == '1') ? 1 : 0;
+    }
+    return on;
+}
+
+static void print_profile(const char* what, const Ctl* c) {
+    const char* names[8] = {"split", "barrier", "list+pop", "tma", "sweeps", "writeback", "activate",
+                            "warp-visits"};
+    double tot = 0;
+    for (int i = 0; i < 7; ++i) tot += (double)c->prof[i];
+    std::fprintf(stderr, "[eik profile %s] rounds=%llu", what, (unsigned long long)c->rounds);
+    for (int i = 0; i < 7; ++i)
+        std::fprintf(stderr, " %s=%.1f%%", names[i], tot > 0 ? 100.0 * c->prof[i] / tot : 0.0);
+    std::fprintf(stderr, " warp-visits=%llu cyc/visit(sweeps)=%.0f cyc/visit(tma)=%.0f cyc/visit(act)=%.0f\n",
+                 (unsigned long long)c->prof[7], c->prof[7] ? (double)c->prof[4] / c->prof[7] : 0.0,
+                 c->prof[7] ? (double)c->prof[3] / c->prof[7] : 0.0,
+                 c->prof[7] ? (double)c->prof[6] / c->prof[7] : 0.0);
+}
 // Queue the whole solve of one instance on `st` (inputs already validated;
 // F on the device).  Reads nothing back.
 int enqueue_solve(Workspace* w, const eik_plan_desc* d, const double* Fdev, const HostSources& hs,
-                  SrcDev* sd, int num_sms, cudaStream_t st) {
+                  SrcDev* sd, int num_sms, cudaStream_t st, cudaEvent_t* ev, int* launches) {
+    int nl = 0;
     const Layout& L = w->L;
     const bool fp32 = d->precision == EIK_FP32_REFINE;
     // upload the (small) source tables
@@ -271,12 +314,15 @@ int enqueue_solve(Workspace* w, const eik_plan_desc* d, const double* Fdev, cons
     cudaMemsetAsync(w->ctl, 0, 2 * sizeof(Ctl) + sizeof(ResidualOut), st);
     cudaMemsetAsync(w->cval, 0xff, (size_t)L.J * 8, st);
     cudaMemsetAsync(w->qflag, 0, (size_t)L.J * 4, st);
-    cudaMemsetAsync(w->dirmask, 0, (size_t)L.J * 4, st);
     cudaMemsetAsync(w->visits, 0, (size_t)L.J * 4, st);
     cudaMemsetAsync(w->has_src, 0, (size_t)L.J, st);
     Ctl* first_ctl = fp32 ? ctl32 : ctl64;
     if (launch_ctl_init(first_ctl, (int)ncell, st) != cudaSuccess) return EIK_ECUDA;
-    if (fp32 && launch_ctl_init(ctl64, 0, st) != cudaSuccess) return EIK_ECUDA;
+    ++nl;
+    if (fp32) {
+        if (launch_ctl_init(ctl64, 0, st) != cudaSuccess) return EIK_ECUDA;
+        ++nl;
+    }
 
     InitParams ip{};
     ip.F = Fdev;
@@ -284,33 +330,32 @@ int enqueue_solve(Workspace* w, const eik_plan_desc* d, const double* Fdev, cons
     ip.ny = L.ny;
     ip.h = d->h;
     ip.f64 = w->f64;
-    ip.f64pitch = L.fpitch;
+    ip.f32 = w->f32;
+    ip.fdf = w->fdf;
+    ip.fpitch = L.fpitch;
     ip.U64 = w->U64;
-    ip.u64pitch = L.upitch;
-    if (fp32) {
-        ip.f32 = w->f32;
-        ip.f32pitch = L.fpitch;
-        ip.U32 = w->U32;
-        ip.u32pitch = L.upitch;
-    }
+    ip.U32 = w->U32;
+    ip.Udf = w->Udf;
+    ip.upitch = L.upitch;
     ip.nxp = L.nxp;
     ip.nyp = L.nyp;
     ip.ctl = first_ctl;
     if (launch_init_grid(ip, st) != cudaSuccess) return EIK_ECUDA;
+    ++nl;
     SourceInit si{d_node, d_q, (int)nsrc, d_cell, d_ckey, (int)ncell, L.nx, L.k, L.cxn};
-    if (launch_init_sources(ip, si, w->cval, w->qflag, w->dirmask, w->has_src, w->lists + 3 * L.J,
-                            st) != cudaSuccess)
+    if (launch_init_sources(ip, si, w->cval, w->qflag, w->has_src, w->lists + 3 * L.J, st) !=
+        cudaSuccess)
         return EIK_ECUDA;
+    if (nsrc) ++nl;
 
     const long long deadline = d->deadline_ns > 0 ? d->deadline_ns : 20000000000ll;
-    LaunchShape shape;
-    if (fp32) {
-        if (solver_shape_f32(L.k, num_sms, &shape)) return EIK_ECUDA;
-        SolveParams<float> p{};
-        p.tmU = w->tmU32;
-        p.tmF = w->tmF32;
-        p.U = w->U32;
-        p.f = w->f32;
+    auto params = [&](const CUtensorMap& tmU, const CUtensorMap& tmF, void* U, const void* f,
+                      Ctl* ctl) {
+        SolveParams p{};
+        p.tmU = tmU;
+        p.tmF = tmF;
+        p.U = U;
+        p.f = f;
         p.upitch = L.upitch;
         p.fpitch = L.fpitch;
         p.nx = L.nx;
@@ -320,67 +365,66 @@ int enqueue_solve(Workspace* w, const eik_plan_desc* d, const double* Fdev, cons
         p.J = L.J;
         p.cval = w->cval;
         p.qflag = w->qflag;
-        p.dirmask = w->dirmask;
         p.visits = w->visits;
         p.has_src = w->has_src;
         p.lists = w->lists;
-        p.ctl = ctl32;
+        p.ctl = ctl;
         p.delta = d->bucket_width;
         p.deadline_ns = deadline;
-        if (launch_solver_f32(L.k, p, shape, st) != cudaSuccess) return EIK_ECUDA;
-        // FP64 refinement seeded from the FP32 result
+        p.profile = profiling();
+        return p;
+    };
+    LaunchShape shape;
+    if (fp32) {
+        // FP32 cell solves
+        if (solver_shape_f32(L.k, num_sms, &shape)) return EIK_ECUDA;
+        const SolveParams p32 = params(w->tmU32, w->tmF32, w->U32, w->f32, ctl32);
+        if (ev) cudaEventRecord(ev[0], st);
+        if (launch_solver_f32(L.k, p32, shape, st) != cudaSuccess) return EIK_ECUDA;
+        if (ev) cudaEventRecord(ev[1], st);
+        ++nl;
+        // refinement pass (double-float) seeded from the FP32 result
         cudaMemsetAsync(w->cval, 0xff, (size_t)L.J * 8, st);
         SeedParams sp{};
         sp.U32 = w->U32;
-        sp.u32pitch = L.upitch;
-        sp.U64 = w->U64;
-        sp.u64pitch = L.upitch;
-        sp.f64 = w->f64;
-        sp.f64pitch = L.fpitch;
+        sp.Udf = w->Udf;
+        sp.fdf = w->fdf;
+        sp.upitch = L.upitch;
+        sp.fpitch = L.fpitch;
         sp.nx = L.nx;
         sp.ny = L.ny;
         sp.k = L.k;
         sp.cxn = L.cxn;
         sp.cyn = L.cyn;
-        sp.beta = 1.0 / 1024.0;
-        sp.q_min = nsrc ? hs.q_min : 0.0;
+        sp.beta = 1.0f / 1024.0f;
         sp.cval = w->cval;
         sp.qflag = w->qflag;
-        sp.dirmask = w->dirmask;
         sp.visits = w->visits;
         sp.far0 = w->lists + 3 * L.J;
         sp.ctl = ctl64;
-        // the FP64 pass needs the bucket-width default too
+        // the refinement pass needs the bucket-width default too
         cudaMemcpyAsync(&ctl64->fmin_f, &ctl32->fmin_f, 8, cudaMemcpyDeviceToDevice, st);
         if (launch_seed_refine(sp, st) != cudaSuccess) return EIK_ECUDA;
-    }
-    if (solver_shape_f64(L.k, num_sms, &shape)) return EIK_ECUDA;
-    SolveParams<double> p{};
-    p.tmU = w->tmU64;
-    p.tmF = w->tmF64;
-    p.U = w->U64;
-    p.f = w->f64;
-    p.upitch = L.upitch;
-    p.fpitch = L.fpitch;
-    p.nx = L.nx;
-    p.ny = L.ny;
-    p.cxn = L.cxn;
-    p.cyn = L.cyn;
-    p.J = L.J;
-    p.cval = w->cval;
-    p.qflag = w->qflag;
-    p.dirmask = w->dirmask;
-    p.visits = w->visits;
-    p.has_src = w->has_src;
-    p.lists = w->lists;
-    p.ctl = ctl64;
-    p.delta = d->bucket_width;
-    p.deadline_ns = deadline;
-    if (launch_solver_f64(L.k, p, shape, st) != cudaSuccess) return EIK_ECUDA;
-    if (fp32) {
-        if (launch_residual(w->U64, L.upitch, w->f64, L.fpitch, L.nx, L.ny, w->res, st) != cudaSuccess)
+        nl += 2;
+        if (solver_shape_df(L.k, num_sms, &shape)) return EIK_ECUDA;
+        const SolveParams pd = params(w->tmUdf, w->tmFdf, w->Udf, w->fdf, ctl64);
+        if (ev) cudaEventRecord(ev[2], st);
+        if (launch_solver_df(L.k, pd, shape, st) != cudaSuccess) return EIK_ECUDA;
+        if (ev) cudaEventRecord(ev[3], st);
+        ++nl;
+        if (launch_residual(w->Udf, L.upitch, w->fdf, L.fpitch, Fdev, d->h, L.nx, L.ny, w->res, st) !=
+            cudaSuccess)
             return EIK_ECUDA;
+        ++nl;
+    } else {
+        if (solver_shape_f64(L.k, num_sms, &shape)) return EIK_ECUDA;
+        const SolveParams p64 = params(w->tmU64, w->tmF64, w->U64, w->f64, ctl64);
+        if (ev) cudaEventRecord(ev[2], st);
+        if (launch_solver_f64(L.k, p64, shape, st) != cudaSuccess) return EIK_ECUDA;
+        if (ev) cudaEventRecord(ev[3], st);
+        ++nl;
     }
+    if (launches) *launches = nl;
     return EIK_OK;
 }
 
@@ -418,18 +462,19 @@ void finish_stats(const Layout& L, const eik_plan_desc* d, const Ctl* c32, const
     s.buckets = adv;
     s.cell_k = L.k;
     const double fmin = dval(c64->fmin_f);
-    s.bucket_width = d->bucket_width > 0 ? d->bucket_width : L.k * fmin;
+    s.bucket_width = d->bucket_width > 0 ? d->bucket_width : 4.0 * L.k * fmin;
     if (fp32) {
+        // values on the device are U - q_min >= 0
         const double rr = dval(r->r_max), umax = dval(r->u_max);
         s.max_residual = rr;
-        // Certificate (comparison principle): for lam > 1, lam (U - q_min) +
-        // q_min is a strict supersolution with margin (lam - 1) f_min / sqrt 2,
-        // so |V - U| <= sqrt 2 r / f_min * (max U - q_min) (and the same from
-        // below with lam < 1).
+        // Certificate (comparison principle for the monotone scheme): for
+        // lam > 1, lam * (U - q_min) is a strict supersolution with margin
+        // (lam - 1) f_min / sqrt 2, and likewise a strict subsolution for
+        // lam < 1; so |V - U| <= sqrt 2 * r / f_min * max(U - q_min).
         double bound = 0.0;
         if (r->n_bad) bound = std::numeric_limits<double>::infinity();
-        else if (rr > 0 && umax > q_min) bound = std::sqrt(2.0) * rr / fmin * (umax - q_min);
-        const double scale = std::max(std::fabs(umax), std::fabs(q_min));
+        else if (rr > 0 && umax > 0) bound = std::sqrt(2.0) * rr / fmin * umax;
+        const double scale = std::max(std::fabs(umax + q_min), std::fabs(q_min));
         s.err_bound = scale > 0 ? bound / scale : bound;
         const double tol = d->tol > 0 ? d->tol : 1e-5;
         if (status == EIK_OK && !(s.err_bound <= tol)) status = EIK_ENOTCONVERGED;
@@ -474,6 +519,8 @@ extern "C" int eik_plan_create(eik_plan* out, const eik_plan_desc* d, void* cuda
     int rc = workspace_alloc(&p->ws, L, d->precision == EIK_FP32_REFINE, p->stream);
     if (!rc && (cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess))
         rc = EIK_ECUDA;
+    for (int e = 0; e < 4 && !rc; ++e)
+        if (cudaEventCreate(&p->pev[e]) != cudaSuccess) rc = EIK_ECUDA;
     if (!rc && cudaMallocHost((void**)&p->host_ctl, 2 * sizeof(Ctl) + sizeof(ResidualOut)) != cudaSuccess)
         rc = EIK_ENOMEM;
     if (!rc && cudaStreamSynchronize(p->stream) != cudaSuccess) rc = EIK_ECUDA;
@@ -493,6 +540,8 @@ extern "C" void eik_plan_destroy(eik_plan p) {
     if (p->src.buf.p) cudaFree(p->src.buf.p);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
+    for (int e = 0; e < 4; ++e)
+        if (p->pev[e]) cudaEventDestroy(p->pev[e]);
     if (p->host_ctl) cudaFreeHost(p->host_ctl);
     if (p->own_stream) cudaStreamDestroy(p->stream);
     delete p;
@@ -515,16 +564,25 @@ extern "C" int eik_solve(eik_plan p, const eik_instance* in, eik_stats* st) {
         Fdev = w->Fstage;
     }
     cudaEventRecord(p->ev0, s);
-    rc = enqueue_solve(w, &p->d, Fdev, hs, &p->src, p->num_sms, s);
+    int nl = 0;
+    rc = enqueue_solve(w, &p->d, Fdev, hs, &p->src, p->num_sms, s, p->pev, &nl);
     if (rc) {
         cudaStreamSynchronize(s);
         cudaGetLastError();
         return rc;
     }
     cudaEventRecord(p->ev1, s);
-    // result: strip the ring and padding
-    cudaMemcpy2DAsync(in->U, (size_t)L.nx * 8, w->U64 + L.upitch + 1, (size_t)L.upitch * 8,
-                      (size_t)L.nx * 8, L.ny, cudaMemcpyDefault, s);
+    // result: strip the ring and padding and undo the q shift
+    const double shift = hs.node.empty() ? 0.0 : hs.q_min;
+    if (is_device_ptr(in->U)) {
+        if (launch_output(w->U64, w->Udf, L.upitch, L.nx, L.ny, shift, in->U, s) != cudaSuccess)
+            return EIK_ECUDA;
+    } else {
+        if (launch_output(w->U64, w->Udf, L.upitch, L.nx, L.ny, shift, w->Fstage, s) != cudaSuccess)
+            return EIK_ECUDA;
+        cudaMemcpyAsync(in->U, w->Fstage, (size_t)L.nx * L.ny * 8, cudaMemcpyDeviceToHost, s);
+    }
+    ++nl;
     cudaMemcpyAsync(p->host_ctl, w->ctl, 2 * sizeof(Ctl) + sizeof(ResidualOut), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
@@ -533,9 +591,17 @@ extern "C" int eik_solve(eik_plan p, const eik_instance* in, eik_stats* st) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, p->ev0, p->ev1);
     const Ctl* c = (const Ctl*)p->host_ctl;
+    if (profiling()) {
+        if (p->d.precision == EIK_FP32_REFINE) print_profile("fp32 pass", &c[0]);
+        print_profile(p->d.precision == EIK_FP32_REFINE ? "refinement pass" : "fp64 pass", &c[1]);
+    }
     eik_stats local;
     finish_stats(L, &p->d, &c[0], &c[1], (const ResidualOut*)(c + 2), hs.node.empty() ? 0.0 : hs.q_min,
                  p->d.precision == EIK_FP32_REFINE, ms, &local);
+    if (p->d.precision == EIK_FP32_REFINE) cudaEventElapsedTime(&ms, p->pev[0], p->pev[1]), local.pass_ms[0] = ms;
+    cudaEventElapsedTime(&ms, p->pev[2], p->pev[3]);
+    local.pass_ms[1] = ms;
+    local.launches = nl;
     if (st) *st = local;
     return local.status;
 }

@@ -1,5 +1,6 @@
-// eik_aux.cu -- per-solve initialisation, the FP32 -> FP64 refinement seed and
-// the FP64 residual that certifies the FP32+refinement result.
+// eik_aux.cu -- per-solve initialisation, the FP32 -> double-float refinement
+// seed, the FP64 residual that certifies the FP32+refinement result, and the
+// output copy.
 #include "eik_solver.cuh"
 
 namespace eik {
@@ -15,6 +16,13 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
         v = w > v ? w : v;
     }
     return v;
+}
+
+// a double as a normalised double-float pair (hi = nearest float)
+__device__ __forceinline__ float2 df_of(double v) {
+    const float hi = __double2float_rn(v);
+    if (!(hi < inf_of<float>()) && !(hi > -inf_of<float>())) return make_float2(hi, 0.0f);
+    return make_float2(hi, __double2float_rn(v - (double)hi));
 }
 
 // f = h/F on every node of the padded grid (+inf on obstacles and padding),
@@ -33,14 +41,16 @@ __global__ void k_init_grid(const InitParams p) {
         else fv = F == 0.0 ? INF : p.h / F;
     }
     if (in) {
-        if (p.f64) p.f64[(size_t)j * p.f64pitch + i] = fv;
-        if (p.f32) {
-            // beyond 1e18 the FP32 quadratic would overflow: treat as an
-            // obstacle in the FP32 pass; the FP64 refinement restores it
-            p.f32[(size_t)j * p.f32pitch + i] = fv < 1e18 ? (float)fv : inf_of<float>();
-        }
-        if (p.U64) p.U64[(size_t)(j + 1) * p.u64pitch + (i + 1)] = INF;
-        if (p.U32) p.U32[(size_t)(j + 1) * p.u32pitch + (i + 1)] = inf_of<float>();
+        const size_t fi = (size_t)(j + 1) * p.fpitch + (i + 1);
+        const size_t ui = (size_t)(j + 1) * p.upitch + (i + 1);
+        if (p.f64) p.f64[fi] = fv;
+        // beyond 1e18 the FP32 quadratic would overflow: an obstacle for the
+        // FP32 pass; the refinement pass (48-bit pairs) restores the node
+        if (p.f32) p.f32[fi] = fv < 1e18 ? (float)fv : inf_of<float>();
+        if (p.fdf) p.fdf[fi] = fv < 1e18 ? df_of(fv) : make_float2(inf_of<float>(), 0.0f);
+        if (p.U64) p.U64[ui] = INF;
+        if (p.U32) p.U32[ui] = inf_of<float>();
+        if (p.Udf) p.Udf[ui] = make_float2(inf_of<float>(), 0.0f);
     }
     if (bad) atomicCAS(&p.ctl->status, 0, EIK_EINVAL);
     unsigned long long k = (fv < INF) ? key_of(fv) : KEY_UNSET;
@@ -58,26 +68,34 @@ __global__ void k_fill32(float* a, size_t n, float v) {
          e += (size_t)gridDim.x * blockDim.x)
         a[e] = v;
 }
+__global__ void k_fill_df(float2* a, size_t n) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+         e += (size_t)gridDim.x * blockDim.x)
+        a[e] = make_float2(inf_of<float>(), 0.0f);
+}
 
-// Sources: U = q and f = -1 (fixed node); source cells get the cell value
-// max q (Sec. 4.2, HCM item 1), all four directional flags, and start queued.
+// Sources: U = q (shifted) and f = -1 (fixed node); source cells get the cell
+// value max q (Sec. 4.2, HCM item 1) and start queued.
 __global__ void k_init_sources(const InitParams p, const SourceInit s, unsigned long long* cval,
-                               int* qflag, int* dirmask, unsigned char* has_src, int* far0) {
+                               int* qflag, unsigned char* has_src, int* far0) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e < s.n) {
         const int node = s.node[e];
         const int i = node % s.nx, j = node / s.nx;
         const double q = s.q[e];
-        if (p.f64) p.f64[(size_t)j * p.f64pitch + i] = -1.0;
-        if (p.f32) p.f32[(size_t)j * p.f32pitch + i] = -1.0f;
-        if (p.U64) p.U64[(size_t)(j + 1) * p.u64pitch + (i + 1)] = q;
-        if (p.U32) p.U32[(size_t)(j + 1) * p.u32pitch + (i + 1)] = (float)q;
+        const size_t fi = (size_t)(j + 1) * p.fpitch + (i + 1);
+        const size_t ui = (size_t)(j + 1) * p.upitch + (i + 1);
+        if (p.f64) p.f64[fi] = -1.0;
+        if (p.f32) p.f32[fi] = -1.0f;
+        if (p.fdf) p.fdf[fi] = make_float2(-1.0f, 0.0f);
+        if (p.U64) p.U64[ui] = q;
+        if (p.U32) p.U32[ui] = (float)q;
+        if (p.Udf) p.Udf[ui] = df_of(q);
     }
     if (e < s.ncell) {
         const int c = s.cell[e];
         cval[c] = s.cell_key[e];
         has_src[c] = 1;
-        dirmask[c] = 0xF;
         qflag[c] = 1;
         far0[e] = c;
     }
@@ -90,28 +108,29 @@ __global__ void k_ctl_init(Ctl* ctl, int nfar0) {
     ctl->fcnt[0] = nfar0;
 }
 
-// FP64 refinement start: V0 = u32 + beta (u32 - q_min) above the FP32 result
-// (a supersolution when the FP32 error is below beta), +inf where the FP32
-// pass found nothing; every cell with a finite start value is queued with key
-// = its smallest start value.
+// Refinement start: V0 = (1 + beta) u32 just above the FP32 result (a
+// supersolution when the FP32 error is below beta; values are >= 0 after the
+// q shift), +inf where the FP32 pass found nothing.  Every cell with a finite
+// start value is queued with key = its smallest start value.
 __global__ void k_seed(const SeedParams p) {
     const int i = blockIdx.x * 32 + (threadIdx.x & 31);
     const int j = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const bool in = i < p.nx && j < p.ny;
-    const double INF = inf_of<double>();
     unsigned long long k = KEY_UNSET;
     if (in) {
-        const double fv = p.f64[(size_t)j * p.f64pitch + i];
-        double* dst = &p.U64[(size_t)(j + 1) * p.u64pitch + (i + 1)];
-        double v;
-        if (fv < 0.0) {
+        const float2 fv = p.fdf[(size_t)(j + 1) * p.fpitch + (i + 1)];
+        float2* dst = &p.Udf[(size_t)(j + 1) * p.upitch + (i + 1)];
+        float2 v;
+        if (fv.x < 0.0f) {
             v = *dst;  // source: keeps q
         } else {
-            const float u = p.U32[(size_t)(j + 1) * p.u32pitch + (i + 1)];
-            v = (fv < INF && u < inf_of<float>()) ? (double)u + p.beta * ((double)u - p.q_min) : INF;
+            const float u = p.U32[(size_t)(j + 1) * p.upitch + (i + 1)];
+            v = (fv.x < inf_of<float>() && u < inf_of<float>())
+                    ? make_float2(u * (1.0f + p.beta), 0.0f)
+                    : make_float2(inf_of<float>(), 0.0f);
             *dst = v;
         }
-        if (v < INF) k = key_of(v);
+        if (v.x < inf_of<float>()) k = key_of((double)v.x + (double)v.y);
     }
     // min over the k-wide segment of the row that lies in one cell
     for (int o = 1; o < p.k && o < 32; o <<= 1) {
@@ -136,39 +155,63 @@ __global__ void k_seed_cells(const SeedParams p, int J) {
     base = __shfl_sync(FULL, base, leader);
     if (queued) {
         p.qflag[c] = 1;
-        p.dirmask[c] = 0;
         p.visits[c] = 0;
         p.far0[base + __popc(m & ((1u << lane) - 1u))] = c;
     }
 }
 
-// r = |V - T(V)| at every non-source node (T = the FP64 local update; +inf
-// against a finite value counts as an infinite residual), and max finite V.
-__global__ void k_residual(const double* U, int up, const double* f, int fp, int nx, int ny,
-                           ResidualOut* out) {
+// r = |V - T(V)| at every non-source node, with T the FP64 local update and
+// f = h/F recomputed in FP64 (+inf against a finite value counts as an
+// infinite residual), and max finite V.
+__global__ void k_residual(const float2* U, int up, const float2* fdf, int fp, const double* F,
+                           double h, int nx, int ny, ResidualOut* out) {
     const int i = blockIdx.x * 32 + (threadIdx.x & 31);
     const int j = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const double INF = inf_of<double>();
-    double r = 0.0, umax = -INF;
+    double r = 0.0, umax = 0.0;
     unsigned long long bad = 0;
     if (i < nx && j < ny) {
         const size_t q = (size_t)(j + 1) * up + (i + 1);
-        const double v = U[q];
-        const double fv = f[(size_t)j * fp + i];
+        auto val = [&](size_t e) {
+            const float2 a = U[e];
+            return a.x < inf_of<float>() ? (double)a.x + (double)a.y : INF;
+        };
+        const double v = val(q);
         if (v < INF) umax = v;
-        if (fv >= 0.0) {
-            const double t = fv < INF ? local_update(U[q - 1], U[q + 1], U[q - up], U[q + up], fv) : INF;
+        if (!(fdf[(size_t)(j + 1) * fp + (i + 1)].x < 0.0f)) {
+            const double Fv = F[(size_t)j * nx + i];
+            const double fv = Fv > 0.0 ? h / Fv : INF;
+            const double t = fv < INF ? update_f64(val(q - 1), val(q + 1), val(q - up), val(q + up), fv,
+                                                   2.0 * fv * fv)
+                                      : INF;
             if (v < INF && t < INF) r = fabs(v - t);
             else if (v < INF || t < INF) { r = INF; bad = 1; }
         }
     }
-    unsigned long long kr = warp_max_u64(key_of(r));
-    unsigned long long ku = warp_max_u64(key_of(umax));
+    const unsigned long long kr = warp_max_u64(key_of(r));
+    const unsigned long long ku = warp_max_u64(key_of(umax));
     for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(FULL, bad, o);
     if ((threadIdx.x & 31) == 0) {
         atomicMax(&out->r_max, kr);
         atomicMax(&out->u_max, ku);
         if (bad) atomicAdd(&out->n_bad, bad);
+    }
+}
+
+__global__ void k_output(const double* U64, const float2* Udf, int up, int nx, int ny, double shift,
+                         double* dst) {
+    const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int j = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i < nx && j < ny) {
+        const size_t q = (size_t)(j + 1) * up + (i + 1);
+        double v;
+        if (U64) {
+            v = U64[q];
+        } else {
+            const float2 a = Udf[q];
+            v = a.x < inf_of<float>() ? (double)a.x + (double)a.y : inf_of<double>();
+        }
+        dst[(size_t)j * nx + i] = v + shift;
     }
 }
 
@@ -191,13 +234,16 @@ cudaError_t launch_fill32(float* a, size_t n, float v, cudaStream_t st) {
     k_fill32<<<1024, 256, 0, st>>>(a, n, v);
     return cudaGetLastError();
 }
+cudaError_t launch_fill_df(float2* a, size_t n, cudaStream_t st) {
+    k_fill_df<<<1024, 256, 0, st>>>(a, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_init_sources(const InitParams& ip, const SourceInit& s, unsigned long long* cval,
-                                int* qflag, int* dirmask, unsigned char* has_src, int* far0,
-                                cudaStream_t st) {
+                                int* qflag, unsigned char* has_src, int* far0, cudaStream_t st) {
     const int n = s.n > s.ncell ? s.n : s.ncell;
     if (n == 0) return cudaSuccess;
-    k_init_sources<<<(n + 255) / 256, 256, 0, st>>>(ip, s, cval, qflag, dirmask, has_src, far0);
+    k_init_sources<<<(n + 255) / 256, 256, 0, st>>>(ip, s, cval, qflag, has_src, far0);
     return cudaGetLastError();
 }
 
@@ -213,9 +259,16 @@ cudaError_t launch_seed_refine(const SeedParams& p, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_residual(const double* U64, int u64pitch, const double* f64, int f64pitch,
-                            int nx, int ny, ResidualOut* out, cudaStream_t st) {
-    k_residual<<<grid2d(nx, ny, 8), 256, 0, st>>>(U64, u64pitch, f64, f64pitch, nx, ny, out);
+cudaError_t launch_output(const double* U64, const float2* Udf, int upitch, int nx, int ny,
+                          double shift, double* dst, cudaStream_t st) {
+    k_output<<<grid2d(nx, ny, 8), 256, 0, st>>>(U64, Udf, upitch, nx, ny, shift, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const float2* Udf, int upitch, const float2* fdf, int fpitch,
+                            const double* F, double h, int nx, int ny, ResidualOut* out,
+                            cudaStream_t st) {
+    k_residual<<<grid2d(nx, ny, 8), 256, 0, st>>>(Udf, upitch, fdf, fpitch, F, h, nx, ny, out);
     return cudaGetLastError();
 }
 

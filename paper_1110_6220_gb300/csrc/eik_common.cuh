@@ -57,6 +57,10 @@ struct Ctl {
     unsigned long long rounds;
     unsigned long long advances;  // bucket threshold moves
     unsigned long long err_info;  // first failing site (debugging aid)
+    // per-phase clock cycles summed over warps, filled only when profiling
+    // (EIK_PROFILE=1): 0 split, 1 barrier, 2 list+pop, 3 TMA wait, 4 sweeps,
+    // 5 write-back, 6 activation, 7 warp-rounds with work
+    unsigned long long prof[8];
 };
 
 // ---------------------------------------------------------------- kernel params
@@ -68,25 +72,23 @@ struct Ctl {
 //       h / F, +inf on obstacles and on padding nodes (i >= nx or j >= ny),
 //       and -1 on source nodes (fixed values).
 //   nxp = cxn * k, nyp = cyn * k: the grid padded to whole cells.
-template <typename T>
 struct SolveParams {
     CUtensorMap tmU;              // 2-D map over U, box (BW x k+2)
-    CUtensorMap tmF;              // 2-D map over f, box (k x k)
-    T* U;
-    const T* f;
+    CUtensorMap tmF;              // 2-D map over f in U's representation, box (k x k)
+    void* U;                      // double*, float* or float2* (double-float pairs)
+    const void* f;                // f in U's representation
     int upitch, fpitch;
     int nx, ny;
     int cxn, cyn, J;
     unsigned long long* cval;     // ordered cell-value keys
     int* qflag;                   // 1 while the cell sits in a list
-    int* dirmask;                 // preferred sweep directions (bits 0..3)
     int* visits;                  // removals so far
     const unsigned char* has_src; // cell contains a source node
     int* lists;                   // 5 * J ints: near[3], far[2]
     Ctl* ctl;
     double delta;                 // bucket width; <= 0: k * min f
     long long deadline_ns;        // relative to kernel start
-    int max_sweeps;               // per cell visit
+    int profile;                  // accumulate Ctl::prof
 };
 
 // ---------------------------------------------------------------- host launchers
@@ -97,32 +99,37 @@ struct LaunchShape {
     int blocks;        // co-resident blocks (cooperative launch)
 };
 
+// one per arithmetic mode (eik_solver_f64.cu, eik_solver_f32.cu, eik_solver_df.cu)
 int solver_shape_f64(int k, int num_sms, LaunchShape* out);
 int solver_shape_f32(int k, int num_sms, LaunchShape* out);
-cudaError_t launch_solver_f64(int k, const SolveParams<double>& p, const LaunchShape& s,
-                              cudaStream_t st);
-cudaError_t launch_solver_f32(int k, const SolveParams<float>& p, const LaunchShape& s,
-                              cudaStream_t st);
+int solver_shape_df(int k, int num_sms, LaunchShape* out);
+cudaError_t launch_solver_f64(int k, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
+cudaError_t launch_solver_f32(int k, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
+cudaError_t launch_solver_df(int k, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
 
 // aux kernels (eik_aux.cu)
+// Device arrays of one instance (null where the precision mode has none):
+//   FP64 mode:       U64, f64
+//   FP32+refinement: U32, f32 (FP32 pass), Udf, fdf (double-float pairs,
+//                    refinement pass).  All U arrays share one layout, all f
+//                    arrays another (see SolveParams).
 struct InitParams {
     const double* F;              // nx*ny row-major speeds (device)
     int nx, ny;
     double h;
-    double* f64; int f64pitch;    // may be null
-    float* f32; int f32pitch;     // may be null
-    double* U64; int u64pitch;    // may be null
-    float* U32; int u32pitch;     // may be null
+    double* f64; float* f32; float2* fdf; int fpitch;
+    double* U64; float* U32; float2* Udf; int upitch;
     int nxp, nyp;
     Ctl* ctl;
 };
 cudaError_t launch_init_grid(const InitParams& p, cudaStream_t st);
 cudaError_t launch_fill(double* a, size_t n, double v, cudaStream_t st);
 cudaError_t launch_fill32(float* a, size_t n, float v, cudaStream_t st);
+cudaError_t launch_fill_df(float2* a, size_t n, cudaStream_t st);  // (+inf, 0)
 
 struct SourceInit {
     const int* node;              // unique source nodes (j*nx + i)
-    const double* q;              // their values
+    const double* q;              // their values, shifted by -min q (>= 0)
     int n;
     const int* cell;              // cells holding a source
     const unsigned long long* cell_key;  // key of max q on that cell
@@ -130,19 +137,18 @@ struct SourceInit {
     int nx, k, cxn;
 };
 cudaError_t launch_init_sources(const InitParams& ip, const SourceInit& s, unsigned long long* cval,
-                                int* qflag, int* dirmask, unsigned char* has_src, int* far0,
-                                cudaStream_t st);
+                                int* qflag, unsigned char* has_src, int* far0, cudaStream_t st);
 
 cudaError_t launch_ctl_init(Ctl* ctl, int nfar0, cudaStream_t st);
 
 struct SeedParams {
-    const float* U32; int u32pitch;
-    double* U64; int u64pitch;
-    const double* f64; int f64pitch;
+    const float* U32;
+    float2* Udf;
+    const float2* fdf;
+    int upitch, fpitch;
     int nx, ny, k, cxn, cyn;
-    double beta;                  // relative bump
-    double q_min;
-    unsigned long long* cval; int* qflag; int* dirmask; int* visits; int* far0;
+    float beta;                   // relative bump (values are >= 0 after the q shift)
+    unsigned long long* cval; int* qflag; int* visits; int* far0;
     Ctl* ctl;
 };
 cudaError_t launch_seed_refine(const SeedParams& p, cudaStream_t st);
@@ -152,7 +158,14 @@ struct ResidualOut {              // reduced with atomics on ordered keys
     unsigned long long u_max;     // max finite V
     unsigned long long n_bad;     // finite/infinite mismatches
 };
-cudaError_t launch_residual(const double* U64, int u64pitch, const double* f64, int f64pitch,
-                            int nx, int ny, ResidualOut* out, cudaStream_t st);
+// FP64 residual of the double-float result Udf, with f = h/F recomputed in
+// FP64 from the input speeds; sources are the nodes with fdf.x < 0.
+cudaError_t launch_residual(const float2* Udf, int upitch, const float2* fdf, int fpitch,
+                            const double* F, double h, int nx, int ny, ResidualOut* out,
+                            cudaStream_t st);
+// dst[j*nx + i] = U[(j+1)*pitch + i+1] + shift (undoes the q shift); exactly
+// one of U64 / Udf is non-null
+cudaError_t launch_output(const double* U64, const float2* Udf, int upitch, int nx, int ny,
+                          double shift, double* dst, cudaStream_t st);
 
 }  // namespace eik

@@ -25,24 +25,25 @@ struct DevBuf {
     size_t cap = 0;
 };
 
-// Device workspace of one instance.
+// Device workspace of one instance (arrays of the other precision mode null).
 struct Workspace {
     Layout L;
     bool fp32;
-    double* U64;
+    double* U64;   // FP64 mode
     double* f64;
-    float* U32;
+    float* U32;    // FP32 + refinement: FP32 pass
     float* f32;
-    double* Fstage;  // device copy of a host F
+    float2* Udf;   // FP32 + refinement: double-float refinement pass
+    float2* fdf;
+    double* Fstage;  // device copy of a host F; also the output staging buffer
     unsigned long long* cval;
     int* qflag;
-    int* dirmask;
     int* visits;
     unsigned char* has_src;
     int* lists;
-    Ctl* ctl;          // [0] FP32 pass, [1] FP64 pass (or the only pass)
+    Ctl* ctl;          // [0] FP32 pass, [1] FP64 or refinement pass
     ResidualOut* res;  // follows ctl[1]
-    CUtensorMap tmU64, tmF64, tmU32, tmF32;
+    CUtensorMap tmU64, tmF64, tmU32, tmF32, tmUdf, tmFdf;
 };
 
 struct HostSources {
@@ -66,8 +67,10 @@ void workspace_free(Workspace* w);
 int prepare_sources(const Layout& L, const eik_instance* in, HostSources* hs);
 bool is_device_ptr(const void* p);
 int grow_staging(DevBuf* b, size_t bytes);
+// Pass timing events (may be null): ev[0..1] around the FP32 pass, ev[2..3]
+// around the FP64 pass.  *launches counts the kernels queued.
 int enqueue_solve(Workspace* w, const eik_plan_desc* d, const double* Fdev, const HostSources& hs,
-                  SrcDev* sd, int num_sms, cudaStream_t st);
+                  SrcDev* sd, int num_sms, cudaStream_t st, cudaEvent_t* ev, int* launches);
 void finish_stats(const Layout& L, const eik_plan_desc* d, const Ctl* c32, const Ctl* c64,
                   const ResidualOut* r, double q_min, bool fp32, double ms, eik_stats* st);
 
@@ -82,5 +85,6 @@ struct eik_plan_s {
     eik::Workspace ws{};
     eik::SrcDev src;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
     void* host_ctl = nullptr;  // pinned copy of ctl[2] + residual
 };

@@ -1,6 +1,5 @@
-// eik_solver.cuh -- the persistent, bucketed cell solver (templated on the
-// value type T and the cell size K).  Included by eik_solver_f64.cu and
-// eik_solver_f32.cu, which instantiate it.
+// eik_solver.cuh -- the persistent, bucketed cell solver, templated on the
+// arithmetic mode and the cell size K.  Instantiated by eik_solver_*.cu.
 //
 // What one launch computes (Chacon & Vladimirsky, Sec. 4.2):
 //   Alg. generic_LC_cells with the HCM refinements -- cells carry cell values
@@ -15,7 +14,13 @@
 // processed in the next round; the others wait in a far list.  Theorem
 // convergence (any removal order, exact per-cell solves) makes the result the
 // exact solution of eq. Eik_discr regardless of this schedule.
+//
+// All stored values are >= +0 (the host shifts q by its minimum), so the
+// bit patterns of doubles and floats order like the values: min and compare
+// run on the integer pipe, which on this part is far faster than FP64.
 #pragma once
+
+#include <type_traits>
 
 #include "eik_common.cuh"
 
@@ -54,7 +59,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 // 2-D tiled TMA load (no multicast) of one box into shared memory, completing
-// on the mbarrier `bar`.  x must be a multiple of 16 bytes / sizeof(T).
+// on the mbarrier `bar`.  x * element size must be a multiple of 16 bytes.
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y,
                                             uint64_t* bar) {
     asm volatile(
@@ -86,63 +91,219 @@ template <> __device__ __forceinline__ float inf_of<float>() {
     return __int_as_float(0x7f800000);
 }
 
-// ---------------------------------------------------------------- local update
-// The update at one node from its four neighbours, using the relevant-quadrant
-// shortcut of Remark regular_FSM_update: a = min(U_W, U_E), b = min(U_S, U_N).
-// If |a - b| < f the two-sided root of (U-a)^2 + (U-b)^2 = f^2
-// (eq. two_sided_update), else the one-sided min(a, b) + f
-// (eq. one_sided_update).  Callers skip sources and obstacles (f < 0 or
-// f = +inf), so f is finite and positive here.
-__device__ __forceinline__ double local_update(double W, double E, double S, double N,
-                                               double f) {
-    const double a = fmin(W, E), b = fmin(S, N);
-    const double lo = fmin(a, b);
-    const double d = a - b;  // NaN only when a = b = +inf, then the one-sided branch
-    const double one = lo + f;
-    const double two = (a + b + sqrt(fma(-d, d, 2.0 * f * f))) * 0.5;
-    return fabs(d) < f ? two : one;
+// ---------------------------------------------------------------- ordered bits
+// For values in [+0, +inf] the signed integer image orders like the value.
+__device__ __forceinline__ long long ob(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ int ob(float x) { return __float_as_int(x); }
+__device__ __forceinline__ double from_ob(long long b) { return __longlong_as_double(b); }
+__device__ __forceinline__ float from_ob(int b) { return __int_as_float(b); }
+constexpr long long INF_BITS64 = 0x7ff0000000000000LL;
+constexpr int INF_BITS32 = 0x7f800000;
+// f in [+0, +inf): a node that is neither a source (f = -1) nor an obstacle
+__device__ __forceinline__ bool updatable(double f) {
+    return (unsigned long long)__double_as_longlong(f) < (unsigned long long)INF_BITS64;
 }
-// FP32: the same root in the cancellation-free form
-//   max(a,b) + (f^2 - d^2) / (d + sqrt(2 f^2 - d^2)),  d = |a - b|,
-// where the small increment carries all the rounding; the quotient and root
-// only need a few correct bits relative to f, far below ulp(U).
-__device__ __forceinline__ float local_update(float W, float E, float S, float N, float f) {
-    const float a = fminf(W, E), b = fminf(S, N);
-    const float lo = fminf(a, b), hi = fmaxf(a, b);
-    const float d = hi - lo;
-    const float one = lo + f;
-    const float root = __fsqrt_rn(fmaf(-d, d, 2.0f * f * f));
-    const float two = hi + __fdividef((f - d) * (f + d), d + root);
-    return d < f ? two : one;
+__device__ __forceinline__ bool updatable(float f) {
+    return (unsigned)__float_as_int(f) < (unsigned)INF_BITS32;
 }
 
-// ---------------------------------------------------------------- tile config
-template <typename T, int K>
+// ---------------------------------------------------------------- local update
+// The update at one node from its four neighbours with the relevant-quadrant
+// shortcut of Remark regular_FSM_update: a = min(U_W, U_E), b = min(U_S, U_N);
+// if |a - b| < f = h/F the two-sided root of (U-a)^2 + (U-b)^2 = f^2
+// (eq. two_sided_update), else the one-sided min(a, b) + f
+// (eq. one_sided_update).  Neighbours are >= 0 (possibly +inf); f is finite.
+
+// FP64 (g = 2 f^2 precomputed): U = hi + (sqrt(g - d^2) - d) / 2, d = hi - lo.
+__device__ __forceinline__ double update_f64(double W, double E, double S, double N, double f,
+                                             double g) {
+    const long long a = min(ob(W), ob(E)), b = min(ob(S), ob(N));
+    const long long lob = min(a, b), hib = max(a, b);
+    const double lo = from_ob(lob), hi = from_ob(hib);
+    const double one = lo + f;
+    const double d = hi - lo;  // finite whenever hi is
+    const bool two_sided = hib < INF_BITS64 && ob(d) < ob(f);
+    const double s = sqrt(two_sided ? fma(-d, d, g) : g);
+    const double two = fma(0.5, s - d, hi);
+    return two_sided ? two : one;
+}
+
+// FP32, with the quadratic in the cancellation-free form
+//   hi + (f^2 - d^2) / (d + sqrt(2 f^2 - d^2))
+// whose small increment carries all the rounding; its quotient and root need
+// only a few correct bits relative to f, far below ulp(U).
+__device__ __forceinline__ float increment_f32(float d, float f) {
+    const float x = fmaf(-d, d, 2.0f * f * f);  // 2 f^2 - d^2 >= f^2 > 0
+    const float root = x * rsqrtf(x);
+    return __fdividef((f - d) * (f + d), d + root);
+}
+__device__ __forceinline__ float update_f32(float W, float E, float S, float N, float f) {
+    const int a = min(ob(W), ob(E)), b = min(ob(S), ob(N));
+    const int lob = min(a, b), hib = max(a, b);
+    const float lo = from_ob(lob), hi = from_ob(hib);
+    const float one = lo + f;
+    const float d = hi - lo;
+    const bool two_sided = hib < INF_BITS32 && ob(d) < ob(f);
+    const float two = hi + increment_f32(two_sided ? d : 0.0f, f);
+    return two_sided ? two : one;
+}
+
+// ---------------------------------------------------------------- double-float
+// Refinement arithmetic entirely on the FP32 pipe: a value is an unevaluated
+// pair hi + lo of floats with |lo| <= ulp(hi)/2 (48 significant bits), kept
+// in a float2 (x = hi, y = lo).  Sums use Knuth's TwoSum and Dekker's
+// Fast2Sum; the quadratic's increment is the FP32 safe form above, computed
+// from the pair difference d.  Its error, a few FP32 ulps of f per update, is
+// far below what the FP64 residual certificate has to certify.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = a + b;
+    return make_float2(s, b - (s - a));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    float2 s = two_sum(a.x, b.x);
+    s.y += a.y + b.y;
+    return fast_two_sum(s.x, s.y);
+}
+__device__ __forceinline__ float2 df_add_f(float2 a, float b) {
+    float2 s = two_sum(a.x, b);
+    s.y += a.y;
+    return fast_two_sum(s.x, s.y);
+}
+
+// order, finiteness and conversion of a stored value, for each representation
+// (normalised pairs with hi >= 0 order lexicographically)
+__device__ __forceinline__ bool lt(float2 a, float2 b) { return a.x < b.x || (a.x == b.x && a.y < b.y); }
+__device__ __forceinline__ bool lt(double a, double b) { return ob(a) < ob(b); }
+__device__ __forceinline__ bool lt(float a, float b) { return ob(a) < ob(b); }
+__device__ __forceinline__ bool is_finite_v(float2 a) { return a.x < inf_of<float>(); }
+__device__ __forceinline__ bool is_finite_v(double a) { return ob(a) < INF_BITS64; }
+__device__ __forceinline__ bool is_finite_v(float a) { return ob(a) < INF_BITS32; }
+__device__ __forceinline__ double to_d(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ double to_d(double a) { return a; }
+__device__ __forceinline__ double to_d(float a) { return (double)a; }
+__device__ __forceinline__ bool updatable(float2 f) { return updatable(f.x); }
+__device__ __forceinline__ bool is_src(float2 f) { return f.x < 0.0f; }
+__device__ __forceinline__ bool is_src(double f) { return f < 0.0; }
+__device__ __forceinline__ bool is_src(float f) { return f < 0.0f; }
+__device__ __forceinline__ float2 shfl_xor(float2 v, int o) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+__device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float shfl_xor(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+template <typename T> __device__ __forceinline__ T zero_v();
+template <> __device__ __forceinline__ double zero_v<double>() { return 0.0; }
+template <> __device__ __forceinline__ float zero_v<float>() { return 0.0f; }
+template <> __device__ __forceinline__ float2 zero_v<float2>() { return make_float2(0.0f, 0.0f); }
+
+__device__ __forceinline__ float2 update_df(float2 W, float2 E, float2 S, float2 N, float2 f) {
+    const float2 a = lt(E, W) ? E : W, b = lt(N, S) ? N : S;
+    const bool ab = lt(a, b);
+    const float2 lo = ab ? a : b, hi = ab ? b : a;
+    const float INF = inf_of<float>();
+    const float2 one = df_add(lo, f);
+    const float d = (hi.x - lo.x) + (hi.y - lo.y);
+    const bool two_sided = hi.x < INF && d < f.x;
+    const float2 two = df_add_f(hi, increment_f32(two_sided ? d : 0.0f, f.x));
+    const float2 r = two_sided ? two : one;
+    return lo.x < INF ? r : make_float2(INF, 0.0f);
+}
+
+// ---------------------------------------------------------------- modes
+enum { MODE_F64 = 0, MODE_F32 = 1, MODE_DF = 2 };
+
+template <int MODE> struct ModeTypes;
+template <> struct ModeTypes<MODE_F64> { using T = double; using FT = double; };
+template <> struct ModeTypes<MODE_F32> { using T = float; using FT = float; };
+template <> struct ModeTypes<MODE_DF> { using T = float2; using FT = float2; };
+
+// One warp works on one cell (two cells for k = 4).  Its lanes sweep the four
+// directions of Alg. FSM_order at the same time: LPD lanes per direction, each
+// lane owning k/LPD rows of the tile.  At wavefront step t the lanes of a
+// direction update the nodes of anti-diagonal t of that direction; lanes that
+// reach the same node in one step read the same inputs and write the same
+// value, so a pass of 2k-1 steps is four Gauss-Seidel sweeps, race free.
+template <int MODE, int K>
 struct TileCfg {
-    static constexpr int LPC = K >= 32 ? 32 : K;        // lanes per cell
-    static constexpr int CPW = 32 / LPC;                // cells per warp (lock-step)
-    static constexpr int RPL = K > 32 ? K / 32 : 1;     // rows per lane
-    // U box: rows k+2; width k+2 for FP64 (multiple of 16 B since k is even),
-    // k+4 for FP32 (k+2 floats is not a multiple of 16 B for k = 4m).
-    static constexpr int BW = sizeof(T) == 8 ? K + 2 : K + 4;
+    using T = typename ModeTypes<MODE>::T;    // a value of U
+    using FT = typename ModeTypes<MODE>::FT;  // f = h/F
+    static constexpr int ES = (int)sizeof(T);
+    static constexpr int LPD = K < 8 ? K : 8;        // lanes per direction
+    static constexpr int LPC = 4 * LPD;              // lanes per cell
+    static constexpr int CPW = 32 / LPC;             // cells per warp (lock-step)
+    static constexpr int RPL = K / LPD;              // rows per lane
+    static constexpr int BPL = (K + LPC - 1) / LPC;  // boundary nodes per lane and side
+    // U box: k+2 rows; k+2 wide for 8-byte values, k+4 for floats (a row of
+    // a TMA box must be a multiple of 16 bytes)
+    static constexpr int BW = ES == 8 ? K + 2 : K + 4;
     static constexpr int BH = K + 2;
-    static constexpr int UBYTES = BW * BH * (int)sizeof(T);
-    static constexpr int FBYTES = K * K * (int)sizeof(T);
-    static constexpr int UBYTES_AL = (UBYTES + 127) / 128 * 128;
-    static constexpr int FBYTES_AL = (FBYTES + 127) / 128 * 128;
-    static constexpr int GROUP_BYTES = UBYTES_AL + FBYTES_AL;
+    static constexpr int UBYTES = BW * BH * ES;
+    static constexpr int FBYTES = BW * BH * (int)sizeof(FT);        // f box incl. halo (TMA)
+    static constexpr int XBYTES = MODE == MODE_F64 ? K * K * 8 : 0;  // 2 f^2 (computed)
+    static constexpr int TX_BYTES = UBYTES + FBYTES;
+    static constexpr int A128(int b) { return (b + 127) / 128 * 128; }
+    static constexpr int F_OFF = A128(UBYTES);
+    static constexpr int X_OFF = F_OFF + A128(FBYTES);
+    static constexpr int GROUP_BYTES = X_OFF + A128(XBYTES);
     static constexpr int MASK_OFF = CPW * GROUP_BYTES;
     static constexpr int BAR_OFF = MASK_OFF + CPW * K * 8;
-    static constexpr int WARP_BYTES = (BAR_OFF + 16 + 127) / 128 * 128;
+    static constexpr int WARP_BYTES = A128(BAR_OFF + 16);
     static constexpr int WPB_SMEM = (200 * 1024) / WARP_BYTES;
     static constexpr int WPB = WPB_SMEM >= 8 ? 8 : (WPB_SMEM < 1 ? 1 : WPB_SMEM);
-    static constexpr int MAX_SWEEPS = 4 * K * K + 8;
+    static constexpr int MAX_PASSES = K * K + 8;
 };
 
+// ---------------------------------------------------------------- one node
+// Candidate value of tile node (i, j) from its four tile neighbours (tU holds
+// the cell plus its halo, row stride BW); false for sources and obstacles.
+template <int MODE, int K>
+__device__ __forceinline__ bool node_candidate(const typename TileCfg<MODE, K>::T* tU,
+                                               const typename TileCfg<MODE, K>::FT* tF,
+                                               const double* tG, int i, int j,
+                                               typename TileCfg<MODE, K>::T& cand,
+                                               typename TileCfg<MODE, K>::T& old) {
+    using C = TileCfg<MODE, K>;
+    const int q = (j + 1) * C::BW + (i + 1);
+    const auto fv = tF[q];
+    if (!updatable(fv)) return false;
+    old = tU[q];
+    if constexpr (MODE == MODE_F64)
+        cand = update_f64(tU[q - 1], tU[q + 1], tU[q - C::BW], tU[q + C::BW], fv, tG[j * K + i]);
+    else if constexpr (MODE == MODE_F32)
+        cand = update_f32(tU[q - 1], tU[q + 1], tU[q - C::BW], tU[q + C::BW], fv);
+    else
+        cand = update_df(tU[q - 1], tU[q + 1], tU[q - C::BW], tU[q + C::BW], fv);
+    return true;
+}
+
+// Fixed-point check of a whole tile (this lane's share): true if some node
+// would still decrease.  It is equivalent to asking whether another pass
+// would change anything -- a pass changes nothing exactly when no node can
+// decrease -- but all nodes are evaluated at once instead of along 2k-1
+// wavefront steps.
+template <int MODE, int K>
+__device__ __forceinline__ bool tile_improvable(const typename TileCfg<MODE, K>::T* tU,
+                                                const typename TileCfg<MODE, K>::FT* tF,
+                                                const double* tG, int dl) {
+    using C = TileCfg<MODE, K>;
+    bool imp = false;
+#pragma unroll 4
+    for (int e = dl; e < K * K; e += C::LPC) {
+        const int j = e / K, i = e - j * K;
+        typename C::T cand, old;
+        if (node_candidate<MODE, K>(tU, tF, tG, i, j, cand, old)) imp |= lt(cand, old);
+    }
+    return imp;
+}
+
 // ---------------------------------------------------------------- grid barrier
-// Sense-counting barrier across all (co-resident) blocks.  Every wait is
-// bounded by the launch deadline and by the abort flag; on expiry the block
-// records EIK_ETIMEDOUT, raises abort and returns false.
+// Counting barrier across all (co-resident) blocks.  Every wait is bounded by
+// the launch deadline and by the abort flag; on expiry the block records
+// EIK_ETIMEDOUT, raises abort and returns false.
 __device__ __forceinline__ bool grid_sync(Ctl* ctl, unsigned long long deadline, int* s_flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -156,6 +317,7 @@ __device__ __forceinline__ bool grid_sync(Ctl* ctl, unsigned long long deadline,
         } else {
             unsigned spins = 0;
             while (ld_vol(&ctl->bar_gen) == gen) {
+                __nanosleep(40);
                 if ((++spins & 63u) == 0) {
                     if (ld_vol(&ctl->abort)) break;
                     if (gtimer() > deadline) {
@@ -211,10 +373,22 @@ __device__ __forceinline__ void lane_push(int* list, int* count, int val, int ca
 }
 
 // ---------------------------------------------------------------- the kernel
-template <typename T, int K>
-__global__ void __launch_bounds__(TileCfg<T, K>::WPB * 32)
-    k_solve(const __grid_constant__ SolveParams<T> p) {
-    using C = TileCfg<T, K>;
+// PROF_MARK(i): add the cycles since the last mark to phase i (profiling only)
+#define PROF_MARK(i)                                    \
+    do {                                                \
+        if (p.profile) {                                \
+            const long long now_ = clock64();           \
+            pacc[i] += (unsigned long long)(now_ - pt); \
+            pt = now_;                                  \
+        }                                               \
+    } while (0)
+
+template <int MODE, int K>
+__global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
+    k_solve(const __grid_constant__ SolveParams p) {
+    using C = TileCfg<MODE, K>;
+    using T = typename C::T;
+    using FT = typename C::FT;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_flag;
@@ -226,15 +400,21 @@ __global__ void __launch_bounds__(TileCfg<T, K>::WPB * 32)
     unsigned char* wbase = smem + warp * C::WARP_BYTES;
     uint64_t* bar = reinterpret_cast<uint64_t*>(wbase + C::BAR_OFF);
     unsigned long long* masks = reinterpret_cast<unsigned long long*>(wbase + C::MASK_OFF);
-    const int g = lane / C::LPC;   // which of the warp's cells this lane works on
-    const int r0 = lane % C::LPC;  // first tile row of this lane
-    T* tU = reinterpret_cast<T*>(wbase + g * C::GROUP_BYTES);
-    T* tF = reinterpret_cast<T*>(wbase + g * C::GROUP_BYTES + C::UBYTES_AL);
+    const int g = lane / C::LPC;     // which of the warp's cells this lane works on
+    const int dl = lane % C::LPC;    // lane within the cell
+    const int dir = dl / C::LPD;     // sweep direction of this lane (Alg. FSM_order)
+    const int rl = dl % C::LPD;      // first tile row of this lane
+    const bool sx = dir <= 1;                  // i increasing
+    const bool sy = (dir == 0) || (dir == 3);  // j increasing
+    unsigned char* gbase = wbase + g * C::GROUP_BYTES;
+    T* tU = reinterpret_cast<T*>(gbase);
+    const FT* tF = reinterpret_cast<const FT*>(gbase + C::F_OFF);
+    const double* tG = reinterpret_cast<const double*>(gbase + C::X_OFF);
     const unsigned gmask = C::LPC == 32 ? FULL : (((1u << C::LPC) - 1u) << (g * C::LPC));
+    T* Ug = reinterpret_cast<T*>(p.U);
 
     Ctl* ctl = p.ctl;
     const unsigned long long deadline = gtimer() + (unsigned long long)p.deadline_ns;
-    const T INF = inf_of<T>();
 
     if (lane == 0) {
         mbar_init(bar, 1);
@@ -243,20 +423,27 @@ __global__ void __launch_bounds__(TileCfg<T, K>::WPB * 32)
     __syncwarp();
     uint32_t phase = 0;
 
-    // bucket width: given, else k times the smallest h/F
-    double delta = p.delta;
-    if (!(delta > 0.0)) delta = (double)K * val_of(ld_cg(&ctl->fmin_f));
-    if (!(delta > 0.0) || !(delta < inf_of<double>())) delta = inf_of<double>();
+    // bucket width: given, else 4 k times the smallest h/F (the time to
+    // cross about four cells at the highest speed)
     const double fmin_glob = val_of(ld_cg(&ctl->fmin_f));
+    double delta = p.delta;
+    if (!(delta > 0.0)) delta = 4.0 * (double)K * fmin_glob;
+    if (!(delta > 0.0) || !(delta < inf_of<double>())) delta = inf_of<double>();
 
     const int J = p.J;
+    const int nb = gridDim.x;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int gthreads = gridDim.x * blockDim.x;
+    // static assignment of list entries: consecutive entries go to different
+    // blocks (SMs) first, then to different warps, then to a warp's cells
+    const int slot = g * C::WPB + warp;
+    constexpr int SLOTS = C::WPB * C::CPW;
 
     unsigned long long st_visits = 0, st_sweeps = 0, st_lane = 0, st_rounds = 0, st_adv = 0;
-    int ns = 0, fs = 0, round = 0;
+    unsigned long long pacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long pt = clock64();
+    int ns = 0, fs = 0;
     unsigned long long theta = 0;
-    bool ok = true;
 
     for (;;) {
         int n_near = min(ld_cg(&ctl->cnt[ns]), J);  // a list never exceeds J entries
@@ -272,7 +459,9 @@ __global__ void __launch_bounds__(TileCfg<T, K>::WPB * 32)
             }
             mn = warp_min_u64(mn);
             if (lane == 0 && mn != KEY_UNSET) atomicMin(&ctl->fmin[fs], mn);
-            if (!(ok = grid_sync(ctl, deadline, &s_flag))) break;
+            PROF_MARK(0);
+            if (!grid_sync(ctl, deadline, &s_flag)) break;
+            PROF_MARK(1);
             const unsigned long long fm = ld_cg(&ctl->fmin[fs]);
             theta = fm == KEY_UNSET ? KEY_UNSET : key_of(val_of(fm) + delta);
             // ... then move every far cell with key <= theta to the near list
@@ -289,7 +478,9 @@ __global__ void __launch_bounds__(TileCfg<T, K>::WPB * 32)
                 warp_push(nearL, &ctl->cnt[ns], c >= 0 && to_near, c, J, ctl);
                 warp_push(far2, &ctl->fcnt[fs ^ 1], c >= 0 && !to_near, c, J, ctl);
             }
-            if (!(ok = grid_sync(ctl, deadline, &s_flag))) break;
+            PROF_MARK(0);
+            if (!grid_sync(ctl, deadline, &s_flag)) break;
+            PROF_MARK(1);
             if (gtid == 0) {
                 ctl->fcnt[fs] = 0;
                 ctl->fmin[fs] = KEY_UNSET;
@@ -303,22 +494,17 @@ __global__ void __launch_bounds__(TileCfg<T, K>::WPB * 32)
         const int nx_slot = ns == 2 ? 0 : ns + 1;
         // deadline, grid-uniformly: raised here, seen by all at this round's barrier
         if (gtid == 0 && gtimer() > deadline) fail(ctl, EIK_ETIMEDOUT, 0x5000000ull);
-        if (gtid == 0) {
-            ctl->cnt[nx_slot == 2 ? 0 : nx_slot + 1] = 0;  // the list consumed last round
-            ctl->cursor[(round + 1) & 1] = 0;
-        }
+        if (gtid == 0) ctl->cnt[nx_slot == 2 ? 0 : nx_slot + 1] = 0;  // consumed last round
         const int* nearL = p.lists + ns * J;
         int* nextL = p.lists + nx_slot * J;
         int* farL = p.lists + (3 + fs) * J;
         int* next_cnt = &ctl->cnt[nx_slot];
         int* far_cnt = &ctl->fcnt[fs];
 
-        for (;;) {
-            int base = 0;
-            if (lane == 0) base = atomicAdd(&ctl->cursor[round & 1], C::CPW);
-            base = __shfl_sync(FULL, base, 0);
-            if (base >= n_near) break;
-            const int idx = base + g;
+        for (int t = 0;; ++t) {
+            const int first_idx = blockIdx.x + nb * (warp + SLOTS * t);  // cell slot 0's entry
+            if (first_idx >= n_near) break;
+            const int idx = blockIdx.x + nb * (slot + SLOTS * t);
             const int c = idx < n_near ? ld_cg(&nearL[idx]) : -1;
             int cg[C::CPW];
 #pragma unroll
@@ -327,32 +513,32 @@ __global__ void __launch_bounds__(TileCfg<T, K>::WPB * 32)
             // ---- remove the cell from the list: clear its flag BEFORE reading
             // its halo, so that a neighbour that improves the halo while we
             // work re-queues it (Alg. generic_LC_cells, activation test)
-            int dm = 0, first = 0;
-            if (r0 == 0 && c >= 0) {
+            int first = 0;
+            if (dl == 0 && c >= 0) {
                 atomicExch(&p.qflag[c], 0);
-                dm = atomicExch(&p.dirmask[c], 0);
                 first = atomicAdd(&p.visits[c], 1) == 0;
             }
-            dm = __shfl_sync(FULL, dm, g * C::LPC);
             first = __shfl_sync(FULL, first, g * C::LPC);
             __threadfence();
             fence_proxy_async_global();
             fence_proxy_async_shared();
             __syncwarp();
+            PROF_MARK(2);
+            pacc[7] += 1;
 
-            // ---- TMA: (k+2) x BW box of U (cell + halo) and k x k box of f
+            // ---- TMA: U box (cell + halo) and f box into shared memory
             if (lane == 0) {
                 int nvalid = 0;
 #pragma unroll
                 for (int gg = 0; gg < C::CPW; ++gg) nvalid += cg[gg] >= 0;
-                mbar_arrive_expect_tx(bar, (uint32_t)(nvalid * (C::UBYTES + C::FBYTES)));
+                mbar_arrive_expect_tx(bar, (uint32_t)(nvalid * C::TX_BYTES));
 #pragma unroll
                 for (int gg = 0; gg < C::CPW; ++gg) {
                     if (cg[gg] >= 0) {
                         const int cx = cg[gg] % p.cxn, cy = cg[gg] / p.cxn;
                         unsigned char* gb = wbase + gg * C::GROUP_BYTES;
                         tma_load_2d(gb, &p.tmU, cx * K, cy * K, bar);
-                        tma_load_2d(gb + C::UBYTES_AL, &p.tmF, cx * K, cy * K, bar);
+                        tma_load_2d(gb + C::F_OFF, &p.tmF, cx * K, cy * K, bar);
                     }
                 }
             }
@@ -369,52 +555,46 @@ __global__ void __launch_bounds__(TileCfg<T, K>::WPB * 32)
                     const unsigned long long d2 = gtimer() + 1000000000ull;
                     while (!mbar_try_wait(bar, phase) && gtimer() < d2) {
                     }
-                    ok = false;
-                    break;
+                    break;  // the round's barrier reports the abort to every block
                 }
             }
             phase ^= 1u;
+            PROF_MARK(3);
+            if constexpr (MODE == MODE_F64) {
+                // 2 f^2 per node, once per visit (saves two FP64 ops per update)
+                for (int e = lane; e < C::CPW * K * K; e += 32) {
+                    const int gg = e / (K * K), r = e - gg * (K * K);
+                    const int jj = r / K, ii = r - jj * K;
+                    unsigned char* gb = wbase + gg * C::GROUP_BYTES;
+                    const double fv = reinterpret_cast<const double*>(gb + C::F_OFF)[(jj + 1) * C::BW + ii + 1];
+                    reinterpret_cast<double*>(gb + C::X_OFF)[r] = 2.0 * fv * fv;
+                }
+                __syncwarp();
+            }
 
-            // ---- sweep order: preferred (flagged) directions first, then the
-            // rest, then the Alg. FSM_order cycle (dir = sweep mod 4).
-            int ord = 0, pos = 0;
-#pragma unroll
-            for (int d = 0; d < 4; ++d)
-                if (dm & (1 << d)) { ord |= d << (2 * pos); ++pos; }
-#pragma unroll
-            for (int d = 0; d < 4; ++d)
-                if (!(dm & (1 << d))) { ord |= d << (2 * pos); ++pos; }
-
+            // ---- passes of four concurrent directional sweeps until a pass
+            // changes nothing or the fixed-point check finds nothing to improve
             unsigned long long chg[C::RPL];
 #pragma unroll
             for (int m = 0; m < C::RPL; ++m) chg[m] = 0ull;
             int gsweeps = 0;
             bool gdone = c < 0;
             int s = 0;
-            for (; s < C::MAX_SWEEPS; ++s) {
-                const int dir = s < 4 ? (ord >> (2 * s)) & 3 : (s & 3);
-                const bool sx = dir <= 1;                 // i increasing
-                const bool sy = (dir == 0) || (dir == 3); // j increasing
+            for (; s < C::MAX_PASSES; ++s) {
                 bool changed = false;
-                for (int t = 0; t < 2 * K - 1; ++t) {
+                for (int t2 = 0; t2 < 2 * K - 1; ++t2) {
 #pragma unroll
                     for (int m = 0; m < C::RPL; ++m) {
-                        const int j = r0 + 32 * m;
+                        const int j = rl + C::LPD * m;
                         const int jj = sy ? j : K - 1 - j;
-                        const int ii = t - jj;
+                        const int ii = t2 - jj;
                         if (c >= 0 && ii >= 0 && ii < K) {
                             const int i = sx ? ii : K - 1 - ii;
-                            const T fv = tF[j * K + i];
-                            if (fv >= (T)0 && fv < INF) {
-                                const int q = (j + 1) * C::BW + (i + 1);
-                                const T old = tU[q];
-                                const T cand =
-                                    local_update(tU[q - 1], tU[q + 1], tU[q - C::BW], tU[q + C::BW], fv);
-                                if (cand < old) {
-                                    tU[q] = cand;
-                                    chg[m] |= 1ull << i;
-                                    changed = true;
-                                }
+                            T cand, old;
+                            if (node_candidate<MODE, K>(tU, tF, tG, i, j, cand, old) && lt(cand, old)) {
+                                tU[(j + 1) * C::BW + (i + 1)] = cand;
+                                chg[m] |= 1ull << i;
+                                changed = true;
                             }
                         }
                     }
@@ -422,33 +602,47 @@ __global__ void __launch_bounds__(TileCfg<T, K>::WPB * 32)
                 }
                 const unsigned any = __ballot_sync(FULL, changed);
                 if (!gdone) {
-                    ++gsweeps;
+                    gsweeps += 4;
                     if (!(any & gmask)) gdone = true;
                 }
-                if (!any) break;
-                if ((s & 31) == 31) {
+                bool imp = false;
+                if (!gdone) imp = tile_improvable<MODE, K>(tU, tF, tG, dl);
+                const unsigned anyi = __ballot_sync(FULL, imp);
+                if (!gdone && !(anyi & gmask)) {
+                    gdone = true;
+                    ++gsweeps;  // counted like the confirming sweep it replaces
+                }
+                if (__ballot_sync(FULL, !gdone) == 0u) break;
+                if ((s & 15) == 15) {
                     // values only decrease, so stopping early leaves valid upper
                     // bounds; the expired deadline aborts the launch
                     const unsigned long long now = __shfl_sync(FULL, gtimer(), 0);
                     if (now > deadline) {
                         if (lane == 0) fail(ctl, EIK_ETIMEDOUT, 0x4000000ull);
-                        s = C::MAX_SWEEPS + 1;
+                        s = C::MAX_PASSES + 1;
                         break;
                     }
                 }
             }
-            if (s == C::MAX_SWEEPS && r0 == 0 && c >= 0) fail(ctl, EIK_ENOTCONVERGED, (unsigned)c);
+            if (s == C::MAX_PASSES && dl == 0 && c >= 0) fail(ctl, EIK_ENOTCONVERGED, (unsigned)c);
             if (lane == 0)
-                st_lane += (unsigned long long)(s < C::MAX_SWEEPS ? s + 1 : C::MAX_SWEEPS) * C::CPW * K * K;
-            if (r0 == 0 && c >= 0) {
+                st_lane += (unsigned long long)(s < C::MAX_PASSES ? s + 1 : C::MAX_PASSES) * 4 * C::CPW * K * K;
+            if (dl == 0 && c >= 0) {
                 ++st_visits;
                 st_sweeps += gsweeps;
             }
+            PROF_MARK(4);
 
-            // ---- write back the nodes that changed (coalesced across lanes)
+            // ---- changed-node masks per row: union over the four directions
 #pragma unroll
-            for (int m = 0; m < C::RPL; ++m) masks[g * K + r0 + 32 * m] = chg[m];
+            for (int m = 0; m < C::RPL; ++m) {
+                unsigned long long v = chg[m];
+                v |= __shfl_xor_sync(FULL, v, C::LPD);
+                v |= __shfl_xor_sync(FULL, v, 2 * C::LPD);
+                if (dir == 0) masks[g * K + rl + C::LPD * m] = v;
+            }
             __syncwarp();
+            // ---- write back the nodes that changed (coalesced across lanes)
             for (int e = lane; e < C::CPW * K * K; e += 32) {
                 const int gg = e / (K * K);
                 const int rem = e - gg * K * K;
@@ -460,111 +654,110 @@ __global__ void __launch_bounds__(TileCfg<T, K>::WPB * 32)
                 if (cc >= 0 && ((masks[gg * K + j] >> i) & 1ull)) {
                     const int cx = cc % p.cxn, cy = cc / p.cxn;
                     const T* gU = reinterpret_cast<const T*>(wbase + gg * C::GROUP_BYTES);
-                    p.U[(size_t)(cy * K + j + 1) * p.upitch + (size_t)(cx * K + i + 1)] =
+                    Ug[(size_t)(cy * K + j + 1) * p.upitch + (size_t)(cx * K + i + 1)] =
                         gU[(j + 1) * C::BW + (i + 1)];
                 }
             }
             __threadfence();  // release the new values before any activation
             fence_proxy_async_global();
             __syncwarp();
+            PROF_MARK(5);
 
             // ---- activation of the neighbours (Alg. generic_LC_cells) and
-            // their cell values (eq. cell_value).  Side s: 0 W, 1 E, 2 S, 3 N.
-            const int cx = c >= 0 ? c % p.cxn : 0, cy = c >= 0 ? c / p.cxn : 0;
-#pragma unroll
-            for (int sd = 0; sd < 4; ++sd) {
-                int nc = -1;
-                if (c >= 0) {
-                    if (sd == 0 && cx > 0) nc = c - 1;
-                    if (sd == 1 && cx + 1 < p.cxn) nc = c + 1;
-                    if (sd == 2 && cy > 0) nc = c - p.cxn;
-                    if (sd == 3 && cy + 1 < p.cyn) nc = c + p.cxn;
-                }
-                const bool nsrc = nc >= 0 && p.has_src[nc];
+            // their cell values (eq. cell_value).  Side sd: 0 W, 1 E, 2 S, 3 N.
+            // The lanes of sweep direction d take side d: LPD lanes per side,
+            // each owning k/LPD boundary nodes; the first lane of each side
+            // then issues that side's atomics, all four sides at once.
+            // Everything the test needs (values, changed flags, and f across
+            // the boundary, whose sign marks sources) is in shared memory.
+            {
+                const int sd = dir;
+                const int cx = c >= 0 ? c % p.cxn : 0, cy = c >= 0 ? c / p.cxn : 0;
+                bool has_nb = false;
+                if (c >= 0) has_nb = sd == 0 ? cx > 0 : sd == 1 ? cx + 1 < p.cxn : sd == 2 ? cy > 0 : cy + 1 < p.cyn;
                 bool cond = false;
-                double vmax = -inf_of<double>();
+                T vmax = zero_v<T>();
                 int bmax = -1;
 #pragma unroll
                 for (int m = 0; m < C::RPL; ++m) {
-                    const int b = r0 + 32 * m;
+                    const int b = rl + C::LPD * m;
                     int bi, bj, ai, aj;
                     if (sd == 0) { bi = 0; bj = b; ai = -1; aj = b; }
                     else if (sd == 1) { bi = K - 1; bj = b; ai = K; aj = b; }
                     else if (sd == 2) { bi = b; bj = 0; ai = b; aj = -1; }
                     else { bi = b; bj = K - 1; ai = b; aj = K; }
-                    if (nc >= 0) {
-                        const T vb = tU[(bj + 1) * C::BW + (bi + 1)];
-                        const T va = tU[(aj + 1) * C::BW + (ai + 1)];
+                    if (has_nb) {
+                        const int qb = (bj + 1) * C::BW + (bi + 1), qa = (aj + 1) * C::BW + (ai + 1);
+                        const T vb = tU[qb], va = tU[qa];
                         const bool ch = (masks[g * K + bj] >> bi) & 1ull;
-                        const bool isrc = tF[bj * K + bi] < (T)0;
-                        bool cnd = (ch || (first && isrc)) && vb < va;
-                        if (cnd && nsrc) {
-                            const T fa = __ldg(&p.f[(size_t)(cy * K + aj) * p.fpitch + (cx * K + ai)]);
-                            if (fa < (T)0) cnd = false;  // x_j in Q: no activation
-                        }
-                        cond = cond || cnd;
-                        if (vb < INF && (double)vb > vmax) { vmax = (double)vb; bmax = b; }
+                        // V_i changed (or x_i in Q on the first removal),
+                        // V_i < V_j, and x_j not in Q
+                        cond = cond || ((ch || (first && is_src(tF[qb]))) && lt(vb, va) && !is_src(tF[qa]));
+                        if (is_finite_v(vb) && (bmax < 0 || lt(vmax, vb))) { vmax = vb; bmax = b; }
                     }
                 }
-                const bool act = (__ballot_sync(FULL, cond) & gmask) != 0u;
-                // max boundary value on this side, and where (argmax)
+                const unsigned smask = ((1u << C::LPD) - 1u) << (g * C::LPC + sd * C::LPD);
+                const bool act = (__ballot_sync(FULL, cond) & smask) != 0u;
+                // max finite boundary value on this side, and where (argmax)
 #pragma unroll
-                for (int o = C::LPC / 2; o > 0; o >>= 1) {
-                    const double ov = __shfl_xor_sync(FULL, vmax, o);
-                    const int ob = __shfl_xor_sync(FULL, bmax, o);
-                    if (ov > vmax || (ov == vmax && ob > bmax)) { vmax = ov; bmax = ob; }
+                for (int o = C::LPD / 2; o > 0; o >>= 1) {
+                    const T ov = shfl_xor(vmax, o);
+                    const int obm = __shfl_xor_sync(FULL, bmax, o);
+                    if (obm >= 0 && (bmax < 0 || lt(vmax, ov) || (!lt(ov, vmax) && obm > bmax))) {
+                        vmax = ov;
+                        bmax = obm;
+                    }
                 }
-                if (nc >= 0 && r0 == sd) {
+                if (rl == 0 && has_nb) {
+                    const int nc = sd == 0 ? c - 1 : sd == 1 ? c + 1 : sd == 2 ? c - p.cxn : c + p.cxn;
                     double vt = inf_of<double>();
                     if (bmax >= 0) {
-                        // y_i: (h + h^c)/2 = (k+1)h/2 from x_i into the
-                        // neighbour; F(y_i) read at the node (k+1)/2 deep
-                        const int dep = (K + 1) / 2;
-                        int yi, yj, ai, aj;
-                        if (sd == 0) { yi = cx * K - dep; yj = cy * K + bmax; ai = cx * K - 1; aj = yj; }
-                        else if (sd == 1) { yi = cx * K + K - 1 + dep; yj = cy * K + bmax; ai = cx * K + K; aj = yj; }
-                        else if (sd == 2) { yi = cx * K + bmax; yj = cy * K - dep; ai = yi; aj = cy * K - 1; }
-                        else { yi = cx * K + bmax; yj = cy * K + K - 1 + dep; ai = yi; aj = cy * K + K; }
-                        double fy = (double)__ldg(&p.f[(size_t)yj * p.fpitch + yi]);
-                        if (!(fy >= 0.0 && fy < inf_of<double>()))
-                            fy = (double)__ldg(&p.f[(size_t)aj * p.fpitch + ai]);
+                        // eq. cell_value: V_i + ((h + h^c)/2) / F(y_i) with
+                        // (h + h^c)/2 = (k+1) h/2; h/F(y_i) read at the node
+                        // across the boundary from x_i (the k x k box in shared
+                        // memory carries a one-node halo of f)
+                        int ai, aj;
+                        if (sd == 0) { ai = -1; aj = bmax; }
+                        else if (sd == 1) { ai = K; aj = bmax; }
+                        else if (sd == 2) { ai = bmax; aj = -1; }
+                        else { ai = bmax; aj = K; }
+                        double fy = to_d(tF[(aj + 1) * C::BW + (ai + 1)]);
                         if (!(fy >= 0.0 && fy < inf_of<double>())) fy = fmin_glob;
-                        vt = vmax + (double)(K + 1) * 0.5 * fy;
+                        vt = to_d(vmax) + (double)(K + 1) * 0.5 * fy;
                     }
-                    unsigned long long cur;
+                    // HCM: update the neighbour's cell value whether or not it
+                    // is activated; the flag exchange is issued alongside
+                    unsigned long long old = KEY_UNSET, kk = KEY_UNSET;
                     if (vt < inf_of<double>()) {
-                        const unsigned long long kk = key_of(vt);
-                        const unsigned long long old = atomicMin(&p.cval[nc], kk);
-                        cur = old < kk ? old : kk;
-                    } else {
-                        cur = ld_cg(&p.cval[nc]);
+                        kk = key_of(vt);
+                        old = atomicMin(&p.cval[nc], kk);
                     }
-                    if (act) {
-                        // flags of the directions the influence travels in
-                        const int bits = sd == 0 ? 0xC : sd == 1 ? 0x3 : sd == 2 ? 0x6 : 0x9;
-                        atomicOr(&p.dirmask[nc], bits);
-                        if (atomicExch(&p.qflag[nc], 1) == 0) {
-                            if (cur <= theta) lane_push(nextL, next_cnt, nc, J, ctl);
-                            else lane_push(farL, far_cnt, nc, J, ctl);
-                        }
+                    const int was = act ? atomicExch(&p.qflag[nc], 1) : 1;
+                    if (!was) {
+                        unsigned long long cur = old < kk ? old : kk;
+                        if (kk == KEY_UNSET) cur = ld_cg(&p.cval[nc]);
+                        if (cur <= theta) lane_push(nextL, next_cnt, nc, J, ctl);
+                        else lane_push(farL, far_cnt, nc, J, ctl);
                     }
                 }
             }
             __syncwarp();
+            PROF_MARK(6);
         }
         // a warp that gave up (abort raised) still reaches the barrier, which
         // then reports the abort to every block
         ++st_rounds;
-        if (!(ok = grid_sync(ctl, deadline, &s_flag))) break;
+        PROF_MARK(2);
+        if (!grid_sync(ctl, deadline, &s_flag)) break;
+        PROF_MARK(1);
         ns = nx_slot;
-        ++round;
     }
 
-    if (lane == 0) {
-        atomicAdd(&ctl->lane_updates, st_lane);
-    }
-    // per-group counters live on the group leaders
-    if (r0 == 0) {
+    if (lane == 0) atomicAdd(&ctl->lane_updates, st_lane);
+    if (p.profile && lane == 0)
+        for (int i = 0; i < 8; ++i) atomicAdd(&ctl->prof[i], pacc[i]);
+    // per-cell counters live on each cell's first lane
+    if (dl == 0) {
         atomicAdd(&ctl->visits, st_visits);
         atomicAdd(&ctl->sweeps, st_sweeps);
     }

@@ -1,52 +1,51 @@
-// FP32 instantiations of the persistent cell solver and their launcher.
+// Instantiations of the persistent cell solver for one arithmetic mode
+// (MODE_F32), all cell sizes, and their launcher.
 #include "eik_solver.cuh"
 
 namespace eik {
 
-template <typename T, int K>
+template <int K>
 static void shape_of(int num_sms, LaunchShape* s) {
-    using C = TileCfg<T, K>;
+    using C = TileCfg<MODE_F32, K>;
     s->threads = C::WPB * 32;
     s->smem = (size_t)C::WPB * C::WARP_BYTES + 128;
-    cudaFuncSetAttribute(k_solve<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem);
+    cudaFuncSetAttribute(k_solve<MODE_F32, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<T, K>, s->threads, s->smem) !=
-            cudaSuccess ||
-        per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<MODE_F32, K>, s->threads,
+                                                      s->smem) != cudaSuccess)
         per_sm = 0;
-    s->blocks = per_sm * num_sms;
+    // at most two blocks per SM: a round rarely has more cells than that, and
+    // every extra block makes each grid barrier slower
+    s->blocks = (per_sm < 2 ? per_sm : 2) * num_sms;
 }
 
-template <typename T, int K>
-static cudaError_t launch_one(const SolveParams<T>& p, const LaunchShape& s, cudaStream_t st) {
+template <int K>
+static cudaError_t launch_one(const SolveParams& p, const LaunchShape& s, cudaStream_t st) {
     void* args[] = {(void*)&p};
-    return cudaLaunchCooperativeKernel((const void*)k_solve<T, K>, dim3(s.blocks), dim3(s.threads),
-                                       args, s.smem, st);
+    return cudaLaunchCooperativeKernel((const void*)k_solve<MODE_F32, K>, dim3(s.blocks),
+                                       dim3(s.threads), args, s.smem, st);
 }
-
-#define EIK_SHAPE_CASES(T)                       \
-    switch (k) {                                 \
-    case 4: shape_of<T, 4>(num_sms, out); break;   \
-    case 8: shape_of<T, 8>(num_sms, out); break;   \
-    case 16: shape_of<T, 16>(num_sms, out); break; \
-    case 32: shape_of<T, 32>(num_sms, out); break; \
-    case 64: shape_of<T, 64>(num_sms, out); break; \
-    default: return -1;                          \
-    }
 
 int solver_shape_f32(int k, int num_sms, LaunchShape* out) {
-    EIK_SHAPE_CASES(float)
+    out->blocks = 0;
+    switch (k) {
+    case 4: shape_of<4>(num_sms, out); break;
+    case 8: shape_of<8>(num_sms, out); break;
+    case 16: shape_of<16>(num_sms, out); break;
+    case 32: shape_of<32>(num_sms, out); break;
+    case 64: shape_of<64>(num_sms, out); break;
+    default: return -1;
+    }
     return out->blocks > 0 ? 0 : -1;
 }
 
-cudaError_t launch_solver_f32(int k, const SolveParams<float>& p, const LaunchShape& s,
-                              cudaStream_t st) {
+cudaError_t launch_solver_f32(int k, const SolveParams& p, const LaunchShape& s, cudaStream_t st) {
     switch (k) {
-    case 4: return launch_one<float, 4>(p, s, st);
-    case 8: return launch_one<float, 8>(p, s, st);
-    case 16: return launch_one<float, 16>(p, s, st);
-    case 32: return launch_one<float, 32>(p, s, st);
-    case 64: return launch_one<float, 64>(p, s, st);
+    case 4: return launch_one<4>(p, s, st);
+    case 8: return launch_one<8>(p, s, st);
+    case 16: return launch_one<16>(p, s, st);
+    case 32: return launch_one<32>(p, s, st);
+    case 64: return launch_one<64>(p, s, st);
     default: return cudaErrorInvalidValue;
     }
 }

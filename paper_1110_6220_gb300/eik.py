@@ -54,11 +54,14 @@ class eik_stats(ctypes.Structure):
                 ("avs", ctypes.c_double), ("max_residual", ctypes.c_double),
                 ("err_bound", ctypes.c_double), ("bucket_width", ctypes.c_double),
                 ("cell_visits", ctypes.c_int64), ("rounds", ctypes.c_int64),
-                ("buckets", ctypes.c_int64), ("cell_k", ctypes.c_int32),
+                ("buckets", ctypes.c_int64), ("pass_ms", ctypes.c_double * 2),
+                ("launches", ctypes.c_int32), ("cell_k", ctypes.c_int32),
                 ("status", ctypes.c_int32)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["pass_ms"] = list(self.pass_ms)
+        return d
 
 
 eik_plan = ctypes.c_void_p

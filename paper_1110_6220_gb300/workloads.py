@@ -82,25 +82,39 @@ def checker_field(n: int, checkers: int = 64, lo: float = 1.0, hi: float = 2.0) 
     return np.where(par == 0, lo, hi).astype(np.float64)
 
 
-def maze_walls(n: int, rng: np.random.Generator, n_walls: int = 32, gaps: int = 4,
-               gap_w: int = 8) -> np.ndarray:
-    """Boolean (ny, nx) mask of 1-node-thick axis-aligned walls, each with
-    ``gaps`` openings ``gap_w`` nodes wide, on distinct seeded rows/columns."""
+def maze_walls(n: int, rng: np.random.Generator, n_walls: int = 32, gap_w: int = 8,
+               p_gap: float = 0.65) -> np.ndarray:
+    """Boolean (ny, nx) mask of 1-node-thick axis-aligned walls on ``n_walls``
+    distinct seeded rows and as many columns.  The walls cut the square into
+    rooms; every wall segment between two crossing walls gets one opening
+    ``gap_w`` nodes wide with probability ``p_gap`` (above the bond-percolation
+    threshold 1/2, so most rooms connect through winding paths, as in the comb
+    mazes of Sec. 5.1)."""
     wall = np.zeros((n, n), dtype=bool)
     lines = np.arange(2, n - 2)
-    rows = rng.choice(lines, size=n_walls, replace=False)
-    cols = rng.choice(lines, size=n_walls, replace=False)
+    n_walls = min(n_walls, lines.size // 4)
+    rows = np.sort(rng.choice(lines, size=n_walls, replace=False))
+    cols = np.sort(rng.choice(lines, size=n_walls, replace=False))
+    wall[rows, :] = True
+    wall[:, cols] = True
+
+    def cut(line_is_row, k, cross):
+        edges = np.concatenate([[-1], cross, [n]])
+        for a, b in zip(edges[:-1], edges[1:]):
+            lo, hi = a + 1, b  # open interval of the segment
+            if hi - lo < gap_w + 2 or rng.random() >= p_gap:
+                continue
+            s0 = int(rng.integers(lo, hi - gap_w + 1))
+            if line_is_row:
+                wall[k, s0:s0 + gap_w] = False
+            else:
+                wall[s0:s0 + gap_w, k] = False
+
     for r in rows:
-        wall[r, :] = True
+        cut(True, r, cols)
     for c in cols:
-        wall[:, c] = True
-    # openings: cut each wall in `gaps` places
-    for r in rows:
-        for s in rng.integers(0, n - gap_w, size=gaps):
-            wall[r, s:s + gap_w] = False
-    for c in cols:
-        for s in rng.integers(0, n - gap_w, size=gaps):
-            wall[s:s + gap_w, c] = False
+        cut(False, c, rows)
+    wall[rows[:, None], cols[None, :]] = True  # crossings stay closed
     return wall
 
 
