@@ -66,7 +66,7 @@ def config_dict(args, k, precision):
     return {"workload": f"single solve, {N_GRID}x{N_GRID} grid on [0,1]^2, "
                         "F=1+0.5 sin(20 pi x) sin(20 pi y), point source at centre",
             "grid": N_GRID, "precision": precision, "cell_k": k,
-            "bucket_width": "auto (k * min h/F)" if args.bucket_width <= 0 else args.bucket_width,
+            "bucket_width": "auto (4 k min h/F)" if args.bucket_width <= 0 else args.bucket_width,
             "parallelism": "replicas (one independent grid per GPU)",
             "l2": "flushed between timed steps (256 MiB write)"}
 
@@ -284,13 +284,17 @@ def run_ours(args):
         rel_err = float(np.abs(Ug[fin] - V[fin]).max() / np.abs(V[fin]).max())
         same_inf = bool((np.isfinite(Ug) == fin).all())
 
-        # ---- roofline of the dominant kernel (the longer persistent pass)
+        # ---- roofline of the dominant kernel (the longer persistent pass).
+        # Algorithmic bytes per grid point (each point read and written once,
+        # plus the halo): FP32 pass 4 B f + 2 x 4 B U, double-float refinement
+        # and FP64 passes 8 B f + 2 x 8 B U, each times (1 + 4/k).
         p32 = statistics.mean(s.pass_ms[0] for s in stats)
         p64 = statistics.mean(s.pass_ms[1] for s in stats)
         if p32 > p64:
-            kname, kms, bpp = "k_solve<float>", p32, 12.0 * (1 + 4.0 / k)
+            kname, kms, bpp = "k_solve<F32>", p32, 12.0 * (1 + 4.0 / k)
         else:
-            kname, kms, bpp = "k_solve<double>", p64, 24.0 * (1 + 4.0 / k)
+            kname = "k_solve<DF>" if prec else "k_solve<F64>"
+            kms, bpp = p64, 24.0 * (1 + 4.0 / k)
         peak, peak_src = measured_hbm()
         achieved = bpp * I.npts / (kms / 1e3) / 1e9
         traffic = ncu_traffic(kname, k)
