@@ -133,6 +133,34 @@ size_t eik_plan_workspace_bytes(const eik_plan_desc* d);
  * non-finite q, an F value that is negative, NaN or infinite.  st may be NULL. */
 int eik_solve(eik_plan p, const eik_instance* in, eik_stats* st);
 
+/* ------------------------------------------------------- no-allocation solve
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot call cudaMalloc: code that runs where device memory is already owned
+ * by another allocator (a framework's caching allocator or a fixed memory
+ * budget), or latency-critical loops that cannot afford the implicit device
+ * synchronisation of an allocation.
+ *
+ * eik_solve_noalloc solves one FP64 instance (d->precision must be EIK_FP64)
+ * like eik_plan_create + eik_solve + eik_plan_destroy, but allocates nothing,
+ * on the device or on the host: the whole workspace lives in one fixed device
+ * array of EIK_NOALLOC_SCRATCH_BYTES inside this library, which every GPU that
+ * loads the library holds until the process exits.
+ *   - in->F and in->U must be device pointers (EIK_EINVAL otherwise); the
+ *     caller still owns and passes all inputs and outputs.
+ *   - at most EIK_NOALLOC_MAX_SOURCES sources (host or device pointers).
+ *   - a grid whose workspace does not fit the fixed array (about 1000 x 1000
+ *     nodes at k = 8) is rejected with EIK_EINVAL.
+ *   - the first call on a device looks up that device's copy of the array;
+ *     make that first call before any stream capture.
+ *   - every call shares the one array: calls that overlap on a GPU (different
+ *     streams or threads) race and corrupt each other; serialise them.
+ *   - work is queued on cuda_stream (NULL: the legacy default stream); the
+ *     call returns when U is written.  st->ms is host wall time of the call. */
+#define EIK_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define EIK_NOALLOC_MAX_SOURCES 256
+int eik_solve_noalloc(const eik_plan_desc* d, const eik_instance* in, eik_stats* st,
+                      void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

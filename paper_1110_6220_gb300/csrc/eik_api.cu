@@ -291,24 +291,46 @@ static void print_profile(const char* what, const Ctl* c) {
 // F on the device).  Reads nothing back.
 int enqueue_solve(Workspace* w, const eik_plan_desc* d, const double* Fdev, const HostSources& hs,
                   SrcDev* sd, int num_sms, cudaStream_t st, cudaEvent_t* ev, int* launches) {
+    // upload the (small) source tables into the plan's growable buffer
+    const size_t nsrc = hs.node.size(), ncell = hs.cell.size();
+    int rc = grow_staging(&sd->buf, src_table_bytes(nsrc, ncell));
+    if (rc) return rc;
+    const SrcTables t = carve_src_tables(sd->buf.p, nsrc, ncell);
+    if (nsrc) {
+        cudaMemcpyAsync(t.node, hs.node.data(), nsrc * 4, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(t.q, hs.q.data(), nsrc * 8, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(t.cell, hs.cell.data(), ncell * 4, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(t.cell_key, hs.cell_key.data(), ncell * 8, cudaMemcpyHostToDevice, st);
+    }
+    return enqueue_solve_tables(w, d, Fdev, t, num_sms, st, ev, launches);
+}
+
+size_t src_table_bytes(size_t nsrc, size_t ncell) {
+    return (nsrc * 4 + 15) / 16 * 16 + nsrc * 8 + (ncell * 4 + 15) / 16 * 16 + ncell * 8 + 64;
+}
+
+SrcTables carve_src_tables(void* base_, size_t nsrc, size_t ncell) {
+    char* base = (char*)base_;
+    SrcTables t;
+    t.node = (int*)base;
+    t.q = (double*)(base + ((nsrc * 4 + 15) / 16 * 16));
+    t.cell = (int*)((char*)t.q + nsrc * 8);
+    t.cell_key = (unsigned long long*)((char*)t.cell + ((ncell * 4 + 15) / 16 * 16));
+    t.nsrc = (int)nsrc;
+    t.ncell = (int)ncell;
+    return t;
+}
+
+int enqueue_solve_tables(Workspace* w, const eik_plan_desc* d, const double* Fdev, const SrcTables& t,
+                         int num_sms, cudaStream_t st, cudaEvent_t* ev, int* launches) {
     int nl = 0;
     const Layout& L = w->L;
     const bool fp32 = d->precision == EIK_FP32_REFINE;
-    // upload the (small) source tables
-    const size_t nsrc = hs.node.size(), ncell = hs.cell.size();
-    int rc = grow_staging(&sd->buf, nsrc * 12 + ncell * 12 + 64);
-    if (rc) return rc;
-    char* base = (char*)sd->buf.p;
-    int* d_node = (int*)base;
-    double* d_q = (double*)(base + ((nsrc * 4 + 15) / 16 * 16));
-    int* d_cell = (int*)((char*)d_q + nsrc * 8);
-    unsigned long long* d_ckey = (unsigned long long*)((char*)d_cell + ((ncell * 4 + 15) / 16 * 16));
-    if (nsrc) {
-        cudaMemcpyAsync(d_node, hs.node.data(), nsrc * 4, cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(d_q, hs.q.data(), nsrc * 8, cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(d_cell, hs.cell.data(), ncell * 4, cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(d_ckey, hs.cell_key.data(), ncell * 8, cudaMemcpyHostToDevice, st);
-    }
+    const size_t nsrc = (size_t)t.nsrc, ncell = (size_t)t.ncell;
+    int* d_node = t.node;
+    double* d_q = t.q;
+    int* d_cell = t.cell;
+    unsigned long long* d_ckey = t.cell_key;
     Ctl* ctl32 = w->ctl;
     Ctl* ctl64 = w->ctl + 1;
     cudaMemsetAsync(w->ctl, 0, 2 * sizeof(Ctl) + sizeof(ResidualOut), st);

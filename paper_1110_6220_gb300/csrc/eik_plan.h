@@ -58,6 +58,17 @@ struct SrcDev {
     DevBuf buf;
 };
 
+// Device copies of the prepared source tables (see HostSources).
+struct SrcTables {
+    int* node;
+    double* q;
+    int* cell;
+    unsigned long long* cell_key;
+    int nsrc, ncell;
+};
+size_t src_table_bytes(size_t nsrc, size_t ncell);
+SrcTables carve_src_tables(void* base, size_t nsrc, size_t ncell);
+
 bool desc_valid(const eik_plan_desc* d);
 int default_k(const eik_plan_desc* d);
 Layout make_layout(int nx, int ny, int k);
@@ -71,6 +82,11 @@ int grow_staging(DevBuf* b, size_t bytes);
 // around the FP64 pass.  *launches counts the kernels queued.
 int enqueue_solve(Workspace* w, const eik_plan_desc* d, const double* Fdev, const HostSources& hs,
                   SrcDev* sd, int num_sms, cudaStream_t st, cudaEvent_t* ev, int* launches);
+// The same, with the source tables already on the device.
+int enqueue_solve_tables(Workspace* w, const eik_plan_desc* d, const double* Fdev, const SrcTables& t,
+                         int num_sms, cudaStream_t st, cudaEvent_t* ev, int* launches);
+bool make_map(CUtensorMap* tm, void* base, bool fp64, int width, int rows, int pitch_elems,
+              int box_w, int box_h);
 void finish_stats(const Layout& L, const eik_plan_desc* d, const Ctl* c32, const Ctl* c64,
                   const ResidualOut* r, double q_min, bool fp32, double ms, eik_stats* st);
 

@@ -78,6 +78,9 @@ _lib.eik_plan_workspace_bytes.argtypes = [_P(eik_plan_desc)]
 _lib.eik_plan_workspace_bytes.restype = ctypes.c_size_t
 _lib.eik_solve.argtypes = [eik_plan, _P(eik_instance), _P(eik_stats)]
 _lib.eik_solve.restype = ctypes.c_int
+_lib.eik_solve_noalloc.argtypes = [_P(eik_plan_desc), _P(eik_instance), _P(eik_stats),
+                                   ctypes.c_void_p]
+_lib.eik_solve_noalloc.restype = ctypes.c_int
 if hasattr(_lib, "eik_solve_batch"):
     _lib.eik_solve_batch.argtypes = [_P(eik_plan_desc), _P(eik_instance), ctypes.c_int32,
                                      _P(eik_stats), ctypes.c_void_p]
@@ -95,7 +98,7 @@ if hasattr(_lib, "eik_server_create"):
     _lib.eik_server_destroy.restype = None
 
 SYMBOLS = ["eik_strerror", "eik_plan_create", "eik_plan_destroy", "eik_plan_workspace_bytes",
-           "eik_solve", "eik_solve_batch", "eik_server_create", "eik_submit", "eik_poll",
+           "eik_solve", "eik_solve_noalloc", "eik_solve_batch", "eik_server_create", "eik_submit", "eik_poll",
            "eik_server_destroy"]
 
 
@@ -129,6 +132,15 @@ def eik_plan_workspace_bytes(desc: eik_plan_desc) -> int:
 def eik_solve(plan: eik_plan, inst: eik_instance) -> tuple[int, eik_stats]:
     st = eik_stats()
     rc = _lib.eik_solve(plan, ctypes.byref(inst), ctypes.byref(st))
+    return rc, st
+
+
+def eik_solve_noalloc(desc: eik_plan_desc, inst: eik_instance, cuda_stream=None):
+    """FP64 solve that allocates nothing (fixed in-library device scratch);
+    F and U must be device tensors.  Returns (status, eik_stats)."""
+    st = eik_stats()
+    rc = _lib.eik_solve_noalloc(ctypes.byref(desc), ctypes.byref(inst), ctypes.byref(st),
+                                _stream_ptr(cuda_stream))
     return rc, st
 
 
