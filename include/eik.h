@@ -133,6 +133,19 @@ size_t eik_plan_workspace_bytes(const eik_plan_desc* d);
  * non-finite q, an F value that is negative, NaN or infinite.  st may be NULL. */
 int eik_solve(eik_plan p, const eik_instance* in, eik_stats* st);
 
+/* Solve n_inst independent instances of (possibly) different shapes together:
+ * one persistent launch per pass for all instances of the same cell size and
+ * precision, with a device-side work queue per instance (Sec. 4.2's lists,
+ * one per grid) and every SM serving cells of any instance.  d[i] describes
+ * instance i (nx, ny, h, cell_k, bucket_width, precision, tol); deadline_ns of
+ * d[0] applies to each launch.  Up to 2048 instances share a launch; more are
+ * run as several launches.  st: NULL or n_inst entries (ms is the device time
+ * of the launch that held the instance).  Blocks until every U is written.
+ * Returns EIK_OK if every instance succeeded, else the first error; the
+ * status of each instance is in st[i].status. */
+int eik_solve_batch(const eik_plan_desc* d, const eik_instance* in, int32_t n_inst,
+                    eik_stats* st, void* cuda_stream);
+
 /* ------------------------------------------------------- no-allocation solve
  * The paper has no counterpart to this entry point; it exists for callers that
  * cannot call cudaMalloc: code that runs where device memory is already owned

@@ -1,12 +1,13 @@
-// eik_api.cu -- the C ABI (include/eik.h): plans, single solves.
-#include <cudaTypedefs.h>
-
+// eik_api.cu -- the C ABI (include/eik.h): plans, single solves and batches,
+// all run as jobs (eik_job.h).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <limits>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -31,8 +32,7 @@ extern "C" const char* eik_strerror(int code) {
 
 namespace eik {
 
-// ---------------------------------------------------------------- layout
-static int round_up(int v, int m) { return (v + m - 1) / m * m; }
+static size_t a256(size_t b) { return (b + 255) / 256 * 256; }
 
 bool desc_valid(const eik_plan_desc* d) {
     if (!d) return false;
@@ -51,140 +51,28 @@ int default_k(const eik_plan_desc* d) {
     return 8;
 }
 
-Layout make_layout(int nx, int ny, int k) {
-    Layout L;
-    L.nx = nx;
-    L.ny = ny;
-    L.k = k;
-    L.cxn = (nx + k - 1) / k;
-    L.cyn = (ny + k - 1) / k;
-    L.J = L.cxn * L.cyn;
-    L.nxp = L.cxn * k;
-    L.nyp = L.cyn * k;
-    // room for the FP32 box (k+4 wide from column cx*k) and a multiple of 16 B rows
-    L.upitch = round_up(L.nxp + 4, 32);
-    L.urows = L.nyp + 2;
-    // f shares U's layout (ring included) so that its TMA box carries the halo
-    L.fpitch = L.upitch;
-    L.frows = L.urows;
-    return L;
-}
-
-size_t layout_bytes(const Layout& L, bool fp32) {
-    size_t b = 0;
-    const size_t un = (size_t)L.upitch * L.urows, fn = (size_t)L.fpitch * L.frows;
-    if (fp32) b += un * (4 + 8) + fn * (4 + 8);  // U32, Udf, f32, fdf
-    else b += un * 8 + fn * 8;                   // U64, f64
-    b += (size_t)L.nx * L.ny * 8;                // staging for host F / output
-    b += (size_t)L.J * (8 + 4 + 4 + 1);          // cval, qflag, visits, has_src
-    b += (size_t)5 * L.J * 4;                    // lists
-    b += 2 * sizeof(Ctl) + sizeof(ResidualOut);
-    return b;
-}
-
-// ---------------------------------------------------------------- tensor maps
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
-    return fn;
-}
-
-bool make_map(CUtensorMap* tm, void* base, bool fp64, int width, int rows, int pitch_elems,
-              int box_w, int box_h) {
-    auto fn = encode_fn();
-    if (!fn) return false;
-    const int es = fp64 ? 8 : 4;
-    cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)pitch_elems * es};
-    cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(tm, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                    base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
-}
-
-// ---------------------------------------------------------------- workspace
-static void* dalloc(size_t bytes, int* err) {
-    void* p = nullptr;
-    if (*err) return nullptr;
-    if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        *err = EIK_ENOMEM;
-        return nullptr;
+        return false;
     }
-    return p;
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-int workspace_alloc(Workspace* w, const Layout& L, bool fp32, cudaStream_t st) {
-    int err = 0;
-    std::memset((void*)w, 0, sizeof(*w));
-    w->L = L;
-    w->fp32 = fp32;
-    const size_t un = (size_t)L.upitch * L.urows, fn = (size_t)L.fpitch * L.frows;
-    if (fp32) {
-        w->U32 = (float*)dalloc(un * 4, &err);
-        w->f32 = (float*)dalloc(fn * 4, &err);
-        w->Udf = (float2*)dalloc(un * 8, &err);
-        w->fdf = (float2*)dalloc(fn * 8, &err);
-    } else {
-        w->U64 = (double*)dalloc(un * 8, &err);
-        w->f64 = (double*)dalloc(fn * 8, &err);
+int grow(DevBuf* b, size_t bytes) {
+    if (b->cap >= bytes) return EIK_OK;
+    if (b->p) cudaFree(b->p);
+    b->p = nullptr;
+    b->cap = 0;
+    const size_t cap = std::max<size_t>(bytes + bytes / 8, 1 << 20);
+    if (cudaMalloc(&b->p, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return EIK_ENOMEM;
     }
-    w->Fstage = (double*)dalloc((size_t)L.nx * L.ny * 8, &err);
-    w->cval = (unsigned long long*)dalloc((size_t)L.J * 8, &err);
-    w->qflag = (int*)dalloc((size_t)L.J * 4, &err);
-    w->visits = (int*)dalloc((size_t)L.J * 4, &err);
-    w->has_src = (unsigned char*)dalloc((size_t)L.J, &err);
-    w->lists = (int*)dalloc((size_t)5 * L.J * 4, &err);
-    w->ctl = (Ctl*)dalloc(2 * sizeof(Ctl) + sizeof(ResidualOut), &err);
-    if (err) {
-        workspace_free(w);
-        return err;
-    }
-    w->res = (ResidualOut*)(w->ctl + 2);
-    // the +inf ring (and padding columns) never change after this fill
-    if (w->U64 && launch_fill(w->U64, un, std::numeric_limits<double>::infinity(), st) != cudaSuccess)
-        err = EIK_ECUDA;
-    if (w->U32 && launch_fill32(w->U32, un, std::numeric_limits<float>::infinity(), st) != cudaSuccess)
-        err = EIK_ECUDA;
-    if (w->Udf && launch_fill_df(w->Udf, un, st) != cudaSuccess) err = EIK_ECUDA;
-    // f's ring: +inf (obstacles) forever
-    if (w->f64 && launch_fill(w->f64, fn, std::numeric_limits<double>::infinity(), st) != cudaSuccess)
-        err = EIK_ECUDA;
-    if (w->f32 && launch_fill32(w->f32, fn, std::numeric_limits<float>::infinity(), st) != cudaSuccess)
-        err = EIK_ECUDA;
-    if (w->fdf && launch_fill_df(w->fdf, fn, st) != cudaSuccess) err = EIK_ECUDA;
-    const int K = L.k;
-    // U maps span the whole pitch, so a box (k+2 or k+4 wide) never leaves the
-    // array; 8-byte values (doubles or float pairs) move as FLOAT64 elements
-    if (fp32) {
-        if (!make_map(&w->tmU32, w->U32, false, L.upitch, L.urows, L.upitch, K + 4, K + 2)) err = EIK_ECUDA;
-        if (!make_map(&w->tmF32, w->f32, false, L.fpitch, L.frows, L.fpitch, K + 4, K + 2)) err = EIK_ECUDA;
-        if (!make_map(&w->tmUdf, w->Udf, true, L.upitch, L.urows, L.upitch, K + 2, K + 2)) err = EIK_ECUDA;
-        if (!make_map(&w->tmFdf, w->fdf, true, L.fpitch, L.frows, L.fpitch, K + 2, K + 2)) err = EIK_ECUDA;
-    } else {
-        if (!make_map(&w->tmU64, w->U64, true, L.upitch, L.urows, L.upitch, K + 2, K + 2)) err = EIK_ECUDA;
-        if (!make_map(&w->tmF64, w->f64, true, L.fpitch, L.frows, L.fpitch, K + 2, K + 2)) err = EIK_ECUDA;
-    }
-    if (err) workspace_free(w);
-    return err;
-}
-
-void workspace_free(Workspace* w) {
-    void* ptrs[] = {w->U64, w->f64, w->U32, w->f32, w->Udf, w->fdf, w->Fstage,
-                    w->cval, w->qflag, w->visits, w->has_src, w->lists, w->ctl};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
-    std::memset((void*)w, 0, sizeof(*w));
+    b->cap = cap;
+    return EIK_OK;
 }
 
 // ---------------------------------------------------------------- sources
@@ -238,280 +126,204 @@ int prepare_sources(const Layout& L, const eik_instance* in, HostSources* hs) {
     return EIK_OK;
 }
 
-bool is_device_ptr(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
+// ---------------------------------------------------------------- jobs
+int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance* in, int k, bool fp32,
+              long long deadline_ns, cudaStream_t st) {
+    if (n < 1 || n > MAX_BATCH) return EIK_EINVAL;
+    std::vector<HostSources> hs((size_t)n);
+    std::vector<char> stageF((size_t)n);
+    hj->L.resize(n);
+    hj->arr.resize(n);
+    hj->shift.resize(n);
+    hj->out_host.resize(n);
+    hj->out_user.resize(n);
+    size_t nsrc = 0, ncs = 0, Jtot = 0, ibytes = 0;
+    std::vector<size_t> inst_off((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        if (!in[i].F || !in[i].U || in[i].nsrc < 0) return EIK_EINVAL;
+        hj->L[i] = make_layout(descs[i].nx, descs[i].ny, k);
+        const int rc = prepare_sources(hj->L[i], &in[i], &hs[i]);
+        if (rc) return rc;
+        stageF[i] = !is_device_ptr(in[i].F);
+        hj->out_host[i] = !is_device_ptr(in[i].U);
+        hj->out_user[i] = in[i].U;
+        hj->shift[i] = hs[i].node.empty() ? 0.0 : hs[i].q_min;
+        nsrc += hs[i].node.size();
+        ncs += hs[i].cell.size();
+        Jtot += (size_t)hj->L[i].J;
+        inst_off[i] = ibytes;
+        ibytes += inst_bytes(hj->L[i], fp32, stageF[i], hj->out_host[i]);
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-int grow_staging(DevBuf* b, size_t bytes) {
-    if (b->cap >= bytes) return EIK_OK;
-    if (b->p) cudaFree(b->p);
-    b->p = nullptr;
-    b->cap = 0;
-    const size_t cap = std::max<size_t>(bytes, 4096);
-    if (cudaMalloc(&b->p, cap) != cudaSuccess) {
-        cudaGetLastError();
-        return EIK_ENOMEM;
-    }
-    b->cap = cap;
-    return EIK_OK;
-}
-
-// ---------------------------------------------------------------- one solve
-// EIK_PROFILE=1 (debugging aid): kernels accumulate per-phase clock cycles and
-// each solve prints them to stderr.
-int profiling() {
-    static int on = -1;
-    if (on < 0) {
-        const char* e = std::getenv("EIK_PROFILE");
-        on = (e && e[0] == '1') ? 1 : 0;
-    }
-    return on;
-}
-
-static void print_profile(const char* what, const Ctl* c) {
-    const char* names[8] = {"split", "barrier", "list+pop", "tma", "sweeps", "writeback", "activate",
-                            "warp-visits"};
-    double tot = 0;
-    for (int i = 0; i < 7; ++i) tot += (double)c->prof[i];
-    std::fprintf(stderr, "[eik profile %s] rounds=%llu", what, (unsigned long long)c->rounds);
-    for (int i = 0; i < 7; ++i)
-        std::fprintf(stderr, " %s=%.1f%%", names[i], tot > 0 ? 100.0 * c->prof[i] / tot : 0.0);
-    std::fprintf(stderr, " warp-visits=%llu cyc/visit(sweeps)=%.0f cyc/visit(tma)=%.0f cyc/visit(act)=%.0f\n",
-                 (unsigned long long)c->prof[7], c->prof[7] ? (double)c->prof[4] / c->prof[7] : 0.0,
-                 c->prof[7] ? (double)c->prof[3] / c->prof[7] : 0.0,
-                 c->prof[7] ? (double)c->prof[6] / c->prof[7] : 0.0);
-}
-// Queue the whole solve of one instance on `st` (inputs already validated;
-// F on the device).  Reads nothing back.
-int enqueue_solve(Workspace* w, const eik_plan_desc* d, const double* Fdev, const HostSources& hs,
-                  SrcDev* sd, int num_sms, cudaStream_t st, cudaEvent_t* ev, int* launches) {
-    // upload the (small) source tables into the plan's growable buffer
-    const size_t nsrc = hs.node.size(), ncell = hs.cell.size();
-    int rc = grow_staging(&sd->buf, src_table_bytes(nsrc, ncell));
+    // ---- arena: [tables | sources] [zero region] [cval] [instances]
+    const size_t t_desc = a256((size_t)n * sizeof(InstDesc));
+    const size_t t_aux = a256((size_t)n * sizeof(AuxInst));
+    const size_t t_pre = a256((size_t)(n + 1) * 4);
+    const size_t ns4 = a256(std::max(nsrc, ncs) * 4 + 4);
+    const size_t t_src = a256(nsrc * 8 + 8) + a256(ncs * 8 + 8) + 4 * ns4;
+    const size_t image_bytes = 2 * t_desc + t_aux + 3 * t_pre + t_src;
+    const size_t z_ctl = a256((size_t)(2 * n + 2) * sizeof(Ctl) + (size_t)n * sizeof(ResidualOut));
+    const size_t zero_bytes = z_ctl + a256(Jtot * 4) * 2;
+    const size_t total = image_bytes + zero_bytes + a256(Jtot * 8) + ibytes + 256;
+    int rc = grow(&hj->arena, total);
     if (rc) return rc;
-    const SrcTables t = carve_src_tables(sd->buf.p, nsrc, ncell);
-    if (nsrc) {
-        cudaMemcpyAsync(t.node, hs.node.data(), nsrc * 4, cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(t.q, hs.q.data(), nsrc * 8, cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(t.cell, hs.cell.data(), ncell * 4, cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(t.cell_key, hs.cell_key.data(), ncell * 8, cudaMemcpyHostToDevice, st);
+    char* base = (char*)hj->arena.p;
+    char* img_dev = base;
+    char* zero_dev = base + image_bytes;
+    char* cval_dev = zero_dev + zero_bytes;
+    char* inst_dev = cval_dev + a256(Jtot * 8);
+
+    hj->image.assign(image_bytes, 0);
+    char* img = hj->image.data();
+    InstDesc* desc_main_h = (InstDesc*)img;
+    InstDesc* desc_f32_h = (InstDesc*)(img + t_desc);
+    AuxInst* aux_h = (AuxInst*)(img + 2 * t_desc);
+    int* blk_pre_h = (int*)(img + 2 * t_desc + t_aux);
+    int* cell_pre_h = (int*)(img + 2 * t_desc + t_aux + t_pre);
+    int* blk_full_h = (int*)(img + 2 * t_desc + t_aux + 2 * t_pre);
+    char* src_h = img + 2 * t_desc + t_aux + 3 * t_pre;
+    const size_t o_q = 0, o_key = a256(nsrc * 8 + 8), o_node = o_key + a256(ncs * 8 + 8);
+    const size_t o_ninst = o_node + ns4, o_cell = o_ninst + ns4, o_cinst = o_cell + ns4;
+
+    Ctl* ictl_dev = (Ctl*)zero_dev;
+    Ctl* gctl_dev = ictl_dev + 2 * n;
+    ResidualOut* res_dev = (ResidualOut*)(gctl_dev + 2);
+    int* qflag_all = (int*)(zero_dev + z_ctl);
+    int* visits_all = (int*)(zero_dev + z_ctl + a256(Jtot * 4));
+    unsigned long long* cval_all = (unsigned long long*)cval_dev;
+
+    bool ok = true;
+    size_t coff = 0, so = 0, co = 0;
+    int boff = 0, bfull = 0;
+    for (int i = 0; i < n; ++i) {
+        const Layout& L = hj->L[i];
+        InstArrays a = carve_inst(L, fp32, stageF[i], hj->out_host[i], inst_dev + inst_off[i]);
+        a.cval = cval_all + coff;
+        a.qflag = qflag_all + coff;
+        a.visits = visits_all + coff;
+        hj->arr[i] = a;
+        const double* F = stageF[i] ? a.Fstage : in[i].F;
+        double* out = hj->out_host[i] ? a.Ostage : in[i].U;
+        fill_inst_tables(L, a, fp32, descs[i].h, descs[i].bucket_width, &ictl_dev[i], &ictl_dev[n + i],
+                         &res_dev[i], F, out, hj->shift[i], &aux_h[i], &desc_main_h[i], &desc_f32_h[i], &ok);
+        blk_pre_h[i] = boff;
+        boff += ((L.nyp + 7) / 8) * ((L.nxp + 31) / 32);
+        blk_full_h[i] = bfull;
+        bfull += ((L.urows + 7) / 8) * ((L.upitch + 31) / 32);
+        cell_pre_h[i] = (int)coff;
+        coff += (size_t)L.J;
+        for (size_t e = 0; e < hs[i].node.size(); ++e, ++so) {
+            ((double*)(src_h + o_q))[so] = hs[i].q[e];
+            ((int*)(src_h + o_node))[so] = hs[i].node[e];
+            ((int*)(src_h + o_ninst))[so] = i;
+        }
+        for (size_t e = 0; e < hs[i].cell.size(); ++e, ++co) {
+            ((unsigned long long*)(src_h + o_key))[co] = hs[i].cell_key[e];
+            ((int*)(src_h + o_cell))[co] = hs[i].cell[e];
+            ((int*)(src_h + o_cinst))[co] = i;
+        }
     }
-    return enqueue_solve_tables(w, d, Fdev, t, num_sms, st, ev, launches);
-}
-
-size_t src_table_bytes(size_t nsrc, size_t ncell) {
-    return (nsrc * 4 + 15) / 16 * 16 + nsrc * 8 + (ncell * 4 + 15) / 16 * 16 + ncell * 8 + 64;
-}
-
-SrcTables carve_src_tables(void* base_, size_t nsrc, size_t ncell) {
-    char* base = (char*)base_;
-    SrcTables t;
-    t.node = (int*)base;
-    t.q = (double*)(base + ((nsrc * 4 + 15) / 16 * 16));
-    t.cell = (int*)((char*)t.q + nsrc * 8);
-    t.cell_key = (unsigned long long*)((char*)t.cell + ((ncell * 4 + 15) / 16 * 16));
-    t.nsrc = (int)nsrc;
-    t.ncell = (int)ncell;
-    return t;
-}
-
-int enqueue_solve_tables(Workspace* w, const eik_plan_desc* d, const double* Fdev, const SrcTables& t,
-                         int num_sms, cudaStream_t st, cudaEvent_t* ev, int* launches) {
-    int nl = 0;
-    const Layout& L = w->L;
-    const bool fp32 = d->precision == EIK_FP32_REFINE;
-    const size_t nsrc = (size_t)t.nsrc, ncell = (size_t)t.ncell;
-    int* d_node = t.node;
-    double* d_q = t.q;
-    int* d_cell = t.cell;
-    unsigned long long* d_ckey = t.cell_key;
-    Ctl* ctl32 = w->ctl;
-    Ctl* ctl64 = w->ctl + 1;
-    cudaMemsetAsync(w->ctl, 0, 2 * sizeof(Ctl) + sizeof(ResidualOut), st);
-    cudaMemsetAsync(w->cval, 0xff, (size_t)L.J * 8, st);
-    cudaMemsetAsync(w->qflag, 0, (size_t)L.J * 4, st);
-    cudaMemsetAsync(w->visits, 0, (size_t)L.J * 4, st);
-    cudaMemsetAsync(w->has_src, 0, (size_t)L.J, st);
-    Ctl* first_ctl = fp32 ? ctl32 : ctl64;
-    if (launch_ctl_init(first_ctl, (int)ncell, st) != cudaSuccess) return EIK_ECUDA;
-    ++nl;
-    if (fp32) {
-        if (launch_ctl_init(ctl64, 0, st) != cudaSuccess) return EIK_ECUDA;
-        ++nl;
-    }
-
-    InitParams ip{};
-    ip.F = Fdev;
-    ip.nx = L.nx;
-    ip.ny = L.ny;
-    ip.h = d->h;
-    ip.f64 = w->f64;
-    ip.f32 = w->f32;
-    ip.fdf = w->fdf;
-    ip.fpitch = L.fpitch;
-    ip.U64 = w->U64;
-    ip.U32 = w->U32;
-    ip.Udf = w->Udf;
-    ip.upitch = L.upitch;
-    ip.nxp = L.nxp;
-    ip.nyp = L.nyp;
-    ip.ctl = first_ctl;
-    if (launch_init_grid(ip, st) != cudaSuccess) return EIK_ECUDA;
-    ++nl;
-    SourceInit si{d_node, d_q, (int)nsrc, d_cell, d_ckey, (int)ncell, L.nx, L.k, L.cxn};
-    if (launch_init_sources(ip, si, w->cval, w->qflag, w->has_src, w->lists + 3 * L.J, st) !=
-        cudaSuccess)
+    blk_pre_h[n] = boff;
+    blk_full_h[n] = bfull;
+    cell_pre_h[n] = (int)coff;
+    if (!ok) return EIK_ECUDA;
+    if (cudaMemcpyAsync(img_dev, img, image_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return EIK_ECUDA;
-    if (nsrc) ++nl;
-
-    const long long deadline = d->deadline_ns > 0 ? d->deadline_ns : 20000000000ll;
-    auto params = [&](const CUtensorMap& tmU, const CUtensorMap& tmF, void* U, const void* f,
-                      Ctl* ctl) {
-        SolveParams p{};
-        p.tmU = tmU;
-        p.tmF = tmF;
-        p.U = U;
-        p.f = f;
-        p.upitch = L.upitch;
-        p.fpitch = L.fpitch;
-        p.nx = L.nx;
-        p.ny = L.ny;
-        p.cxn = L.cxn;
-        p.cyn = L.cyn;
-        p.J = L.J;
-        p.cval = w->cval;
-        p.qflag = w->qflag;
-        p.visits = w->visits;
-        p.has_src = w->has_src;
-        p.lists = w->lists;
-        p.ctl = ctl;
-        p.delta = d->bucket_width;
-        p.deadline_ns = deadline;
-        p.profile = profiling();
-        return p;
-    };
-    LaunchShape shape;
-    if (fp32) {
-        // FP32 cell solves
-        if (solver_shape_f32(L.k, num_sms, &shape)) return EIK_ECUDA;
-        const SolveParams p32 = params(w->tmU32, w->tmF32, w->U32, w->f32, ctl32);
-        if (ev) cudaEventRecord(ev[0], st);
-        if (launch_solver_f32(L.k, p32, shape, st) != cudaSuccess) return EIK_ECUDA;
-        if (ev) cudaEventRecord(ev[1], st);
-        ++nl;
-        // refinement pass (double-float) seeded from the FP32 result
-        cudaMemsetAsync(w->cval, 0xff, (size_t)L.J * 8, st);
-        SeedParams sp{};
-        sp.U32 = w->U32;
-        sp.Udf = w->Udf;
-        sp.fdf = w->fdf;
-        sp.upitch = L.upitch;
-        sp.fpitch = L.fpitch;
-        sp.nx = L.nx;
-        sp.ny = L.ny;
-        sp.k = L.k;
-        sp.cxn = L.cxn;
-        sp.cyn = L.cyn;
-        sp.beta = 1.0f / 1024.0f;
-        sp.cval = w->cval;
-        sp.qflag = w->qflag;
-        sp.visits = w->visits;
-        sp.far0 = w->lists + 3 * L.J;
-        sp.ctl = ctl64;
-        // the refinement pass needs the bucket-width default too
-        cudaMemcpyAsync(&ctl64->fmin_f, &ctl32->fmin_f, 8, cudaMemcpyDeviceToDevice, st);
-        if (launch_seed_refine(sp, st) != cudaSuccess) return EIK_ECUDA;
-        nl += 2;
-        if (solver_shape_df(L.k, num_sms, &shape)) return EIK_ECUDA;
-        const SolveParams pd = params(w->tmUdf, w->tmFdf, w->Udf, w->fdf, ctl64);
-        if (ev) cudaEventRecord(ev[2], st);
-        if (launch_solver_df(L.k, pd, shape, st) != cudaSuccess) return EIK_ECUDA;
-        if (ev) cudaEventRecord(ev[3], st);
-        ++nl;
-        if (launch_residual(w->Udf, L.upitch, w->fdf, L.fpitch, Fdev, d->h, L.nx, L.ny, w->res, st) !=
-            cudaSuccess)
+    for (int i = 0; i < n; ++i)
+        if (stageF[i] && cudaMemcpyAsync(hj->arr[i].Fstage, in[i].F, (size_t)descs[i].nx * descs[i].ny * 8,
+                                         cudaMemcpyHostToDevice, st) != cudaSuccess)
             return EIK_ECUDA;
-        ++nl;
-    } else {
-        if (solver_shape_f64(L.k, num_sms, &shape)) return EIK_ECUDA;
-        const SolveParams p64 = params(w->tmU64, w->tmF64, w->U64, w->f64, ctl64);
-        if (ev) cudaEventRecord(ev[2], st);
-        if (launch_solver_f64(L.k, p64, shape, st) != cudaSuccess) return EIK_ECUDA;
-        if (ev) cudaEventRecord(ev[3], st);
-        ++nl;
+
+    JobDev& j = hj->j;
+    j.n = n;
+    j.k = k;
+    j.fp32 = fp32;
+    j.desc_main = (InstDesc*)img_dev;
+    j.desc_f32 = (InstDesc*)(img_dev + t_desc);
+    j.aux = (AuxInst*)(img_dev + 2 * t_desc);
+    j.blk_pre = (int*)(img_dev + 2 * t_desc + t_aux);
+    j.cell_pre = (int*)(img_dev + 2 * t_desc + t_aux + t_pre);
+    j.blk_full = (int*)(img_dev + 2 * t_desc + t_aux + 2 * t_pre);
+    j.nblocks = boff;
+    j.nblocks_full = bfull;
+    j.ncells = (int)coff;
+    j.ictl = ictl_dev;
+    j.gctl = gctl_dev;
+    j.res = res_dev;
+    char* src_dev = img_dev + 2 * t_desc + t_aux + 3 * t_pre;
+    j.src.q = (const double*)(src_dev + o_q);
+    j.src.node = (const int*)(src_dev + o_node);
+    j.src.node_inst = (const int*)(src_dev + o_ninst);
+    j.src.n = (int)nsrc;
+    j.src.cell_key = (const unsigned long long*)(src_dev + o_key);
+    j.src.cell = (const int*)(src_dev + o_cell);
+    j.src.cell_inst = (const int*)(src_dev + o_cinst);
+    j.src.ncell = (int)ncs;
+    j.nsrc_total = (int)nsrc;
+    j.ncell_total = (int)ncs;
+    j.deadline_ns = deadline_ns;
+    j.zero_base = zero_dev;
+    j.zero_bytes = zero_bytes;
+    j.cval_all = cval_all;
+    j.ncval = Jtot;
+    j.qflag_all = qflag_all;
+    j.visits_all = visits_all;
+    // pinned readback buffer for the control blocks
+    if (hj->zero_cap < z_ctl) {
+        if (hj->zero_host) cudaFreeHost(hj->zero_host);
+        hj->zero_host = nullptr;
+        hj->zero_cap = 0;
+        if (cudaMallocHost((void**)&hj->zero_host, z_ctl) != cudaSuccess) {
+            cudaGetLastError();
+            return EIK_ENOMEM;
+        }
+        hj->zero_cap = z_ctl;
     }
-    if (launches) *launches = nl;
     return EIK_OK;
 }
 
-static double dval(unsigned long long k) {
-    long long b = bits_from_key(k);
-    double v;
-    std::memcpy(&v, &b, 8);
-    return v;
+int finish_job(HostJob* hj, const eik_plan_desc* descs, cudaStream_t st, double ms, eik_stats* st_out) {
+    const JobDev& j = hj->j;
+    const int n = j.n;
+    for (int i = 0; i < n; ++i)
+        if (hj->out_host[i])
+            cudaMemcpyAsync(hj->out_user[i], hj->arr[i].Ostage, (size_t)hj->L[i].nx * hj->L[i].ny * 8,
+                            cudaMemcpyDeviceToHost, st);
+    const size_t rb = (size_t)(2 * n + 2) * sizeof(Ctl) + (size_t)n * sizeof(ResidualOut);
+    cudaMemcpyAsync(hj->zero_host, j.zero_base, rb, cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return EIK_ECUDA;
+    }
+    const Ctl* ic = (const Ctl*)hj->zero_host;
+    const Ctl* g = ic + 2 * n;
+    const ResidualOut* r = (const ResidualOut*)(g + 2);
+    int first_err = EIK_OK;
+    for (int i = 0; i < n; ++i) {
+        eik_stats s;
+        job_stats(hj->L[i], &descs[i], j.fp32, &ic[i], &ic[n + i], &g[0], &g[1], &r[i], hj->shift[i], ms, &s);
+        if (st_out) st_out[i] = s;
+        if (s.status && !first_err) first_err = s.status;
+    }
+    return first_err;
 }
 
-// Fill *st from the control blocks copied back to the host.
-void finish_stats(const Layout& L, const eik_plan_desc* d, const Ctl* c32, const Ctl* c64,
-                  const ResidualOut* r, double q_min, bool fp32, double ms, eik_stats* st) {
-    eik_stats s;
-    std::memset(&s, 0, sizeof(s));
-    int status = c64->status;
-    if (fp32 && c32->status) status = c32->status;
-    unsigned long long visits = c64->visits, sweeps = c64->sweeps, lane = c64->lane_updates;
-    long long rounds = (long long)c64->rounds, adv = (long long)c64->advances;
-    if (fp32) {
-        visits += c32->visits;
-        sweeps += c32->sweeps;
-        lane += c32->lane_updates;
-        rounds += (long long)c32->rounds;
-        adv += (long long)c32->advances;
-    }
-    const double npts = (double)L.nx * L.ny;
-    s.ms = ms;
-    s.mpts_per_s = ms > 0 ? npts / ms / 1000.0 : 0.0;
-    s.updates_per_pt = (double)lane / npts;
-    s.avhr = (double)visits / L.J;
-    s.avs = (double)sweeps / L.J;
-    s.cell_visits = (long long)visits;
-    s.rounds = rounds;
-    s.buckets = adv;
-    s.cell_k = L.k;
-    const double fmin = dval(c64->fmin_f);
-    s.bucket_width = d->bucket_width > 0 ? d->bucket_width : 4.0 * L.k * fmin;
-    if (fp32) {
-        // values on the device are U - q_min >= 0
-        const double rr = dval(r->r_max), umax = dval(r->u_max);
-        s.max_residual = rr;
-        // Certificate (comparison principle for the monotone scheme): for
-        // lam > 1, lam * (U - q_min) is a strict supersolution with margin
-        // (lam - 1) f_min / sqrt 2, and likewise a strict subsolution for
-        // lam < 1; so |V - U| <= sqrt 2 * r / f_min * max(U - q_min).
-        double bound = 0.0;
-        if (r->n_bad) bound = std::numeric_limits<double>::infinity();
-        else if (rr > 0 && umax > 0) bound = std::sqrt(2.0) * rr / fmin * umax;
-        const double scale = std::max(std::fabs(umax + q_min), std::fabs(q_min));
-        s.err_bound = scale > 0 ? bound / scale : bound;
-        const double tol = d->tol > 0 ? d->tol : 1e-5;
-        if (status == EIK_OK && !(s.err_bound <= tol)) status = EIK_ENOTCONVERGED;
-    }
-    s.status = status;
-    if (st) *st = s;
+void free_job(HostJob* hj) {
+    if (hj->arena.p) cudaFree(hj->arena.p);
+    hj->arena.p = nullptr;
+    hj->arena.cap = 0;
+    if (hj->zero_host) cudaFreeHost(hj->zero_host);
+    hj->zero_host = nullptr;
+    hj->zero_cap = 0;
 }
 
 }  // namespace eik
 
-// ================================================================= C ABI
+// ================================================================= plans
 extern "C" size_t eik_plan_workspace_bytes(const eik_plan_desc* d) {
     if (!desc_valid(d)) return 0;
     const Layout L = make_layout(d->nx, d->ny, default_k(d));
-    return layout_bytes(L, d->precision == EIK_FP32_REFINE);
+    const bool fp32 = d->precision == EIK_FP32_REFINE;
+    return inst_bytes(L, fp32, true, true) + (size_t)L.J * 16 + 64 * 1024;
 }
 
 extern "C" int eik_plan_create(eik_plan* out, const eik_plan_desc* d, void* cuda_stream) {
@@ -532,20 +344,18 @@ extern "C" int eik_plan_create(eik_plan* out, const eik_plan_desc* d, void* cuda
         p->stream = (cudaStream_t)cuda_stream;
     } else {
         if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
             delete p;
             return EIK_ECUDA;
         }
         p->own_stream = true;
     }
-    const Layout L = make_layout(d->nx, d->ny, p->d.cell_k);
-    int rc = workspace_alloc(&p->ws, L, d->precision == EIK_FP32_REFINE, p->stream);
-    if (!rc && (cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess))
-        rc = EIK_ECUDA;
+    int rc = EIK_OK;
+    if (cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess) rc = EIK_ECUDA;
     for (int e = 0; e < 4 && !rc; ++e)
         if (cudaEventCreate(&p->pev[e]) != cudaSuccess) rc = EIK_ECUDA;
-    if (!rc && cudaMallocHost((void**)&p->host_ctl, 2 * sizeof(Ctl) + sizeof(ResidualOut)) != cudaSuccess)
-        rc = EIK_ENOMEM;
-    if (!rc && cudaStreamSynchronize(p->stream) != cudaSuccess) rc = EIK_ECUDA;
+    // reserve the workspace now, so that solves do not allocate
+    if (!rc) rc = grow(&p->job.arena, eik_plan_workspace_bytes(&p->d));
     if (rc) {
         cudaGetLastError();
         eik_plan_destroy(p);
@@ -558,13 +368,11 @@ extern "C" int eik_plan_create(eik_plan* out, const eik_plan_desc* d, void* cuda
 extern "C" void eik_plan_destroy(eik_plan p) {
     if (!p) return;
     if (p->stream) cudaStreamSynchronize(p->stream);
-    workspace_free(&p->ws);
-    if (p->src.buf.p) cudaFree(p->src.buf.p);
+    free_job(&p->job);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
     for (int e = 0; e < 4; ++e)
         if (p->pev[e]) cudaEventDestroy(p->pev[e]);
-    if (p->host_ctl) cudaFreeHost(p->host_ctl);
     if (p->own_stream) cudaStreamDestroy(p->stream);
     delete p;
 }
@@ -572,58 +380,126 @@ extern "C" void eik_plan_destroy(eik_plan p) {
 extern "C" int eik_solve(eik_plan p, const eik_instance* in, eik_stats* st) {
     if (!p || !in || !in->F || !in->U || in->nsrc < 0) return EIK_EINVAL;
     cudaSetDevice(p->device);
-    Workspace* w = &p->ws;
-    const Layout& L = w->L;
-    HostSources hs;
-    int rc = prepare_sources(L, in, &hs);
-    if (rc) return rc;
     cudaStream_t s = p->stream;
-    const double* Fdev = in->F;
-    if (!is_device_ptr(in->F)) {
-        if (cudaMemcpyAsync(w->Fstage, in->F, (size_t)L.nx * L.ny * 8, cudaMemcpyHostToDevice, s) !=
-            cudaSuccess)
-            return EIK_ECUDA;
-        Fdev = w->Fstage;
+    const bool fp32 = p->d.precision == EIK_FP32_REFINE;
+    int rc = build_job(&p->job, 1, &p->d, in, p->d.cell_k, fp32, p->d.deadline_ns, s);
+    if (rc) {
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        return rc;
     }
     cudaEventRecord(p->ev0, s);
     int nl = 0;
-    rc = enqueue_solve(w, &p->d, Fdev, hs, &p->src, p->num_sms, s, p->pev, &nl);
+    rc = enqueue_job(p->job.j, p->num_sms, s, p->pev, &nl);
     if (rc) {
         cudaStreamSynchronize(s);
         cudaGetLastError();
         return rc;
     }
     cudaEventRecord(p->ev1, s);
-    // result: strip the ring and padding and undo the q shift
-    const double shift = hs.node.empty() ? 0.0 : hs.q_min;
-    if (is_device_ptr(in->U)) {
-        if (launch_output(w->U64, w->Udf, L.upitch, L.nx, L.ny, shift, in->U, s) != cudaSuccess)
-            return EIK_ECUDA;
-    } else {
-        if (launch_output(w->U64, w->Udf, L.upitch, L.nx, L.ny, shift, w->Fstage, s) != cudaSuccess)
-            return EIK_ECUDA;
-        cudaMemcpyAsync(in->U, w->Fstage, (size_t)L.nx * L.ny * 8, cudaMemcpyDeviceToHost, s);
-    }
-    ++nl;
-    cudaMemcpyAsync(p->host_ctl, w->ctl, 2 * sizeof(Ctl) + sizeof(ResidualOut), cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) {
-        cudaGetLastError();
-        return EIK_ECUDA;
-    }
+    eik_stats local;
+    finish_job(&p->job, &p->d, s, 0.0, &local);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, p->ev0, p->ev1);
-    const Ctl* c = (const Ctl*)p->host_ctl;
-    if (profiling()) {
-        if (p->d.precision == EIK_FP32_REFINE) print_profile("fp32 pass", &c[0]);
-        print_profile(p->d.precision == EIK_FP32_REFINE ? "refinement pass" : "fp64 pass", &c[1]);
-    }
-    eik_stats local;
-    finish_stats(L, &p->d, &c[0], &c[1], (const ResidualOut*)(c + 2), hs.node.empty() ? 0.0 : hs.q_min,
-                 p->d.precision == EIK_FP32_REFINE, ms, &local);
-    if (p->d.precision == EIK_FP32_REFINE) cudaEventElapsedTime(&ms, p->pev[0], p->pev[1]), local.pass_ms[0] = ms;
+    local.ms = ms;
+    local.mpts_per_s = ms > 0 ? (double)p->d.nx * p->d.ny / ms / 1000.0 : 0.0;
+    if (fp32) cudaEventElapsedTime(&ms, p->pev[0], p->pev[1]), local.pass_ms[0] = ms;
     cudaEventElapsedTime(&ms, p->pev[2], p->pev[3]);
     local.pass_ms[1] = ms;
     local.launches = nl;
     if (st) *st = local;
     return local.status;
+}
+
+// ================================================================= batches
+namespace {
+struct BatchCtx {
+    std::mutex mu;
+    HostJob job;
+    cudaEvent_t ev[6] = {};
+    int num_sms = 0;
+};
+std::mutex g_batch_mu;
+std::map<int, BatchCtx*> g_batch;
+
+BatchCtx* batch_ctx(int dev) {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    auto it = g_batch.find(dev);
+    if (it != g_batch.end()) return it->second;
+    BatchCtx* c = new (std::nothrow) BatchCtx();
+    if (!c) return nullptr;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    for (auto& e : c->ev) cudaEventCreate(&e);
+    g_batch[dev] = c;
+    return c;
+}
+}  // namespace
+
+extern "C" int eik_solve_batch(const eik_plan_desc* d, const eik_instance* in, int32_t n_inst,
+                               eik_stats* st, void* cuda_stream) {
+    if (n_inst < 0 || (n_inst > 0 && (!d || !in))) return EIK_EINVAL;
+    if (n_inst == 0) return EIK_OK;
+    for (int i = 0; i < n_inst; ++i)
+        if (!desc_valid(&d[i])) return EIK_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return EIK_ECUDA;
+    }
+    BatchCtx* ctx = batch_ctx(dev);
+    if (!ctx) return EIK_ENOMEM;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // group the instances by (k, precision); each group runs as jobs of at
+    // most MAX_BATCH instances, one persistent launch per pass
+    std::map<std::pair<int, int>, std::vector<int>> groups;
+    for (int i = 0; i < n_inst; ++i) groups[{default_k(&d[i]), d[i].precision}].push_back(i);
+    int first_err = EIK_OK;
+    std::vector<eik_plan_desc> gd;
+    std::vector<eik_instance> gi;
+    std::vector<eik_stats> gs;
+    for (auto& kv : groups) {
+        const int k = kv.first.first;
+        const bool fp32 = kv.first.second == EIK_FP32_REFINE;
+        const std::vector<int>& idx = kv.second;
+        for (size_t b0 = 0; b0 < idx.size(); b0 += MAX_BATCH) {
+            const int m = (int)std::min<size_t>(MAX_BATCH, idx.size() - b0);
+            gd.resize(m);
+            gi.resize(m);
+            gs.resize(m);
+            for (int e = 0; e < m; ++e) {
+                gd[e] = d[idx[b0 + e]];
+                gd[e].cell_k = k;
+                gi[e] = in[idx[b0 + e]];
+            }
+            int rc = build_job(&ctx->job, m, gd.data(), gi.data(), k, fp32, d[0].deadline_ns, s);
+            if (!rc) {
+                cudaEventRecord(ctx->ev[0], s);
+                int nl = 0;
+                rc = enqueue_job(ctx->job.j, ctx->num_sms, s, ctx->ev + 2, &nl);
+                cudaEventRecord(ctx->ev[1], s);
+                if (!rc) {
+                    rc = finish_job(&ctx->job, gd.data(), s, 0.0, gs.data());
+                    float ms = 0.f, p0 = 0.f, p1 = 0.f;
+                    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+                    if (fp32) cudaEventElapsedTime(&p0, ctx->ev[2], ctx->ev[3]);
+                    cudaEventElapsedTime(&p1, ctx->ev[4], ctx->ev[5]);
+                    for (int e = 0; e < m; ++e) {
+                        gs[e].ms = ms;  // the whole launch (all instances of the group)
+                        gs[e].mpts_per_s = ms > 0 ? (double)gd[e].nx * gd[e].ny / ms / 1000.0 : 0.0;
+                        gs[e].pass_ms[0] = p0;
+                        gs[e].pass_ms[1] = p1;
+                        gs[e].launches = nl;
+                        if (st) st[idx[b0 + e]] = gs[e];
+                    }
+                }
+            }
+            if (rc) {
+                cudaStreamSynchronize(s);
+                cudaGetLastError();
+                if (!first_err) first_err = rc;
+            }
+        }
+    }
+    return first_err;
 }

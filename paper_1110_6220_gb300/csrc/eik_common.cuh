@@ -68,27 +68,37 @@ struct Ctl {
 //   U : (nyp + 2) rows of `upitch` elements; node (i, j) at
 //       (j + 1) * upitch + (i + 1).  Row 0, row nyp + 1, column 0 and every
 //       column >= nxp + 1 hold +inf forever (the ring of outside neighbours).
-//   f : nyp rows of `fpitch` elements, node (i, j) at j * fpitch + i; holds
-//       h / F, +inf on obstacles and on padding nodes (i >= nx or j >= ny),
-//       and -1 on source nodes (fixed values).
+//   f : the same layout; holds h / F, +inf on obstacles, on padding nodes
+//       (i >= nx or j >= ny) and on the ring, and -1 on source nodes (fixed
+//       values).  Its TMA box therefore carries a one-node halo of f too.
 //   nxp = cxn * k, nyp = cyn * k: the grid padded to whole cells.
-struct SolveParams {
+//
+// One persistent launch solves n_inst instances (a single solve is a batch of
+// one).  Each instance has a descriptor in device memory; its tensor maps live
+// there too (64-byte aligned; written by the host before the launch).
+struct __align__(64) InstDesc {
     CUtensorMap tmU;              // 2-D map over U, box (BW x k+2)
-    CUtensorMap tmF;              // 2-D map over f in U's representation, box (k x k)
+    CUtensorMap tmF;              // 2-D map over f, same box
     void* U;                      // double*, float* or float2* (double-float pairs)
     const void* f;                // f in U's representation
-    int upitch, fpitch;
-    int nx, ny;
-    int cxn, cyn, J;
     unsigned long long* cval;     // ordered cell-value keys
     int* qflag;                   // 1 while the cell sits in a list
     int* visits;                  // removals so far
-    const unsigned char* has_src; // cell contains a source node
     int* lists;                   // 5 * J ints: near[3], far[2]
-    Ctl* ctl;
-    double delta;                 // bucket width; <= 0: k * min f
+    Ctl* ctl;                     // this instance's lists, counters and status
+    int upitch;
+    int cxn, cyn, J;
+    double delta;                 // bucket width; <= 0: 4 k min f (from ctl->fmin_f)
+};
+
+constexpr int MAX_BATCH = 2048;   // instances per persistent launch
+
+struct SolveParams {
+    const InstDesc* inst;         // n_inst descriptors (device memory)
+    int n_inst;
+    Ctl* gctl;                    // grid barrier, abort flag, launch status, rounds
     long long deadline_ns;        // relative to kernel start
-    int profile;                  // accumulate Ctl::prof
+    int profile;                  // accumulate gctl->prof
 };
 
 // ---------------------------------------------------------------- host launchers
@@ -100,72 +110,62 @@ struct LaunchShape {
 };
 
 // one per arithmetic mode (eik_solver_f64.cu, eik_solver_f32.cu, eik_solver_df.cu)
-int solver_shape_f64(int k, int num_sms, LaunchShape* out);
-int solver_shape_f32(int k, int num_sms, LaunchShape* out);
-int solver_shape_df(int k, int num_sms, LaunchShape* out);
+int solver_shape_f64(int k, int num_sms, int n_inst, LaunchShape* out);
+int solver_shape_f32(int k, int num_sms, int n_inst, LaunchShape* out);
+int solver_shape_df(int k, int num_sms, int n_inst, LaunchShape* out);
 cudaError_t launch_solver_f64(int k, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
 cudaError_t launch_solver_f32(int k, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
 cudaError_t launch_solver_df(int k, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
 
 // aux kernels (eik_aux.cu)
-// Device arrays of one instance (null where the precision mode has none):
+// ---------------------------------------------------------------- aux kernels
+// Per-instance view for the node-wise kernels (eik_aux.cu), which run once
+// over all instances of a job: a block covers 8 rows x 32 columns of one
+// instance's padded grid, found from `blk_pre` (prefix sums of blocks per
+// instance).  Arrays of the other precision mode are null:
 //   FP64 mode:       U64, f64
 //   FP32+refinement: U32, f32 (FP32 pass), Udf, fdf (double-float pairs,
-//                    refinement pass).  All U arrays share one layout, all f
-//                    arrays another (see SolveParams).
-struct InitParams {
-    const double* F;              // nx*ny row-major speeds (device)
-    int nx, ny;
-    double h;
-    double* f64; float* f32; float2* fdf; int fpitch;
-    double* U64; float* U32; float2* Udf; int upitch;
-    int nxp, nyp;
-    Ctl* ctl;
-};
-cudaError_t launch_init_grid(const InitParams& p, cudaStream_t st);
-cudaError_t launch_fill(double* a, size_t n, double v, cudaStream_t st);
-cudaError_t launch_fill32(float* a, size_t n, float v, cudaStream_t st);
-cudaError_t launch_fill_df(float2* a, size_t n, cudaStream_t st);  // (+inf, 0)
-
-struct SourceInit {
-    const int* node;              // unique source nodes (j*nx + i)
-    const double* q;              // their values, shifted by -min q (>= 0)
-    int n;
-    const int* cell;              // cells holding a source
-    const unsigned long long* cell_key;  // key of max q on that cell
-    int ncell;
-    int nx, k, cxn;
-};
-cudaError_t launch_init_sources(const InitParams& ip, const SourceInit& s, unsigned long long* cval,
-                                int* qflag, unsigned char* has_src, int* far0, cudaStream_t st);
-
-cudaError_t launch_ctl_init(Ctl* ctl, int nfar0, cudaStream_t st);
-
-struct SeedParams {
-    const float* U32;
-    float2* Udf;
-    const float2* fdf;
-    int upitch, fpitch;
-    int nx, ny, k, cxn, cyn;
-    float beta;                   // relative bump (values are >= 0 after the q shift)
-    unsigned long long* cval; int* qflag; int* visits; int* far0;
-    Ctl* ctl;
-};
-cudaError_t launch_seed_refine(const SeedParams& p, cudaStream_t st);
-
+//                    refinement pass).  All share the layout of SolveParams.
 struct ResidualOut {              // reduced with atomics on ordered keys
     unsigned long long r_max;     // max |V - T(V)| over non-source nodes
     unsigned long long u_max;     // max finite V
     unsigned long long n_bad;     // finite/infinite mismatches
 };
-// FP64 residual of the double-float result Udf, with f = h/F recomputed in
-// FP64 from the input speeds; sources are the nodes with fdf.x < 0.
-cudaError_t launch_residual(const float2* Udf, int upitch, const float2* fdf, int fpitch,
-                            const double* F, double h, int nx, int ny, ResidualOut* out,
-                            cudaStream_t st);
-// dst[j*nx + i] = U[(j+1)*pitch + i+1] + shift (undoes the q shift); exactly
-// one of U64 / Udf is non-null
-cudaError_t launch_output(const double* U64, const float2* Udf, int upitch, int nx, int ny,
-                          double shift, double* dst, cudaStream_t st);
+
+struct AuxInst {
+    const double* F;              // nx*ny row-major speeds (device)
+    double* out;                  // nx*ny result (device; the caller's or staging)
+    double h;
+    double shift;                 // min q: stored values are U - shift
+    int nx, ny, nxp, nyp, upitch, k, cxn, cyn;
+    double* U64; double* f64;
+    float* U32; float* f32;
+    float2* Udf; float2* fdf;
+    unsigned long long* cval; int* qflag; int* visits; int* far0;
+    Ctl* ctl;                     // the instance's control block of the first pass
+    Ctl* ctl2;                    // ... of the refinement pass (FP32+refinement)
+    ResidualOut* res;
+    int J;
+};
+
+// Sources of all instances: node (j*nx + i) and shifted q, with instance id;
+// source cells with their key (max q) and instance id.
+struct SourceTable {
+    const int* node; const double* q; const int* node_inst; int n;
+    const int* cell; const unsigned long long* cell_key; const int* cell_inst; int ncell;
+};
+
+cudaError_t launch_fill(double* a, size_t n, double v, cudaStream_t st);
+cudaError_t launch_fill32(float* a, size_t n, float v, cudaStream_t st);
+cudaError_t launch_fill_df(float2* a, size_t n, cudaStream_t st);  // (+inf, 0)
+cudaError_t launch_ctl_init(Ctl* ctl, int count, cudaStream_t st);  // count control blocks
+// f, U interiors; validation of F; min h/F per instance
+cudaError_t launch_init_grid(const AuxInst* a, const int* blk_pre, int n, int nblocks, cudaStream_t st);
+cudaError_t launch_init_sources(const AuxInst* a, const SourceTable& s, cudaStream_t st);
+// FP32 result -> double-float start values, cell keys; then queue the cells
+cudaError_t launch_seed_refine(const AuxInst* a, const int* blk_pre, int n, int nblocks,
+                               const int* cell_pre, int ncells, float beta, cudaStream_t st);
+cudaError_t launch_residual(const AuxInst* a, const int* blk_pre, int n, int nblocks, cudaStream_t st);
+cudaError_t launch_output(const AuxInst* a, const int* blk_pre, int n, int nblocks, cudaStream_t st);
 
 }  // namespace eik

@@ -1,0 +1,84 @@
+// eik_job.h -- a job: n instances solved together (same cell size k and
+// precision mode): one launch per kernel for all of them.  Plans (n = 1),
+// batches and the no-allocation solve all run through enqueue_job.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "eik_common.cuh"
+
+namespace eik {
+
+struct Layout {
+    int nx, ny, k;
+    int cxn, cyn, J;
+    int nxp, nyp;
+    int upitch, urows;  // U and f arrays: urows x upitch elements (ring included)
+};
+
+Layout make_layout(int nx, int ny, int k);
+
+// Device arrays of one instance inside a job's arena.
+struct InstArrays {
+    double* U64; double* f64;   // FP64 mode
+    float* U32; float* f32;     // FP32 + refinement: FP32 pass
+    float2* Udf; float2* fdf;   //                    refinement pass
+    unsigned long long* cval;
+    int* qflag;
+    int* visits;
+    int* lists;                 // 5 J
+    double* Fstage;             // device copy of a host F (null if F is on the device)
+    double* Ostage;             // result staging for a host U (null if U is on the device)
+};
+
+// Bytes instance arrays need (256-byte aligned pieces).
+size_t inst_bytes(const Layout& L, bool fp32, bool stage_F, bool stage_U);
+// Assign the arrays of one instance from base (which must have inst_bytes).
+InstArrays carve_inst(const Layout& L, bool fp32, bool stage_F, bool stage_U, char* base);
+
+// Control blocks and tables of a job, all in device memory.
+struct JobDev {
+    int n;                      // instances
+    int k;
+    bool fp32;
+    InstDesc* desc_main;        // n: FP64 pass or refinement pass
+    InstDesc* desc_f32;         // n: FP32 pass (fp32 only)
+    AuxInst* aux;               // n
+    int* blk_pre;               // n + 1: prefix of 8x32 blocks over each padded interior
+    int* blk_full;              // n + 1: prefix of 8x32 blocks over each whole array (ring too)
+    int* cell_pre;              // n + 1: prefix of cells per instance
+    int nblocks, nblocks_full, ncells;
+    Ctl* ictl;                  // 2n: [0, n) first pass, [n, 2n) refinement pass
+    Ctl* gctl;                  // 2: launch-wide control of each pass
+    ResidualOut* res;           // n
+    SourceTable src;            // device pointers
+    int nsrc_total, ncell_total;
+    long long deadline_ns;
+    // everything that enqueue_job zeroes before a solve: [zero_base, + zero_bytes)
+    void* zero_base;
+    size_t zero_bytes;
+    // cval / qflag / visits of all instances, contiguous
+    unsigned long long* cval_all; size_t ncval;
+    int* qflag_all;
+    int* visits_all;
+};
+
+// Host-side pieces used to fill a JobDev's tables.
+bool make_map(CUtensorMap* tm, void* base, bool fp64, int width, int rows, int pitch_elems,
+              int box_w, int box_h);
+void fill_inst_tables(const Layout& L, const InstArrays& a, bool fp32, double h, double bucket_width,
+                      Ctl* ictl_first, Ctl* ictl_main, ResidualOut* res, const double* F,
+                      double* out, double shift, AuxInst* aux, InstDesc* desc_main, InstDesc* desc_f32,
+                      bool* ok);
+
+// Queue the whole solve of a job on st (tables and sources already uploaded).
+// ev: null or 4 events around the FP32 pass [0,1] and the main pass [2,3].
+int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, int* launches);
+
+// Fill *st for instance i from the control blocks copied back to the host.
+void job_stats(const Layout& L, const eik_plan_desc* d, bool fp32, const Ctl* ictl_first,
+               const Ctl* ictl_main, const Ctl* g_first, const Ctl* g_main, const ResidualOut* r,
+               double q_min, double ms, eik_stats* st);
+
+}  // namespace eik

@@ -149,62 +149,113 @@ extern "C" int eik_solve_noalloc(const eik_plan_desc* d, const eik_instance* in,
     if (rc) return rc;
 
     // carve the scratch; grids that do not fit are rejected
-    const size_t un = (size_t)L.upitch * L.urows, fn = (size_t)L.fpitch * L.frows;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t at = off;
         off = align256(off + bytes);
         return (char*)scratch + at;
     };
-    Workspace w;
-    std::memset((void*)&w, 0, sizeof(w));
-    w.L = L;
-    w.U64 = (double*)take(un * 8);
-    w.f64 = (double*)take(fn * 8);
-    w.cval = (unsigned long long*)take((size_t)L.J * 8);
-    w.qflag = (int*)take((size_t)L.J * 4);
-    w.visits = (int*)take((size_t)L.J * 4);
-    w.has_src = (unsigned char*)take((size_t)L.J);
-    w.lists = (int*)take((size_t)5 * L.J * 4);
-    w.ctl = (Ctl*)take(2 * sizeof(Ctl) + sizeof(ResidualOut));
-    w.res = (ResidualOut*)(w.ctl + 2);
-    void* tables = take(src_table_bytes((size_t)ss.n, (size_t)ss.ncell));
+    struct alignas(64) Tables {
+        InstDesc desc;
+        AuxInst aux;
+        int blk_pre[2];
+        int blk_full[2];
+        int cell_pre[2];
+        double q[MAX_SOURCES];
+        unsigned long long key[MAX_SOURCES];
+        int node[MAX_SOURCES], node_inst[MAX_SOURCES], cell[MAX_SOURCES], cell_inst[MAX_SOURCES];
+    };
+    static_assert(sizeof(Tables) < 32 * 1024, "tables live on the stack");
+    Tables tb;
+    std::memset((void*)&tb, 0, sizeof(tb));
+    Tables* tdev = (Tables*)take(sizeof(Tables));
+    const size_t z_ctl = align256(4 * sizeof(Ctl) + sizeof(ResidualOut));
+    const size_t zero_bytes = z_ctl + 2 * align256((size_t)L.J * 4);
+    char* zero = take(zero_bytes);
+    unsigned long long* cval = (unsigned long long*)take((size_t)L.J * 8);
+    char* inst = take(inst_bytes(L, false, false, false));
     if (off > SCRATCH_BYTES) return EIK_EINVAL;  // grid too large for the fixed scratch
 
-    cudaStream_t s = (cudaStream_t)cuda_stream;
-    const int K = L.k;
-    if (!make_map(&w.tmU64, w.U64, true, L.upitch, L.urows, L.upitch, K + 2, K + 2) ||
-        !make_map(&w.tmF64, w.f64, true, L.fpitch, L.frows, L.fpitch, K + 2, K + 2))
-        return EIK_ECUDA;
-    // the scratch holds the previous call's data: rebuild the +inf rings
-    if (launch_fill(w.U64, un, std::numeric_limits<double>::infinity(), s) != cudaSuccess ||
-        launch_fill(w.f64, fn, std::numeric_limits<double>::infinity(), s) != cudaSuccess)
-        return EIK_ECUDA;
-    const SrcTables t = carve_src_tables(tables, (size_t)ss.n, (size_t)ss.ncell);
-    if (ss.n) {
-        cudaMemcpyAsync(t.node, ss.node, (size_t)ss.n * 4, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(t.q, ss.q, (size_t)ss.n * 8, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(t.cell, ss.cell, (size_t)ss.ncell * 4, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(t.cell_key, ss.key, (size_t)ss.ncell * 8, cudaMemcpyHostToDevice, s);
+    Ctl* ictl = (Ctl*)zero;  // [0] unused first pass, [1] the FP64 pass
+    Ctl* gctl = ictl + 2;
+    ResidualOut* res = (ResidualOut*)(gctl + 2);
+    InstArrays a = carve_inst(L, false, false, false, inst);
+    a.cval = cval;
+    a.qflag = (int*)(zero + z_ctl);
+    a.visits = (int*)(zero + z_ctl + align256((size_t)L.J * 4));
+    const double shift = ss.n ? ss.q_min : 0.0;
+    bool ok = true;
+    InstDesc unused;
+    fill_inst_tables(L, a, false, d->h, d->bucket_width, &ictl[0], &ictl[1], res, in->F, in->U, shift,
+                     &tb.aux, &tb.desc, &unused, &ok);
+    if (!ok) return EIK_ECUDA;
+    tb.blk_pre[0] = 0;
+    tb.blk_pre[1] = ((L.nyp + 7) / 8) * ((L.nxp + 31) / 32);
+    tb.blk_full[0] = 0;
+    tb.blk_full[1] = ((L.urows + 7) / 8) * ((L.upitch + 31) / 32);
+    tb.cell_pre[0] = 0;
+    tb.cell_pre[1] = L.J;
+    for (int e = 0; e < ss.n; ++e) {
+        tb.q[e] = ss.q[e];
+        tb.node[e] = ss.node[e];
+        tb.node_inst[e] = 0;
     }
-    int nl = 2;
-    int launched = 0;
-    rc = enqueue_solve_tables(&w, &dd, in->F, t, sms, s, nullptr, &launched);
+    for (int e = 0; e < ss.ncell; ++e) {
+        tb.key[e] = ss.key[e];
+        tb.cell[e] = ss.cell[e];
+        tb.cell_inst[e] = 0;
+    }
+
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // (the scratch holds the previous call's data: the init kernel rewrites
+    // every element of the padded arrays, the +inf rings included)
+    if (cudaMemcpyAsync(tdev, &tb, sizeof(tb), cudaMemcpyHostToDevice, s) != cudaSuccess) return EIK_ECUDA;
+
+    JobDev j;
+    std::memset((void*)&j, 0, sizeof(j));
+    j.n = 1;
+    j.k = L.k;
+    j.fp32 = false;
+    j.desc_main = &tdev->desc;
+    j.aux = &tdev->aux;
+    j.blk_pre = tdev->blk_pre;
+    j.blk_full = tdev->blk_full;
+    j.nblocks_full = tb.blk_full[1];
+    j.cell_pre = tdev->cell_pre;
+    j.nblocks = tb.blk_pre[1];
+    j.ncells = L.J;
+    j.ictl = ictl;
+    j.gctl = gctl;
+    j.res = res;
+    j.src.q = tdev->q;
+    j.src.node = tdev->node;
+    j.src.node_inst = tdev->node_inst;
+    j.src.n = ss.n;
+    j.src.cell_key = tdev->key;
+    j.src.cell = tdev->cell;
+    j.src.cell_inst = tdev->cell_inst;
+    j.src.ncell = ss.ncell;
+    j.nsrc_total = ss.n;
+    j.ncell_total = ss.ncell;
+    j.deadline_ns = d->deadline_ns;
+    j.zero_base = zero;
+    j.zero_bytes = zero_bytes;
+    j.cval_all = cval;
+    j.ncval = (size_t)L.J;
+    j.qflag_all = a.qflag;
+    j.visits_all = a.visits;
+    int nl = 0;
+    rc = enqueue_job(j, sms, s, nullptr, &nl);
     if (rc) {
         cudaStreamSynchronize(s);
         cudaGetLastError();
         return rc;
     }
-    nl += launched;
-    const double shift = ss.n ? ss.q_min : 0.0;
-    if (launch_output(w.U64, nullptr, L.upitch, L.nx, L.ny, shift, in->U, s) != cudaSuccess)
-        return EIK_ECUDA;
-    ++nl;
     struct {
-        Ctl c[2];
+        Ctl c[4];
         ResidualOut r;
     } host;
-    cudaMemcpyAsync(&host, w.ctl, sizeof(host), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&host, zero, sizeof(host), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         return EIK_ECUDA;
@@ -212,7 +263,7 @@ extern "C" int eik_solve_noalloc(const eik_plan_desc* d, const eik_instance* in,
     const double ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     eik_stats local;
-    finish_stats(L, &dd, &host.c[0], &host.c[1], &host.r, shift, false, ms, &local);
+    job_stats(L, &dd, false, &host.c[0], &host.c[1], &host.c[2], &host.c[3], &host.r, shift, ms, &local);
     local.launches = nl;
     if (st) *st = local;
     return local.status;

@@ -68,6 +68,12 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
         "l"((unsigned long long)tm), "r"(x), "r"(y), "r"(smem_addr(bar))
         : "memory");
 }
+// the tensor maps live in global memory (written by the host before launch):
+// order that write before their use by the TMA unit
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* tm) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((unsigned long long)tm)
+                 : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
@@ -372,6 +378,70 @@ __device__ __forceinline__ void lane_push(int* list, int* count, int val, int ca
     else fail(ctl, EIK_ECUDA, 0x2000000ull + (unsigned)pos);
 }
 
+// ---------------------------------------------------------------- block scan
+// Exclusive prefix sums of in[0..n) into out[0..n], out[n] = total; every
+// thread of the block must call it (uses `scratch`, >= 33 ints).
+__device__ __forceinline__ int block_exclusive_scan(const int* in, int* out, int n, int* scratch) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, wid = tid >> 5, nw = (nt + 31) >> 5;
+    const int per = (n + nt - 1) / nt;
+    const int lo = min(tid * per, n), hi = min(lo + per, n);
+    int s = 0;
+    for (int e = lo; e < hi; ++e) s += in[e];
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) scratch[wid] = incl;
+    __syncthreads();
+    if (tid == 0) {
+        int run = 0;
+        for (int w = 0; w < nw; ++w) {
+            const int v = scratch[w];
+            scratch[w] = run;
+            run += v;
+        }
+        scratch[32] = run;
+    }
+    __syncthreads();
+    int run = scratch[wid] + incl - s;
+    for (int e = lo; e < hi; ++e) {
+        out[e] = run;
+        run += in[e];
+    }
+    const int total = scratch[32];
+    if (tid == 0) out[n] = total;
+    __syncthreads();
+    return total;
+}
+
+// index of the instance whose [pre[i], pre[i+1]) range holds e (pre ascending)
+__device__ __forceinline__ int find_inst(const int* pre, int n, int e) {
+    int lo = 0, hi = n;  // pre[lo] <= e < pre[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= e) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// per-instance state kept (identically) in every block's shared memory
+struct InstState {
+    unsigned long long* theta;  // current bucket's upper key
+    int* pre;                   // prefix sums (n + 1)
+    int* nn;                    // near-list length this round
+    int* nf;                    // far-list length this round
+    unsigned char* ns;          // near-list slot (0..2)
+    unsigned char* fs;          // far-list slot (0..1)
+    int* scan_scratch;          // 33 ints
+};
+__host__ __device__ constexpr int inst_state_bytes(int n) {
+    return n * 8 + (n + 1) * 4 + n * 4 + n * 4 + n + n + 33 * 4 + 64;
+}
+
 // ---------------------------------------------------------------- the kernel
 // PROF_MARK(i): add the cycles since the last mark to phase i (profiling only)
 #define PROF_MARK(i)                                    \
@@ -395,6 +465,25 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
     // TMA destinations must be 128-byte aligned: the host asks for 128 spare bytes
     unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
 
+    const int NI = p.n_inst;
+    InstState S;
+    {
+        unsigned char* sp = smem + C::WPB * C::WARP_BYTES;
+        S.theta = reinterpret_cast<unsigned long long*>(sp);
+        sp += NI * 8;
+        S.pre = reinterpret_cast<int*>(sp);
+        sp += (NI + 1) * 4;
+        S.nn = reinterpret_cast<int*>(sp);
+        sp += NI * 4;
+        S.nf = reinterpret_cast<int*>(sp);
+        sp += NI * 4;
+        S.scan_scratch = reinterpret_cast<int*>(sp);
+        sp += 33 * 4;
+        S.ns = sp;
+        sp += NI;
+        S.fs = sp;
+    }
+
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     unsigned char* wbase = smem + warp * C::WARP_BYTES;
@@ -411,26 +500,23 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
     const FT* tF = reinterpret_cast<const FT*>(gbase + C::F_OFF);
     const double* tG = reinterpret_cast<const double*>(gbase + C::X_OFF);
     const unsigned gmask = C::LPC == 32 ? FULL : (((1u << C::LPC) - 1u) << (g * C::LPC));
-    T* Ug = reinterpret_cast<T*>(p.U);
 
-    Ctl* ctl = p.ctl;
+    Ctl* gctl = p.gctl;
+    const InstDesc* inst = p.inst;
     const unsigned long long deadline = gtimer() + (unsigned long long)p.deadline_ns;
 
     if (lane == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
     }
-    __syncwarp();
+    for (int i = threadIdx.x; i < NI; i += blockDim.x) {
+        S.theta[i] = 0;
+        S.ns[i] = 0;
+        S.fs[i] = 0;
+    }
+    __syncthreads();
     uint32_t phase = 0;
 
-    // bucket width: given, else 4 k times the smallest h/F (the time to
-    // cross about four cells at the highest speed)
-    const double fmin_glob = val_of(ld_cg(&ctl->fmin_f));
-    double delta = p.delta;
-    if (!(delta > 0.0)) delta = 4.0 * (double)K * fmin_glob;
-    if (!(delta > 0.0) || !(delta < inf_of<double>())) delta = inf_of<double>();
-
-    const int J = p.J;
     const int nb = gridDim.x;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int gthreads = gridDim.x * blockDim.x;
@@ -439,84 +525,125 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
     const int slot = g * C::WPB + warp;
     constexpr int SLOTS = C::WPB * C::CPW;
 
-    unsigned long long st_visits = 0, st_sweeps = 0, st_lane = 0, st_rounds = 0, st_adv = 0;
+    unsigned long long st_lane = 0, st_rounds = 0;
     unsigned long long pacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long long pt = clock64();
-    int ns = 0, fs = 0;
-    unsigned long long theta = 0;
 
     for (;;) {
-        int n_near = min(ld_cg(&ctl->cnt[ns]), J);  // a list never exceeds J entries
-        if (n_near == 0) {
-            const int nfar = min(ld_cg(&ctl->fcnt[fs]), J);
-            if (nfar == 0) break;  // every list empty: converged
-            // --- release the next bucket: min key over the far list ...
-            const int* far = p.lists + (3 + fs) * J;
-            unsigned long long mn = KEY_UNSET;
-            for (int e = gtid; e < nfar; e += gthreads) {
-                const unsigned long long kk = ld_cg(&p.cval[ld_cg(&far[e])]);
-                mn = kk < mn ? kk : mn;
+        // ---- every instance's list lengths (the same in every block)
+        int my_split = 0, my_work = 0;
+        for (int i = threadIdx.x; i < NI; i += blockDim.x) {
+            const Ctl* c = inst[i].ctl;
+            const int J = inst[i].J;
+            const int a = min(ld_cg(&c->cnt[S.ns[i]]), J), b = min(ld_cg(&c->fcnt[S.fs[i]]), J);
+            S.nn[i] = a;
+            S.nf[i] = b;
+            my_split |= (a == 0 && b > 0);
+            my_work |= (a > 0 || b > 0);
+        }
+        const int any_split = __syncthreads_or(my_split);
+        const int any_work = __syncthreads_or(my_work);
+        if (!any_work) break;  // every list of every instance empty: converged
+
+        if (any_split) {
+            // ---- release the next bucket of every instance whose near list
+            // is empty: min key over its far list ...
+            // far-list lengths of the splitting instances (0 for the others),
+            // prefix-summed into pre: the concatenated index space of this phase
+            for (int i = threadIdx.x; i < NI; i += blockDim.x)
+                if (S.nn[i] != 0) S.nf[i] = 0;
+            __syncthreads();
+            const int total = block_exclusive_scan(S.nf, S.pre, NI, S.scan_scratch);
+            for (int e = gtid; e < total; e += gthreads) {
+                const int i = find_inst(S.pre, NI, e);
+                const InstDesc& d = inst[i];
+                const int* far = d.lists + (3 + S.fs[i]) * d.J;
+                const unsigned long long kk = ld_cg(&d.cval[ld_cg(&far[e - S.pre[i]])]);
+                if (kk != KEY_UNSET) atomicMin(&d.ctl->fmin[S.fs[i]], kk);
             }
-            mn = warp_min_u64(mn);
-            if (lane == 0 && mn != KEY_UNSET) atomicMin(&ctl->fmin[fs], mn);
             PROF_MARK(0);
-            if (!grid_sync(ctl, deadline, &s_flag)) break;
+            if (!grid_sync(gctl, deadline, &s_flag)) break;
             PROF_MARK(1);
-            const unsigned long long fm = ld_cg(&ctl->fmin[fs]);
-            theta = fm == KEY_UNSET ? KEY_UNSET : key_of(val_of(fm) + delta);
-            // ... then move every far cell with key <= theta to the near list
-            int* far2 = p.lists + (3 + (fs ^ 1)) * J;
-            int* nearL = p.lists + ns * J;
-            for (int e0 = gtid - lane; e0 < nfar; e0 += gthreads) {
-                const int e = e0 + lane;
-                int c = -1;
-                bool to_near = false;
-                if (e < nfar) {
-                    c = ld_cg(&far[e]);
-                    to_near = ld_cg(&p.cval[c]) <= theta;
+            for (int i = threadIdx.x; i < NI; i += blockDim.x) {
+                if (S.nn[i] == 0 && S.pre[i + 1] > S.pre[i]) {
+                    const InstDesc& d = inst[i];
+                    double delta = d.delta;
+                    if (!(delta > 0.0)) delta = 4.0 * (double)K * val_of(ld_cg(&d.ctl->fmin_f));
+                    if (!(delta > 0.0) || !(delta < inf_of<double>())) delta = inf_of<double>();
+                    const unsigned long long fm = ld_cg(&d.ctl->fmin[S.fs[i]]);
+                    S.theta[i] = fm == KEY_UNSET ? KEY_UNSET : key_of(val_of(fm) + delta);
                 }
-                warp_push(nearL, &ctl->cnt[ns], c >= 0 && to_near, c, J, ctl);
-                warp_push(far2, &ctl->fcnt[fs ^ 1], c >= 0 && !to_near, c, J, ctl);
+            }
+            __syncthreads();
+            // ... then move every far cell with key <= theta to the near list
+            for (int e0 = gtid - lane; e0 < total; e0 += gthreads) {
+                const int e = e0 + lane;
+                if (e < total) {
+                    const int i = find_inst(S.pre, NI, e);
+                    const InstDesc& d = inst[i];
+                    const int c = ld_cg(&d.lists[(3 + S.fs[i]) * d.J + (e - S.pre[i])]);
+                    if (ld_cg(&d.cval[c]) <= S.theta[i])
+                        lane_push(d.lists + S.ns[i] * d.J, &d.ctl->cnt[S.ns[i]], c, d.J, gctl);
+                    else
+                        lane_push(d.lists + (3 + (S.fs[i] ^ 1)) * d.J, &d.ctl->fcnt[S.fs[i] ^ 1], c, d.J, gctl);
+                }
             }
             PROF_MARK(0);
-            if (!grid_sync(ctl, deadline, &s_flag)) break;
+            if (!grid_sync(gctl, deadline, &s_flag)) break;
             PROF_MARK(1);
-            if (gtid == 0) {
-                ctl->fcnt[fs] = 0;
-                ctl->fmin[fs] = KEY_UNSET;
+            for (int i = threadIdx.x; i < NI; i += blockDim.x) {
+                if (S.nn[i] == 0 && S.pre[i + 1] > S.pre[i]) {
+                    const InstDesc& d = inst[i];
+                    if (blockIdx.x == 0) {
+                        d.ctl->fcnt[S.fs[i]] = 0;
+                        d.ctl->fmin[S.fs[i]] = KEY_UNSET;
+                        d.ctl->advances += 1;
+                    }
+                    S.fs[i] ^= 1;
+                    S.nn[i] = min(ld_cg(&d.ctl->cnt[S.ns[i]]), d.J);
+                }
             }
-            fs ^= 1;
-            ++st_adv;
-            n_near = min(ld_cg(&ctl->cnt[ns]), J);
+            __syncthreads();
         }
 
-        // --- one round: process every cell of the near list
-        const int nx_slot = ns == 2 ? 0 : ns + 1;
+        // ---- one round: process the near lists of all instances
+        const int total = block_exclusive_scan(S.nn, S.pre, NI, S.scan_scratch);
         // deadline, grid-uniformly: raised here, seen by all at this round's barrier
-        if (gtid == 0 && gtimer() > deadline) fail(ctl, EIK_ETIMEDOUT, 0x5000000ull);
-        if (gtid == 0) ctl->cnt[nx_slot == 2 ? 0 : nx_slot + 1] = 0;  // consumed last round
-        const int* nearL = p.lists + ns * J;
-        int* nextL = p.lists + nx_slot * J;
-        int* farL = p.lists + (3 + fs) * J;
-        int* next_cnt = &ctl->cnt[nx_slot];
-        int* far_cnt = &ctl->fcnt[fs];
+        if (gtid == 0 && gtimer() > deadline) fail(gctl, EIK_ETIMEDOUT, 0x5000000ull);
+        if (blockIdx.x == 0)
+            for (int i = threadIdx.x; i < NI; i += blockDim.x) {
+                const int nsl = S.ns[i];
+                inst[i].ctl->cnt[nsl == 0 ? 2 : nsl - 1] = 0;  // the list consumed last round
+            }
 
         for (int t = 0;; ++t) {
             const int first_idx = blockIdx.x + nb * (warp + SLOTS * t);  // cell slot 0's entry
-            if (first_idx >= n_near) break;
+            if (first_idx >= total) break;
             const int idx = blockIdx.x + nb * (slot + SLOTS * t);
-            const int c = idx < n_near ? ld_cg(&nearL[idx]) : -1;
-            int cg[C::CPW];
+            int c = -1, ii_ = 0;
+            if (idx < total) {
+                ii_ = find_inst(S.pre, NI, idx);
+                const InstDesc& d0 = inst[ii_];
+                c = ld_cg(&d0.lists[S.ns[ii_] * d0.J + (idx - S.pre[ii_])]);
+            }
+            const InstDesc& d = inst[ii_];
+            int cg[C::CPW], ig[C::CPW];
 #pragma unroll
-            for (int gg = 0; gg < C::CPW; ++gg) cg[gg] = __shfl_sync(FULL, c, gg * C::LPC);
+            for (int gg = 0; gg < C::CPW; ++gg) {
+                cg[gg] = __shfl_sync(FULL, c, gg * C::LPC);
+                ig[gg] = __shfl_sync(FULL, ii_, gg * C::LPC);
+            }
+            T* Ug = reinterpret_cast<T*>(d.U);
+            Ctl* ictl = d.ctl;
+            const int cxn = d.cxn, cyn = d.cyn, upitch = d.upitch, J = d.J;
 
             // ---- remove the cell from the list: clear its flag BEFORE reading
             // its halo, so that a neighbour that improves the halo while we
             // work re-queues it (Alg. generic_LC_cells, activation test)
             int first = 0;
             if (dl == 0 && c >= 0) {
-                atomicExch(&p.qflag[c], 0);
-                first = atomicAdd(&p.visits[c], 1) == 0;
+                atomicExch(&d.qflag[c], 0);
+                first = atomicAdd(&d.visits[c], 1) == 0;
             }
             first = __shfl_sync(FULL, first, g * C::LPC);
             __threadfence();
@@ -526,7 +653,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
             PROF_MARK(2);
             pacc[7] += 1;
 
-            // ---- TMA: U box (cell + halo) and f box into shared memory
+            // ---- TMA: U box (cell + halo) and f box (+ halo) into shared memory
             if (lane == 0) {
                 int nvalid = 0;
 #pragma unroll
@@ -535,10 +662,13 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
 #pragma unroll
                 for (int gg = 0; gg < C::CPW; ++gg) {
                     if (cg[gg] >= 0) {
-                        const int cx = cg[gg] % p.cxn, cy = cg[gg] / p.cxn;
+                        const InstDesc& dg = inst[ig[gg]];
+                        const int cxg = cg[gg] % dg.cxn, cyg = cg[gg] / dg.cxn;
                         unsigned char* gb = wbase + gg * C::GROUP_BYTES;
-                        tma_load_2d(gb, &p.tmU, cx * K, cy * K, bar);
-                        tma_load_2d(gb + C::F_OFF, &p.tmF, cx * K, cy * K, bar);
+                        tensormap_acquire(&dg.tmU);
+                        tensormap_acquire(&dg.tmF);
+                        tma_load_2d(gb, &dg.tmU, cxg * K, cyg * K, bar);
+                        tma_load_2d(gb + C::F_OFF, &dg.tmF, cxg * K, cyg * K, bar);
                     }
                 }
             }
@@ -550,7 +680,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
                     if ((++spins & 255u) == 0 && gtimer() > deadline) break;
                 }
                 if (!got) {
-                    fail(ctl, EIK_ETIMEDOUT, 0x3000000ull);
+                    fail(gctl, EIK_ETIMEDOUT, 0x3000000ull);
                     // let our own copies land before the block leaves (bounded)
                     const unsigned long long d2 = gtimer() + 1000000000ull;
                     while (!mbar_try_wait(bar, phase) && gtimer() < d2) {
@@ -564,9 +694,9 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
                 // 2 f^2 per node, once per visit (saves two FP64 ops per update)
                 for (int e = lane; e < C::CPW * K * K; e += 32) {
                     const int gg = e / (K * K), r = e - gg * (K * K);
-                    const int jj = r / K, ii = r - jj * K;
+                    const int jj = r / K, i2 = r - jj * K;
                     unsigned char* gb = wbase + gg * C::GROUP_BYTES;
-                    const double fv = reinterpret_cast<const double*>(gb + C::F_OFF)[(jj + 1) * C::BW + ii + 1];
+                    const double fv = reinterpret_cast<const double*>(gb + C::F_OFF)[(jj + 1) * C::BW + i2 + 1];
                     reinterpret_cast<double*>(gb + C::X_OFF)[r] = 2.0 * fv * fv;
                 }
                 __syncwarp();
@@ -618,18 +748,23 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
                     // bounds; the expired deadline aborts the launch
                     const unsigned long long now = __shfl_sync(FULL, gtimer(), 0);
                     if (now > deadline) {
-                        if (lane == 0) fail(ctl, EIK_ETIMEDOUT, 0x4000000ull);
+                        if (lane == 0) fail(gctl, EIK_ETIMEDOUT, 0x4000000ull);
                         s = C::MAX_PASSES + 1;
                         break;
                     }
                 }
             }
-            if (s == C::MAX_PASSES && dl == 0 && c >= 0) fail(ctl, EIK_ENOTCONVERGED, (unsigned)c);
-            if (lane == 0)
-                st_lane += (unsigned long long)(s < C::MAX_PASSES ? s + 1 : C::MAX_PASSES) * 4 * C::CPW * K * K;
+            if (s == C::MAX_PASSES && dl == 0 && c >= 0) {
+                atomicCAS(&ictl->status, 0, EIK_ENOTCONVERGED);
+                fail(gctl, EIK_ENOTCONVERGED, (unsigned)c);
+            }
             if (dl == 0 && c >= 0) {
-                ++st_visits;
-                st_sweeps += gsweeps;
+                // node evaluations executed for this cell (lock-step passes included)
+                const unsigned long long ev = (unsigned long long)(s < C::MAX_PASSES ? s + 1 : C::MAX_PASSES) * 4 * K * K;
+                atomicAdd(&ictl->visits, 1ull);
+                atomicAdd(&ictl->sweeps, (unsigned long long)gsweeps);
+                atomicAdd(&ictl->lane_updates, ev);
+                st_lane += ev;
             }
             PROF_MARK(4);
 
@@ -647,14 +782,15 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
                 const int gg = e / (K * K);
                 const int rem = e - gg * K * K;
                 const int j = rem / K, i = rem - j * K;
-                int cc = cg[0];
+                int cc = cg[0], ic = ig[0];
 #pragma unroll
                 for (int q = 1; q < C::CPW; ++q)
-                    if (gg == q) cc = cg[q];
+                    if (gg == q) { cc = cg[q]; ic = ig[q]; }
                 if (cc >= 0 && ((masks[gg * K + j] >> i) & 1ull)) {
-                    const int cx = cc % p.cxn, cy = cc / p.cxn;
+                    const InstDesc& dc = inst[ic];
+                    const int cx = cc % dc.cxn, cy = cc / dc.cxn;
                     const T* gU = reinterpret_cast<const T*>(wbase + gg * C::GROUP_BYTES);
-                    Ug[(size_t)(cy * K + j + 1) * p.upitch + (size_t)(cx * K + i + 1)] =
+                    reinterpret_cast<T*>(dc.U)[(size_t)(cy * K + j + 1) * dc.upitch + (size_t)(cx * K + i + 1)] =
                         gU[(j + 1) * C::BW + (i + 1)];
                 }
             }
@@ -672,9 +808,9 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
             // the boundary, whose sign marks sources) is in shared memory.
             {
                 const int sd = dir;
-                const int cx = c >= 0 ? c % p.cxn : 0, cy = c >= 0 ? c / p.cxn : 0;
+                const int cx = c >= 0 ? c % cxn : 0, cy = c >= 0 ? c / cxn : 0;
                 bool has_nb = false;
-                if (c >= 0) has_nb = sd == 0 ? cx > 0 : sd == 1 ? cx + 1 < p.cxn : sd == 2 ? cy > 0 : cy + 1 < p.cyn;
+                if (c >= 0) has_nb = sd == 0 ? cx > 0 : sd == 1 ? cx + 1 < cxn : sd == 2 ? cy > 0 : cy + 1 < cyn;
                 bool cond = false;
                 T vmax = zero_v<T>();
                 int bmax = -1;
@@ -709,12 +845,12 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
                     }
                 }
                 if (rl == 0 && has_nb) {
-                    const int nc = sd == 0 ? c - 1 : sd == 1 ? c + 1 : sd == 2 ? c - p.cxn : c + p.cxn;
+                    const int nc = sd == 0 ? c - 1 : sd == 1 ? c + 1 : sd == 2 ? c - cxn : c + cxn;
                     double vt = inf_of<double>();
                     if (bmax >= 0) {
                         // eq. cell_value: V_i + ((h + h^c)/2) / F(y_i) with
                         // (h + h^c)/2 = (k+1) h/2; h/F(y_i) read at the node
-                        // across the boundary from x_i (the k x k box in shared
+                        // across the boundary from x_i (the box in shared
                         // memory carries a one-node halo of f)
                         int ai, aj;
                         if (sd == 0) { ai = -1; aj = bmax; }
@@ -722,7 +858,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
                         else if (sd == 2) { ai = bmax; aj = -1; }
                         else { ai = bmax; aj = K; }
                         double fy = to_d(tF[(aj + 1) * C::BW + (ai + 1)]);
-                        if (!(fy >= 0.0 && fy < inf_of<double>())) fy = fmin_glob;
+                        if (!(fy >= 0.0 && fy < inf_of<double>())) fy = val_of(ld_cg(&ictl->fmin_f));
                         vt = to_d(vmax) + (double)(K + 1) * 0.5 * fy;
                     }
                     // HCM: update the neighbour's cell value whether or not it
@@ -730,14 +866,18 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
                     unsigned long long old = KEY_UNSET, kk = KEY_UNSET;
                     if (vt < inf_of<double>()) {
                         kk = key_of(vt);
-                        old = atomicMin(&p.cval[nc], kk);
+                        old = atomicMin(&d.cval[nc], kk);
                     }
-                    const int was = act ? atomicExch(&p.qflag[nc], 1) : 1;
+                    const int was = act ? atomicExch(&d.qflag[nc], 1) : 1;
                     if (!was) {
                         unsigned long long cur = old < kk ? old : kk;
-                        if (kk == KEY_UNSET) cur = ld_cg(&p.cval[nc]);
-                        if (cur <= theta) lane_push(nextL, next_cnt, nc, J, ctl);
-                        else lane_push(farL, far_cnt, nc, J, ctl);
+                        if (kk == KEY_UNSET) cur = ld_cg(&d.cval[nc]);
+                        const int nsl = S.ns[ii_];
+                        if (cur <= S.theta[ii_])
+                            lane_push(d.lists + (nsl == 2 ? 0 : nsl + 1) * J, &ictl->cnt[nsl == 2 ? 0 : nsl + 1],
+                                      nc, J, gctl);
+                        else
+                            lane_push(d.lists + (3 + S.fs[ii_]) * J, &ictl->fcnt[S.fs[ii_]], nc, J, gctl);
                     }
                 }
             }
@@ -748,23 +888,16 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
         // then reports the abort to every block
         ++st_rounds;
         PROF_MARK(2);
-        if (!grid_sync(ctl, deadline, &s_flag)) break;
+        if (!grid_sync(gctl, deadline, &s_flag)) break;
         PROF_MARK(1);
-        ns = nx_slot;
+        for (int i = threadIdx.x; i < NI; i += blockDim.x) S.ns[i] = S.ns[i] == 2 ? 0 : S.ns[i] + 1;
+        __syncthreads();
     }
 
-    if (lane == 0) atomicAdd(&ctl->lane_updates, st_lane);
+    if (st_lane) atomicAdd(&gctl->lane_updates, st_lane);
     if (p.profile && lane == 0)
-        for (int i = 0; i < 8; ++i) atomicAdd(&ctl->prof[i], pacc[i]);
-    // per-cell counters live on each cell's first lane
-    if (dl == 0) {
-        atomicAdd(&ctl->visits, st_visits);
-        atomicAdd(&ctl->sweeps, st_sweeps);
-    }
-    if (gtid == 0) {
-        ctl->rounds = st_rounds;
-        ctl->advances = st_adv;
-    }
+        for (int i = 0; i < 8; ++i) atomicAdd(&gctl->prof[i], pacc[i]);
+    if (gtid == 0) gctl->rounds = st_rounds;
 }
 
 }  // namespace eik

@@ -5,17 +5,24 @@
 namespace eik {
 
 template <int K>
-static void shape_of(int num_sms, LaunchShape* s) {
+static void shape_of(int num_sms, int n_inst, LaunchShape* s) {
     using C = TileCfg<MODE_F32, K>;
     s->threads = C::WPB * 32;
-    s->smem = (size_t)C::WPB * C::WARP_BYTES + 128;
-    cudaFuncSetAttribute(k_solve<MODE_F32, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem);
+    s->smem = (size_t)C::WPB * C::WARP_BYTES + 128 + (size_t)inst_state_bytes(n_inst);
+    s->blocks = 0;
+    if (cudaFuncSetAttribute(k_solve<MODE_F32, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)s->smem) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<MODE_F32, K>, s->threads,
-                                                      s->smem) != cudaSuccess)
+                                                      s->smem) != cudaSuccess) {
+        cudaGetLastError();
         per_sm = 0;
-    // at most two blocks per SM: a round rarely has more cells than that, and
-    // every extra block makes each grid barrier slower
+    }
+    // at most two blocks per SM: every extra block makes each grid barrier
+    // slower, and a round of a single grid rarely has more cells than that
     s->blocks = (per_sm < 2 ? per_sm : 2) * num_sms;
 }
 
@@ -26,14 +33,14 @@ static cudaError_t launch_one(const SolveParams& p, const LaunchShape& s, cudaSt
                                        dim3(s.threads), args, s.smem, st);
 }
 
-int solver_shape_f32(int k, int num_sms, LaunchShape* out) {
+int solver_shape_f32(int k, int num_sms, int n_inst, LaunchShape* out) {
     out->blocks = 0;
     switch (k) {
-    case 4: shape_of<4>(num_sms, out); break;
-    case 8: shape_of<8>(num_sms, out); break;
-    case 16: shape_of<16>(num_sms, out); break;
-    case 32: shape_of<32>(num_sms, out); break;
-    case 64: shape_of<64>(num_sms, out); break;
+    case 4: shape_of<4>(num_sms, n_inst, out); break;
+    case 8: shape_of<8>(num_sms, n_inst, out); break;
+    case 16: shape_of<16>(num_sms, n_inst, out); break;
+    case 32: shape_of<32>(num_sms, n_inst, out); break;
+    case 64: shape_of<64>(num_sms, n_inst, out); break;
     default: return -1;
     }
     return out->blocks > 0 ? 0 : -1;
