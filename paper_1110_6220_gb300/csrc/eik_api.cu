@@ -158,9 +158,17 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     const size_t t_desc = a256((size_t)n * sizeof(InstDesc));
     const size_t t_aux = a256((size_t)n * sizeof(AuxInst));
     const size_t t_pre = a256((size_t)(n + 1) * 4);
+    // block prefixes carry their owner tables (one int per block) behind them
+    size_t nb_int = 0, nb_full = 0;
+    for (int i = 0; i < n; ++i) {
+        nb_int += (size_t)((hj->L[i].nyp + 7) / 8) * ((hj->L[i].nxp + 31) / 32);
+        nb_full += (size_t)((hj->L[i].urows + 7) / 8) * ((hj->L[i].upitch + 31) / 32);
+    }
+    const size_t t_own_int = a256((size_t)(n + 1) * 4 + nb_int * 4);
+    const size_t t_own_full = a256((size_t)(n + 1) * 4 + nb_full * 4);
     const size_t ns4 = a256(std::max(nsrc, ncs) * 4 + 4);
     const size_t t_src = a256(nsrc * 8 + 8) + a256(ncs * 8 + 8) + 4 * ns4;
-    const size_t image_bytes = 2 * t_desc + t_aux + 3 * t_pre + t_src;
+    const size_t image_bytes = 2 * t_desc + t_aux + t_own_int + t_pre + t_own_full + t_src;
     const size_t z_ctl = a256((size_t)(2 * n + 2) * sizeof(Ctl) + (size_t)n * sizeof(ResidualOut));
     const size_t zero_bytes = z_ctl + a256(Jtot * 4) * 2;
     const size_t total = image_bytes + zero_bytes + a256(Jtot * 8) + ibytes + 256;
@@ -177,10 +185,12 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     InstDesc* desc_main_h = (InstDesc*)img;
     InstDesc* desc_f32_h = (InstDesc*)(img + t_desc);
     AuxInst* aux_h = (AuxInst*)(img + 2 * t_desc);
-    int* blk_pre_h = (int*)(img + 2 * t_desc + t_aux);
-    int* cell_pre_h = (int*)(img + 2 * t_desc + t_aux + t_pre);
-    int* blk_full_h = (int*)(img + 2 * t_desc + t_aux + 2 * t_pre);
-    char* src_h = img + 2 * t_desc + t_aux + 3 * t_pre;
+    const size_t o_blk = 2 * t_desc + t_aux, o_cpre = o_blk + t_own_int, o_full = o_cpre + t_pre;
+    const size_t o_src = o_full + t_own_full;
+    int* blk_pre_h = (int*)(img + o_blk);
+    int* cell_pre_h = (int*)(img + o_cpre);
+    int* blk_full_h = (int*)(img + o_full);
+    char* src_h = img + o_src;
     const size_t o_q = 0, o_key = a256(nsrc * 8 + 8), o_node = o_key + a256(ncs * 8 + 8);
     const size_t o_ninst = o_node + ns4, o_cell = o_ninst + ns4, o_cinst = o_cell + ns4;
 
@@ -240,16 +250,16 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     j.desc_main = (InstDesc*)img_dev;
     j.desc_f32 = (InstDesc*)(img_dev + t_desc);
     j.aux = (AuxInst*)(img_dev + 2 * t_desc);
-    j.blk_pre = (int*)(img_dev + 2 * t_desc + t_aux);
-    j.cell_pre = (int*)(img_dev + 2 * t_desc + t_aux + t_pre);
-    j.blk_full = (int*)(img_dev + 2 * t_desc + t_aux + 2 * t_pre);
+    j.blk_pre = (int*)(img_dev + o_blk);
+    j.cell_pre = (int*)(img_dev + o_cpre);
+    j.blk_full = (int*)(img_dev + o_full);
     j.nblocks = boff;
     j.nblocks_full = bfull;
     j.ncells = (int)coff;
     j.ictl = ictl_dev;
     j.gctl = gctl_dev;
     j.res = res_dev;
-    char* src_dev = img_dev + 2 * t_desc + t_aux + 3 * t_pre;
+    char* src_dev = img_dev + o_src;
     j.src.q = (const double*)(src_dev + o_q);
     j.src.node = (const int*)(src_dev + o_node);
     j.src.node_inst = (const int*)(src_dev + o_ninst);

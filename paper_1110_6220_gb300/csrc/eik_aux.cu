@@ -33,12 +33,8 @@ struct Where {
 };
 __device__ __forceinline__ Where locate(const AuxInst* a, const int* blk_pre, int n) {
     const int b = blockIdx.x;
-    int lo = 0, hi = n;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (blk_pre[mid] <= b) lo = mid;
-        else hi = mid;
-    }
+    // blk_pre[n + 1 + b] holds the instance of block b (see k_block_owner)
+    const int lo = blk_pre[n + 1 + b];
     const int local = b - blk_pre[lo];
     const int tx = (a[lo].nxp + 31) / 32;
     Where w;
@@ -48,18 +44,21 @@ __device__ __forceinline__ Where locate(const AuxInst* a, const int* blk_pre, in
     return w;
 }
 
+// owner[b] = instance of block b, for the prefix pre[0..n]: one block per
+// instance fills its range
+__global__ void k_block_owner(const int* pre, int n, int* owner) {
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    for (int b = pre[i] + threadIdx.x; b < pre[i + 1]; b += blockDim.x) owner[b] = i;
+}
+
 // Every element of the padded arrays (ring included): f = h/F on grid nodes,
 // +inf on obstacles, padding nodes and the ring; U = +inf.  Rejects F < 0,
 // NaN, +inf; reduces the smallest finite h/F into the instance's control
 // blocks.  Blocks map onto whole padded arrays (blk_full), 8 rows x 32 columns.
 __global__ void k_init_grid(const AuxInst* A, const int* blk_full, int n) {
     const int b = blockIdx.x;
-    int lo = 0, hi = n;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (blk_full[mid] <= b) lo = mid;
-        else hi = mid;
-    }
+    const int lo = blk_full[n + 1 + b];
     const AuxInst& p = A[lo];
     const int local = b - blk_full[lo];
     const int tx = (p.upitch + 31) / 32;
@@ -279,6 +278,11 @@ cudaError_t launch_fill_df(float2* a, size_t n, cudaStream_t st) {
 
 cudaError_t launch_ctl_init(Ctl* ctl, int count, cudaStream_t st) {
     k_ctl_init<<<(count + 255) / 256, 256, 0, st>>>(ctl, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_owner(const int* pre, int n, cudaStream_t st) {
+    k_block_owner<<<n, 256, 0, st>>>(pre, n, const_cast<int*>(pre) + n + 1);
     return cudaGetLastError();
 }
 

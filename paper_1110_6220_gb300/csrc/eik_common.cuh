@@ -159,6 +159,9 @@ cudaError_t launch_fill(double* a, size_t n, double v, cudaStream_t st);
 cudaError_t launch_fill32(float* a, size_t n, float v, cudaStream_t st);
 cudaError_t launch_fill_df(float2* a, size_t n, cudaStream_t st);  // (+inf, 0)
 cudaError_t launch_ctl_init(Ctl* ctl, int count, cudaStream_t st);  // count control blocks
+// A block prefix pre[0..n] is followed in memory by its owner table
+// (pre[n + 1 + b] = instance of block b), filled on the device by this:
+cudaError_t launch_block_owner(const int* pre, int n, cudaStream_t st);
 // f, U interiors; validation of F; min h/F per instance
 cudaError_t launch_init_grid(const AuxInst* a, const int* blk_pre, int n, int nblocks, cudaStream_t st);
 cudaError_t launch_init_sources(const AuxInst* a, const SourceTable& s, cudaStream_t st);

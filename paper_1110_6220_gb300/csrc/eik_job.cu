@@ -177,6 +177,10 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
     cudaMemsetAsync(j.zero_base, 0, j.zero_bytes, st);
     cudaMemsetAsync(j.cval_all, 0xff, j.ncval * 8, st);
     if (launch_ctl_init(j.ictl, 2 * n, st) != cudaSuccess) return EIK_ECUDA;
+    if (launch_block_owner(j.blk_pre, n, st) != cudaSuccess ||
+        launch_block_owner(j.blk_full, n, st) != cudaSuccess)
+        return EIK_ECUDA;
+    nl += 2;
     if (launch_init_grid(j.aux, j.blk_full, n, j.nblocks_full, st) != cudaSuccess) return EIK_ECUDA;
     nl += 2;
     if (j.nsrc_total) {

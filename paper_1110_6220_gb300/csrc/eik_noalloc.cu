@@ -158,8 +158,6 @@ extern "C" int eik_solve_noalloc(const eik_plan_desc* d, const eik_instance* in,
     struct alignas(64) Tables {
         InstDesc desc;
         AuxInst aux;
-        int blk_pre[2];
-        int blk_full[2];
         int cell_pre[2];
         double q[MAX_SOURCES];
         unsigned long long key[MAX_SOURCES];
@@ -169,6 +167,13 @@ extern "C" int eik_solve_noalloc(const eik_plan_desc* d, const eik_instance* in,
     Tables tb;
     std::memset((void*)&tb, 0, sizeof(tb));
     Tables* tdev = (Tables*)take(sizeof(Tables));
+    // block prefixes, each followed by its owner table (filled on the device)
+    const int nbi = ((L.nyp + 7) / 8) * ((L.nxp + 31) / 32);
+    const int nbf = ((L.urows + 7) / 8) * ((L.upitch + 31) / 32);
+    int* blk_pre_dev = (int*)take((size_t)(2 + nbi) * 4);
+    int* blk_full_dev = (int*)take((size_t)(2 + nbf) * 4);
+    const int blk_pre_h[2] = {0, nbi};
+    const int blk_full_h[2] = {0, nbf};
     const size_t z_ctl = align256(4 * sizeof(Ctl) + sizeof(ResidualOut));
     const size_t zero_bytes = z_ctl + 2 * align256((size_t)L.J * 4);
     char* zero = take(zero_bytes);
@@ -189,10 +194,6 @@ extern "C" int eik_solve_noalloc(const eik_plan_desc* d, const eik_instance* in,
     fill_inst_tables(L, a, false, d->h, d->bucket_width, &ictl[0], &ictl[1], res, in->F, in->U, shift,
                      &tb.aux, &tb.desc, &unused, &ok);
     if (!ok) return EIK_ECUDA;
-    tb.blk_pre[0] = 0;
-    tb.blk_pre[1] = ((L.nyp + 7) / 8) * ((L.nxp + 31) / 32);
-    tb.blk_full[0] = 0;
-    tb.blk_full[1] = ((L.urows + 7) / 8) * ((L.upitch + 31) / 32);
     tb.cell_pre[0] = 0;
     tb.cell_pre[1] = L.J;
     for (int e = 0; e < ss.n; ++e) {
@@ -209,7 +210,10 @@ extern "C" int eik_solve_noalloc(const eik_plan_desc* d, const eik_instance* in,
     cudaStream_t s = (cudaStream_t)cuda_stream;
     // (the scratch holds the previous call's data: the init kernel rewrites
     // every element of the padded arrays, the +inf rings included)
-    if (cudaMemcpyAsync(tdev, &tb, sizeof(tb), cudaMemcpyHostToDevice, s) != cudaSuccess) return EIK_ECUDA;
+    if (cudaMemcpyAsync(tdev, &tb, sizeof(tb), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(blk_pre_dev, blk_pre_h, 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(blk_full_dev, blk_full_h, 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return EIK_ECUDA;
 
     JobDev j;
     std::memset((void*)&j, 0, sizeof(j));
@@ -218,11 +222,11 @@ extern "C" int eik_solve_noalloc(const eik_plan_desc* d, const eik_instance* in,
     j.fp32 = false;
     j.desc_main = &tdev->desc;
     j.aux = &tdev->aux;
-    j.blk_pre = tdev->blk_pre;
-    j.blk_full = tdev->blk_full;
-    j.nblocks_full = tb.blk_full[1];
+    j.blk_pre = blk_pre_dev;
+    j.blk_full = blk_full_dev;
+    j.nblocks_full = nbf;
     j.cell_pre = tdev->cell_pre;
-    j.nblocks = tb.blk_pre[1];
+    j.nblocks = nbi;
     j.ncells = L.J;
     j.ictl = ictl;
     j.gctl = gctl;

@@ -68,12 +68,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
         "l"((unsigned long long)tm), "r"(x), "r"(y), "r"(smem_addr(bar))
         : "memory");
 }
-// the tensor maps live in global memory (written by the host before launch):
-// order that write before their use by the TMA unit
-__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* tm) {
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((unsigned long long)tm)
-                 : "memory");
-}
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
@@ -442,6 +436,17 @@ __host__ __device__ constexpr int inst_state_bytes(int n) {
     return n * 8 + (n + 1) * 4 + n * 4 + n * 4 + n + n + 33 * 4 + 64;
 }
 
+__device__ __forceinline__ void flush_counters(const InstDesc* inst, int i, unsigned long long& v,
+                                               unsigned long long& sw, unsigned long long& l) {
+    if (i >= 0 && v) {
+        Ctl* c = inst[i].ctl;
+        atomicAdd(&c->visits, v);
+        atomicAdd(&c->sweeps, sw);
+        atomicAdd(&c->lane_updates, l);
+    }
+    v = sw = l = 0;
+}
+
 // ---------------------------------------------------------------- the kernel
 // PROF_MARK(i): add the cycles since the last mark to phase i (profiling only)
 #define PROF_MARK(i)                                    \
@@ -526,6 +531,8 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
     constexpr int SLOTS = C::WPB * C::CPW;
 
     unsigned long long st_lane = 0, st_rounds = 0;
+    int acc_inst = -1;
+    unsigned long long acc_visits = 0, acc_sweeps = 0, acc_lane = 0;
     unsigned long long pacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long long pt = clock64();
 
@@ -665,8 +672,6 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
                         const InstDesc& dg = inst[ig[gg]];
                         const int cxg = cg[gg] % dg.cxn, cyg = cg[gg] / dg.cxn;
                         unsigned char* gb = wbase + gg * C::GROUP_BYTES;
-                        tensormap_acquire(&dg.tmU);
-                        tensormap_acquire(&dg.tmF);
                         tma_load_2d(gb, &dg.tmU, cxg * K, cyg * K, bar);
                         tma_load_2d(gb + C::F_OFF, &dg.tmF, cxg * K, cyg * K, bar);
                     }
@@ -759,11 +764,18 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
                 fail(gctl, EIK_ENOTCONVERGED, (unsigned)c);
             }
             if (dl == 0 && c >= 0) {
-                // node evaluations executed for this cell (lock-step passes included)
+                // node evaluations executed for this cell (lock-step passes
+                // included); counters gather per lane while the instance stays
+                // the same (one flush per instance change instead of three
+                // atomics per visit on one address)
                 const unsigned long long ev = (unsigned long long)(s < C::MAX_PASSES ? s + 1 : C::MAX_PASSES) * 4 * K * K;
-                atomicAdd(&ictl->visits, 1ull);
-                atomicAdd(&ictl->sweeps, (unsigned long long)gsweeps);
-                atomicAdd(&ictl->lane_updates, ev);
+                if (ii_ != acc_inst) {
+                    flush_counters(inst, acc_inst, acc_visits, acc_sweeps, acc_lane);
+                    acc_inst = ii_;
+                }
+                acc_visits += 1;
+                acc_sweeps += (unsigned long long)gsweeps;
+                acc_lane += ev;
                 st_lane += ev;
             }
             PROF_MARK(4);
@@ -894,6 +906,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
         __syncthreads();
     }
 
+    flush_counters(inst, acc_inst, acc_visits, acc_sweeps, acc_lane);
     if (st_lane) atomicAdd(&gctl->lane_updates, st_lane);
     if (p.profile && lane == 0)
         for (int i = 0; i < 8; ++i) atomicAdd(&gctl->prof[i], pacc[i]);

@@ -21,9 +21,11 @@ static void shape_of(int num_sms, int n_inst, LaunchShape* s) {
         cudaGetLastError();
         per_sm = 0;
     }
-    // at most two blocks per SM: every extra block makes each grid barrier
-    // slower, and a round of a single grid rarely has more cells than that
-    s->blocks = (per_sm < 2 ? per_sm : 2) * num_sms;
+    // a single grid: at most two blocks per SM (a round rarely has more cells
+    // than that, and every extra block makes each grid barrier slower); a
+    // batch keeps every SM full, so it takes the occupancy limit
+    const int cap = n_inst > 1 ? per_sm : 2;
+    s->blocks = (per_sm < cap ? per_sm : cap) * num_sms;
 }
 
 template <int K>
