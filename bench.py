@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -48,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-grid batch measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the Poisson serving measurement")
+    ap.add_argument("--serving-requests", type=int, default=128)
     return ap.parse_args()
 
 
@@ -230,6 +233,120 @@ def batch_measure(eik, torch, steps=3, warmup=2, k=16):
             "max_err_bound": max(s.err_bound for s in st), "launches_per_batch": st[0].launches}
 
 
+def _pct(xs, p):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    i = min(len(xs) - 1, max(0, int(math.ceil(p / 100.0 * len(xs))) - 1))
+    return xs[i]
+
+
+def serving_measure(eik, torch, count=128, seed=5, budget=64 << 30):
+    """The serving workload: a seeded Poisson stream of FP32 + refinement
+    solves, side lengths log-uniform in [129, 2049], sin-product, random-block
+    and checkerboard+maze speeds in equal shares, served through
+    eik_submit / eik_poll with a 64 GB admission budget.  Reports the
+    saturated throughput (all requests submitted at once) and p50/p99
+    latency at 0.5x and 0.9x of that rate, beside the same stream solved as
+    serial plain solves (one eik_solve per request in arrival order; their
+    latency follows from the measured service times and the arrival times)."""
+    from paper_1110_6220_gb300 import workloads as W
+    stream = W.poisson_stream(count, 1.0, seed=seed)
+    insts = [I for _, I in stream]
+    unit_arrivals = [t for t, _ in stream]  # rate 1 per second; rescaled below
+    npts = sum(I.npts for I in insts)
+    dev = []
+    for I in insts:
+        F = torch.from_numpy(I.F).cuda()
+        dev.append((F, torch.from_numpy(I.src_ij).cuda(), torch.from_numpy(I.sq).cuda(),
+                    torch.empty_like(F)))
+    descs = [eik.make_desc(I.nx, I.ny, I.h, 0, eik.EIK_FP32_REFINE) for I in insts]
+    ins = [eik.make_instance(*d) for d in dev]
+    torch.cuda.synchronize()
+
+    # serial plain solves, back to back, one plan per request shape
+    plans = {}
+    for I in insts:
+        if (I.nx, I.ny) not in plans:
+            plans[(I.nx, I.ny)] = eik.Plan(I.nx, I.ny, I.h, 0, eik.EIK_FP32_REFINE)
+    for e in range(min(4, count)):  # warm-up
+        plans[(insts[e].nx, insts[e].ny)].solve(*dev[e])
+    service = []
+    t0 = time.perf_counter()
+    for I, d in zip(insts, dev):
+        a = time.perf_counter()
+        rc, _ = plans[(I.nx, I.ny)].solve(*d)
+        if rc:
+            raise RuntimeError(f"eik_solve: {eik.eik_strerror(rc)}")
+        service.append(time.perf_counter() - a)
+    serial_s = time.perf_counter() - t0
+    for p in plans.values():
+        p.close()
+
+    def serial_latency(arr):
+        lat, free = [], 0.0
+        for a, s in zip(arr, service):
+            start = max(a, free)
+            free = start + s
+            lat.append(free - a)
+        return lat
+
+    srv = eik.eik_server_create(budget, count)
+    try:
+        def run(arrivals):
+            """Submit each request at its arrival time (None: all at once);
+            returns (makespan s, latencies s, stats)."""
+            pending, lat, sts = {}, [0.0] * count, [None] * count
+            nxt = 0
+            t0 = time.perf_counter()
+            while nxt < count or pending:
+                now = time.perf_counter() - t0
+                while nxt < count and (arrivals is None or arrivals[nxt] <= now):
+                    rc, t = eik.eik_submit(srv, descs[nxt], ins[nxt])
+                    if rc:
+                        raise RuntimeError(f"eik_submit: {eik.eik_strerror(rc)}")
+                    pending[t] = (nxt, now if arrivals is not None else 0.0)
+                    nxt += 1
+                for t in list(pending):
+                    rc, st = eik.eik_poll(srv, t)
+                    if rc == eik.EIK_EAGAIN:
+                        continue
+                    e, arr = pending.pop(t)
+                    if rc:
+                        raise RuntimeError(f"eik_poll: {eik.eik_strerror(rc)}")
+                    lat[e] = time.perf_counter() - t0 - arr
+                    sts[e] = st
+                time.sleep(5e-5)
+            return time.perf_counter() - t0, lat, sts
+
+        run(None)  # warm-up
+        sat_s, sat_lat, sts = run(None)
+        rate = count / sat_s
+        out = {"workload": f"{count} requests, Poisson arrivals (seed {seed}), n log-uniform in "
+                           "[129, 2049], sin-product / random-block / checkerboard+maze F, "
+                           "1-8 sources, 64 GB admission budget",
+               "precision": "fp32ref", "requests": count, "points": npts,
+               "saturated": {"req_per_s": rate, "value": npts / sat_s / 1e6, "unit": UNIT,
+                             "makespan_s": sat_s},
+               "serial_plain": {"req_per_s": count / serial_s, "value": npts / serial_s / 1e6,
+                                "unit": UNIT, "p50_service_ms": 1e3 * _pct(service, 50),
+                                "p99_service_ms": 1e3 * _pct(service, 99)},
+               "max_err_bound": max(s.err_bound for s in sts), "load": []}
+        for frac in (0.5, 0.9):
+            lam = frac * rate
+            arr = [t / lam for t in unit_arrivals]
+            span, lat, _ = run(arr)
+            sl = serial_latency(arr)
+            out["load"].append({
+                "rate_frac_of_saturated": frac, "req_per_s": lam,
+                "p50_ms": 1e3 * _pct(lat, 50), "p99_ms": 1e3 * _pct(lat, 99),
+                "serial_p50_ms": 1e3 * _pct(sl, 50), "serial_p99_ms": 1e3 * _pct(sl, 99),
+                "value": npts / span / 1e6, "unit": UNIT})
+        return out
+    finally:
+        eik.eik_server_destroy(srv)
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -358,6 +475,8 @@ def run_ours(args):
                                                  "cite": "Tab. sinu_1, HCM 176x176 cells"}}}
         if not args.no_batch:
             line["batch"] = batch_measure(eik, torch)
+        if not args.no_serving:
+            line["serving"] = serving_measure(eik, torch, count=args.serving_requests)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(I, args.cpu_seconds)
         print(json.dumps(line), flush=True)

@@ -146,6 +146,42 @@ int eik_solve(eik_plan p, const eik_instance* in, eik_stats* st);
 int eik_solve_batch(const eik_plan_desc* d, const eik_instance* in, int32_t n_inst,
                     eik_stats* st, void* cuda_stream);
 
+/* ------------------------------------------------------- serving
+ * A request loop that keeps grids and cell queues on the device.  A server
+ * thread takes submitted requests in arrival order and launches the oldest
+ * ones of one (cell size, precision) class as a batched job (as
+ * eik_solve_batch) on one of two job slots, each with its own stream and
+ * device workspace.  A request is admitted when its device memory fits
+ * hbm_budget_bytes together with the other running job, so requests that
+ * arrive while a job runs start in the other slot as soon as memory and the
+ * slot are free, and the two jobs share the GPU's SMs (continuous batching).
+ * Results do not depend on the mix: each instance has its own queue and
+ * arrays (Theorem convergence makes the result schedule-independent up to
+ * rounding).
+ *
+ * eik_server_create: max_inflight bounds requests submitted but not yet
+ * polled to completion (<= 0: 64).  cuda_stream: NULL, or the stream on
+ * which the caller produces request inputs -- each request then waits for the
+ * work queued on it before submission.  EIK_EINVAL for a zero budget. */
+typedef struct eik_server_s* eik_server;
+int eik_server_create(eik_server* out, size_t hbm_budget_bytes, int32_t max_inflight,
+                      void* cuda_stream);
+
+/* Queue one request and return at once with a ticket.  The descriptor is
+ * copied; the instance's buffers must stay valid until eik_poll returns a
+ * final status for the ticket.  EIK_EBUSY: the request alone exceeds the
+ * budget, or max_inflight requests are pending.  EIK_EINVAL: bad arguments. */
+int eik_submit(eik_server s, const eik_plan_desc* d, const eik_instance* in, uint64_t* ticket);
+
+/* Non-blocking: EIK_EAGAIN while the request is pending; otherwise its final
+ * status (st, if not NULL, filled; st->ms is the device time of the job that
+ * served it).  A ticket is polled to completion once; later polls and unknown
+ * tickets return EIK_EINVAL. */
+int eik_poll(eik_server s, uint64_t ticket, eik_stats* st);
+
+/* Finish every queued request, then release the server.  NULL is ignored. */
+void eik_server_destroy(eik_server s);
+
 /* ------------------------------------------------------- no-allocation solve
  * The paper has no counterpart to this entry point; it exists for callers that
  * cannot call cudaMalloc: code that runs where device memory is already owned

@@ -271,6 +271,7 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     j.nsrc_total = (int)nsrc;
     j.ncell_total = (int)ncs;
     j.deadline_ns = deadline_ns;
+    j.sm_cap = 0;
     j.zero_base = zero_dev;
     j.zero_bytes = zero_bytes;
     j.cval_all = cval_all;

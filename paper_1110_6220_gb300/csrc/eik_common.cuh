@@ -107,12 +107,13 @@ struct LaunchShape {
     int threads;       // per block
     size_t smem;       // dynamic shared memory per block
     int blocks;        // co-resident blocks (cooperative launch)
+    int per_sm;        // occupancy limit: blocks of this shape one SM holds
 };
 
 // one per arithmetic mode (eik_solver_f64.cu, eik_solver_f32.cu, eik_solver_df.cu)
-int solver_shape_f64(int k, int num_sms, int n_inst, LaunchShape* out);
-int solver_shape_f32(int k, int num_sms, int n_inst, LaunchShape* out);
-int solver_shape_df(int k, int num_sms, int n_inst, LaunchShape* out);
+int solver_shape_f64(int k, int num_sms, int n_inst, int sm_cap, LaunchShape* out);
+int solver_shape_f32(int k, int num_sms, int n_inst, int sm_cap, LaunchShape* out);
+int solver_shape_df(int k, int num_sms, int n_inst, int sm_cap, LaunchShape* out);
 cudaError_t launch_solver_f64(int k, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
 cudaError_t launch_solver_f32(int k, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
 cudaError_t launch_solver_df(int k, const SolveParams& p, const LaunchShape& s, cudaStream_t st);

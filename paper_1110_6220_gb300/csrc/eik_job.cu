@@ -193,7 +193,7 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
     p.profile = profiling();
     LaunchShape shape;
     if (j.fp32) {
-        if (solver_shape_f32(j.k, num_sms, n, &shape)) return EIK_ECUDA;
+        if (solver_shape_f32(j.k, num_sms, n, j.sm_cap, &shape)) return EIK_ECUDA;
         p.inst = j.desc_f32;
         p.gctl = j.gctl;
         if (ev) cudaEventRecord(ev[0], st);
@@ -206,7 +206,7 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
             cudaSuccess)
             return EIK_ECUDA;
         nl += 2;
-        if (solver_shape_df(j.k, num_sms, n, &shape)) return EIK_ECUDA;
+        if (solver_shape_df(j.k, num_sms, n, j.sm_cap, &shape)) return EIK_ECUDA;
         p.inst = j.desc_main;
         p.gctl = j.gctl + 1;
         if (ev) cudaEventRecord(ev[2], st);
@@ -216,7 +216,7 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
         if (launch_residual(j.aux, j.blk_pre, n, j.nblocks, st) != cudaSuccess) return EIK_ECUDA;
         ++nl;
     } else {
-        if (solver_shape_f64(j.k, num_sms, n, &shape)) return EIK_ECUDA;
+        if (solver_shape_f64(j.k, num_sms, n, j.sm_cap, &shape)) return EIK_ECUDA;
         p.inst = j.desc_main;
         p.gctl = j.gctl + 1;
         if (ev) cudaEventRecord(ev[2], st);
@@ -228,6 +228,17 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
     ++nl;
     if (launches) *launches = nl;
     return EIK_OK;
+}
+
+bool job_pairable(const JobDev& j, int num_sms) {
+    LaunchShape a{}, b{};
+    if (j.fp32) {
+        if (solver_shape_f32(j.k, num_sms, j.n, 1, &a) || solver_shape_df(j.k, num_sms, j.n, 1, &b))
+            return false;
+        return a.per_sm >= 2 && b.per_sm >= 2;
+    }
+    if (solver_shape_f64(j.k, num_sms, j.n, 1, &a)) return false;
+    return a.per_sm >= 2;
 }
 
 // ---------------------------------------------------------------- statistics

@@ -55,6 +55,7 @@ struct JobDev {
     SourceTable src;            // device pointers
     int nsrc_total, ncell_total;
     long long deadline_ns;
+    int sm_cap;                 // > 0: at most this many blocks per SM (room for other jobs)
     // everything that enqueue_job zeroes before a solve: [zero_base, + zero_bytes)
     void* zero_base;
     size_t zero_bytes;
@@ -75,6 +76,11 @@ void fill_inst_tables(const Layout& L, const InstArrays& a, bool fp32, double h,
 // Queue the whole solve of a job on st (tables and sources already uploaded).
 // ev: null or 4 events around the FP32 pass [0,1] and the main pass [2,3].
 int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, int* launches);
+
+// True when every solver launch of j, capped to one block per SM, takes at
+// most half of an SM's resources, so that two such jobs are co-resident in
+// full on separate streams (cooperative grids never wait on each other).
+bool job_pairable(const JobDev& j, int num_sms);
 
 // Fill *st for instance i from the control blocks copied back to the host.
 void job_stats(const Layout& L, const eik_plan_desc* d, bool fp32, const Ctl* ictl_first,

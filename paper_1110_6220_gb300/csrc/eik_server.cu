@@ -1,0 +1,334 @@
+// eik_server.cu -- eik_server_create / eik_submit / eik_poll /
+// eik_server_destroy: a request loop with HBM admission and continuous
+// batching.
+//
+// A server thread keeps a FIFO of submitted requests and JOB_SLOTS job slots,
+// each with its own stream, arena and events.  Whenever a slot is free it
+// takes the oldest waiting requests of one (cell size, precision) class that
+// fit the memory budget left by the other slots, and launches them as one
+// batched job (eik_job.h) capped to its share of the SMs, so that a job built
+// from requests that arrived while another job runs overlaps it on the
+// device.  Finished jobs are detected with events (no blocking), their
+// results copied out and their tickets completed.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "eik_common.cuh"
+#include "eik_plan.h"
+
+using namespace eik;
+
+namespace {
+
+constexpr int JOB_SLOTS = 2;
+
+struct Request {
+    uint64_t ticket;
+    eik_plan_desc d;
+    eik_instance in;
+    size_t bytes;       // device workspace estimate
+    cudaEvent_t ready = nullptr;  // inputs ready on the caller's stream
+    int state = 0;      // 0 waiting, 1 running, 2 done
+    eik_stats st{};
+    int rc = EIK_EAGAIN;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev[6] = {};
+    HostJob job;
+    std::vector<Request*> reqs;
+    std::vector<eik_plan_desc> descs;
+    std::vector<eik_instance> insts;
+    size_t bytes = 0;   // budget held while running
+    bool busy = false;
+    bool shared = false;  // runs capped to one block per SM beside the other slot
+};
+
+}  // namespace
+
+struct eik_server_s {
+    int device = 0;
+    int num_sms = 0;
+    size_t budget = 0;
+    int max_inflight = 64;
+    cudaStream_t user_stream = nullptr;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Request*> waiting;
+    std::map<uint64_t, Request*> all;
+    uint64_t next_ticket = 1;
+    int inflight = 0;
+    bool stop = false;
+    bool blocked = false;  // the head job waits for the other slot to drain
+    Slot slots[JOB_SLOTS];
+    std::thread worker;
+};
+
+namespace {
+
+size_t request_bytes(const eik_plan_desc& d, const eik_instance& in) {
+    const Layout L = make_layout(d.nx, d.ny, default_k(&d));
+    const bool fp32 = d.precision == EIK_FP32_REFINE;
+    // arrays + staging for host buffers + cell state, lists and tables
+    return inst_bytes(L, fp32, !is_device_ptr(in.F), !is_device_ptr(in.U)) + (size_t)L.J * 16 +
+           4 * sizeof(Ctl) + 4096;
+}
+
+// Finish a slot whose job has completed (called with the lock held).
+void complete_slot(eik_server_s* s, Slot& sl) {
+    std::vector<eik_stats> st(sl.reqs.size());
+    int rc = finish_job(&sl.job, sl.descs.data(), sl.stream, 0.0, st.data());
+    float ms = 0.f, p0 = 0.f, p1 = 0.f;
+    cudaEventElapsedTime(&ms, sl.ev[0], sl.ev[1]);
+    cudaEventElapsedTime(&p0, sl.ev[2], sl.ev[3]);
+    cudaEventElapsedTime(&p1, sl.ev[4], sl.ev[5]);
+    for (size_t e = 0; e < sl.reqs.size(); ++e) {
+        Request* r = sl.reqs[e];
+        r->st = st[e];
+        r->st.ms = ms;
+        r->st.mpts_per_s = ms > 0 ? (double)r->d.nx * r->d.ny / ms / 1000.0 : 0.0;
+        r->st.pass_ms[0] = sl.descs[e].precision == EIK_FP32_REFINE ? p0 : 0.0;
+        r->st.pass_ms[1] = p1;
+        r->rc = rc == EIK_ECUDA ? rc : r->st.status;
+        r->state = 2;
+        --s->inflight;
+    }
+    sl.reqs.clear();
+    sl.busy = false;
+    sl.bytes = 0;
+}
+
+// Launch the oldest admissible waiting requests on a free slot (lock held;
+// the CUDA calls happen with the lock released by the caller's structure:
+// build and enqueue are quick and non-blocking apart from small copies).
+bool launch_slot(eik_server_s* s, Slot& sl, size_t held_by_others) {
+    if (s->waiting.empty()) return false;
+    const Request* head = s->waiting.front();
+    const int k = default_k(&head->d);
+    const int prec = head->d.precision;
+    size_t bytes = 0;
+    sl.reqs.clear();
+    for (auto it = s->waiting.begin(); it != s->waiting.end() && (int)sl.reqs.size() < MAX_BATCH;) {
+        Request* r = *it;
+        if (default_k(&r->d) == k && r->d.precision == prec) {
+            if (held_by_others + bytes + r->bytes > s->budget) break;  // keep FIFO order
+            bytes += r->bytes;
+            sl.reqs.push_back(r);
+            it = s->waiting.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    if (sl.reqs.empty()) return false;
+    sl.descs.resize(sl.reqs.size());
+    sl.insts.resize(sl.reqs.size());
+    for (size_t e = 0; e < sl.reqs.size(); ++e) {
+        sl.descs[e] = sl.reqs[e]->d;
+        sl.descs[e].cell_k = k;
+        sl.insts[e] = sl.reqs[e]->in;
+        sl.reqs[e]->state = 1;
+    }
+    // A job shares the SMs with the other slot's job only when both fit an
+    // SM side by side; otherwise it runs alone with full occupancy once the
+    // other slot is idle (two cooperative grids must never wait for each
+    // other's blocks to become resident).
+    JobDev probe{};
+    probe.n = (int)sl.reqs.size();
+    probe.k = k;
+    probe.fp32 = prec == EIK_FP32_REFINE;
+    sl.shared = job_pairable(probe, s->num_sms);
+    const Slot* other = nullptr;
+    for (const Slot& o : s->slots)
+        if (&o != &sl && o.busy) other = &o;
+    if (other && (!sl.shared || !other->shared)) {
+        // keep the requests at the head of the queue, in order
+        for (auto it = sl.reqs.rbegin(); it != sl.reqs.rend(); ++it) {
+            (*it)->state = 0;
+            s->waiting.push_front(*it);
+        }
+        sl.reqs.clear();
+        s->blocked = true;
+        return false;
+    }
+    for (Request* r : sl.reqs)
+        if (r->ready) cudaStreamWaitEvent(sl.stream, r->ready, 0);
+    int rc = build_job(&sl.job, (int)sl.reqs.size(), sl.descs.data(), sl.insts.data(), k,
+                       prec == EIK_FP32_REFINE, head->d.deadline_ns, sl.stream);
+    if (!rc) {
+        sl.job.j.sm_cap = sl.shared ? 1 : 0;
+        cudaEventRecord(sl.ev[0], sl.stream);
+        int nl = 0;
+        rc = enqueue_job(sl.job.j, s->num_sms, sl.stream, sl.ev + 2, &nl);
+        cudaEventRecord(sl.ev[1], sl.stream);
+    }
+    if (rc) {
+        cudaStreamSynchronize(sl.stream);
+        cudaGetLastError();
+        for (Request* r : sl.reqs) {
+            r->rc = rc;
+            r->st.status = rc;
+            r->state = 2;
+            --s->inflight;
+        }
+        sl.reqs.clear();
+        return true;
+    }
+    sl.busy = true;
+    sl.bytes = bytes;
+    return true;
+}
+
+void server_loop(eik_server_s* s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lock(s->mu);
+    for (;;) {
+        bool progressed = false;
+        for (Slot& sl : s->slots) {
+            if (sl.busy && cudaEventQuery(sl.ev[1]) == cudaSuccess) {
+                complete_slot(s, sl);
+                progressed = true;
+            }
+        }
+        for (int i = 0; i < JOB_SLOTS; ++i) {
+            Slot& sl = s->slots[i];
+            if (sl.busy || s->waiting.empty() || (s->blocked && !progressed)) continue;
+            s->blocked = false;
+            size_t others = 0;
+            for (int o = 0; o < JOB_SLOTS; ++o)
+                if (o != i && s->slots[o].busy) others += s->slots[o].bytes;
+            if (launch_slot(s, sl, others)) progressed = true;
+        }
+        bool any_busy = false;
+        for (Slot& sl : s->slots) any_busy |= sl.busy;
+        if (s->stop && s->waiting.empty() && !any_busy) break;
+        if (!progressed) {
+            // poll running jobs every 50 us; sleep until woken when idle
+            if (any_busy) s->cv.wait_for(lock, std::chrono::microseconds(50));
+            else s->cv.wait_for(lock, std::chrono::milliseconds(50));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int eik_server_create(eik_server* out, size_t hbm_budget_bytes, int32_t max_inflight,
+                                 void* cuda_stream) {
+    if (!out) return EIK_EINVAL;
+    *out = nullptr;
+    if (hbm_budget_bytes == 0) return EIK_EINVAL;
+    eik_server_s* s = new (std::nothrow) eik_server_s();
+    if (!s) return EIK_ENOMEM;
+    s->budget = hbm_budget_bytes;
+    s->max_inflight = max_inflight > 0 ? max_inflight : 64;
+    s->user_stream = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&s->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return EIK_ECUDA;
+    }
+    for (Slot& sl : s->slots) {
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            eik_server_destroy(s);
+            return EIK_ECUDA;
+        }
+        for (auto& e : sl.ev) cudaEventCreate(&e);
+    }
+    try {
+        s->worker = std::thread(server_loop, s);
+    } catch (...) {
+        eik_server_destroy(s);
+        return EIK_ENOMEM;
+    }
+    *out = s;
+    return EIK_OK;
+}
+
+extern "C" int eik_submit(eik_server s, const eik_plan_desc* d, const eik_instance* in,
+                          uint64_t* ticket) {
+    if (!s || !d || !in || !ticket || !desc_valid(d) || !in->F || !in->U || in->nsrc < 0) return EIK_EINVAL;
+    Request* r = new (std::nothrow) Request();
+    if (!r) return EIK_ENOMEM;
+    r->d = *d;
+    r->in = *in;
+    r->bytes = request_bytes(*d, *in);
+    if (r->bytes > s->budget) {
+        delete r;
+        return EIK_EBUSY;
+    }
+    if (s->user_stream) {
+        // the job that serves this request waits for the caller's stream
+        if (cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(r->ready, s->user_stream) != cudaSuccess) {
+            cudaGetLastError();
+            if (r->ready) cudaEventDestroy(r->ready);
+            delete r;
+            return EIK_ECUDA;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (s->stop) {
+            delete r;
+            return EIK_EINVAL;
+        }
+        if (s->inflight >= s->max_inflight) {
+            delete r;
+            return EIK_EBUSY;
+        }
+        r->ticket = s->next_ticket++;
+        s->all[r->ticket] = r;
+        s->waiting.push_back(r);
+        ++s->inflight;
+        *ticket = r->ticket;
+    }
+    s->cv.notify_all();
+    return EIK_OK;
+}
+
+extern "C" int eik_poll(eik_server s, uint64_t ticket, eik_stats* st) {
+    if (!s) return EIK_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return EIK_EINVAL;
+    Request* r = it->second;
+    if (r->state != 2) return EIK_EAGAIN;
+    if (st) *st = r->st;
+    const int rc = r->rc;
+    s->all.erase(it);
+    if (r->ready) cudaEventDestroy(r->ready);
+    delete r;
+    return rc;
+}
+
+extern "C" void eik_server_destroy(eik_server s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    for (Slot& sl : s->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        free_job(&sl.job);
+        for (auto& e : sl.ev)
+            if (e) cudaEventDestroy(e);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+    }
+    for (auto& kv : s->all) {
+        if (kv.second->ready) cudaEventDestroy(kv.second->ready);
+        delete kv.second;
+    }
+    delete s;
+}

@@ -5,11 +5,12 @@
 namespace eik {
 
 template <int K>
-static void shape_of(int num_sms, int n_inst, LaunchShape* s) {
+static void shape_of(int num_sms, int n_inst, int sm_cap, LaunchShape* s) {
     using C = TileCfg<MODE_DF, K>;
     s->threads = C::WPB * 32;
     s->smem = (size_t)C::WPB * C::WARP_BYTES + 128 + (size_t)inst_state_bytes(n_inst);
     s->blocks = 0;
+    s->per_sm = 0;
     if (cudaFuncSetAttribute(k_solve<MODE_DF, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)s->smem) != cudaSuccess) {
         cudaGetLastError();
@@ -24,8 +25,10 @@ static void shape_of(int num_sms, int n_inst, LaunchShape* s) {
     // a single grid: at most two blocks per SM (a round rarely has more cells
     // than that, and every extra block makes each grid barrier slower); a
     // batch keeps every SM full, so it takes the occupancy limit
-    const int cap = n_inst > 1 ? per_sm : 2;
+    int cap = n_inst > 1 ? per_sm : 2;
+    if (sm_cap > 0 && sm_cap < cap) cap = sm_cap;  // leave room for other jobs
     s->blocks = (per_sm < cap ? per_sm : cap) * num_sms;
+    s->per_sm = per_sm;
 }
 
 template <int K>
@@ -35,14 +38,14 @@ static cudaError_t launch_one(const SolveParams& p, const LaunchShape& s, cudaSt
                                        dim3(s.threads), args, s.smem, st);
 }
 
-int solver_shape_df(int k, int num_sms, int n_inst, LaunchShape* out) {
+int solver_shape_df(int k, int num_sms, int n_inst, int sm_cap, LaunchShape* out) {
     out->blocks = 0;
     switch (k) {
-    case 4: shape_of<4>(num_sms, n_inst, out); break;
-    case 8: shape_of<8>(num_sms, n_inst, out); break;
-    case 16: shape_of<16>(num_sms, n_inst, out); break;
-    case 32: shape_of<32>(num_sms, n_inst, out); break;
-    case 64: shape_of<64>(num_sms, n_inst, out); break;
+    case 4: shape_of<4>(num_sms, n_inst, sm_cap, out); break;
+    case 8: shape_of<8>(num_sms, n_inst, sm_cap, out); break;
+    case 16: shape_of<16>(num_sms, n_inst, sm_cap, out); break;
+    case 32: shape_of<32>(num_sms, n_inst, sm_cap, out); break;
+    case 64: shape_of<64>(num_sms, n_inst, sm_cap, out); break;
     default: return -1;
     }
     return out->blocks > 0 ? 0 : -1;

@@ -1,0 +1,157 @@
+"""Serving loop (eik_server_create / eik_submit / eik_poll): every request's
+result matches the oracle and its own solve alone, whatever it was batched
+with; admission by memory budget and by in-flight count; inputs produced on
+the caller's stream are waited for."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1110_6220_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def eik():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1110_6220_gb300 import build
+    build.build()
+    from paper_1110_6220_gb300 import eik as e
+    return e
+
+
+def _check(U, V, tol, what):
+    fin = np.isfinite(V)
+    assert (np.isfinite(U) == fin).all(), f"{what}: +inf pattern"
+    if fin.any():
+        scale = np.abs(V[fin]).max()
+        err = np.abs(U[fin] - V[fin]).max()
+        assert err <= tol * scale, f"{what}: {err:.3e} > {tol:g} * {scale:.3e}"
+
+
+def _device(I):
+    import torch
+    F = torch.from_numpy(I.F).cuda()
+    src = torch.from_numpy(I.src_ij).cuda()
+    q = torch.from_numpy(np.ascontiguousarray(I.sq)).cuda()
+    return F, src, q, torch.empty_like(F)
+
+
+def _wait(eik, srv, ticket, limit_s=60.0):
+    t0 = time.perf_counter()
+    while True:
+        rc, st = eik.eik_poll(srv, ticket)
+        if rc != eik.EIK_EAGAIN:
+            return rc, st
+        assert time.perf_counter() - t0 < limit_s, "request did not finish"
+        time.sleep(2e-4)
+
+
+def test_serving_mix_matches_alone_and_oracle(eik, orc):
+    """A stream of uneven grids of two cell sizes and both precisions; each
+    result equals the oracle and the instance's own single solve (within
+    tolerance: concurrent schedules reach the fixed point a few ulps apart)."""
+    import torch
+    insts = W.batch_mix(20, seed=11, n_lo=33, n_hi=260)
+    combos = [(8, eik.EIK_FP64), (8, eik.EIK_FP32_REFINE), (16, eik.EIK_FP64)]
+    torch.cuda.synchronize()
+    srv = eik.eik_server_create(1 << 30, 64)
+    try:
+        sub = []
+        for e, I in enumerate(insts):
+            k, prec = combos[e % len(combos)]
+            bufs = _device(I)
+            d = eik.make_desc(I.nx, I.ny, I.h, k, prec)
+            rc, t = eik.eik_submit(srv, d, eik.make_instance(*bufs))
+            assert rc == 0, eik.eik_strerror(rc)
+            sub.append((I, k, prec, bufs, t))
+            if e % 5 == 4:
+                time.sleep(0.002)  # later arrivals join while earlier jobs run
+        done = []
+        for I, k, prec, bufs, t in sub:
+            rc, st = _wait(eik, srv, t)
+            assert rc == 0 and st.status == 0, eik.eik_strerror(rc)
+            if prec == eik.EIK_FP32_REFINE:
+                assert st.err_bound <= TOL32
+            done.append((I, k, prec, bufs[3].cpu().numpy()))
+    finally:
+        eik.eik_server_destroy(srv)
+    # the same instances alone, once the server has drained
+    for I, k, prec, U in done:
+        tol = TOL64 if prec == eik.EIK_FP64 else TOL32
+        _check(U, orc.fmm(I.F, I.h, I.si, I.sj, I.sq), tol, I.name)
+        alone, _ = eik.solve(I.F, I.h, I.si, I.sj, I.sq, cell_k=k, precision=prec)
+        _check(U, alone, 2 * tol, I.name + " alone")
+
+
+def test_serving_host_buffers(eik, orc):
+    insts = [W.sin_point(129), W.const_point(65), W.tiny_random(np.random.default_rng(3))]
+    srv = eik.eik_server_create(256 << 20, 0)
+    try:
+        keep = []
+        for I in insts:
+            U = np.empty_like(I.F)
+            src = I.src_ij
+            rc, t = eik.eik_submit(srv, eik.make_desc(I.nx, I.ny, I.h, 8),
+                                   eik.make_instance(I.F, src, I.sq, U))
+            assert rc == 0
+            keep.append((I, U, src, t))
+        for I, U, _, t in keep:
+            rc, st = _wait(eik, srv, t)
+            assert rc == 0
+            _check(U, orc.fmm(I.F, I.h, I.si, I.sj, I.sq), TOL64, I.name)
+    finally:
+        eik.eik_server_destroy(srv)
+
+
+def test_serving_admission_and_stream_order(eik, orc):
+    """Inputs written on the caller's stream behind a long sleep: requests
+    stay pending (EAGAIN), the in-flight limit answers EBUSY, an over-budget
+    request answers EBUSY, and the results use the inputs as written."""
+    import torch
+    user = torch.cuda.Stream()
+    I = W.sin_point(257)
+    srv = eik.eik_server_create(64 << 20, 2, user)
+    try:
+        big = W.const_point(2049)
+        Ub = np.empty_like(big.F)
+        rc, _ = eik.eik_submit(srv, eik.make_desc(big.nx, big.ny, big.h, 8),
+                               eik.make_instance(big.F, big.src_ij, big.sq, Ub))
+        assert rc == eik.EIK_EBUSY  # needs more than the 64 MiB budget alone
+        Fsrc = torch.from_numpy(I.F).cuda()
+        src = torch.from_numpy(I.src_ij).cuda()
+        q = torch.from_numpy(np.ascontiguousarray(I.sq)).cuda()
+        extra = _device(I)
+        torch.cuda.synchronize()
+        bufs = []
+        with torch.cuda.stream(user):
+            torch.cuda._sleep(200_000_000)  # ~0.1 s at 2 GHz
+            for _ in range(2):
+                F = torch.zeros_like(Fsrc)
+                F.copy_(Fsrc)  # device to device, behind the sleep
+                bufs.append((F, src, q, torch.empty_like(F)))
+        tickets = []
+        for b in bufs:
+            rc, t = eik.eik_submit(srv, eik.make_desc(I.nx, I.ny, I.h, 8), eik.make_instance(*b))
+            assert rc == 0
+            tickets.append(t)
+        rc, _ = eik.eik_poll(srv, tickets[0])
+        assert rc == eik.EIK_EAGAIN
+        rc, _ = eik.eik_submit(srv, eik.make_desc(I.nx, I.ny, I.h, 8), eik.make_instance(*extra))
+        assert rc == eik.EIK_EBUSY  # max_inflight = 2
+        V = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+        for b, t in zip(bufs, tickets):
+            rc, st = _wait(eik, srv, t)
+            assert rc == 0
+            _check(b[3].cpu().numpy(), V, TOL64, "after the caller's stream")
+        rc, _ = eik.eik_poll(srv, tickets[0])
+        assert rc == eik.EIK_EINVAL  # polled to completion already
+        rc, _ = eik.eik_poll(srv, 987654321)
+        assert rc == eik.EIK_EINVAL
+    finally:
+        eik.eik_server_destroy(srv)
