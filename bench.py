@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-grid batch measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the Poisson serving measurement")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the cell-size sweep")
     ap.add_argument("--serving-requests", type=int, default=128)
     return ap.parse_args()
 
@@ -70,7 +71,7 @@ def config_dict(args, k, precision):
     return {"workload": f"single solve, {N_GRID}x{N_GRID} grid on [0,1]^2, "
                         "F=1+0.5 sin(20 pi x) sin(20 pi y), point source at centre",
             "grid": N_GRID, "precision": precision, "cell_k": k,
-            "bucket_width": "auto (4 k min h/F)" if args.bucket_width <= 0 else args.bucket_width,
+            "bucket_width": "library choice per pass" if args.bucket_width == 0 else args.bucket_width,
             "parallelism": "replicas (one independent grid per GPU)",
             "l2": "flushed between timed steps (256 MiB write)"}
 
@@ -199,7 +200,32 @@ def ncu_traffic(kernel, k):
     return e.get("dram_bytes_per_launch")
 
 
-def batch_measure(eik, torch, steps=3, warmup=2, k=16):
+def k_sweep(eik, torch, I, F, src, q, V, reps=3):
+    """The single 1025^2 solve at every cell size, both precisions: device
+    time of whole solves (median of reps) and the error against the oracle."""
+    fin = np.isfinite(V)
+    out = []
+    for prec, pname in ((eik.EIK_FP64, "fp64"), (eik.EIK_FP32_REFINE, "fp32ref")):
+        for k in (4, 8, 16, 32, 64):
+            U = torch.empty_like(F)
+            with eik.Plan(I.nx, I.ny, I.h, k, prec) as p:
+                ms = []
+                for r in range(reps + 1):
+                    rc, st = p.solve(F, src, q, U)
+                    if rc:
+                        raise RuntimeError(f"eik_solve k={k}: {eik.eik_strerror(rc)}")
+                    if r:
+                        ms.append(st.ms)
+            Ug = U.cpu().numpy()
+            err = float(np.abs(Ug[fin] - V[fin]).max() / np.abs(V[fin]).max())
+            med = statistics.median(ms)
+            out.append({"precision": pname, "cell_k": k, "ms": med, "value": I.npts / med / 1e3,
+                        "unit": UNIT, "max_rel_err": err, "rounds": st.rounds, "avhr": st.avhr,
+                        "pass_ms": list(st.pass_ms)})
+    return out
+
+
+def batch_measure(eik, torch, steps=3, warmup=2, k=0):
     """The batched workload: 512 grids with side lengths log-uniform in
     [65, 1025] (sin-product or random-block speeds, 1-8 sources), FP32 +
     refinement, one persistent launch per pass; inputs resident on the device."""
@@ -230,7 +256,8 @@ def batch_measure(eik, torch, steps=3, warmup=2, k=16):
                         "1-8 sources, seed 1", "precision": "fp32ref", "cell_k": k,
             "points": npts, "ms_per_batch": med, "value": npts / (med / 1e3) / 1e6, "unit": UNIT,
             "device_ms": statistics.median([st[0].ms]), "pass_ms": list(st[0].pass_ms),
-            "max_err_bound": max(s.err_bound for s in st), "launches_per_batch": st[0].launches}
+            "max_err_bound": max(s.err_bound for s in st), "launches_per_batch": st[0].launches,
+            "cell_k_used": st[0].cell_k}
 
 
 def _pct(xs, p):
@@ -362,7 +389,7 @@ def run_ours(args):
 
     I = workload()
     prec = eik.EIK_FP32_REFINE if args.precision == "fp32ref" else eik.EIK_FP64
-    k = args.k or 8
+    k = args.k  # 0: the library's choice (tuned table or built-in)
     stream = torch.cuda.current_stream()
     dev = torch.device("cuda", local)
     F = torch.from_numpy(I.F).to(dev)
@@ -379,7 +406,7 @@ def run_ours(args):
         return st
 
     for _ in range(max(args.warmup, 3)):
-        step()
+        k = step().cell_k
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -473,6 +500,9 @@ def run_ours(args):
                            "pass_ms": [p32, p64], "solve_ms_device": statistics.mean(s.ms for s in stats),
                            "paper_hcm_k8_1408": {"avhr": 1.117, "avs": 4.350,
                                                  "cite": "Tab. sinu_1, HCM 176x176 cells"}}}
+        line["solver"]["bucket_width_main"] = s0.bucket_width
+        if not args.no_sweep:
+            line["k_sweep"] = k_sweep(eik, torch, I, F, src, q, V)
         if not args.no_batch:
             line["batch"] = batch_measure(eik, torch)
         if not args.no_serving:

@@ -74,7 +74,9 @@ typedef struct {
     int32_t nx, ny;        /* grid nodes per side, each >= 2 */
     double h;              /* grid spacing, > 0 */
     int32_t cell_k;        /* cell side k in nodes: 4, 8, 16, 32 or 64; 0 = choose */
-    double bucket_width;   /* width of a bucket of cell values; <= 0: k * min(h/F) */
+    double bucket_width;   /* width Delta of a bucket of cell values (Sec. 2's Dial buckets):
+                              > 0: absolute; < 0: |bucket_width| * k * min(h/F);
+                              0: the tuned or built-in choice (see autotuning) */
     int32_t precision;     /* EIK_FP64 or EIK_FP32_REFINE */
     double tol;            /* FP32_REFINE: certified max error / max|u|; <= 0: 1e-5 */
     int64_t deadline_ns;   /* device wall-clock limit per solve; <= 0: 20 s */
@@ -145,6 +147,46 @@ int eik_solve(eik_plan p, const eik_instance* in, eik_stats* st);
  * status of each instance is in st[i].status. */
 int eik_solve_batch(const eik_plan_desc* d, const eik_instance* in, int32_t n_inst,
                     eik_stats* st, void* cuda_stream);
+
+/* ------------------------------------------------------- autotuning
+ * The cell size k (Sec. 4) and the width of the value buckets (Sec. 2's
+ * Dial buckets) trade grid-wide rounds against repeated cell visits, and the
+ * best choice depends on the grid, its speed field and on whether it runs
+ * alone or in a batch.  The library keeps a table of choices per class of
+ * job: (precision, one instance or a batch, mean side length rounded to a
+ * power of two).  A descriptor that leaves cell_k at 0 gets the table's k;
+ * one that leaves bucket_width at 0 gets the table's widths (one for the FP32
+ * pass, one for the FP64 or refinement pass).  Classes not in the table use
+ * built-in choices measured on GB300.  Plans take the choice at
+ * eik_plan_create; batches and served jobs at each call.
+ *
+ * eik_tune: time trial solves of the given instances, run as one job like
+ * eik_solve_batch (n_inst = 1: like eik_solve), over k in {8, 16, 32} and
+ * relative widths {2, 4, 16, 64, 256}, timing each pass on its own; record
+ * the fastest choice for the job's class (never one slower than the choice
+ * in force before) and return it.  Blocks; about twenty solves.  Each U
+ * receives a valid result.  All descriptors must have one precision;
+ * their cell_k and bucket_width are ignored.  The table is per process and
+ * shared by all threads and devices.  EIK_TUNE_FILE, if set, names a file
+ * loaded on first use. */
+typedef struct {
+    int32_t cell_k;        /* chosen k */
+    double bucket_first;   /* relative width of the FP32 pass (FP32_REFINE) */
+    double bucket_main;    /* relative width of the FP64 / refinement pass */
+    double ms;             /* device time of the job with the chosen values */
+    double ms_before;      /* device time with the choice in force before */
+    int32_t trials;        /* solves run */
+} eik_tune_result;
+
+int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t n_inst, void* cuda_stream,
+             eik_tune_result* out);
+/* Write / merge the table as text ("eik-tune 1" then one line per class).
+ * EIK_EINVAL if the file cannot be written / read or is malformed (nothing
+ * merged then). */
+int eik_tune_save(const char* path);
+int eik_tune_load(const char* path);
+/* Forget every tuned entry (the built-in choices remain). */
+void eik_tune_reset(void);
 
 /* ------------------------------------------------------- serving
  * A request loop that keeps grids and cell queues on the device.  A server

@@ -46,10 +46,7 @@ bool desc_valid(const eik_plan_desc* d) {
     return true;
 }
 
-int default_k(const eik_plan_desc* d) {
-    if (d->cell_k) return d->cell_k;
-    return 8;
-}
+int default_k(const eik_plan_desc* d) { return choose_params(d, 1).k; }
 
 bool is_device_ptr(const void* p) {
     if (!p) return false;
@@ -127,9 +124,11 @@ int prepare_sources(const Layout& L, const eik_instance* in, HostSources* hs) {
 }
 
 // ---------------------------------------------------------------- jobs
-int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance* in, int k, bool fp32,
-              long long deadline_ns, cudaStream_t st) {
+int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance* in, const JobParams& P,
+              bool fp32, long long deadline_ns, cudaStream_t st) {
     if (n < 1 || n > MAX_BATCH) return EIK_EINVAL;
+    const int k = P.k;
+    hj->bw_main.resize(n);
     std::vector<HostSources> hs((size_t)n);
     std::vector<char> stageF((size_t)n);
     hj->L.resize(n);
@@ -213,7 +212,10 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
         hj->arr[i] = a;
         const double* F = stageF[i] ? a.Fstage : in[i].F;
         double* out = hj->out_host[i] ? a.Ostage : in[i].U;
-        fill_inst_tables(L, a, fp32, descs[i].h, descs[i].bucket_width, &ictl_dev[i], &ictl_dev[n + i],
+        const double bw = descs[i].bucket_width;
+        hj->bw_main[i] = bw != 0.0 ? bw : P.w_main;
+        fill_inst_tables(L, a, fp32, descs[i].h, bw != 0.0 ? bw : P.w_first, hj->bw_main[i], &ictl_dev[i],
+                         &ictl_dev[n + i],
                          &res_dev[i], F, out, hj->shift[i], &aux_h[i], &desc_main_h[i], &desc_f32_h[i], &ok);
         blk_pre_h[i] = boff;
         boff += ((L.nyp + 7) / 8) * ((L.nxp + 31) / 32);
@@ -311,7 +313,8 @@ int finish_job(HostJob* hj, const eik_plan_desc* descs, cudaStream_t st, double 
     int first_err = EIK_OK;
     for (int i = 0; i < n; ++i) {
         eik_stats s;
-        job_stats(hj->L[i], &descs[i], j.fp32, &ic[i], &ic[n + i], &g[0], &g[1], &r[i], hj->shift[i], ms, &s);
+        job_stats(hj->L[i], &descs[i], j.fp32, &ic[i], &ic[n + i], &g[0], &g[1], &r[i], hj->shift[i],
+                  hj->bw_main[i], ms, &s);
         if (st_out) st_out[i] = s;
         if (s.status && !first_err) first_err = s.status;
     }
@@ -325,6 +328,38 @@ void free_job(HostJob* hj) {
     if (hj->zero_host) cudaFreeHost(hj->zero_host);
     hj->zero_host = nullptr;
     hj->zero_cap = 0;
+}
+
+int run_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance* in, const JobParams& P,
+            bool fp32, long long deadline_ns, int num_sms, cudaStream_t s, cudaEvent_t* ev,
+            eik_stats* st_out, float* t) {
+    int rc = build_job(hj, n, descs, in, P, fp32, deadline_ns, s);
+    int nl = 0;
+    if (!rc) {
+        cudaEventRecord(ev[0], s);
+        rc = enqueue_job(hj->j, num_sms, s, ev + 2, &nl);
+        cudaEventRecord(ev[1], s);
+    }
+    if (rc) {
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        return rc;
+    }
+    rc = finish_job(hj, descs, s, 0.0, st_out);
+    float ms = 0.f, p0 = 0.f, p1 = 0.f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    if (fp32) cudaEventElapsedTime(&p0, ev[2], ev[3]);
+    cudaEventElapsedTime(&p1, ev[4], ev[5]);
+    if (st_out)
+        for (int e = 0; e < n; ++e) {
+            st_out[e].ms = ms;  // the whole job (all of its instances)
+            st_out[e].mpts_per_s = ms > 0 ? (double)descs[e].nx * descs[e].ny / ms / 1000.0 : 0.0;
+            st_out[e].pass_ms[0] = p0;
+            st_out[e].pass_ms[1] = p1;
+            st_out[e].launches = nl;
+        }
+    if (t) t[0] = ms, t[1] = p0, t[2] = p1;
+    return rc;
 }
 
 }  // namespace eik
@@ -344,7 +379,8 @@ extern "C" int eik_plan_create(eik_plan* out, const eik_plan_desc* d, void* cuda
     eik_plan_s* p = new (std::nothrow) eik_plan_s();
     if (!p) return EIK_ENOMEM;
     p->d = *d;
-    p->d.cell_k = default_k(d);
+    p->P = choose_params(d, 1);
+    p->d.cell_k = p->P.k;
     if (cudaGetDevice(&p->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
         cudaGetLastError();
@@ -393,7 +429,7 @@ extern "C" int eik_solve(eik_plan p, const eik_instance* in, eik_stats* st) {
     cudaSetDevice(p->device);
     cudaStream_t s = p->stream;
     const bool fp32 = p->d.precision == EIK_FP32_REFINE;
-    int rc = build_job(&p->job, 1, &p->d, in, p->d.cell_k, fp32, p->d.deadline_ns, s);
+    int rc = build_job(&p->job, 1, &p->d, in, p->P, fp32, p->d.deadline_ns, s);
     if (rc) {
         cudaStreamSynchronize(s);
         cudaGetLastError();
@@ -461,16 +497,17 @@ extern "C" int eik_solve_batch(const eik_plan_desc* d, const eik_instance* in, i
     if (!ctx) return EIK_ENOMEM;
     std::lock_guard<std::mutex> lock(ctx->mu);
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    // group the instances by (k, precision); each group runs as jobs of at
-    // most MAX_BATCH instances, one persistent launch per pass
+    // group the instances by (cell_k as given, precision): instances that
+    // leave cell_k at 0 are grouped together and get the tuned choice for
+    // the group; each group runs as jobs of at most MAX_BATCH instances, one
+    // persistent launch per pass
     std::map<std::pair<int, int>, std::vector<int>> groups;
-    for (int i = 0; i < n_inst; ++i) groups[{default_k(&d[i]), d[i].precision}].push_back(i);
+    for (int i = 0; i < n_inst; ++i) groups[{d[i].cell_k, d[i].precision}].push_back(i);
     int first_err = EIK_OK;
     std::vector<eik_plan_desc> gd;
     std::vector<eik_instance> gi;
     std::vector<eik_stats> gs;
     for (auto& kv : groups) {
-        const int k = kv.first.first;
         const bool fp32 = kv.first.second == EIK_FP32_REFINE;
         const std::vector<int>& idx = kv.second;
         for (size_t b0 = 0; b0 < idx.size(); b0 += MAX_BATCH) {
@@ -480,36 +517,15 @@ extern "C" int eik_solve_batch(const eik_plan_desc* d, const eik_instance* in, i
             gs.resize(m);
             for (int e = 0; e < m; ++e) {
                 gd[e] = d[idx[b0 + e]];
-                gd[e].cell_k = k;
                 gi[e] = in[idx[b0 + e]];
             }
-            int rc = build_job(&ctx->job, m, gd.data(), gi.data(), k, fp32, d[0].deadline_ns, s);
-            if (!rc) {
-                cudaEventRecord(ctx->ev[0], s);
-                int nl = 0;
-                rc = enqueue_job(ctx->job.j, ctx->num_sms, s, ctx->ev + 2, &nl);
-                cudaEventRecord(ctx->ev[1], s);
-                if (!rc) {
-                    rc = finish_job(&ctx->job, gd.data(), s, 0.0, gs.data());
-                    float ms = 0.f, p0 = 0.f, p1 = 0.f;
-                    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
-                    if (fp32) cudaEventElapsedTime(&p0, ctx->ev[2], ctx->ev[3]);
-                    cudaEventElapsedTime(&p1, ctx->ev[4], ctx->ev[5]);
-                    for (int e = 0; e < m; ++e) {
-                        gs[e].ms = ms;  // the whole launch (all instances of the group)
-                        gs[e].mpts_per_s = ms > 0 ? (double)gd[e].nx * gd[e].ny / ms / 1000.0 : 0.0;
-                        gs[e].pass_ms[0] = p0;
-                        gs[e].pass_ms[1] = p1;
-                        gs[e].launches = nl;
-                        if (st) st[idx[b0 + e]] = gs[e];
-                    }
-                }
-            }
-            if (rc) {
-                cudaStreamSynchronize(s);
-                cudaGetLastError();
-                if (!first_err) first_err = rc;
-            }
+            const JobParams P = choose_params(gd.data(), m);
+            for (int e = 0; e < m; ++e) gd[e].cell_k = P.k;
+            int rc = run_job(&ctx->job, m, gd.data(), gi.data(), P, fp32, d[0].deadline_ns, ctx->num_sms, s,
+                             ctx->ev, gs.data(), nullptr);
+            if (st)
+                for (int e = 0; e < m; ++e) st[idx[b0 + e]] = gs[e];
+            if (rc && !first_err) first_err = rc;
         }
     }
     return first_err;

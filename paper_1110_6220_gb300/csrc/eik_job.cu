@@ -119,7 +119,8 @@ static void fill_desc(InstDesc* d, const Layout& L, void* U, const void* f, bool
     d->delta = bucket_width;
 }
 
-void fill_inst_tables(const Layout& L, const InstArrays& a, bool fp32, double h, double bucket_width,
+void fill_inst_tables(const Layout& L, const InstArrays& a, bool fp32, double h, double bw_first,
+                      double bw_main,
                       Ctl* ictl_first, Ctl* ictl_main, ResidualOut* res, const double* F,
                       double* out, double shift, AuxInst* aux, InstDesc* desc_main, InstDesc* desc_f32,
                       bool* ok) {
@@ -127,10 +128,10 @@ void fill_inst_tables(const Layout& L, const InstArrays& a, bool fp32, double h,
     if (fp32) {
         // 4-byte values: a box row of k+2 floats is not a multiple of 16
         // bytes, so the FP32 box is k+4 wide; pairs are 8-byte elements
-        fill_desc(desc_f32, L, a.U32, a.f32, false, K + 4, a, ictl_first, bucket_width, ok);
-        fill_desc(desc_main, L, a.Udf, a.fdf, true, K + 2, a, ictl_main, bucket_width, ok);
+        fill_desc(desc_f32, L, a.U32, a.f32, false, K + 4, a, ictl_first, bw_first, ok);
+        fill_desc(desc_main, L, a.Udf, a.fdf, true, K + 2, a, ictl_main, bw_main, ok);
     } else {
-        fill_desc(desc_main, L, a.U64, a.f64, true, K + 2, a, ictl_main, bucket_width, ok);
+        fill_desc(desc_main, L, a.U64, a.f64, true, K + 2, a, ictl_main, bw_main, ok);
     }
     std::memset((void*)aux, 0, sizeof(*aux));
     aux->F = F;
@@ -263,7 +264,8 @@ static void print_profile(const char* what, const Ctl* c) {
 
 void job_stats(const Layout& L, const eik_plan_desc* d, bool fp32, const Ctl* ictl_first,
                const Ctl* ictl_main, const Ctl* g_first, const Ctl* g_main, const ResidualOut* r,
-               double q_min, double ms, eik_stats* st) {
+               double q_min, double bw_main, double ms,
+               eik_stats* st) {
     eik_stats s;
     std::memset(&s, 0, sizeof(s));
     int status = g_main->status ? g_main->status : ictl_main->status;
@@ -291,7 +293,7 @@ void job_stats(const Layout& L, const eik_plan_desc* d, bool fp32, const Ctl* ic
     s.buckets = adv;
     s.cell_k = L.k;
     const double fmin = dval(ictl_main->fmin_f);
-    s.bucket_width = d->bucket_width > 0 ? d->bucket_width : 4.0 * L.k * fmin;
+    s.bucket_width = bw_main > 0 ? bw_main : (bw_main < 0 ? -bw_main : 4.0) * L.k * fmin;
     if (fp32) {
         // values on the device are U - q_min >= 0
         const double rr = dval(r->r_max), umax = dval(r->u_max);

@@ -68,7 +68,10 @@ struct JobDev {
 // Host-side pieces used to fill a JobDev's tables.
 bool make_map(CUtensorMap* tm, void* base, bool fp64, int width, int rows, int pitch_elems,
               int box_w, int box_h);
-void fill_inst_tables(const Layout& L, const InstArrays& a, bool fp32, double h, double bucket_width,
+// bw_first / bw_main: bucket width of the FP32 pass and of the FP64 (or
+// refinement) pass, > 0 absolute, < 0 relative to k min(h/F), 0 default.
+void fill_inst_tables(const Layout& L, const InstArrays& a, bool fp32, double h, double bw_first,
+                      double bw_main,
                       Ctl* ictl_first, Ctl* ictl_main, ResidualOut* res, const double* F,
                       double* out, double shift, AuxInst* aux, InstDesc* desc_main, InstDesc* desc_f32,
                       bool* ok);
@@ -85,6 +88,7 @@ bool job_pairable(const JobDev& j, int num_sms);
 // Fill *st for instance i from the control blocks copied back to the host.
 void job_stats(const Layout& L, const eik_plan_desc* d, bool fp32, const Ctl* ictl_first,
                const Ctl* ictl_main, const Ctl* g_first, const Ctl* g_main, const ResidualOut* r,
-               double q_min, double ms, eik_stats* st);
+               double q_min, double bw_main, double ms,
+               eik_stats* st);
 
 }  // namespace eik

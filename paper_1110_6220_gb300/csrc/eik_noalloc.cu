@@ -142,7 +142,9 @@ extern "C" int eik_solve_noalloc(const eik_plan_desc* d, const eik_instance* in,
     if (rc) return rc;
 
     eik_plan_desc dd = *d;
-    dd.cell_k = default_k(d);
+    const JobParams P = choose_params(d, 1);
+    dd.cell_k = P.k;
+    const double bw_main = d->bucket_width != 0.0 ? d->bucket_width : P.w_main;
     const Layout L = make_layout(d->nx, d->ny, dd.cell_k);
     StackSources ss;
     rc = prepare_stack_sources(L, in, &ss);
@@ -191,7 +193,7 @@ extern "C" int eik_solve_noalloc(const eik_plan_desc* d, const eik_instance* in,
     const double shift = ss.n ? ss.q_min : 0.0;
     bool ok = true;
     InstDesc unused;
-    fill_inst_tables(L, a, false, d->h, d->bucket_width, &ictl[0], &ictl[1], res, in->F, in->U, shift,
+    fill_inst_tables(L, a, false, d->h, bw_main, bw_main, &ictl[0], &ictl[1], res, in->F, in->U, shift,
                      &tb.aux, &tb.desc, &unused, &ok);
     if (!ok) return EIK_ECUDA;
     tb.cell_pre[0] = 0;
@@ -267,7 +269,8 @@ extern "C" int eik_solve_noalloc(const eik_plan_desc* d, const eik_instance* in,
     const double ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     eik_stats local;
-    job_stats(L, &dd, false, &host.c[0], &host.c[1], &host.c[2], &host.c[3], &host.r, shift, ms, &local);
+    job_stats(L, &dd, false, &host.c[0], &host.c[1], &host.c[2], &host.c[3], &host.r, shift, bw_main, ms,
+              &local);
     local.launches = nl;
     if (st) *st = local;
     return local.status;

@@ -25,8 +25,21 @@ struct HostSources {
     double q_min = 0.0;
 };
 
+// Cell size and bucket widths of a job.  Widths follow eik_plan_desc's
+// convention: > 0 absolute, < 0 relative (|w| * k * min(h/F)).  w_first is
+// the FP32 pass of FP32_REFINE, w_main the FP64 or refinement pass.
+struct JobParams {
+    int k;
+    double w_first, w_main;
+};
+
 bool desc_valid(const eik_plan_desc* d);
-int default_k(const eik_plan_desc* d);
+// Parameters of a job of n instances of one precision (eik_tune.cu): an
+// explicit cell_k wins; otherwise the tuned entry of the job's class, else
+// the built-in defaults.  Widths: the table's for the chosen k (an instance
+// whose bucket_width is set keeps its own, see build_job).
+JobParams choose_params(const eik_plan_desc* d, int n);
+int default_k(const eik_plan_desc* d);  // choose_params(d, 1).k
 int prepare_sources(const Layout& L, const eik_instance* in, HostSources* hs);
 bool is_device_ptr(const void* p);
 int grow(DevBuf* b, size_t bytes);
@@ -42,23 +55,32 @@ struct HostJob {
     std::vector<double> shift;   // per instance: min q
     std::vector<char> out_host;  // per instance: U is a host pointer
     std::vector<double*> out_user;
+    std::vector<double> bw_main;  // per instance: bucket width of the main pass
     char* zero_host = nullptr;   // readback buffer (pinned) of the zero region
     size_t zero_cap = 0;
 };
 
-// Lay out, upload and queue a job of n instances (same k and precision);
-// descs[i] gives nx, ny, h, bucket_width of instance i.
-int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance* in, int k, bool fp32,
-              long long deadline_ns, cudaStream_t st);
+// Lay out and upload a job of n instances (one k and precision); descs[i]
+// gives nx, ny, h of instance i, and its bucket width if set (else P's).
+int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance* in, const JobParams& P,
+              bool fp32, long long deadline_ns, cudaStream_t st);
 // Copy results to host buffers, read back control blocks, fill stats (may be
 // null).  Synchronises st.
 int finish_job(HostJob* hj, const eik_plan_desc* descs, cudaStream_t st, double ms, eik_stats* st_out);
 void free_job(HostJob* hj);
 
+// Build, queue and finish one job on st, timed with ev[6] (whole job, FP32
+// pass, main pass).  st_out: null or n entries, each with ms = the job's
+// device time.  t: null or {job, FP32 pass, main pass} in ms.
+int run_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance* in, const JobParams& P,
+            bool fp32, long long deadline_ns, int num_sms, cudaStream_t st, cudaEvent_t* ev,
+            eik_stats* st_out, float* t);
+
 }  // namespace eik
 
 struct eik_plan_s {
     eik_plan_desc d;
+    eik::JobParams P{};
     int device = 0;
     int num_sms = 0;
     cudaStream_t stream = nullptr;

@@ -76,11 +76,21 @@ struct eik_server_s {
 namespace {
 
 size_t request_bytes(const eik_plan_desc& d, const eik_instance& in) {
-    const Layout L = make_layout(d.nx, d.ny, default_k(&d));
     const bool fp32 = d.precision == EIK_FP32_REFINE;
-    // arrays + staging for host buffers + cell state, lists and tables
-    return inst_bytes(L, fp32, !is_device_ptr(in.F), !is_device_ptr(in.U)) + (size_t)L.J * 16 +
-           4 * sizeof(Ctl) + 4096;
+    const bool sF = !is_device_ptr(in.F), sU = !is_device_ptr(in.U);
+    // arrays + staging for host buffers + cell state, lists and tables; a
+    // request that leaves the cell size open is charged its largest choice
+    size_t most = 0;
+    for (int k : {8, 16, 32}) {
+        if (d.cell_k && k != d.cell_k) continue;
+        const Layout L = make_layout(d.nx, d.ny, k);
+        most = std::max(most, inst_bytes(L, fp32, sF, sU) + (size_t)L.J * 16);
+    }
+    if (d.cell_k && !most) {
+        const Layout L = make_layout(d.nx, d.ny, d.cell_k);
+        most = inst_bytes(L, fp32, sF, sU) + (size_t)L.J * 16;
+    }
+    return most + 4 * sizeof(Ctl) + 4096;
 }
 
 // Finish a slot whose job has completed (called with the lock held).
@@ -113,13 +123,13 @@ void complete_slot(eik_server_s* s, Slot& sl) {
 bool launch_slot(eik_server_s* s, Slot& sl, size_t held_by_others) {
     if (s->waiting.empty()) return false;
     const Request* head = s->waiting.front();
-    const int k = default_k(&head->d);
+    const int kreq = head->d.cell_k;  // 0: chosen for the job
     const int prec = head->d.precision;
     size_t bytes = 0;
     sl.reqs.clear();
     for (auto it = s->waiting.begin(); it != s->waiting.end() && (int)sl.reqs.size() < MAX_BATCH;) {
         Request* r = *it;
-        if (default_k(&r->d) == k && r->d.precision == prec) {
+        if (r->d.cell_k == kreq && r->d.precision == prec) {
             if (held_by_others + bytes + r->bytes > s->budget) break;  // keep FIFO order
             bytes += r->bytes;
             sl.reqs.push_back(r);
@@ -133,17 +143,18 @@ bool launch_slot(eik_server_s* s, Slot& sl, size_t held_by_others) {
     sl.insts.resize(sl.reqs.size());
     for (size_t e = 0; e < sl.reqs.size(); ++e) {
         sl.descs[e] = sl.reqs[e]->d;
-        sl.descs[e].cell_k = k;
         sl.insts[e] = sl.reqs[e]->in;
         sl.reqs[e]->state = 1;
     }
+    const JobParams P = choose_params(sl.descs.data(), (int)sl.descs.size());
+    for (auto& dd : sl.descs) dd.cell_k = P.k;
     // A job shares the SMs with the other slot's job only when both fit an
     // SM side by side; otherwise it runs alone with full occupancy once the
     // other slot is idle (two cooperative grids must never wait for each
     // other's blocks to become resident).
     JobDev probe{};
     probe.n = (int)sl.reqs.size();
-    probe.k = k;
+    probe.k = P.k;
     probe.fp32 = prec == EIK_FP32_REFINE;
     sl.shared = job_pairable(probe, s->num_sms);
     const Slot* other = nullptr;
@@ -161,7 +172,7 @@ bool launch_slot(eik_server_s* s, Slot& sl, size_t held_by_others) {
     }
     for (Request* r : sl.reqs)
         if (r->ready) cudaStreamWaitEvent(sl.stream, r->ready, 0);
-    int rc = build_job(&sl.job, (int)sl.reqs.size(), sl.descs.data(), sl.insts.data(), k,
+    int rc = build_job(&sl.job, (int)sl.reqs.size(), sl.descs.data(), sl.insts.data(), P,
                        prec == EIK_FP32_REFINE, head->d.deadline_ns, sl.stream);
     if (!rc) {
         sl.job.j.sm_cap = sl.shared ? 1 : 0;

@@ -575,7 +575,11 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
                 if (S.nn[i] == 0 && S.pre[i + 1] > S.pre[i]) {
                     const InstDesc& d = inst[i];
                     double delta = d.delta;
-                    if (!(delta > 0.0)) delta = 4.0 * (double)K * val_of(ld_cg(&d.ctl->fmin_f));
+                    if (!(delta > 0.0)) {
+                        // relative width: |delta| (default 4) cells' worth of the fastest crossing
+                        const double m = delta < 0.0 ? -delta : 4.0;
+                        delta = m * (double)K * val_of(ld_cg(&d.ctl->fmin_f));
+                    }
                     if (!(delta > 0.0) || !(delta < inf_of<double>())) delta = inf_of<double>();
                     const unsigned long long fm = ld_cg(&d.ctl->fmin[S.fs[i]]);
                     S.theta[i] = fm == KEY_UNSET ? KEY_UNSET : key_of(val_of(fm) + delta);

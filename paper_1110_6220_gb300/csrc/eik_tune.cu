@@ -1,0 +1,231 @@
+// eik_tune.cu -- the cell size k and the bucket width of each pass, per
+// class of job, and the autotuner that fills that table by timing trial
+// solves (eik_tune / eik_tune_save / eik_tune_load / eik_tune_reset).
+//
+// The paper leaves k to the user (Sec. 4's HCM/FHCM tables sweep it) and the
+// bucket width of Dial's method (Sec. 2) is a free parameter of the bucketed
+// release.  On the GPU both trade rounds (each ends in a grid barrier, so a
+// round costs a few microseconds however little it does) against repeated
+// cell visits.  The two passes of FP32_REFINE want different widths: the FP32
+// pass is round-bound and gains from wide buckets, the double-float
+// refinement pass repeats expensive visits when too many cells are released
+// at once.  A class of jobs is (precision, single or batch, the job's mean
+// side length rounded to a power of two).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "eik_common.cuh"
+#include "eik_plan.h"
+
+namespace eik {
+namespace {
+
+struct Key {
+    int prec, batch, side;
+    bool operator<(const Key& o) const {
+        return std::tie(prec, batch, side) < std::tie(o.prec, o.batch, o.side);
+    }
+};
+
+struct Entry {
+    int k;
+    double m_first, m_main;  // relative widths: bucket = m * k * min(h/F)
+    double ms;               // device time measured when tuned (0: built in)
+};
+
+std::mutex g_mu;
+std::map<Key, Entry> g_table;
+bool g_env_loaded = false;
+
+int side_class(const eik_plan_desc* d, int n) {
+    double pts = 0.0;
+    for (int i = 0; i < n; ++i) pts += (double)d[i].nx * d[i].ny;
+    pts /= std::max(n, 1);
+    return (int)std::lround(0.5 * std::log2(std::max(pts, 1.0)));
+}
+
+// Built-in choices, from sweeps on GB300 over k in {8, 16, 32} and relative
+// widths 2..256 (single 1025^2 sin-product grid in both precisions, 4097^2
+// checkerboard + maze, 512 uneven grids):
+//  - single grid, FP64: k = 8 with one wide bucket (pure label correcting in
+//    rounds) was fastest, 1.7x the time of 4-cell buckets;
+//  - single grid, FP32 + refinement: k = 8, FP32 pass at 256, refinement at 16;
+//  - batches: k = 16, FP32 pass at 64, refinement (and FP64) at 4.
+Entry builtin(int prec, bool batch) {
+    if (batch) return prec == EIK_FP32_REFINE ? Entry{16, 64.0, 4.0, 0.0} : Entry{16, 4.0, 4.0, 0.0};
+    return prec == EIK_FP32_REFINE ? Entry{8, 256.0, 16.0, 0.0} : Entry{8, 256.0, 256.0, 0.0};
+}
+
+int load_file(const char* path) {
+    FILE* f = std::fopen(path, "r");
+    if (!f) return EIK_EINVAL;
+    char line[256];
+    int rc = EIK_OK;
+    if (!std::fgets(line, sizeof line, f) || std::strncmp(line, "eik-tune 1", 10) != 0) {
+        rc = EIK_EINVAL;
+    } else {
+        std::map<Key, Entry> t;
+        while (std::fgets(line, sizeof line, f)) {
+            Key key;
+            Entry e;
+            if (std::sscanf(line, "%d %d %d %d %lf %lf %lf", &key.prec, &key.batch, &key.side, &e.k, &e.m_first,
+                            &e.m_main, &e.ms) != 7 ||
+                (e.k != 4 && e.k != 8 && e.k != 16 && e.k != 32 && e.k != 64) || !(e.m_first > 0) ||
+                !(e.m_main > 0)) {
+                rc = EIK_EINVAL;
+                break;
+            }
+            t[key] = e;
+        }
+        if (!rc)
+            for (auto& kv : t) g_table[kv.first] = kv.second;
+    }
+    std::fclose(f);
+    return rc;
+}
+
+void maybe_load_env() {  // g_mu held
+    if (g_env_loaded) return;
+    g_env_loaded = true;
+    const char* p = std::getenv("EIK_TUNE_FILE");
+    if (p && p[0]) load_file(p);
+}
+
+}  // namespace
+
+JobParams choose_params(const eik_plan_desc* d, int n) {
+    const int prec = d[0].precision;
+    const bool batch = n > 1;
+    Entry e = builtin(prec, batch);
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        maybe_load_env();
+        auto it = g_table.find(Key{prec, batch ? 1 : 0, side_class(d, n)});
+        if (it != g_table.end()) e = it->second;
+    }
+    JobParams P;
+    P.k = d[0].cell_k ? d[0].cell_k : e.k;
+    P.w_first = -e.m_first;
+    P.w_main = -e.m_main;
+    return P;
+}
+
+}  // namespace eik
+
+using namespace eik;
+
+extern "C" int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t n_inst, void* cuda_stream,
+                        eik_tune_result* out) {
+    if (!d || !in || n_inst < 1 || n_inst > MAX_BATCH) return EIK_EINVAL;
+    for (int i = 0; i < n_inst; ++i)
+        if (!desc_valid(&d[i]) || d[i].precision != d[0].precision) return EIK_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return EIK_ECUDA;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const bool fp32 = d[0].precision == EIK_FP32_REFINE;
+    // trials leave k and the widths to the tuner
+    std::vector<eik_plan_desc> dd(d, d + n_inst);
+    for (auto& x : dd) x.bucket_width = 0.0, x.cell_k = 0;
+    const JobParams before = choose_params(dd.data(), n_inst);
+
+    HostJob job;
+    cudaEvent_t ev[6] = {};
+    int rc = EIK_OK;
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) rc = EIK_ECUDA;
+    int trials = 0;
+    auto trial = [&](const JobParams& P, float* t) -> int {
+        for (auto& x : dd) x.cell_k = P.k;
+        ++trials;
+        return run_job(&job, n_inst, dd.data(), in, P, fp32, d[0].deadline_ns, sms, s, ev, nullptr, t);
+    };
+    float t_before[3] = {0, 0, 0};
+    if (!rc) {
+        float warm[3];
+        trial(before, warm);  // first launches load the kernels
+        rc = trial(before, t_before);
+    }
+    const double widths[] = {2.0, 4.0, 16.0, 64.0, 256.0};
+    struct Best {
+        int k = 0;
+        double mf = 0, mm = 0, est = 1e300;
+    } best;
+    if (!rc) {
+        for (int k : {8, 16, 32}) {
+            float t[3];
+            if (trial(JobParams{k, -4.0, -4.0}, t)) continue;  // warm-up of this k
+            double bf = 1e300, bm = 1e300, mf = 4.0, mm = 4.0;
+            std::vector<double> over;
+            for (double m : widths) {
+                if (trial(JobParams{k, -m, -m}, t)) continue;
+                if (fp32 && t[1] < bf) bf = t[1], mf = m;
+                if (t[2] < bm) bm = t[2], mm = m;
+                over.push_back(t[0] - t[1] - t[2]);
+            }
+            if (over.empty()) continue;
+            std::sort(over.begin(), over.end());
+            const double est = (fp32 ? bf : 0.0) + bm + over[over.size() / 2];
+            if (!fp32) mf = mm;
+            if (est < best.est) best = Best{k, mf, mm, est};
+        }
+    }
+    Entry chosen{before.k, -before.w_first, -before.w_main, t_before[0]};
+    float t_new[3] = {0, 0, 0};
+    if (!rc && best.k && trial(JobParams{best.k, -best.mf, -best.mm}, t_new) == EIK_OK &&
+        t_new[0] < t_before[0])
+        chosen = Entry{best.k, best.mf, best.mm, t_new[0]};
+    if (!rc) {
+        std::lock_guard<std::mutex> lock(g_mu);
+        maybe_load_env();
+        g_table[Key{d[0].precision, n_inst > 1 ? 1 : 0, side_class(dd.data(), n_inst)}] = chosen;
+    }
+    free_job(&job);
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    if (rc) return rc;
+    if (out) {
+        out->cell_k = chosen.k;
+        out->bucket_first = chosen.m_first;
+        out->bucket_main = chosen.m_main;
+        out->ms = chosen.ms;
+        out->ms_before = t_before[0];
+        out->trials = trials;
+    }
+    return EIK_OK;
+}
+
+extern "C" int eik_tune_save(const char* path) {
+    if (!path) return EIK_EINVAL;
+    std::lock_guard<std::mutex> lock(g_mu);
+    FILE* f = std::fopen(path, "w");
+    if (!f) return EIK_EINVAL;
+    std::fprintf(f, "eik-tune 1\n");
+    for (auto& kv : g_table)
+        std::fprintf(f, "%d %d %d %d %.17g %.17g %.17g\n", kv.first.prec, kv.first.batch, kv.first.side,
+                     kv.second.k, kv.second.m_first, kv.second.m_main, kv.second.ms);
+    return std::fclose(f) == 0 ? EIK_OK : EIK_EINVAL;
+}
+
+extern "C" int eik_tune_load(const char* path) {
+    if (!path) return EIK_EINVAL;
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_env_loaded = true;
+    return load_file(path);
+}
+
+extern "C" void eik_tune_reset(void) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_table.clear();
+    g_env_loaded = true;
+}

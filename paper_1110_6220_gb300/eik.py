@@ -64,6 +64,12 @@ class eik_stats(ctypes.Structure):
         return d
 
 
+class eik_tune_result(ctypes.Structure):
+    _fields_ = [("cell_k", ctypes.c_int32), ("bucket_first", ctypes.c_double),
+                ("bucket_main", ctypes.c_double), ("ms", ctypes.c_double),
+                ("ms_before", ctypes.c_double), ("trials", ctypes.c_int32)]
+
+
 eik_plan = ctypes.c_void_p
 eik_server = ctypes.c_void_p
 _P = ctypes.POINTER
@@ -81,24 +87,31 @@ _lib.eik_solve.restype = ctypes.c_int
 _lib.eik_solve_noalloc.argtypes = [_P(eik_plan_desc), _P(eik_instance), _P(eik_stats),
                                    ctypes.c_void_p]
 _lib.eik_solve_noalloc.restype = ctypes.c_int
-if hasattr(_lib, "eik_solve_batch"):
-    _lib.eik_solve_batch.argtypes = [_P(eik_plan_desc), _P(eik_instance), ctypes.c_int32,
-                                     _P(eik_stats), ctypes.c_void_p]
-    _lib.eik_solve_batch.restype = ctypes.c_int
-if hasattr(_lib, "eik_server_create"):
-    _lib.eik_server_create.argtypes = [_P(eik_server), ctypes.c_size_t, ctypes.c_int32,
-                                       ctypes.c_void_p]
-    _lib.eik_server_create.restype = ctypes.c_int
-    _lib.eik_submit.argtypes = [eik_server, _P(eik_plan_desc), _P(eik_instance),
-                                _P(ctypes.c_uint64)]
-    _lib.eik_submit.restype = ctypes.c_int
-    _lib.eik_poll.argtypes = [eik_server, ctypes.c_uint64, _P(eik_stats)]
-    _lib.eik_poll.restype = ctypes.c_int
-    _lib.eik_server_destroy.argtypes = [eik_server]
-    _lib.eik_server_destroy.restype = None
+_lib.eik_solve_batch.argtypes = [_P(eik_plan_desc), _P(eik_instance), ctypes.c_int32,
+                                 _P(eik_stats), ctypes.c_void_p]
+_lib.eik_solve_batch.restype = ctypes.c_int
+_lib.eik_tune.argtypes = [_P(eik_plan_desc), _P(eik_instance), ctypes.c_int32, ctypes.c_void_p,
+                          _P(eik_tune_result)]
+_lib.eik_tune.restype = ctypes.c_int
+_lib.eik_tune_save.argtypes = [ctypes.c_char_p]
+_lib.eik_tune_save.restype = ctypes.c_int
+_lib.eik_tune_load.argtypes = [ctypes.c_char_p]
+_lib.eik_tune_load.restype = ctypes.c_int
+_lib.eik_tune_reset.argtypes = []
+_lib.eik_tune_reset.restype = None
+_lib.eik_server_create.argtypes = [_P(eik_server), ctypes.c_size_t, ctypes.c_int32,
+                                   ctypes.c_void_p]
+_lib.eik_server_create.restype = ctypes.c_int
+_lib.eik_submit.argtypes = [eik_server, _P(eik_plan_desc), _P(eik_instance), _P(ctypes.c_uint64)]
+_lib.eik_submit.restype = ctypes.c_int
+_lib.eik_poll.argtypes = [eik_server, ctypes.c_uint64, _P(eik_stats)]
+_lib.eik_poll.restype = ctypes.c_int
+_lib.eik_server_destroy.argtypes = [eik_server]
+_lib.eik_server_destroy.restype = None
 
 SYMBOLS = ["eik_strerror", "eik_plan_create", "eik_plan_destroy", "eik_plan_workspace_bytes",
-           "eik_solve", "eik_solve_noalloc", "eik_solve_batch", "eik_server_create", "eik_submit", "eik_poll",
+           "eik_solve", "eik_solve_noalloc", "eik_solve_batch", "eik_tune", "eik_tune_save",
+           "eik_tune_load", "eik_tune_reset", "eik_server_create", "eik_submit", "eik_poll",
            "eik_server_destroy"]
 
 
@@ -151,6 +164,27 @@ def eik_solve_batch(descs, insts, cuda_stream=None):
     S = (eik_stats * n)()
     rc = _lib.eik_solve_batch(D, I, n, S, _stream_ptr(cuda_stream))
     return rc, list(S)
+
+
+def eik_tune(descs, insts, cuda_stream=None):
+    n = len(descs)
+    D = (eik_plan_desc * n)(*descs)
+    I = (eik_instance * n)(*insts)
+    r = eik_tune_result()
+    rc = _lib.eik_tune(D, I, n, _stream_ptr(cuda_stream), ctypes.byref(r))
+    return rc, r
+
+
+def eik_tune_save(path) -> int:
+    return _lib.eik_tune_save(os.fsencode(path))
+
+
+def eik_tune_load(path) -> int:
+    return _lib.eik_tune_load(os.fsencode(path))
+
+
+def eik_tune_reset() -> None:
+    _lib.eik_tune_reset()
 
 
 def eik_server_create(hbm_budget_bytes: int, max_inflight: int = 0, cuda_stream=None) -> eik_server:

@@ -57,3 +57,39 @@ def test_plan_create_rejects_bad_descriptors_before_touching_cuda():
     with pytest.raises(eik.EikError) as e:
         eik.eik_plan_create(eik.make_desc(129, 1, 0.1))
     assert e.value.code == eik.EIK_EINVAL
+
+
+def test_tune_table_round_trip_and_use_without_gpu(tmp_path):
+    """A loaded table decides k for descriptors that leave it open (seen
+    through the workspace size, which needs no GPU); save writes back what
+    was loaded; malformed files merge nothing; reset restores the built-in
+    choice."""
+    from paper_1110_6220_gb300 import eik
+    eik.eik_tune_reset()
+    d0 = eik.make_desc(1025, 1025, 1 / 1024, 0, eik.EIK_FP64)
+    w_auto = eik.eik_plan_workspace_bytes(d0)
+    w8 = eik.eik_plan_workspace_bytes(eik.make_desc(1025, 1025, 1 / 1024, 8, eik.EIK_FP64))
+    w32 = eik.eik_plan_workspace_bytes(eik.make_desc(1025, 1025, 1 / 1024, 32, eik.EIK_FP64))
+    assert w_auto == w8 and w32 != w8  # built-in: k = 8 for one FP64 grid
+    f = tmp_path / "tune.txt"
+    # class: FP64, single grid, side 2^10
+    f.write_text("eik-tune 1\n0 0 10 32 8 8 1.5\n")
+    assert eik.eik_tune_load(str(f)) == 0
+    assert eik.eik_plan_workspace_bytes(d0) == w32
+    # another side class keeps the built-in choice
+    assert eik.eik_plan_workspace_bytes(eik.make_desc(129, 129, 1 / 128, 0, eik.EIK_FP64)) == \
+        eik.eik_plan_workspace_bytes(eik.make_desc(129, 129, 1 / 128, 8, eik.EIK_FP64))
+    g = tmp_path / "out.txt"
+    assert eik.eik_tune_save(str(g)) == 0
+    lines = g.read_text().splitlines()
+    assert lines[0] == "eik-tune 1"
+    assert [float(x) for x in lines[1].split()] == [0, 0, 10, 32, 8, 8, 1.5]
+    bad = tmp_path / "bad.txt"
+    bad.write_text("eik-tune 1\n1 0 10 12 8 8 1.0\n")  # k = 12 is not a cell size
+    assert eik.eik_tune_load(str(bad)) == eik.EIK_EINVAL
+    bad.write_text("something else\n")
+    assert eik.eik_tune_load(str(bad)) == eik.EIK_EINVAL
+    assert eik.eik_tune_load(str(tmp_path / "missing.txt")) == eik.EIK_EINVAL
+    assert eik.eik_plan_workspace_bytes(d0) == w32
+    eik.eik_tune_reset()
+    assert eik.eik_plan_workspace_bytes(d0) == w8
