@@ -160,9 +160,14 @@ int eik_solve_batch(const eik_plan_desc* d, const eik_instance* in, int32_t n_in
  * built-in choices measured on GB300.  Plans take the choice at
  * eik_plan_create; batches and served jobs at each call.
  *
+ * Each pass runs either in bucketed rounds (a grid barrier per round) or
+ * round-free: warps take cells from a device-side ring as they come, in
+ * first-in first-out order, with no buckets.
+ *
  * eik_tune: time trial solves of the given instances, run as one job like
- * eik_solve_batch (n_inst = 1: like eik_solve), over k in {8, 16, 32} and
- * relative widths {2, 4, 16, 64, 256}, timing each pass on its own; record
+ * eik_solve_batch (n_inst = 1: like eik_solve), over k in {8, 16, 32}, rounds
+ * with relative widths {2, 4, 16, 64, 256} and the round-free schedule,
+ * timing each pass on its own; record
  * the fastest choice for the job's class (never one slower than the choice
  * in force before) and return it.  Blocks; about twenty solves.  Each U
  * receives a valid result.  All descriptors must have one precision;
@@ -173,6 +178,8 @@ typedef struct {
     int32_t cell_k;        /* chosen k */
     double bucket_first;   /* relative width of the FP32 pass (FP32_REFINE) */
     double bucket_main;    /* relative width of the FP64 / refinement pass */
+    int32_t async_first;   /* 1: the FP32 pass runs round-free (no buckets) */
+    int32_t async_main;    /* 1: the FP64 / refinement pass runs round-free */
     double ms;             /* device time of the job with the chosen values */
     double ms_before;      /* device time with the choice in force before */
     int32_t trials;        /* solves run */
@@ -180,7 +187,7 @@ typedef struct {
 
 int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t n_inst, void* cuda_stream,
              eik_tune_result* out);
-/* Write / merge the table as text ("eik-tune 1" then one line per class).
+/* Write / merge the table as text ("eik-tune 2" then one line per class).
  * EIK_EINVAL if the file cannot be written / read or is malformed (nothing
  * merged then). */
 int eik_tune_save(const char* path);

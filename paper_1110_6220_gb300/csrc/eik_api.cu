@@ -170,14 +170,20 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     const size_t image_bytes = 2 * t_desc + t_aux + t_own_int + t_pre + t_own_full + t_src;
     const size_t z_ctl = a256((size_t)(2 * n + 2) * sizeof(Ctl) + (size_t)n * sizeof(ResidualOut));
     const size_t zero_bytes = z_ctl + a256(Jtot * 4) * 2;
-    const size_t total = image_bytes + zero_bytes + a256(Jtot * 8) + ibytes + 256;
+    // ring of the round-free schedule: a power of two >= twice the job's
+    // cells and the warps of a launch, behind its three counters
+    size_t Q = 8192;
+    while (Q < 2 * Jtot) Q <<= 1;
+    const size_t ring_bytes = a256(384 + Q * 8);
+    const size_t total = image_bytes + zero_bytes + a256(Jtot * 8) + ring_bytes + ibytes + 256;
     int rc = grow(&hj->arena, total);
     if (rc) return rc;
     char* base = (char*)hj->arena.p;
     char* img_dev = base;
     char* zero_dev = base + image_bytes;
     char* cval_dev = zero_dev + zero_bytes;
-    char* inst_dev = cval_dev + a256(Jtot * 8);
+    char* ring_dev = cval_dev + a256(Jtot * 8);
+    char* inst_dev = ring_dev + ring_bytes;
 
     hj->image.assign(image_bytes, 0);
     char* img = hj->image.data();
@@ -217,6 +223,8 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
         fill_inst_tables(L, a, fp32, descs[i].h, bw != 0.0 ? bw : P.w_first, hj->bw_main[i], &ictl_dev[i],
                          &ictl_dev[n + i],
                          &res_dev[i], F, out, hj->shift[i], &aux_h[i], &desc_main_h[i], &desc_f32_h[i], &ok);
+        desc_main_h[i].cell_base = (int)coff;
+        if (fp32) desc_f32_h[i].cell_base = (int)coff;
         blk_pre_h[i] = boff;
         boff += ((L.nyp + 7) / 8) * ((L.nxp + 31) / 32);
         blk_full_h[i] = bfull;
@@ -274,6 +282,11 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     j.ncell_total = (int)ncs;
     j.deadline_ns = deadline_ns;
     j.sm_cap = 0;
+    j.async_first = P.async_first;
+    j.async_main = P.async_main;
+    j.qctl = (unsigned*)ring_dev;
+    j.ring = (unsigned long long*)(ring_dev + 384);
+    j.ring_mask = (unsigned)(Q - 1);
     j.zero_base = zero_dev;
     j.zero_bytes = zero_bytes;
     j.cval_all = cval_all;
@@ -369,7 +382,9 @@ extern "C" size_t eik_plan_workspace_bytes(const eik_plan_desc* d) {
     if (!desc_valid(d)) return 0;
     const Layout L = make_layout(d->nx, d->ny, default_k(d));
     const bool fp32 = d->precision == EIK_FP32_REFINE;
-    return inst_bytes(L, fp32, true, true) + (size_t)L.J * 16 + 64 * 1024;
+    size_t Q = 8192;
+    while (Q < 2 * (size_t)L.J) Q <<= 1;
+    return inst_bytes(L, fp32, true, true) + (size_t)L.J * 16 + Q * 8 + 64 * 1024;
 }
 
 extern "C" int eik_plan_create(eik_plan* out, const eik_plan_desc* d, void* cuda_stream) {

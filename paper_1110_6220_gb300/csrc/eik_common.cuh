@@ -82,13 +82,14 @@ struct __align__(64) InstDesc {
     void* U;                      // double*, float* or float2* (double-float pairs)
     const void* f;                // f in U's representation
     unsigned long long* cval;     // ordered cell-value keys
-    int* qflag;                   // 1 while the cell sits in a list
+    int* qflag;                   // rounds: 1 while queued; async: bit 0 requested, bit 1 running
     int* visits;                  // removals so far
     int* lists;                   // 5 * J ints: near[3], far[2]
     Ctl* ctl;                     // this instance's lists, counters and status
     int upitch;
     int cxn, cyn, J;
-    double delta;                 // bucket width; <= 0: 4 k min f (from ctl->fmin_f)
+    double delta;                 // bucket width; < 0: |delta| k min f (from ctl->fmin_f); 0: 4 k min f
+    int cell_base;                // index of this instance's first cell among the job's cells
 };
 
 constexpr int MAX_BATCH = 2048;   // instances per persistent launch
@@ -99,6 +100,15 @@ struct SolveParams {
     Ctl* gctl;                    // grid barrier, abort flag, launch status, rounds
     long long deadline_ns;        // relative to kernel start
     int profile;                  // accumulate gctl->prof
+    // asynchronous scheduling only: ring of (sequence << 32 | global cell)
+    // words, ring_mask + 1 (a power of two) >= twice the job's cells and the
+    // launch's warps; the global
+    // cell index of (instance i, cell c) is inst[i].cell_base + c, and
+    // cell_pre (n_inst + 1 entries) holds the instances' first indices
+    unsigned long long* ring;
+    unsigned int ring_mask;
+    const int* cell_pre;
+    unsigned int* qctl;           // ring head, tail and pending count, 128 bytes apart
 };
 
 // ---------------------------------------------------------------- host launchers
@@ -111,12 +121,14 @@ struct LaunchShape {
 };
 
 // one per arithmetic mode (eik_solver_f64.cu, eik_solver_f32.cu, eik_solver_df.cu)
-int solver_shape_f64(int k, int num_sms, int n_inst, int sm_cap, LaunchShape* out);
-int solver_shape_f32(int k, int num_sms, int n_inst, int sm_cap, LaunchShape* out);
-int solver_shape_df(int k, int num_sms, int n_inst, int sm_cap, LaunchShape* out);
-cudaError_t launch_solver_f64(int k, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
-cudaError_t launch_solver_f32(int k, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
-cudaError_t launch_solver_df(int k, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
+int solver_shape_f64(int k, int num_sms, int n_inst, int sm_cap, bool async, LaunchShape* out);
+int solver_shape_f32(int k, int num_sms, int n_inst, int sm_cap, bool async, LaunchShape* out);
+int solver_shape_df(int k, int num_sms, int n_inst, int sm_cap, bool async, LaunchShape* out);
+// async: the round-free kernel (k_solve_async, cell sizes >= 8) instead of
+// the bucketed rounds (k_solve)
+cudaError_t launch_solver_f64(int k, bool async, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
+cudaError_t launch_solver_f32(int k, bool async, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
+cudaError_t launch_solver_df(int k, bool async, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
 
 // aux kernels (eik_aux.cu)
 // ---------------------------------------------------------------- aux kernels

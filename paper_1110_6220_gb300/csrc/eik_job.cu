@@ -192,13 +192,18 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
     p.n_inst = n;
     p.deadline_ns = j.deadline_ns > 0 ? j.deadline_ns : 20000000000ll;
     p.profile = profiling();
+    p.ring = j.ring;
+    p.ring_mask = j.ring_mask;
+    p.cell_pre = j.cell_pre;
+    p.qctl = j.qctl;
+    const bool af = j.async_first && j.ring && j.k >= 8, am = j.async_main && j.ring && j.k >= 8;
     LaunchShape shape;
     if (j.fp32) {
-        if (solver_shape_f32(j.k, num_sms, n, j.sm_cap, &shape)) return EIK_ECUDA;
+        if (solver_shape_f32(j.k, num_sms, n, j.sm_cap, af, &shape)) return EIK_ECUDA;
         p.inst = j.desc_f32;
         p.gctl = j.gctl;
         if (ev) cudaEventRecord(ev[0], st);
-        if (launch_solver_f32(j.k, p, shape, st) != cudaSuccess) return EIK_ECUDA;
+        if (launch_solver_f32(j.k, af, p, shape, st) != cudaSuccess) return EIK_ECUDA;
         if (ev) cudaEventRecord(ev[1], st);
         ++nl;
         // refinement pass (double-float) seeded from the FP32 result
@@ -207,21 +212,21 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
             cudaSuccess)
             return EIK_ECUDA;
         nl += 2;
-        if (solver_shape_df(j.k, num_sms, n, j.sm_cap, &shape)) return EIK_ECUDA;
+        if (solver_shape_df(j.k, num_sms, n, j.sm_cap, am, &shape)) return EIK_ECUDA;
         p.inst = j.desc_main;
         p.gctl = j.gctl + 1;
         if (ev) cudaEventRecord(ev[2], st);
-        if (launch_solver_df(j.k, p, shape, st) != cudaSuccess) return EIK_ECUDA;
+        if (launch_solver_df(j.k, am, p, shape, st) != cudaSuccess) return EIK_ECUDA;
         if (ev) cudaEventRecord(ev[3], st);
         ++nl;
         if (launch_residual(j.aux, j.blk_pre, n, j.nblocks, st) != cudaSuccess) return EIK_ECUDA;
         ++nl;
     } else {
-        if (solver_shape_f64(j.k, num_sms, n, j.sm_cap, &shape)) return EIK_ECUDA;
+        if (solver_shape_f64(j.k, num_sms, n, j.sm_cap, am, &shape)) return EIK_ECUDA;
         p.inst = j.desc_main;
         p.gctl = j.gctl + 1;
         if (ev) cudaEventRecord(ev[2], st);
-        if (launch_solver_f64(j.k, p, shape, st) != cudaSuccess) return EIK_ECUDA;
+        if (launch_solver_f64(j.k, am, p, shape, st) != cudaSuccess) return EIK_ECUDA;
         if (ev) cudaEventRecord(ev[3], st);
         ++nl;
     }
@@ -234,11 +239,12 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
 bool job_pairable(const JobDev& j, int num_sms) {
     LaunchShape a{}, b{};
     if (j.fp32) {
-        if (solver_shape_f32(j.k, num_sms, j.n, 1, &a) || solver_shape_df(j.k, num_sms, j.n, 1, &b))
+        if (solver_shape_f32(j.k, num_sms, j.n, 1, j.async_first, &a) ||
+            solver_shape_df(j.k, num_sms, j.n, 1, j.async_main, &b))
             return false;
         return a.per_sm >= 2 && b.per_sm >= 2;
     }
-    if (solver_shape_f64(j.k, num_sms, j.n, 1, &a)) return false;
+    if (solver_shape_f64(j.k, num_sms, j.n, 1, j.async_main, &a)) return false;
     return a.per_sm >= 2;
 }
 

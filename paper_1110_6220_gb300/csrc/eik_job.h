@@ -56,6 +56,10 @@ struct JobDev {
     int nsrc_total, ncell_total;
     long long deadline_ns;
     int sm_cap;                 // > 0: at most this many blocks per SM (room for other jobs)
+    bool async_first, async_main;  // round-free schedule (k_solve_async) for the FP32 / main pass
+    unsigned long long* ring;   // async: ring of ring_mask + 1 words
+    unsigned ring_mask;
+    unsigned* qctl;             // async: head, tail, pending (384 bytes before the ring)
     // everything that enqueue_job zeroes before a solve: [zero_base, + zero_bytes)
     void* zero_base;
     size_t zero_bytes;

@@ -31,6 +31,7 @@ struct HostSources {
 struct JobParams {
     int k;
     double w_first, w_main;
+    bool async_first = false, async_main = false;  // round-free schedule per pass (k >= 8)
 };
 
 bool desc_valid(const eik_plan_desc* d);

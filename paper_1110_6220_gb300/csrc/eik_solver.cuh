@@ -447,23 +447,331 @@ __device__ __forceinline__ void flush_counters(const InstDesc* inst, int i, unsi
     v = sw = l = 0;
 }
 
-// ---------------------------------------------------------------- the kernel
+// ---------------------------------------------------------------- one visit
 // PROF_MARK(i): add the cycles since the last mark to phase i (profiling only)
 #define PROF_MARK(i)                                    \
     do {                                                \
-        if (p.profile) {                                \
+        if (prof_on) {                                  \
             const long long now_ = clock64();           \
             pacc[i] += (unsigned long long)(now_ - pt); \
             pt = now_;                                  \
         }                                               \
     } while (0)
 
+// Per-warp state of the solver kernels: the warp's tile buffers in shared
+// memory, its lane roles and its counters.
+template <int MODE, int K>
+struct WarpState {
+    using C = TileCfg<MODE, K>;
+    using T = typename C::T;
+    using FT = typename C::FT;
+    int lane, g, dl, dir, rl;
+    bool sx, sy;
+    unsigned char* wbase;
+    uint64_t* bar;
+    unsigned long long* masks;
+    T* tU;
+    const FT* tF;
+    const double* tG;
+    unsigned gmask;
+    uint32_t phase;
+    // counters gather per lane while the instance stays the same (one flush
+    // per instance change instead of three atomics per visit on one address)
+    int acc_inst;
+    unsigned long long acc_visits, acc_sweeps, acc_lane, st_lane;
+
+    __device__ __forceinline__ void init(unsigned char* smem) {
+        lane = threadIdx.x & 31;
+        const int warp = threadIdx.x >> 5;
+        wbase = smem + warp * C::WARP_BYTES;
+        bar = reinterpret_cast<uint64_t*>(wbase + C::BAR_OFF);
+        masks = reinterpret_cast<unsigned long long*>(wbase + C::MASK_OFF);
+        g = lane / C::LPC;    // which of the warp's cells this lane works on
+        dl = lane % C::LPC;   // lane within the cell
+        dir = dl / C::LPD;    // sweep direction of this lane (Alg. FSM_order)
+        rl = dl % C::LPD;     // first tile row of this lane
+        sx = dir <= 1;                  // i increasing
+        sy = (dir == 0) || (dir == 3);  // j increasing
+        unsigned char* gbase = wbase + g * C::GROUP_BYTES;
+        tU = reinterpret_cast<T*>(gbase);
+        tF = reinterpret_cast<const FT*>(gbase + C::F_OFF);
+        tG = reinterpret_cast<const double*>(gbase + C::X_OFF);
+        gmask = C::LPC == 32 ? 0xffffffffu : (((1u << C::LPC) - 1u) << (g * C::LPC));
+        phase = 0;
+        acc_inst = -1;
+        acc_visits = acc_sweeps = acc_lane = st_lane = 0;
+        if (lane == 0) {
+            mbar_init(bar, 1);
+            fence_mbar_init();
+        }
+    }
+};
+
+// Solve the warp's cells cg[0..CPW) of instances ig[] (cell -1: none), which
+// the caller has already claimed (flag cleared, fences issued): TMA load of
+// each tile with its halo, passes of four concurrent directional sweeps to
+// the fixed point, write-back of the changed nodes, then the activation test
+// of every side (Alg. generic_LC_cells) with the neighbour's cell value
+// (eq. cell_value, min-updated here).  For each side with a neighbour, one
+// lane calls act(d, nc, key, old, activate): key/old the proposed and the
+// previous cell value of neighbour cell nc of instance d, activate the
+// outcome of the test -- the scheduler's part.  c, ii, first: this lane's
+// cell, its instance and whether this is the cell's first removal.  Returns
+// false when the TMA wait gave up (abort raised).
+template <int MODE, int K, class Act>
+__device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDesc* inst, Ctl* gctl,
+                                            unsigned long long deadline, int c, int ii, int first,
+                                            const int* cg, const int* ig, int prof_on,
+                                            unsigned long long* pacc, long long& pt, Act&& act) {
+    using C = TileCfg<MODE, K>;
+    using T = typename C::T;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = w.lane, g = w.g, dl = w.dl, dir = w.dir, rl = w.rl;
+    const bool sx = w.sx, sy = w.sy;
+    T* tU = w.tU;
+    const auto* tF = w.tF;
+    const double* tG = w.tG;
+    unsigned char* wbase = w.wbase;
+    unsigned long long* masks = w.masks;
+    const InstDesc& d = inst[ii];
+    Ctl* ictl = d.ctl;
+    const int cxn = d.cxn, cyn = d.cyn;
+
+    // ---- TMA: U box (cell + halo) and f box (+ halo) into shared memory
+    if (lane == 0) {
+        int nvalid = 0;
+#pragma unroll
+        for (int gg = 0; gg < C::CPW; ++gg) nvalid += cg[gg] >= 0;
+        mbar_arrive_expect_tx(w.bar, (uint32_t)(nvalid * C::TX_BYTES));
+#pragma unroll
+        for (int gg = 0; gg < C::CPW; ++gg) {
+            if (cg[gg] >= 0) {
+                const InstDesc& dg = inst[ig[gg]];
+                const int cxg = cg[gg] % dg.cxn, cyg = cg[gg] / dg.cxn;
+                unsigned char* gb = wbase + gg * C::GROUP_BYTES;
+                tma_load_2d(gb, &dg.tmU, cxg * K, cyg * K, w.bar);
+                tma_load_2d(gb + C::F_OFF, &dg.tmF, cxg * K, cyg * K, w.bar);
+            }
+        }
+    }
+    {
+        bool got = false;
+        unsigned spins = 0;
+        for (;;) {
+            if (mbar_try_wait(w.bar, w.phase)) { got = true; break; }
+            if ((++spins & 255u) == 0 && gtimer() > deadline) break;
+        }
+        if (!got) {
+            fail(gctl, EIK_ETIMEDOUT, 0x3000000ull);
+            // let our own copies land before the block leaves (bounded)
+            const unsigned long long d2 = gtimer() + 1000000000ull;
+            while (!mbar_try_wait(w.bar, w.phase) && gtimer() < d2) {
+            }
+            return false;
+        }
+    }
+    w.phase ^= 1u;
+    PROF_MARK(3);
+    if constexpr (MODE == MODE_F64) {
+        // 2 f^2 per node, once per visit (saves two FP64 ops per update)
+        for (int e = lane; e < C::CPW * K * K; e += 32) {
+            const int gg = e / (K * K), r = e - gg * (K * K);
+            const int jj = r / K, i2 = r - jj * K;
+            unsigned char* gb = wbase + gg * C::GROUP_BYTES;
+            const double fv = reinterpret_cast<const double*>(gb + C::F_OFF)[(jj + 1) * C::BW + i2 + 1];
+            reinterpret_cast<double*>(gb + C::X_OFF)[r] = 2.0 * fv * fv;
+        }
+        __syncwarp();
+    }
+
+    // ---- passes of four concurrent directional sweeps until a pass
+    // changes nothing or the fixed-point check finds nothing to improve
+    unsigned long long chg[C::RPL];
+#pragma unroll
+    for (int m = 0; m < C::RPL; ++m) chg[m] = 0ull;
+    int gsweeps = 0;
+    bool gdone = c < 0;
+    int s = 0;
+    for (; s < C::MAX_PASSES; ++s) {
+        bool changed = false;
+        for (int t2 = 0; t2 < 2 * K - 1; ++t2) {
+#pragma unroll
+            for (int m = 0; m < C::RPL; ++m) {
+                const int j = rl + C::LPD * m;
+                const int jj = sy ? j : K - 1 - j;
+                const int ii2 = t2 - jj;
+                if (c >= 0 && ii2 >= 0 && ii2 < K) {
+                    const int i = sx ? ii2 : K - 1 - ii2;
+                    T cand, old;
+                    if (node_candidate<MODE, K>(tU, tF, tG, i, j, cand, old) && lt(cand, old)) {
+                        tU[(j + 1) * C::BW + (i + 1)] = cand;
+                        chg[m] |= 1ull << i;
+                        changed = true;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        const unsigned any = __ballot_sync(FULL, changed);
+        if (!gdone) {
+            gsweeps += 4;
+            if (!(any & w.gmask)) gdone = true;
+        }
+        bool imp = false;
+        if (!gdone) imp = tile_improvable<MODE, K>(tU, tF, tG, dl);
+        const unsigned anyi = __ballot_sync(FULL, imp);
+        if (!gdone && !(anyi & w.gmask)) {
+            gdone = true;
+            ++gsweeps;  // counted like the confirming sweep it replaces
+        }
+        if (__ballot_sync(FULL, !gdone) == 0u) break;
+        if ((s & 15) == 15) {
+            // values only decrease, so stopping early leaves valid upper
+            // bounds; the expired deadline aborts the launch
+            const unsigned long long now = __shfl_sync(FULL, gtimer(), 0);
+            if (now > deadline) {
+                if (lane == 0) fail(gctl, EIK_ETIMEDOUT, 0x4000000ull);
+                s = C::MAX_PASSES + 1;
+                break;
+            }
+        }
+    }
+    if (s == C::MAX_PASSES && dl == 0 && c >= 0) {
+        atomicCAS(&ictl->status, 0, EIK_ENOTCONVERGED);
+        fail(gctl, EIK_ENOTCONVERGED, (unsigned)c);
+    }
+    if (dl == 0 && c >= 0) {
+        // node evaluations executed for this cell (lock-step passes included)
+        const unsigned long long ev =
+            (unsigned long long)(s < C::MAX_PASSES ? s + 1 : C::MAX_PASSES) * 4 * K * K;
+        if (ii != w.acc_inst) {
+            flush_counters(inst, w.acc_inst, w.acc_visits, w.acc_sweeps, w.acc_lane);
+            w.acc_inst = ii;
+        }
+        w.acc_visits += 1;
+        w.acc_sweeps += (unsigned long long)gsweeps;
+        w.acc_lane += ev;
+        w.st_lane += ev;
+    }
+    PROF_MARK(4);
+
+    // ---- changed-node masks per row: union over the four directions
+#pragma unroll
+    for (int m = 0; m < C::RPL; ++m) {
+        unsigned long long v = chg[m];
+        v |= __shfl_xor_sync(FULL, v, C::LPD);
+        v |= __shfl_xor_sync(FULL, v, 2 * C::LPD);
+        if (dir == 0) masks[g * K + rl + C::LPD * m] = v;
+    }
+    __syncwarp();
+    // ---- write back the nodes that changed (coalesced across lanes)
+    for (int e = lane; e < C::CPW * K * K; e += 32) {
+        const int gg = e / (K * K);
+        const int rem = e - gg * K * K;
+        const int j = rem / K, i = rem - j * K;
+        int cc = cg[0], ic = ig[0];
+#pragma unroll
+        for (int q = 1; q < C::CPW; ++q)
+            if (gg == q) { cc = cg[q]; ic = ig[q]; }
+        if (cc >= 0 && ((masks[gg * K + j] >> i) & 1ull)) {
+            const InstDesc& dc = inst[ic];
+            const int cx = cc % dc.cxn, cy = cc / dc.cxn;
+            const T* gU = reinterpret_cast<const T*>(wbase + gg * C::GROUP_BYTES);
+            reinterpret_cast<T*>(dc.U)[(size_t)(cy * K + j + 1) * dc.upitch + (size_t)(cx * K + i + 1)] =
+                gU[(j + 1) * C::BW + (i + 1)];
+        }
+    }
+    __threadfence();  // release the new values before any activation
+    fence_proxy_async_global();
+    __syncwarp();
+    PROF_MARK(5);
+
+    // ---- activation of the neighbours (Alg. generic_LC_cells) and their
+    // cell values (eq. cell_value).  Side sd: 0 W, 1 E, 2 S, 3 N.  The lanes
+    // of sweep direction d take side d: LPD lanes per side, each owning
+    // k/LPD boundary nodes; the first lane of each side then issues that
+    // side's atomics, all four sides at once.  Everything the test needs
+    // (values, changed flags, and f across the boundary, whose sign marks
+    // sources) is in shared memory.
+    {
+        const int sd = dir;
+        const int cx = c >= 0 ? c % cxn : 0, cy = c >= 0 ? c / cxn : 0;
+        bool has_nb = false;
+        if (c >= 0) has_nb = sd == 0 ? cx > 0 : sd == 1 ? cx + 1 < cxn : sd == 2 ? cy > 0 : cy + 1 < cyn;
+        bool cond = false;
+        T vmax = zero_v<T>();
+        int bmax = -1;
+#pragma unroll
+        for (int m = 0; m < C::RPL; ++m) {
+            const int b = rl + C::LPD * m;
+            int bi, bj, ai, aj;
+            if (sd == 0) { bi = 0; bj = b; ai = -1; aj = b; }
+            else if (sd == 1) { bi = K - 1; bj = b; ai = K; aj = b; }
+            else if (sd == 2) { bi = b; bj = 0; ai = b; aj = -1; }
+            else { bi = b; bj = K - 1; ai = b; aj = K; }
+            if (has_nb) {
+                const int qb = (bj + 1) * C::BW + (bi + 1), qa = (aj + 1) * C::BW + (ai + 1);
+                const T vb = tU[qb], va = tU[qa];
+                const bool ch = (masks[g * K + bj] >> bi) & 1ull;
+                // V_i changed (or x_i in Q on the first removal),
+                // V_i < V_j, and x_j not in Q
+                cond = cond || ((ch || (first && is_src(tF[qb]))) && lt(vb, va) && !is_src(tF[qa]));
+                if (is_finite_v(vb) && (bmax < 0 || lt(vmax, vb))) { vmax = vb; bmax = b; }
+            }
+        }
+        const unsigned smask = ((1u << C::LPD) - 1u) << (g * C::LPC + sd * C::LPD);
+        const bool activate = (__ballot_sync(FULL, cond) & smask) != 0u;
+        // max finite boundary value on this side, and where (argmax)
+#pragma unroll
+        for (int o = C::LPD / 2; o > 0; o >>= 1) {
+            const T ov = shfl_xor(vmax, o);
+            const int obm = __shfl_xor_sync(FULL, bmax, o);
+            if (obm >= 0 && (bmax < 0 || lt(vmax, ov) || (!lt(ov, vmax) && obm > bmax))) {
+                vmax = ov;
+                bmax = obm;
+            }
+        }
+        if (rl == 0 && has_nb) {
+            const int nc = sd == 0 ? c - 1 : sd == 1 ? c + 1 : sd == 2 ? c - cxn : c + cxn;
+            double vt = inf_of<double>();
+            if (bmax >= 0) {
+                // eq. cell_value: V_i + ((h + h^c)/2) / F(y_i) with
+                // (h + h^c)/2 = (k+1) h/2; h/F(y_i) read at the node across
+                // the boundary from x_i (the box in shared memory carries a
+                // one-node halo of f)
+                int ai, aj;
+                if (sd == 0) { ai = -1; aj = bmax; }
+                else if (sd == 1) { ai = K; aj = bmax; }
+                else if (sd == 2) { ai = bmax; aj = -1; }
+                else { ai = bmax; aj = K; }
+                double fy = to_d(tF[(aj + 1) * C::BW + (ai + 1)]);
+                if (!(fy >= 0.0 && fy < inf_of<double>())) fy = val_of(ld_cg(&ictl->fmin_f));
+                vt = to_d(vmax) + (double)(K + 1) * 0.5 * fy;
+            }
+            // HCM: update the neighbour's cell value whether or not it is
+            // activated
+            unsigned long long old = KEY_UNSET, kk = KEY_UNSET;
+            if (vt < inf_of<double>()) {
+                kk = key_of(vt);
+                old = atomicMin(&d.cval[nc], kk);
+            }
+            act(d, nc, kk, old, activate);
+        }
+    }
+    __syncwarp();
+    PROF_MARK(6);
+    return true;
+}
+
+// ---------------------------------------------------------------- rounds
+// The bucketed schedule: every round releases the near lists of all
+// instances, the warps process them, re-activations go to the next near list
+// (key <= theta) or to the far list, and a grid barrier ends the round; when
+// an instance's near list runs dry its next bucket is split off the far list.
 template <int MODE, int K>
 __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
     k_solve(const __grid_constant__ SolveParams p) {
     using C = TileCfg<MODE, K>;
-    using T = typename C::T;
-    using FT = typename C::FT;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_flag;
@@ -489,38 +797,22 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
         S.fs = sp;
     }
 
-    const int lane = threadIdx.x & 31;
+    WarpState<MODE, K> w;
+    w.init(smem);
+    const int lane = w.lane, g = w.g, dl = w.dl;
     const int warp = threadIdx.x >> 5;
-    unsigned char* wbase = smem + warp * C::WARP_BYTES;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(wbase + C::BAR_OFF);
-    unsigned long long* masks = reinterpret_cast<unsigned long long*>(wbase + C::MASK_OFF);
-    const int g = lane / C::LPC;     // which of the warp's cells this lane works on
-    const int dl = lane % C::LPC;    // lane within the cell
-    const int dir = dl / C::LPD;     // sweep direction of this lane (Alg. FSM_order)
-    const int rl = dl % C::LPD;      // first tile row of this lane
-    const bool sx = dir <= 1;                  // i increasing
-    const bool sy = (dir == 0) || (dir == 3);  // j increasing
-    unsigned char* gbase = wbase + g * C::GROUP_BYTES;
-    T* tU = reinterpret_cast<T*>(gbase);
-    const FT* tF = reinterpret_cast<const FT*>(gbase + C::F_OFF);
-    const double* tG = reinterpret_cast<const double*>(gbase + C::X_OFF);
-    const unsigned gmask = C::LPC == 32 ? FULL : (((1u << C::LPC) - 1u) << (g * C::LPC));
+    const int prof_on = p.profile;
 
     Ctl* gctl = p.gctl;
     const InstDesc* inst = p.inst;
     const unsigned long long deadline = gtimer() + (unsigned long long)p.deadline_ns;
 
-    if (lane == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
-    }
     for (int i = threadIdx.x; i < NI; i += blockDim.x) {
         S.theta[i] = 0;
         S.ns[i] = 0;
         S.fs[i] = 0;
     }
     __syncthreads();
-    uint32_t phase = 0;
 
     const int nb = gridDim.x;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -530,9 +822,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
     const int slot = g * C::WPB + warp;
     constexpr int SLOTS = C::WPB * C::CPW;
 
-    unsigned long long st_lane = 0, st_rounds = 0;
-    int acc_inst = -1;
-    unsigned long long acc_visits = 0, acc_sweeps = 0, acc_lane = 0;
+    unsigned long long st_rounds = 0;
     unsigned long long pacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long long pt = clock64();
 
@@ -644,9 +934,6 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
                 cg[gg] = __shfl_sync(FULL, c, gg * C::LPC);
                 ig[gg] = __shfl_sync(FULL, ii_, gg * C::LPC);
             }
-            T* Ug = reinterpret_cast<T*>(d.U);
-            Ctl* ictl = d.ctl;
-            const int cxn = d.cxn, cyn = d.cyn, upitch = d.upitch, J = d.J;
 
             // ---- remove the cell from the list: clear its flag BEFORE reading
             // its halo, so that a neighbour that improves the halo while we
@@ -664,241 +951,23 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
             PROF_MARK(2);
             pacc[7] += 1;
 
-            // ---- TMA: U box (cell + halo) and f box (+ halo) into shared memory
-            if (lane == 0) {
-                int nvalid = 0;
-#pragma unroll
-                for (int gg = 0; gg < C::CPW; ++gg) nvalid += cg[gg] >= 0;
-                mbar_arrive_expect_tx(bar, (uint32_t)(nvalid * C::TX_BYTES));
-#pragma unroll
-                for (int gg = 0; gg < C::CPW; ++gg) {
-                    if (cg[gg] >= 0) {
-                        const InstDesc& dg = inst[ig[gg]];
-                        const int cxg = cg[gg] % dg.cxn, cyg = cg[gg] / dg.cxn;
-                        unsigned char* gb = wbase + gg * C::GROUP_BYTES;
-                        tma_load_2d(gb, &dg.tmU, cxg * K, cyg * K, bar);
-                        tma_load_2d(gb + C::F_OFF, &dg.tmF, cxg * K, cyg * K, bar);
-                    }
-                }
-            }
-            {
-                bool got = false;
-                unsigned spins = 0;
-                for (;;) {
-                    if (mbar_try_wait(bar, phase)) { got = true; break; }
-                    if ((++spins & 255u) == 0 && gtimer() > deadline) break;
-                }
-                if (!got) {
-                    fail(gctl, EIK_ETIMEDOUT, 0x3000000ull);
-                    // let our own copies land before the block leaves (bounded)
-                    const unsigned long long d2 = gtimer() + 1000000000ull;
-                    while (!mbar_try_wait(bar, phase) && gtimer() < d2) {
-                    }
-                    break;  // the round's barrier reports the abort to every block
-                }
-            }
-            phase ^= 1u;
-            PROF_MARK(3);
-            if constexpr (MODE == MODE_F64) {
-                // 2 f^2 per node, once per visit (saves two FP64 ops per update)
-                for (int e = lane; e < C::CPW * K * K; e += 32) {
-                    const int gg = e / (K * K), r = e - gg * (K * K);
-                    const int jj = r / K, i2 = r - jj * K;
-                    unsigned char* gb = wbase + gg * C::GROUP_BYTES;
-                    const double fv = reinterpret_cast<const double*>(gb + C::F_OFF)[(jj + 1) * C::BW + i2 + 1];
-                    reinterpret_cast<double*>(gb + C::X_OFF)[r] = 2.0 * fv * fv;
-                }
-                __syncwarp();
-            }
-
-            // ---- passes of four concurrent directional sweeps until a pass
-            // changes nothing or the fixed-point check finds nothing to improve
-            unsigned long long chg[C::RPL];
-#pragma unroll
-            for (int m = 0; m < C::RPL; ++m) chg[m] = 0ull;
-            int gsweeps = 0;
-            bool gdone = c < 0;
-            int s = 0;
-            for (; s < C::MAX_PASSES; ++s) {
-                bool changed = false;
-                for (int t2 = 0; t2 < 2 * K - 1; ++t2) {
-#pragma unroll
-                    for (int m = 0; m < C::RPL; ++m) {
-                        const int j = rl + C::LPD * m;
-                        const int jj = sy ? j : K - 1 - j;
-                        const int ii = t2 - jj;
-                        if (c >= 0 && ii >= 0 && ii < K) {
-                            const int i = sx ? ii : K - 1 - ii;
-                            T cand, old;
-                            if (node_candidate<MODE, K>(tU, tF, tG, i, j, cand, old) && lt(cand, old)) {
-                                tU[(j + 1) * C::BW + (i + 1)] = cand;
-                                chg[m] |= 1ull << i;
-                                changed = true;
-                            }
-                        }
-                    }
-                    __syncwarp();
-                }
-                const unsigned any = __ballot_sync(FULL, changed);
-                if (!gdone) {
-                    gsweeps += 4;
-                    if (!(any & gmask)) gdone = true;
-                }
-                bool imp = false;
-                if (!gdone) imp = tile_improvable<MODE, K>(tU, tF, tG, dl);
-                const unsigned anyi = __ballot_sync(FULL, imp);
-                if (!gdone && !(anyi & gmask)) {
-                    gdone = true;
-                    ++gsweeps;  // counted like the confirming sweep it replaces
-                }
-                if (__ballot_sync(FULL, !gdone) == 0u) break;
-                if ((s & 15) == 15) {
-                    // values only decrease, so stopping early leaves valid upper
-                    // bounds; the expired deadline aborts the launch
-                    const unsigned long long now = __shfl_sync(FULL, gtimer(), 0);
-                    if (now > deadline) {
-                        if (lane == 0) fail(gctl, EIK_ETIMEDOUT, 0x4000000ull);
-                        s = C::MAX_PASSES + 1;
-                        break;
-                    }
-                }
-            }
-            if (s == C::MAX_PASSES && dl == 0 && c >= 0) {
-                atomicCAS(&ictl->status, 0, EIK_ENOTCONVERGED);
-                fail(gctl, EIK_ENOTCONVERGED, (unsigned)c);
-            }
-            if (dl == 0 && c >= 0) {
-                // node evaluations executed for this cell (lock-step passes
-                // included); counters gather per lane while the instance stays
-                // the same (one flush per instance change instead of three
-                // atomics per visit on one address)
-                const unsigned long long ev = (unsigned long long)(s < C::MAX_PASSES ? s + 1 : C::MAX_PASSES) * 4 * K * K;
-                if (ii_ != acc_inst) {
-                    flush_counters(inst, acc_inst, acc_visits, acc_sweeps, acc_lane);
-                    acc_inst = ii_;
-                }
-                acc_visits += 1;
-                acc_sweeps += (unsigned long long)gsweeps;
-                acc_lane += ev;
-                st_lane += ev;
-            }
-            PROF_MARK(4);
-
-            // ---- changed-node masks per row: union over the four directions
-#pragma unroll
-            for (int m = 0; m < C::RPL; ++m) {
-                unsigned long long v = chg[m];
-                v |= __shfl_xor_sync(FULL, v, C::LPD);
-                v |= __shfl_xor_sync(FULL, v, 2 * C::LPD);
-                if (dir == 0) masks[g * K + rl + C::LPD * m] = v;
-            }
-            __syncwarp();
-            // ---- write back the nodes that changed (coalesced across lanes)
-            for (int e = lane; e < C::CPW * K * K; e += 32) {
-                const int gg = e / (K * K);
-                const int rem = e - gg * K * K;
-                const int j = rem / K, i = rem - j * K;
-                int cc = cg[0], ic = ig[0];
-#pragma unroll
-                for (int q = 1; q < C::CPW; ++q)
-                    if (gg == q) { cc = cg[q]; ic = ig[q]; }
-                if (cc >= 0 && ((masks[gg * K + j] >> i) & 1ull)) {
-                    const InstDesc& dc = inst[ic];
-                    const int cx = cc % dc.cxn, cy = cc / dc.cxn;
-                    const T* gU = reinterpret_cast<const T*>(wbase + gg * C::GROUP_BYTES);
-                    reinterpret_cast<T*>(dc.U)[(size_t)(cy * K + j + 1) * dc.upitch + (size_t)(cx * K + i + 1)] =
-                        gU[(j + 1) * C::BW + (i + 1)];
-                }
-            }
-            __threadfence();  // release the new values before any activation
-            fence_proxy_async_global();
-            __syncwarp();
-            PROF_MARK(5);
-
-            // ---- activation of the neighbours (Alg. generic_LC_cells) and
-            // their cell values (eq. cell_value).  Side sd: 0 W, 1 E, 2 S, 3 N.
-            // The lanes of sweep direction d take side d: LPD lanes per side,
-            // each owning k/LPD boundary nodes; the first lane of each side
-            // then issues that side's atomics, all four sides at once.
-            // Everything the test needs (values, changed flags, and f across
-            // the boundary, whose sign marks sources) is in shared memory.
-            {
-                const int sd = dir;
-                const int cx = c >= 0 ? c % cxn : 0, cy = c >= 0 ? c / cxn : 0;
-                bool has_nb = false;
-                if (c >= 0) has_nb = sd == 0 ? cx > 0 : sd == 1 ? cx + 1 < cxn : sd == 2 ? cy > 0 : cy + 1 < cyn;
-                bool cond = false;
-                T vmax = zero_v<T>();
-                int bmax = -1;
-#pragma unroll
-                for (int m = 0; m < C::RPL; ++m) {
-                    const int b = rl + C::LPD * m;
-                    int bi, bj, ai, aj;
-                    if (sd == 0) { bi = 0; bj = b; ai = -1; aj = b; }
-                    else if (sd == 1) { bi = K - 1; bj = b; ai = K; aj = b; }
-                    else if (sd == 2) { bi = b; bj = 0; ai = b; aj = -1; }
-                    else { bi = b; bj = K - 1; ai = b; aj = K; }
-                    if (has_nb) {
-                        const int qb = (bj + 1) * C::BW + (bi + 1), qa = (aj + 1) * C::BW + (ai + 1);
-                        const T vb = tU[qb], va = tU[qa];
-                        const bool ch = (masks[g * K + bj] >> bi) & 1ull;
-                        // V_i changed (or x_i in Q on the first removal),
-                        // V_i < V_j, and x_j not in Q
-                        cond = cond || ((ch || (first && is_src(tF[qb]))) && lt(vb, va) && !is_src(tF[qa]));
-                        if (is_finite_v(vb) && (bmax < 0 || lt(vmax, vb))) { vmax = vb; bmax = b; }
-                    }
-                }
-                const unsigned smask = ((1u << C::LPD) - 1u) << (g * C::LPC + sd * C::LPD);
-                const bool act = (__ballot_sync(FULL, cond) & smask) != 0u;
-                // max finite boundary value on this side, and where (argmax)
-#pragma unroll
-                for (int o = C::LPD / 2; o > 0; o >>= 1) {
-                    const T ov = shfl_xor(vmax, o);
-                    const int obm = __shfl_xor_sync(FULL, bmax, o);
-                    if (obm >= 0 && (bmax < 0 || lt(vmax, ov) || (!lt(ov, vmax) && obm > bmax))) {
-                        vmax = ov;
-                        bmax = obm;
-                    }
-                }
-                if (rl == 0 && has_nb) {
-                    const int nc = sd == 0 ? c - 1 : sd == 1 ? c + 1 : sd == 2 ? c - cxn : c + cxn;
-                    double vt = inf_of<double>();
-                    if (bmax >= 0) {
-                        // eq. cell_value: V_i + ((h + h^c)/2) / F(y_i) with
-                        // (h + h^c)/2 = (k+1) h/2; h/F(y_i) read at the node
-                        // across the boundary from x_i (the box in shared
-                        // memory carries a one-node halo of f)
-                        int ai, aj;
-                        if (sd == 0) { ai = -1; aj = bmax; }
-                        else if (sd == 1) { ai = K; aj = bmax; }
-                        else if (sd == 2) { ai = bmax; aj = -1; }
-                        else { ai = bmax; aj = K; }
-                        double fy = to_d(tF[(aj + 1) * C::BW + (ai + 1)]);
-                        if (!(fy >= 0.0 && fy < inf_of<double>())) fy = val_of(ld_cg(&ictl->fmin_f));
-                        vt = to_d(vmax) + (double)(K + 1) * 0.5 * fy;
-                    }
-                    // HCM: update the neighbour's cell value whether or not it
-                    // is activated; the flag exchange is issued alongside
-                    unsigned long long old = KEY_UNSET, kk = KEY_UNSET;
-                    if (vt < inf_of<double>()) {
-                        kk = key_of(vt);
-                        old = atomicMin(&d.cval[nc], kk);
-                    }
-                    const int was = act ? atomicExch(&d.qflag[nc], 1) : 1;
+            const bool ok = visit_cells<MODE, K>(
+                w, inst, gctl, deadline, c, ii_, first, cg, ig, prof_on, pacc, pt,
+                [&](const InstDesc& dn, int nc, unsigned long long kk, unsigned long long old, bool activate) {
+                    const int was = activate ? atomicExch(&dn.qflag[nc], 1) : 1;
                     if (!was) {
                         unsigned long long cur = old < kk ? old : kk;
-                        if (kk == KEY_UNSET) cur = ld_cg(&d.cval[nc]);
+                        if (kk == KEY_UNSET) cur = ld_cg(&dn.cval[nc]);
                         const int nsl = S.ns[ii_];
+                        const int J = dn.J;
                         if (cur <= S.theta[ii_])
-                            lane_push(d.lists + (nsl == 2 ? 0 : nsl + 1) * J, &ictl->cnt[nsl == 2 ? 0 : nsl + 1],
-                                      nc, J, gctl);
+                            lane_push(dn.lists + (nsl == 2 ? 0 : nsl + 1) * J,
+                                      &dn.ctl->cnt[nsl == 2 ? 0 : nsl + 1], nc, J, gctl);
                         else
-                            lane_push(d.lists + (3 + S.fs[ii_]) * J, &ictl->fcnt[S.fs[ii_]], nc, J, gctl);
+                            lane_push(dn.lists + (3 + S.fs[ii_]) * J, &dn.ctl->fcnt[S.fs[ii_]], nc, J, gctl);
                     }
-                }
-            }
-            __syncwarp();
-            PROF_MARK(6);
+                });
+            if (!ok) break;  // the round's barrier reports the abort to every block
         }
         // a warp that gave up (abort raised) still reaches the barrier, which
         // then reports the abort to every block
@@ -910,11 +979,175 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
         __syncthreads();
     }
 
-    flush_counters(inst, acc_inst, acc_visits, acc_sweeps, acc_lane);
-    if (st_lane) atomicAdd(&gctl->lane_updates, st_lane);
+    flush_counters(inst, w.acc_inst, w.acc_visits, w.acc_sweeps, w.acc_lane);
+    if (w.st_lane) atomicAdd(&gctl->lane_updates, w.st_lane);
     if (p.profile && lane == 0)
         for (int i = 0; i < 8; ++i) atomicAdd(&gctl->prof[i], pacc[i]);
     if (gtid == 0) gctl->rounds = st_rounds;
+}
+
+// ---------------------------------------------------------------- async
+// The round-free schedule.  The job's cells share one ring (a bounded
+// multi-producer multi-consumer queue of global cell indices: each 64-bit
+// word holds a sequence number over the index).  Producers and consumers
+// both take tickets with one atomicAdd: a producer waits for the consumer of
+// the slot's previous lap, a consumer for the producer of its own ticket, so
+// an idle warp holds a ticket and watches only its own slot, and every push
+// goes straight to the warp that has waited longest.  Each cell's flag has
+// two bits: requested (bit 0) and running (bit 1).
+//   activate: set bit 0; the caller that set it on an idle cell pushes it.
+//   claim:    flag := running (the request is consumed) before the halo load.
+//   finish:   clear bit 1; if bit 0 came back meanwhile, push the cell again.
+// So a cell sits in the ring at most once and never runs on two warps, and a
+// neighbour that changed the halo after the load always makes the cell run
+// again.  `pending` counts cells requested or running; a waiting warp that
+// sees it at 0 is done (a running cell's activations are counted before its
+// own finish, so it cannot reach 0 early).  There are no rounds: a cell runs
+// as soon as a warp is free.  The order is the ring's, first in first out --
+// label correcting without buckets, exact by Theorem convergence like any
+// removal order.  head, tail and pending live on separate 128-byte lines.
+__device__ __forceinline__ unsigned long long ld_vol64(const unsigned long long* p) {
+    return *(const volatile unsigned long long*)p;
+}
+__device__ __forceinline__ void st_vol64(unsigned long long* p, unsigned long long v) {
+    *(volatile unsigned long long*)p = v;
+}
+constexpr int Q_HEAD = 0, Q_TAIL = 32, Q_PENDING = 64;  // qctl word offsets (128 B apart)
+
+__device__ __forceinline__ bool ring_push(const SolveParams& p, Ctl* gctl, unsigned e,
+                                          unsigned long long deadline) {
+    const unsigned t = atomicAdd(&p.qctl[Q_TAIL], 1u);
+    unsigned long long* sl = p.ring + (t & p.ring_mask);
+    unsigned spins = 0;
+    while ((unsigned)(ld_vol64(sl) >> 32) != t) {  // the previous lap's consumer is still reading
+        if ((++spins & 255u) == 0 && (gtimer() > deadline || ld_vol(&gctl->abort))) {
+            fail(gctl, EIK_ETIMEDOUT, 0x6000000ull);
+            return false;
+        }
+    }
+    st_vol64(sl, ((unsigned long long)(t + 1u) << 32) | e);
+    return true;
+}
+// Take the next ticket and wait for its cell: >= 0 the cell, -1 converged
+// (nothing requested or running), -2 gave up (abort raised or deadline).
+__device__ __forceinline__ int ring_pop(const SolveParams& p, Ctl* gctl, unsigned long long deadline) {
+    const unsigned h = atomicAdd(&p.qctl[Q_HEAD], 1u);
+    unsigned long long* sl = p.ring + (h & p.ring_mask);
+    unsigned long long v;
+    unsigned spins = 0, ns = 16;
+    while ((unsigned)((v = ld_vol64(sl)) >> 32) != h + 1u) {
+        if ((++spins & 31u) == 0) {
+            if (ld_vol(reinterpret_cast<const int*>(&p.qctl[Q_PENDING])) == 0) return -1;
+            if (ld_vol(&gctl->abort)) return -2;
+            if (gtimer() > deadline) {
+                fail(gctl, EIK_ETIMEDOUT, 0x7000000ull);
+                return -2;
+            }
+        }
+        __nanosleep(ns);
+        ns = ns < 256 ? 2 * ns : 256;
+    }
+    st_vol64(sl, ((unsigned long long)(h + p.ring_mask + 1u) << 32) | 0xffffffffull);
+    return (int)(unsigned)v;
+}
+
+template <int MODE, int K>
+__global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
+    k_solve_async(const __grid_constant__ SolveParams p) {
+    using C = TileCfg<MODE, K>;
+    static_assert(C::CPW == 1, "one cell per warp");
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ int s_flag;
+    unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+
+    const int NI = p.n_inst;
+    int* s_cnt = reinterpret_cast<int*>(smem + C::WPB * C::WARP_BYTES);
+    int* s_pre = s_cnt + NI;
+    int* s_scr = s_pre + NI + 1;
+
+    WarpState<MODE, K> w;
+    w.init(smem);
+    const int lane = w.lane;
+    const int prof_on = p.profile;
+    Ctl* gctl = p.gctl;
+    const InstDesc* inst = p.inst;
+    const unsigned long long deadline = gtimer() + (unsigned long long)p.deadline_ns;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gthreads = gridDim.x * blockDim.x;
+    unsigned long long pacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long pt = clock64();
+
+    // ---- seed the ring with every instance's initially queued cells (their
+    // flags are already 1: requested), in one pass over the whole ring
+    for (int i = threadIdx.x; i < NI; i += blockDim.x) s_cnt[i] = min(ld_cg(&inst[i].ctl->fcnt[0]), inst[i].J);
+    __syncthreads();
+    const int total = block_exclusive_scan(s_cnt, s_pre, NI, s_scr);
+    const unsigned Q = p.ring_mask + 1u;
+    for (unsigned e = gtid; e < Q; e += gthreads) {
+        unsigned long long v;
+        if ((int)e < total) {
+            const int i = find_inst(s_pre, NI, (int)e);
+            const InstDesc& d = inst[i];
+            const int c = ld_cg(&d.lists[3 * d.J + ((int)e - s_pre[i])]);
+            v = ((unsigned long long)(e + 1u) << 32) | (unsigned)(d.cell_base + c);
+        } else {
+            v = ((unsigned long long)e << 32) | 0xffffffffull;
+        }
+        p.ring[e] = v;
+    }
+    if (gtid == 0) {
+        p.qctl[Q_HEAD] = 0;
+        p.qctl[Q_TAIL] = (unsigned)total;
+        p.qctl[Q_PENDING] = (unsigned)total;
+    }
+    if (!grid_sync(gctl, deadline, &s_flag)) return;
+
+    // ---- each warp: take a cell, solve it, hand on its activations
+    for (;;) {
+        int e = 0;
+        if (lane == 0) e = ring_pop(p, gctl, deadline);
+        e = __shfl_sync(FULL, e, 0);
+        if (e < 0) break;
+        const int ii = find_inst(p.cell_pre, NI, e);
+        const InstDesc& d = inst[ii];
+        const int c = e - d.cell_base;
+        // ---- claim: running, the request consumed, before the halo load
+        int first = 0;
+        if (lane == 0) {
+            atomicExch(&d.qflag[c], 2);
+            first = atomicAdd(&d.visits[c], 1) == 0;
+        }
+        first = __shfl_sync(FULL, first, 0);
+        __threadfence();
+        fence_proxy_async_global();
+        fence_proxy_async_shared();
+        __syncwarp();
+        PROF_MARK(2);
+        pacc[7] += 1;
+        const int cg[1] = {c}, ig[1] = {ii};
+        const bool ok = visit_cells<MODE, K>(
+            w, inst, gctl, deadline, c, ii, first, cg, ig, prof_on, pacc, pt,
+            [&](const InstDesc& dn, int nc, unsigned long long, unsigned long long, bool activate) {
+                if (activate && atomicOr(&dn.qflag[nc], 1) == 0) {
+                    atomicAdd(&p.qctl[Q_PENDING], 1u);
+                    ring_push(p, gctl, (unsigned)(dn.cell_base + nc), deadline);
+                }
+            });
+        // ---- finish: push again if a neighbour asked meanwhile
+        if (lane == 0) {
+            const int old = atomicAnd(&d.qflag[c], ~2);
+            if (old & 1) ring_push(p, gctl, (unsigned)e, deadline);
+            else atomicSub(&p.qctl[Q_PENDING], 1u);
+        }
+        __syncwarp();
+        if (!ok) break;
+    }
+
+    flush_counters(inst, w.acc_inst, w.acc_visits, w.acc_sweeps, w.acc_lane);
+    if (w.st_lane) atomicAdd(&gctl->lane_updates, w.st_lane);
+    if (p.profile && lane == 0)
+        for (int i = 0; i < 8; ++i) atomicAdd(&gctl->prof[i], pacc[i]);
 }
 
 }  // namespace eik

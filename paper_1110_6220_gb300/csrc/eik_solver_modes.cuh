@@ -1,0 +1,76 @@
+// eik_solver_modes.cuh -- launch shape and launcher of the persistent solver
+// kernels for one arithmetic mode; included once by each eik_solver_*.cu.
+#pragma once
+
+#include "eik_solver.cuh"
+
+namespace eik {
+
+template <int MODE, int K>
+static const void* solver_fn(bool async) {
+    if constexpr (TileCfg<MODE, K>::CPW == 1)
+        if (async) return (const void*)k_solve_async<MODE, K>;
+    return (const void*)k_solve<MODE, K>;
+}
+
+template <int MODE, int K>
+static void shape_of(int num_sms, int n_inst, int sm_cap, bool async, LaunchShape* s) {
+    using C = TileCfg<MODE, K>;
+    const void* fn = solver_fn<MODE, K>(async);
+    s->threads = C::WPB * 32;
+    s->smem = (size_t)C::WPB * C::WARP_BYTES + 128 + (size_t)inst_state_bytes(n_inst);
+    s->blocks = 0;
+    s->per_sm = 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, s->threads, s->smem) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 0;
+    }
+    // a single grid: at most two blocks per SM (a round rarely has more cells
+    // than that, and every extra block makes each grid barrier slower); a
+    // batch keeps every SM full, so it takes the occupancy limit
+    int cap = n_inst > 1 ? per_sm : 2;
+    if (sm_cap > 0 && sm_cap < cap) cap = sm_cap;  // leave room for other jobs
+    s->blocks = (per_sm < cap ? per_sm : cap) * num_sms;
+    s->per_sm = per_sm;
+}
+
+template <int MODE>
+static int solver_shape_mode(int k, int num_sms, int n_inst, int sm_cap, bool async, LaunchShape* out) {
+    out->blocks = 0;
+    switch (k) {
+    case 4: shape_of<MODE, 4>(num_sms, n_inst, sm_cap, async, out); break;
+    case 8: shape_of<MODE, 8>(num_sms, n_inst, sm_cap, async, out); break;
+    case 16: shape_of<MODE, 16>(num_sms, n_inst, sm_cap, async, out); break;
+    case 32: shape_of<MODE, 32>(num_sms, n_inst, sm_cap, async, out); break;
+    case 64: shape_of<MODE, 64>(num_sms, n_inst, sm_cap, async, out); break;
+    default: return -1;
+    }
+    return out->blocks > 0 ? 0 : -1;
+}
+
+template <int MODE, int K>
+static cudaError_t launch_one(bool async, const SolveParams& p, const LaunchShape& s, cudaStream_t st) {
+    void* args[] = {(void*)&p};
+    return cudaLaunchCooperativeKernel(solver_fn<MODE, K>(async), dim3(s.blocks), dim3(s.threads), args, s.smem,
+                                       st);
+}
+
+template <int MODE>
+static cudaError_t launch_solver_mode(int k, bool async, const SolveParams& p, const LaunchShape& s,
+                                      cudaStream_t st) {
+    switch (k) {
+    case 4: return launch_one<MODE, 4>(async, p, s, st);
+    case 8: return launch_one<MODE, 8>(async, p, s, st);
+    case 16: return launch_one<MODE, 16>(async, p, s, st);
+    case 32: return launch_one<MODE, 32>(async, p, s, st);
+    case 64: return launch_one<MODE, 64>(async, p, s, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace eik

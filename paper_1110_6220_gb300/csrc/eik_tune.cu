@@ -38,6 +38,7 @@ struct Entry {
     int k;
     double m_first, m_main;  // relative widths: bucket = m * k * min(h/F)
     double ms;               // device time measured when tuned (0: built in)
+    bool async_first = false, async_main = false;  // round-free schedule per pass
 };
 
 std::mutex g_mu;
@@ -58,9 +59,14 @@ int side_class(const eik_plan_desc* d, int n) {
 //    rounds) was fastest, 1.7x the time of 4-cell buckets;
 //  - single grid, FP32 + refinement: k = 8, FP32 pass at 256, refinement at 16;
 //  - batches: k = 16, FP32 pass at 64, refinement (and FP64) at 4.
+//  - the FP32 pass runs round-free (k_solve_async) in both cases: 1.33 ms
+//    instead of 2.09 ms on the 1025^2 grid, 9.4 ms instead of 12.9 ms on the
+//    batch; the FP64 and refinement passes stay on rounds (without buckets
+//    they visit each cell 4-5x as often, and those visits are the costly ones).
 Entry builtin(int prec, bool batch) {
-    if (batch) return prec == EIK_FP32_REFINE ? Entry{16, 64.0, 4.0, 0.0} : Entry{16, 4.0, 4.0, 0.0};
-    return prec == EIK_FP32_REFINE ? Entry{8, 256.0, 16.0, 0.0} : Entry{8, 256.0, 256.0, 0.0};
+    if (batch)
+        return prec == EIK_FP32_REFINE ? Entry{16, 64.0, 4.0, 0.0, true, false} : Entry{16, 4.0, 4.0, 0.0};
+    return prec == EIK_FP32_REFINE ? Entry{8, 256.0, 16.0, 0.0, true, false} : Entry{8, 256.0, 256.0, 0.0};
 }
 
 int load_file(const char* path) {
@@ -68,20 +74,23 @@ int load_file(const char* path) {
     if (!f) return EIK_EINVAL;
     char line[256];
     int rc = EIK_OK;
-    if (!std::fgets(line, sizeof line, f) || std::strncmp(line, "eik-tune 1", 10) != 0) {
+    if (!std::fgets(line, sizeof line, f) || std::strncmp(line, "eik-tune 2", 10) != 0) {
         rc = EIK_EINVAL;
     } else {
         std::map<Key, Entry> t;
         while (std::fgets(line, sizeof line, f)) {
             Key key;
             Entry e;
-            if (std::sscanf(line, "%d %d %d %d %lf %lf %lf", &key.prec, &key.batch, &key.side, &e.k, &e.m_first,
-                            &e.m_main, &e.ms) != 7 ||
+            int af = 0, am = 0;
+            if (std::sscanf(line, "%d %d %d %d %lf %lf %d %d %lf", &key.prec, &key.batch, &key.side, &e.k,
+                            &e.m_first, &e.m_main, &af, &am, &e.ms) != 9 ||
                 (e.k != 4 && e.k != 8 && e.k != 16 && e.k != 32 && e.k != 64) || !(e.m_first > 0) ||
-                !(e.m_main > 0)) {
+                !(e.m_main > 0) || (af != 0 && af != 1) || (am != 0 && am != 1)) {
                 rc = EIK_EINVAL;
                 break;
             }
+            e.async_first = af;
+            e.async_main = am;
             t[key] = e;
         }
         if (!rc)
@@ -114,6 +123,15 @@ JobParams choose_params(const eik_plan_desc* d, int n) {
     P.k = d[0].cell_k ? d[0].cell_k : e.k;
     P.w_first = -e.m_first;
     P.w_main = -e.m_main;
+    P.async_first = e.async_first;
+    P.async_main = e.async_main;
+    // EIK_SCHED="<first>,<main>" with r (rounds) or a (async) overrides the
+    // schedule of each pass (for measurements)
+    static const char* sched = std::getenv("EIK_SCHED");
+    if (sched && std::strlen(sched) >= 3) {
+        P.async_first = sched[0] == 'a';
+        P.async_main = sched[2] == 'a';
+    }
     return P;
 }
 
@@ -160,12 +178,15 @@ extern "C" int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t 
     struct Best {
         int k = 0;
         double mf = 0, mm = 0, est = 1e300;
+        bool af = false, am = false;
     } best;
     if (!rc) {
         for (int k : {8, 16, 32}) {
             float t[3];
             if (trial(JobParams{k, -4.0, -4.0}, t)) continue;  // warm-up of this k
+            // bucketed rounds at every width: each pass keeps its best width
             double bf = 1e300, bm = 1e300, mf = 4.0, mm = 4.0;
+            bool af = false, am = false;
             std::vector<double> over;
             for (double m : widths) {
                 if (trial(JobParams{k, -m, -m}, t)) continue;
@@ -173,18 +194,28 @@ extern "C" int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t 
                 if (t[2] < bm) bm = t[2], mm = m;
                 over.push_back(t[0] - t[1] - t[2]);
             }
+            // the round-free schedule for both passes (k >= 8)
+            JobParams A{k, -mf, -mm};
+            A.async_first = A.async_main = true;
+            if (trial(A, t) == EIK_OK) {
+                if (fp32 && t[1] < bf) bf = t[1], af = true;
+                if (t[2] < bm) bm = t[2], am = true;
+                over.push_back(t[0] - t[1] - t[2]);
+            }
             if (over.empty()) continue;
             std::sort(over.begin(), over.end());
             const double est = (fp32 ? bf : 0.0) + bm + over[over.size() / 2];
-            if (!fp32) mf = mm;
-            if (est < best.est) best = Best{k, mf, mm, est};
+            if (!fp32) mf = mm, af = am;
+            if (est < best.est) best = Best{k, mf, mm, est, af, am};
         }
     }
-    Entry chosen{before.k, -before.w_first, -before.w_main, t_before[0]};
+    Entry chosen{before.k, -before.w_first, -before.w_main, t_before[0], before.async_first, before.async_main};
     float t_new[3] = {0, 0, 0};
-    if (!rc && best.k && trial(JobParams{best.k, -best.mf, -best.mm}, t_new) == EIK_OK &&
-        t_new[0] < t_before[0])
-        chosen = Entry{best.k, best.mf, best.mm, t_new[0]};
+    JobParams B{best.k, -best.mf, -best.mm};
+    B.async_first = best.af;
+    B.async_main = best.am;
+    if (!rc && best.k && trial(B, t_new) == EIK_OK && t_new[0] < t_before[0])
+        chosen = Entry{best.k, best.mf, best.mm, t_new[0], best.af, best.am};
     if (!rc) {
         std::lock_guard<std::mutex> lock(g_mu);
         maybe_load_env();
@@ -198,6 +229,8 @@ extern "C" int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t 
         out->cell_k = chosen.k;
         out->bucket_first = chosen.m_first;
         out->bucket_main = chosen.m_main;
+        out->async_first = chosen.async_first;
+        out->async_main = chosen.async_main;
         out->ms = chosen.ms;
         out->ms_before = t_before[0];
         out->trials = trials;
@@ -210,10 +243,11 @@ extern "C" int eik_tune_save(const char* path) {
     std::lock_guard<std::mutex> lock(g_mu);
     FILE* f = std::fopen(path, "w");
     if (!f) return EIK_EINVAL;
-    std::fprintf(f, "eik-tune 1\n");
+    std::fprintf(f, "eik-tune 2\n");
     for (auto& kv : g_table)
-        std::fprintf(f, "%d %d %d %d %.17g %.17g %.17g\n", kv.first.prec, kv.first.batch, kv.first.side,
-                     kv.second.k, kv.second.m_first, kv.second.m_main, kv.second.ms);
+        std::fprintf(f, "%d %d %d %d %.17g %.17g %d %d %.17g\n", kv.first.prec, kv.first.batch, kv.first.side,
+                     kv.second.k, kv.second.m_first, kv.second.m_main, (int)kv.second.async_first,
+                     (int)kv.second.async_main, kv.second.ms);
     return std::fclose(f) == 0 ? EIK_OK : EIK_EINVAL;
 }
 
