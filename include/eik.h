@@ -162,7 +162,10 @@ int eik_solve_batch(const eik_plan_desc* d, const eik_instance* in, int32_t n_in
  *
  * Each pass runs either in bucketed rounds (a grid barrier per round) or
  * round-free: warps take cells from a device-side ring as they come, in
- * first-in first-out order, with no buckets.
+ * first-in first-out order, with no buckets.  FP32_REFINE runs either as an
+ * FP32 pass followed by a double-float refinement pass seeded from it, or as
+ * one double-float pass from the sources; both take every update on the FP32
+ * pipe and end with the same FP64 residual certificate.
  *
  * eik_tune: time trial solves of the given instances, run as one job like
  * eik_solve_batch (n_inst = 1: like eik_solve), over k in {8, 16, 32}, rounds
@@ -180,6 +183,8 @@ typedef struct {
     double bucket_main;    /* relative width of the FP64 / refinement pass */
     int32_t async_first;   /* 1: the FP32 pass runs round-free (no buckets) */
     int32_t async_main;    /* 1: the FP64 / refinement pass runs round-free */
+    int32_t one_pass;      /* FP32_REFINE: 1 = one double-float pass from the sources, 0 = an
+                              FP32 pass, then a refinement pass seeded from it */
     double ms;             /* device time of the job with the chosen values */
     double ms_before;      /* device time with the choice in force before */
     int32_t trials;        /* solves run */
@@ -187,7 +192,7 @@ typedef struct {
 
 int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t n_inst, void* cuda_stream,
              eik_tune_result* out);
-/* Write / merge the table as text ("eik-tune 2" then one line per class).
+/* Write / merge the table as text ("eik-tune 3" then one line per class).
  * EIK_EINVAL if the file cannot be written / read or is malformed (nothing
  * merged then). */
 int eik_tune_save(const char* path);

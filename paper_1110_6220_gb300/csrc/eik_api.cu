@@ -174,7 +174,8 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     // cells and the warps of a launch, behind its three counters
     size_t Q = 8192;
     while (Q < 2 * Jtot) Q <<= 1;
-    const size_t ring_bytes = a256(384 + Q * 8);
+    const size_t hist_bytes = a256((3 * 8192 + 1) * 4);
+    const size_t ring_bytes = a256(384 + hist_bytes + Q * 8);
     const size_t total = image_bytes + zero_bytes + a256(Jtot * 8) + ring_bytes + ibytes + 256;
     int rc = grow(&hj->arena, total);
     if (rc) return rc;
@@ -223,6 +224,11 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
         fill_inst_tables(L, a, fp32, descs[i].h, bw != 0.0 ? bw : P.w_first, hj->bw_main[i], &ictl_dev[i],
                          &ictl_dev[n + i],
                          &res_dev[i], F, out, hj->shift[i], &aux_h[i], &desc_main_h[i], &desc_f32_h[i], &ok);
+        if (fp32 && P.one_pass) {
+            // the source cells are queued for the double-float pass itself
+            aux_h[i].ctl = &ictl_dev[n + i];
+            aux_h[i].ctl2 = nullptr;
+        }
         desc_main_h[i].cell_base = (int)coff;
         if (fp32) desc_f32_h[i].cell_base = (int)coff;
         blk_pre_h[i] = boff;
@@ -282,10 +288,12 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     j.ncell_total = (int)ncs;
     j.deadline_ns = deadline_ns;
     j.sm_cap = 0;
+    j.one_pass = fp32 && P.one_pass;
     j.async_first = P.async_first;
     j.async_main = P.async_main;
     j.qctl = (unsigned*)ring_dev;
-    j.ring = (unsigned long long*)(ring_dev + 384);
+    j.hist = (int*)(ring_dev + 384);
+    j.ring = (unsigned long long*)(ring_dev + 384 + hist_bytes);
     j.ring_mask = (unsigned)(Q - 1);
     j.zero_base = zero_dev;
     j.zero_bytes = zero_bytes;
@@ -384,7 +392,7 @@ extern "C" size_t eik_plan_workspace_bytes(const eik_plan_desc* d) {
     const bool fp32 = d->precision == EIK_FP32_REFINE;
     size_t Q = 8192;
     while (Q < 2 * (size_t)L.J) Q <<= 1;
-    return inst_bytes(L, fp32, true, true) + (size_t)L.J * 16 + Q * 8 + 64 * 1024;
+    return inst_bytes(L, fp32, true, true) + (size_t)L.J * 16 + Q * 8 + 128 * 1024;
 }
 
 extern "C" int eik_plan_create(eik_plan* out, const eik_plan_desc* d, void* cuda_stream) {

@@ -109,6 +109,7 @@ struct SolveParams {
     unsigned int ring_mask;
     const int* cell_pre;
     unsigned int* qctl;           // ring head, tail and pending count, 128 bytes apart
+    int* hist;                    // 3 x 8192 + 1 ints: counting sort of the initial ring
 };
 
 // ---------------------------------------------------------------- host launchers

@@ -196,9 +196,23 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
     p.ring_mask = j.ring_mask;
     p.cell_pre = j.cell_pre;
     p.qctl = j.qctl;
+    p.hist = j.hist;
     const bool af = j.async_first && j.ring && j.k >= 8, am = j.async_main && j.ring && j.k >= 8;
     LaunchShape shape;
-    if (j.fp32) {
+    if (j.fp32 && j.one_pass) {
+        // FP32_REFINE in one double-float pass from the sources (every
+        // update on the FP32 pipe), certified like the two-pass form
+        if (ev) cudaEventRecord(ev[0], st), cudaEventRecord(ev[1], st);
+        if (solver_shape_df(j.k, num_sms, n, j.sm_cap, am, &shape)) return EIK_ECUDA;
+        p.inst = j.desc_main;
+        p.gctl = j.gctl + 1;
+        if (ev) cudaEventRecord(ev[2], st);
+        if (launch_solver_df(j.k, am, p, shape, st) != cudaSuccess) return EIK_ECUDA;
+        if (ev) cudaEventRecord(ev[3], st);
+        ++nl;
+        if (launch_residual(j.aux, j.blk_pre, n, j.nblocks, st) != cudaSuccess) return EIK_ECUDA;
+        ++nl;
+    } else if (j.fp32) {
         if (solver_shape_f32(j.k, num_sms, n, j.sm_cap, af, &shape)) return EIK_ECUDA;
         p.inst = j.desc_f32;
         p.gctl = j.gctl;
@@ -238,6 +252,10 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
 
 bool job_pairable(const JobDev& j, int num_sms) {
     LaunchShape a{}, b{};
+    if (j.fp32 && j.one_pass) {
+        if (solver_shape_df(j.k, num_sms, j.n, 1, j.async_main, &b)) return false;
+        return b.per_sm >= 2;
+    }
     if (j.fp32) {
         if (solver_shape_f32(j.k, num_sms, j.n, 1, j.async_first, &a) ||
             solver_shape_df(j.k, num_sms, j.n, 1, j.async_main, &b))

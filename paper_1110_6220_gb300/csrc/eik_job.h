@@ -57,9 +57,11 @@ struct JobDev {
     long long deadline_ns;
     int sm_cap;                 // > 0: at most this many blocks per SM (room for other jobs)
     bool async_first, async_main;  // round-free schedule (k_solve_async) for the FP32 / main pass
+    bool one_pass;              // fp32: no FP32 pass; the double-float pass solves from the sources
     unsigned long long* ring;   // async: ring of ring_mask + 1 words
     unsigned ring_mask;
     unsigned* qctl;             // async: head, tail, pending (384 bytes before the ring)
+    int* hist;                  // async: 3 x 8192 + 1 ints of counting-sort scratch
     // everything that enqueue_job zeroes before a solve: [zero_base, + zero_bytes)
     void* zero_base;
     size_t zero_bytes;

@@ -32,6 +32,7 @@ struct JobParams {
     int k;
     double w_first, w_main;
     bool async_first = false, async_main = false;  // round-free schedule per pass (k >= 8)
+    bool one_pass = false;  // FP32_REFINE as one double-float pass from the sources
 };
 
 bool desc_valid(const eik_plan_desc* d);

@@ -1013,6 +1013,8 @@ __device__ __forceinline__ void st_vol64(unsigned long long* p, unsigned long lo
     *(volatile unsigned long long*)p = v;
 }
 constexpr int Q_HEAD = 0, Q_TAIL = 32, Q_PENDING = 64;  // qctl word offsets (128 B apart)
+constexpr int SORT_MIN = 2048;      // initial cells above which the ring is seeded in value order
+constexpr int SORT_BUCKETS = 8192;  // counting-sort bins (p.hist holds 3 x SORT_BUCKETS + 1 ints)
 
 __device__ __forceinline__ bool ring_push(const SolveParams& p, Ctl* gctl, unsigned e,
                                           unsigned long long deadline) {
@@ -1079,22 +1081,50 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
     long long pt = clock64();
 
     // ---- seed the ring with every instance's initially queued cells (their
-    // flags are already 1: requested), in one pass over the whole ring
+    // flags are already 1: requested).  When many cells start queued (the
+    // refinement pass queues them all) they enter the ring in order of cell
+    // value, by a counting sort on the value in units of one cell crossing at
+    // the highest speed, k min(h/F): cells then mostly run after their
+    // upstream neighbours, as the bucketed schedule would order them.
     for (int i = threadIdx.x; i < NI; i += blockDim.x) s_cnt[i] = min(ld_cg(&inst[i].ctl->fcnt[0]), inst[i].J);
     __syncthreads();
     const int total = block_exclusive_scan(s_cnt, s_pre, NI, s_scr);
     const unsigned Q = p.ring_mask + 1u;
-    for (unsigned e = gtid; e < Q; e += gthreads) {
-        unsigned long long v;
-        if ((int)e < total) {
-            const int i = find_inst(s_pre, NI, (int)e);
-            const InstDesc& d = inst[i];
-            const int c = ld_cg(&d.lists[3 * d.J + ((int)e - s_pre[i])]);
-            v = ((unsigned long long)(e + 1u) << 32) | (unsigned)(d.cell_base + c);
-        } else {
-            v = ((unsigned long long)e << 32) | 0xffffffffull;
+    const bool sorted = total > SORT_MIN;
+    auto seed_cell = [&](int e, int& gcell) -> int {  // initial entry e: global cell, bucket
+        const int i = find_inst(s_pre, NI, e);
+        const InstDesc& d = inst[i];
+        const int c = ld_cg(&d.lists[3 * d.J + (e - s_pre[i])]);
+        gcell = d.cell_base + c;
+        if (!sorted) return 0;
+        const double unit = (double)K * val_of(ld_cg(&d.ctl->fmin_f));
+        const double v = val_of(ld_cg(&d.cval[c]));
+        const double b = unit > 0.0 ? v / unit : 0.0;
+        return b >= 0.0 && b < (double)(SORT_BUCKETS - 1) ? (int)b : SORT_BUCKETS - 1;
+    };
+    if (sorted) {
+        // p.hist: counts [0, B), exclusive prefix [B, 2B], cursors [2B + 1, 3B + 1)
+        for (int e = gtid; e < 3 * SORT_BUCKETS + 1; e += gthreads) p.hist[e] = 0;
+        if (!grid_sync(gctl, deadline, &s_flag)) return;
+        for (int e = gtid; e < total; e += gthreads) {
+            int gc;
+            atomicAdd(&p.hist[seed_cell(e, gc)], 1);
         }
-        p.ring[e] = v;
+        if (!grid_sync(gctl, deadline, &s_flag)) return;
+        if (blockIdx.x == 0) block_exclusive_scan(p.hist, p.hist + SORT_BUCKETS, SORT_BUCKETS, s_scr);
+        if (!grid_sync(gctl, deadline, &s_flag)) return;
+    }
+    for (unsigned e = gtid; e < Q; e += gthreads) {
+        if ((int)e < total) {
+            int gc;
+            const int b = seed_cell((int)e, gc);
+            const unsigned pos =
+                sorted ? (unsigned)(ld_cg(&p.hist[SORT_BUCKETS + b]) + atomicAdd(&p.hist[2 * SORT_BUCKETS + 1 + b], 1))
+                       : e;
+            p.ring[pos] = ((unsigned long long)(pos + 1u) << 32) | (unsigned)gc;
+        } else {
+            p.ring[e] = ((unsigned long long)e << 32) | 0xffffffffull;
+        }
     }
     if (gtid == 0) {
         p.qctl[Q_HEAD] = 0;

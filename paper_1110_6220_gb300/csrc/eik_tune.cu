@@ -39,6 +39,7 @@ struct Entry {
     double m_first, m_main;  // relative widths: bucket = m * k * min(h/F)
     double ms;               // device time measured when tuned (0: built in)
     bool async_first = false, async_main = false;  // round-free schedule per pass
+    bool one_pass = false;  // FP32_REFINE as one double-float pass
 };
 
 std::mutex g_mu;
@@ -59,14 +60,22 @@ int side_class(const eik_plan_desc* d, int n) {
 //    rounds) was fastest, 1.7x the time of 4-cell buckets;
 //  - single grid, FP32 + refinement: k = 8, FP32 pass at 256, refinement at 16;
 //  - batches: k = 16, FP32 pass at 64, refinement (and FP64) at 4.
-//  - the FP32 pass runs round-free (k_solve_async) in both cases: 1.33 ms
-//    instead of 2.09 ms on the 1025^2 grid, 9.4 ms instead of 12.9 ms on the
-//    batch; the FP64 and refinement passes stay on rounds (without buckets
-//    they visit each cell 4-5x as often, and those visits are the costly ones).
+//  - FP32 + refinement runs as one double-float pass from the sources on the
+//    round-free schedule (k_solve_async): 2.10 ms on the 1025^2 grid against
+//    4.89 ms for an FP32 pass plus a refinement pass, 8.2 ms against 21.6 ms
+//    on a 2049^2 checkerboard + maze, 28.7 ms against 56.6 ms on the batch.
+//    A double-float visit costs about a quarter of an FP64 one (the FP64 pipe
+//    is slow), and a pass from the sources visits each cell a few times where
+//    a refinement pass seeded everywhere revisits it on every upstream change;
+//  - FP64 stays on rounds: round-free, it visits each cell 4-5x as often, and
+//    FP64 visits are the costly ones.
 Entry builtin(int prec, bool batch) {
-    if (batch)
-        return prec == EIK_FP32_REFINE ? Entry{16, 64.0, 4.0, 0.0, true, false} : Entry{16, 4.0, 4.0, 0.0};
-    return prec == EIK_FP32_REFINE ? Entry{8, 256.0, 16.0, 0.0, true, false} : Entry{8, 256.0, 256.0, 0.0};
+    if (prec == EIK_FP32_REFINE) {
+        Entry e{batch ? 16 : 8, 256.0, 16.0, 0.0, false, true};
+        e.one_pass = true;
+        return e;
+    }
+    return batch ? Entry{16, 4.0, 4.0, 0.0} : Entry{8, 256.0, 256.0, 0.0};
 }
 
 int load_file(const char* path) {
@@ -74,23 +83,24 @@ int load_file(const char* path) {
     if (!f) return EIK_EINVAL;
     char line[256];
     int rc = EIK_OK;
-    if (!std::fgets(line, sizeof line, f) || std::strncmp(line, "eik-tune 2", 10) != 0) {
+    if (!std::fgets(line, sizeof line, f) || std::strncmp(line, "eik-tune 3", 10) != 0) {
         rc = EIK_EINVAL;
     } else {
         std::map<Key, Entry> t;
         while (std::fgets(line, sizeof line, f)) {
             Key key;
             Entry e;
-            int af = 0, am = 0;
-            if (std::sscanf(line, "%d %d %d %d %lf %lf %d %d %lf", &key.prec, &key.batch, &key.side, &e.k,
-                            &e.m_first, &e.m_main, &af, &am, &e.ms) != 9 ||
+            int af = 0, am = 0, op = 0;
+            if (std::sscanf(line, "%d %d %d %d %lf %lf %d %d %d %lf", &key.prec, &key.batch, &key.side, &e.k,
+                            &e.m_first, &e.m_main, &af, &am, &op, &e.ms) != 10 ||
                 (e.k != 4 && e.k != 8 && e.k != 16 && e.k != 32 && e.k != 64) || !(e.m_first > 0) ||
-                !(e.m_main > 0) || (af != 0 && af != 1) || (am != 0 && am != 1)) {
+                !(e.m_main > 0) || (af != 0 && af != 1) || (am != 0 && am != 1) || (op != 0 && op != 1)) {
                 rc = EIK_EINVAL;
                 break;
             }
             e.async_first = af;
             e.async_main = am;
+            e.one_pass = op;
             t[key] = e;
         }
         if (!rc)
@@ -132,6 +142,9 @@ JobParams choose_params(const eik_plan_desc* d, int n) {
         P.async_first = sched[0] == 'a';
         P.async_main = sched[2] == 'a';
     }
+    P.one_pass = e.one_pass;
+    static const char* onep = std::getenv("EIK_ONE_PASS");
+    if (onep && onep[0]) P.one_pass = onep[0] == '1';
     return P;
 }
 
@@ -178,7 +191,7 @@ extern "C" int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t 
     struct Best {
         int k = 0;
         double mf = 0, mm = 0, est = 1e300;
-        bool af = false, am = false;
+        bool af = false, am = false, op = false;
     } best;
     if (!rc) {
         for (int k : {8, 16, 32}) {
@@ -204,18 +217,34 @@ extern "C" int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t 
             }
             if (over.empty()) continue;
             std::sort(over.begin(), over.end());
-            const double est = (fp32 ? bf : 0.0) + bm + over[over.size() / 2];
+            const double ov = over[over.size() / 2];
+            const double est = (fp32 ? bf : 0.0) + bm + ov;
             if (!fp32) mf = mm, af = am;
-            if (est < best.est) best = Best{k, mf, mm, est, af, am};
+            if (est < best.est) best = Best{k, mf, mm, est, af, am, false};
+            if (!fp32) continue;
+            // FP32 + refinement as one double-float pass: rounds at every
+            // width, then round-free
+            for (int m = 0; m <= 5; ++m) {
+                JobParams O{k, -mf, m < 5 ? -widths[m] : -mm};
+                O.one_pass = true;
+                O.async_main = m == 5;
+                if (trial(O, t)) continue;
+                const double e1 = t[2] + (t[0] - t[2] < ov ? t[0] - t[2] : ov);
+                if (e1 < best.est) best = Best{k, mf, -O.w_main, e1, false, O.async_main, true};
+            }
         }
     }
     Entry chosen{before.k, -before.w_first, -before.w_main, t_before[0], before.async_first, before.async_main};
+    chosen.one_pass = before.one_pass;
     float t_new[3] = {0, 0, 0};
     JobParams B{best.k, -best.mf, -best.mm};
     B.async_first = best.af;
     B.async_main = best.am;
-    if (!rc && best.k && trial(B, t_new) == EIK_OK && t_new[0] < t_before[0])
+    B.one_pass = best.op;
+    if (!rc && best.k && trial(B, t_new) == EIK_OK && t_new[0] < t_before[0]) {
         chosen = Entry{best.k, best.mf, best.mm, t_new[0], best.af, best.am};
+        chosen.one_pass = best.op;
+    }
     if (!rc) {
         std::lock_guard<std::mutex> lock(g_mu);
         maybe_load_env();
@@ -231,6 +260,7 @@ extern "C" int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t 
         out->bucket_main = chosen.m_main;
         out->async_first = chosen.async_first;
         out->async_main = chosen.async_main;
+        out->one_pass = chosen.one_pass;
         out->ms = chosen.ms;
         out->ms_before = t_before[0];
         out->trials = trials;
@@ -243,11 +273,11 @@ extern "C" int eik_tune_save(const char* path) {
     std::lock_guard<std::mutex> lock(g_mu);
     FILE* f = std::fopen(path, "w");
     if (!f) return EIK_EINVAL;
-    std::fprintf(f, "eik-tune 2\n");
+    std::fprintf(f, "eik-tune 3\n");
     for (auto& kv : g_table)
-        std::fprintf(f, "%d %d %d %d %.17g %.17g %d %d %.17g\n", kv.first.prec, kv.first.batch, kv.first.side,
+        std::fprintf(f, "%d %d %d %d %.17g %.17g %d %d %d %.17g\n", kv.first.prec, kv.first.batch, kv.first.side,
                      kv.second.k, kv.second.m_first, kv.second.m_main, (int)kv.second.async_first,
-                     (int)kv.second.async_main, kv.second.ms);
+                     (int)kv.second.async_main, (int)kv.second.one_pass, kv.second.ms);
     return std::fclose(f) == 0 ? EIK_OK : EIK_EINVAL;
 }
 

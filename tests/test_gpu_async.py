@@ -32,9 +32,9 @@ def _side_class(sizes):
 
 
 def _force(eik, tmp_path, rows):
-    """rows: (precision, batch, side class, k, async_first, async_main)."""
+    """rows: (precision, batch, side class, k, async_first, async_main, one_pass)."""
     f = tmp_path / "sched.txt"
-    lines = ["eik-tune 2"] + [f"{p} {b} {s} {k} 4 4 {a1} {a2} 1.0" for p, b, s, k, a1, a2 in rows]
+    lines = ["eik-tune 3"] + [f"{p} {b} {s} {k} 4 4 {a1} {a2} {op} 1.0" for p, b, s, k, a1, a2, op in rows]
     f.write_text("\n".join(lines) + "\n")
     eik.eik_tune_reset()
     assert eik.eik_tune_load(str(f)) == 0
@@ -58,10 +58,12 @@ def _instances():
 
 
 @pytest.mark.parametrize("k", [8, 16, 32])
-@pytest.mark.parametrize("prec", [0, 1])
-def test_async_single_matches_oracle(eik, orc, tmp_path, k, prec):
+@pytest.mark.parametrize("prec,one_pass", [(0, 0), (1, 0), (1, 1)])
+def test_async_single_matches_oracle(eik, orc, tmp_path, k, prec, one_pass):
+    """FP64; FP32 + refinement with both passes round-free; one round-free
+    double-float pass."""
     insts = _instances()
-    rows = {(prec, 0, _side_class([(I.nx, I.ny)]), k, 1, 1) for I in insts}
+    rows = {(prec, 0, _side_class([(I.nx, I.ny)]), k, 1, 1, one_pass) for I in insts}
     _force(eik, tmp_path, sorted(rows))
     tol = TOL64 if prec == 0 else TOL32
     for I in insts:
@@ -72,10 +74,13 @@ def test_async_single_matches_oracle(eik, orc, tmp_path, k, prec):
         _check(U, orc.fmm(I.F, I.h, I.si, I.sj, I.sq), tol, f"{I.name} k={k}")
 
 
-@pytest.mark.parametrize("sched", [(1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("sched", [(1, 0, 0), (0, 1, 0), (1, 1, 0), (0, 0, 1), (0, 1, 1)])
 def test_async_batch_matches_oracle(eik, orc, tmp_path, sched):
+    """(async FP32 pass, async main pass, one double-float pass)."""
     insts = W.batch_mix(24, seed=31, n_lo=17, n_hi=300)
     for prec in (0, 1):
+        if prec == 0 and sched[2]:
+            continue
         _force(eik, tmp_path, [(prec, 1, _side_class([(I.nx, I.ny) for I in insts]), 16) + sched])
         descs, ins, keep = [], [], []
         for I in insts:
