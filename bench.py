@@ -469,10 +469,12 @@ def run_ours(args):
         # and FP64 passes 8 B f + 2 x 8 B U, each times (1 + 4/k).
         p32 = statistics.mean(s.pass_ms[0] for s in stats)
         p64 = statistics.mean(s.pass_ms[1] for s in stats)
+        sched = stats[-1].schedule
         if p32 > p64:
-            kname, kms, bpp = "k_solve<F32>", p32, 12.0 * (1 + 4.0 / k)
+            kname = "k_solve_async<F32>" if sched & 1 else "k_solve<F32>"
+            kms, bpp = p32, 12.0 * (1 + 4.0 / k)
         else:
-            kname = "k_solve<DF>" if prec else "k_solve<F64>"
+            kname = ("k_solve_async" if sched & 2 else "k_solve") + ("<DF>" if prec else "<F64>")
             kms, bpp = p64, 24.0 * (1 + 4.0 / k)
         peak, peak_src = measured_hbm()
         achieved = bpp * I.npts / (kms / 1e3) / 1e9
@@ -501,6 +503,9 @@ def run_ours(args):
                            "paper_hcm_k8_1408": {"avhr": 1.117, "avs": 4.350,
                                                  "cite": "Tab. sinu_1, HCM 176x176 cells"}}}
         line["solver"]["bucket_width_main"] = s0.bucket_width
+        line["solver"]["schedule"] = {"fp32_pass_round_free": bool(s0.schedule & 1),
+                                      "main_pass_round_free": bool(s0.schedule & 2),
+                                      "one_double_float_pass": bool(s0.schedule & 4)}
         if not args.no_sweep:
             line["k_sweep"] = k_sweep(eik, torch, I, F, src, q, V)
         if not args.no_batch:

@@ -109,6 +109,8 @@ typedef struct {
                                (CUDA events on the plan's stream; 0 if not run) */
     int32_t launches;       /* kernels this solve launched */
     int32_t cell_k;         /* cell size used */
+    int32_t schedule;       /* bit 0: FP32 pass round-free; bit 1: FP64 / double-float pass
+                               round-free; bit 2: FP32_REFINE as one double-float pass */
     int32_t status;         /* EIK_OK or the error of this solve */
 } eik_stats;
 

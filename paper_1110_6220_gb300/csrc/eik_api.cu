@@ -336,6 +336,8 @@ int finish_job(HostJob* hj, const eik_plan_desc* descs, cudaStream_t st, double 
         eik_stats s;
         job_stats(hj->L[i], &descs[i], j.fp32, &ic[i], &ic[n + i], &g[0], &g[1], &r[i], hj->shift[i],
                   hj->bw_main[i], ms, &s);
+        s.schedule = (j.fp32 && !j.one_pass && j.async_first && j.k >= 8 ? 1 : 0) |
+                     (j.async_main && j.k >= 8 ? 2 : 0) | (j.one_pass ? 4 : 0);
         if (st_out) st_out[i] = s;
         if (s.status && !first_err) first_err = s.status;
     }

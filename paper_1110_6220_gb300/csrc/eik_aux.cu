@@ -1,7 +1,8 @@
 // eik_aux.cu -- the node-wise kernels around the persistent solver, each
 // launched once for all instances of a job: per-solve initialisation, the
-// FP32 -> double-float refinement seed, the FP64 residual that certifies the
-// FP32+refinement result, and the output copy.
+// FP32 -> double-float refinement seed, the residual that certifies the
+// FP32+refinement result (with the output copy of the pair modes), and the
+// output copy of the FP64 mode.
 #include "eik_solver.cuh"
 
 namespace eik {
@@ -25,6 +26,37 @@ __device__ __forceinline__ float2 df_of(double v) {
     const float hi = __double2float_rn(v);
     if (!(hi < inf_of<float>()) && !(hi > -inf_of<float>())) return make_float2(hi, 0.0f);
     return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
+// A positive double as a double-float pair without the FP64 pipe: hi keeps
+// the leading 24 significand bits (exact in a float), lo the next 24 of the
+// remaining 29 (rounded; 2^-53 relative).  False outside [2^-74, 2^127]
+// (the caller takes the FP64 route there).
+__device__ __forceinline__ bool split_pos(double v, float2* out) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e < 1023 - 74 || e > 1023 + 127) return false;
+    const float hi = __uint_as_float(((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff));
+    const float lo = __int2float_rn((int)(b & 0x1fffffffull)) * __uint_as_float((unsigned)(e - 1075 + 127) << 23);
+    *out = make_float2(hi, lo);
+    return true;
+}
+// A float as a double without the FP64 pipe (exponent rebias); subnormals,
+// infinities and NaN take the ordinary conversion.
+__device__ __forceinline__ double widen(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 255u) return (u & 0x7fffffffu) == 0u ? (u ? -0.0 : 0.0) : (double)x;
+    return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                            ((unsigned long long)(e + 896u) << 52) |
+                                            ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+// h / F for the pair modes: a double-float quotient from the split F, or the
+// FP64 quotient where F cannot be split
+__device__ __forceinline__ float2 f_pair(float hx, float hy, double h, double F) {
+    float2 Fp;
+    if (split_pos(F, &Fp)) return df_div(make_float2(hx, hy), Fp);
+    return df_of(h / F);
 }
 
 // The instance and the (row, column) of this thread's node in its padded grid.
@@ -67,31 +99,51 @@ __global__ void k_init_grid(const AuxInst* A, const int* blk_full, int n) {
     const int i = c - 1, j = r - 1;                          // grid node (ring: outside)
     const bool in = c < p.upitch && r < p.nyp + 2;
     const double INF = inf_of<double>();
-    double fv = INF;
+    const float FINF = inf_of<float>();
     bool bad = false;
+    double F = 0.0;
     if (in && i >= 0 && j >= 0 && i < p.nx && j < p.ny) {
-        const double F = p.F[(size_t)j * p.nx + i];
+        F = p.F[(size_t)j * p.nx + i];
         if (!(F >= 0.0) || F == INF) bad = true;
-        else fv = F == 0.0 ? INF : p.h / F;
     }
-    if (in) {
-        const size_t q = (size_t)r * p.upitch + c;
-        if (p.f64) p.f64[q] = fv;
-        // beyond 1e18 the FP32 quadratic would overflow: an obstacle for the
-        // FP32 pass; the refinement pass (48-bit pairs) restores the node
-        if (p.f32) p.f32[q] = fv < 1e18 ? (float)fv : inf_of<float>();
-        if (p.fdf) p.fdf[q] = fv < 1e18 ? df_of(fv) : make_float2(inf_of<float>(), 0.0f);
-        if (p.U64) p.U64[q] = INF;
-        if (p.U32) p.U32[q] = inf_of<float>();
-        if (p.Udf) p.Udf[q] = make_float2(inf_of<float>(), 0.0f);
+    const bool finite_f = !bad && F > 0.0;  // a grid node with a positive speed
+    if (p.f64) {
+        // FP64 mode: f = h/F in FP64
+        const double fv = finite_f ? p.h / F : INF;
+        if (in) {
+            const size_t q = (size_t)r * p.upitch + c;
+            p.f64[q] = fv;
+            p.U64[q] = INF;
+        }
+        unsigned long long k = (fv < INF) ? key_of(fv) : KEY_UNSET;
+        k = warp_min_u64(k);  // a warp lies in one row of one instance
+        if ((threadIdx.x & 31) == 0 && k != KEY_UNSET) atomicMin(&p.ctl->fmin_f, k);
+    } else {
+        // pair modes: f = h/F as a double-float quotient on the FP32 pipe;
+        // beyond 1e18 the FP32 quadratic would overflow: an obstacle
+        float2 fp = make_float2(FINF, 0.0f);
+        if (finite_f) {
+            fp = f_pair(p.hx, p.hy, p.h, F);
+            if (!(fp.x < 1e18f)) fp = make_float2(FINF, 0.0f);
+        }
+        if (in) {
+            const size_t q = (size_t)r * p.upitch + c;
+            p.fdf[q] = fp;
+            p.Udf[q] = make_float2(FINF, 0.0f);
+            if (p.f32) p.f32[q] = fp.x;
+            if (p.U32) p.U32[q] = FINF;
+        }
+        // smallest f of the row, then (one lane) a lower bound of it as a key
+        unsigned m = fp.x < FINF ? __float_as_uint(fp.x) : 0xffffffffu;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(FULL, m, o));
+        if ((threadIdx.x & 31) == 0 && m != 0xffffffffu) {
+            const unsigned long long k = key_of(widen(__uint_as_float(m)) * (1.0 - 0x1p-20));
+            atomicMin(&p.ctl->fmin_f, k);
+            if (p.ctl2) atomicMin(&p.ctl2->fmin_f, k);
+        }
     }
     if (bad) atomicCAS(&p.ctl->status, 0, EIK_EINVAL);
-    unsigned long long k = (fv < INF) ? key_of(fv) : KEY_UNSET;
-    k = warp_min_u64(k);  // a warp lies in one row of one instance
-    if ((threadIdx.x & 31) == 0 && k != KEY_UNSET) {
-        atomicMin(&p.ctl->fmin_f, k);
-        if (p.ctl2) atomicMin(&p.ctl2->fmin_f, k);
-    }
 }
 
 __global__ void k_fill(double* a, size_t n, double v) {
@@ -205,41 +257,73 @@ __global__ void k_seed_cells(const AuxInst* A, const int* cell_pre, int n, int n
     }
 }
 
-// r = |V - T(V)| at every non-source node, with T the FP64 local update and
-// f = h/F recomputed in FP64 from F (+inf against a finite value counts as an
-// infinite residual), and max finite V.
+// Certificate data of the pair modes, and the output.  At every non-source
+// node, an upper bound of r = |V - T(V)|: T the exact local update (eqs.
+// one_sided_update / two_sided_update with the relevant-quadrant shortcut)
+// with f = h/F recomputed from F.  T(V) - V is evaluated relative to V in
+// double-float arithmetic on the FP32 pipe -- the upwind offsets, 2 f^2 - d^2,
+// its root and the quotient of the cancellation-free form all carry ~46 bits
+// -- and an allowance of 2^-40 (V + min(a, b) + 4 f) covers every rounding of
+// that evaluation and of f (over a hundred times the worst case of the dozen
+// pair operations involved).  +inf against a finite value counts as an
+// infinite residual.  Also the max finite V, and out = V + min q.
 __global__ void k_residual(const AuxInst* A, const int* blk_pre, int n) {
     const Where w = locate(A, blk_pre, n);
     const AuxInst& p = A[w.inst];
     const int i = w.i, j = w.j;
-    const double INF = inf_of<double>();
-    double r = 0.0, umax = 0.0;
+    const float FINF = inf_of<float>();
+    float r = 0.0f, umax = 0.0f;
     unsigned long long bad = 0;
     if (i < p.nx && j < p.ny) {
         const size_t q = (size_t)(j + 1) * p.upitch + (i + 1);
         const int up = p.upitch;
-        auto val = [&](size_t e) {
-            const float2 a = p.Udf[e];
-            return a.x < inf_of<float>() ? (double)a.x + (double)a.y : INF;
-        };
-        const double v = val(q);
-        if (v < INF) umax = v;
-        if (!(p.fdf[q].x < 0.0f)) {
+        const float2 V = p.Udf[q];
+        const bool vfin = V.x < FINF;
+        if (vfin) umax = V.x;
+        p.out[(size_t)j * p.nx + i] = vfin ? widen(V.x) + widen(V.y) + p.shift : inf_of<double>();
+        if (!(p.fdf[q].x < 0.0f)) {  // not a source
             const double Fv = p.F[(size_t)j * p.nx + i];
-            const double fv = Fv > 0.0 ? p.h / Fv : INF;
-            const double t = fv < INF ? update_f64(val(q - 1), val(q + 1), val(q - up), val(q + up), fv,
-                                                   2.0 * fv * fv)
-                                      : INF;
-            if (v < INF && t < INF) r = fabs(v - t);
-            else if (v < INF || t < INF) { r = INF; bad = 1; }
+            float2 f = make_float2(FINF, 0.0f);
+            if (Fv > 0.0) {
+                f = f_pair(p.hx, p.hy, p.h, Fv);
+                if (!(f.x < 1e18f)) f = make_float2(FINF, 0.0f);
+            }
+            const float2 W = p.Udf[q - 1], E = p.Udf[q + 1], S = p.Udf[q - up], N = p.Udf[q + up];
+            const float2 a = lt(E, W) ? E : W, b = lt(N, S) ? N : S;
+            const bool ab = lt(a, b);
+            const float2 lo = ab ? a : b, hi = ab ? b : a;
+            const bool tfin = f.x < FINF && lo.x < FINF;
+            if (vfin && tfin) {
+                const float2 d = hi.x < FINF ? df_sub(hi, lo) : make_float2(FINF, 0.0f);
+                float2 R;  // T(V) - V
+                if (lt(d, f)) {
+                    const float2 x = df_sub(df_add(df_mul(f, f), df_mul(f, f)), df_mul(d, d));
+                    const float2 inc = df_div(df_mul(df_sub(f, d), df_add(f, d)), df_add(d, df_sqrt(x)));
+                    R = df_add(df_sub(hi, V), inc);
+                } else {
+                    R = df_add(df_sub(lo, V), f);
+                }
+                const float allow = 0x1p-40f * (V.x + lo.x + 4.0f * f.x);
+                r = (fabsf(R.x) + fabsf(R.y) + allow) * (1.0f + 0x1p-20f);
+            } else if (vfin || tfin) {
+                r = FINF;
+                bad = 1;
+            }
         }
     }
-    const unsigned long long kr = warp_max_u64(key_of(r));
-    const unsigned long long ku = warp_max_u64(key_of(umax));
-    for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(FULL, bad, o);
+    // maxima of the warp on the float images (all >= 0), one atomic per warp
+    unsigned rb = __float_as_uint(r), ub = __float_as_uint(umax);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rb = max(rb, __shfl_xor_sync(FULL, rb, o));
+        ub = max(ub, __shfl_xor_sync(FULL, ub, o));
+        bad += __shfl_xor_sync(FULL, bad, o);
+    }
     if ((threadIdx.x & 31) == 0) {
-        atomicMax(&p.res->r_max, kr);
-        atomicMax(&p.res->u_max, ku);
+        const float rf = __uint_as_float(rb);
+        atomicMax(&p.res->r_max, key_of(rf < FINF ? widen(rf) : inf_of<double>()));
+        // V.y < ulp(V.x): a bound of max V
+        atomicMax(&p.res->u_max, key_of(widen(__uint_as_float(ub)) * (1.0 + 0x1p-20)));
         if (bad) atomicAdd(&p.res->n_bad, bad);
     }
 }

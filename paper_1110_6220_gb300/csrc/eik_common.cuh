@@ -150,6 +150,7 @@ struct AuxInst {
     const double* F;              // nx*ny row-major speeds (device)
     double* out;                  // nx*ny result (device; the caller's or staging)
     double h;
+    float hx, hy;                 // h as a double-float pair
     double shift;                 // min q: stored values are U - shift
     int nx, ny, nxp, nyp, upitch, k, cxn, cyn;
     double* U64; double* f64;

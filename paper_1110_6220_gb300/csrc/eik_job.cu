@@ -137,6 +137,8 @@ void fill_inst_tables(const Layout& L, const InstArrays& a, bool fp32, double h,
     aux->F = F;
     aux->out = out;
     aux->h = h;
+    aux->hx = (float)h;
+    aux->hy = (float)(h - (double)aux->hx);
     aux->shift = shift;
     aux->nx = L.nx;
     aux->ny = L.ny;
@@ -244,8 +246,10 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
         if (ev) cudaEventRecord(ev[3], st);
         ++nl;
     }
-    if (launch_output(j.aux, j.blk_pre, n, j.nblocks, st) != cudaSuccess) return EIK_ECUDA;
-    ++nl;
+    if (!j.fp32) {  // the pair modes' residual kernel writes the output
+        if (launch_output(j.aux, j.blk_pre, n, j.nblocks, st) != cudaSuccess) return EIK_ECUDA;
+        ++nl;
+    }
     if (launches) *launches = nl;
     return EIK_OK;
 }

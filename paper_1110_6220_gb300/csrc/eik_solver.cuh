@@ -175,6 +175,39 @@ __device__ __forceinline__ float2 df_add_f(float2 a, float b) {
     return fast_two_sum(s.x, s.y);
 }
 
+// Products, quotients and square roots of pairs (the refinement's residual
+// and its start values).  two_prod is exact (Dekker's product through one
+// fused multiply-add); df_mul keeps the cross terms; df_div and df_sqrt take
+// the FP32 quotient / root and add one Newton correction computed from the
+// exact residual of that first approximation (Markstein's and Heron's
+// correction steps).  Each is accurate to a few units of 2^-46 relative to
+// its operands.
+__device__ __forceinline__ float2 two_prod(float a, float b) {
+    const float p = a * b;
+    return make_float2(p, fmaf(a, b, -p));
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 df_sub(float2 a, float2 b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    float2 p = two_prod(a.x, b.x);
+    p.y = fmaf(a.x, b.y, fmaf(a.y, b.x, p.y));
+    return fast_two_sum(p.x, p.y);
+}
+__device__ __forceinline__ float2 df_div(float2 a, float2 b) {  // b > 0 finite
+    const float q0 = a.x / b.x;
+    const float2 p = two_prod(q0, b.x);  // q0 b.x exactly
+    // a - q0 b: a.x - p.x is exact (the two agree to within a rounding)
+    const float r = ((a.x - p.x) - p.y) + fmaf(-q0, b.y, a.y);
+    return fast_two_sum(q0, r / b.x);
+}
+__device__ __forceinline__ float2 df_sqrt(float2 a) {  // a >= 0 finite
+    if (!(a.x > 0.0f)) return make_float2(0.0f, 0.0f);
+    const float y0 = sqrtf(a.x);
+    const float2 p = two_prod(y0, y0);
+    const float r = ((a.x - p.x) - p.y) + a.y;  // a - y0^2
+    return fast_two_sum(y0, r / (2.0f * y0));
+}
+
 // order, finiteness and conversion of a stored value, for each representation
 // (normalised pairs with hi >= 0 order lexicographically)
 __device__ __forceinline__ bool lt(float2 a, float2 b) { return a.x < b.x || (a.x == b.x && a.y < b.y); }
@@ -512,13 +545,14 @@ struct WarpState {
 // each tile with its halo, passes of four concurrent directional sweeps to
 // the fixed point, write-back of the changed nodes, then the activation test
 // of every side (Alg. generic_LC_cells) with the neighbour's cell value
-// (eq. cell_value, min-updated here).  For each side with a neighbour, one
+// (eq. cell_value, min-updated here when CVAL: the bucketed schedule orders
+// by it, the round-free one does not need it).  For each side with a neighbour, one
 // lane calls act(d, nc, key, old, activate): key/old the proposed and the
 // previous cell value of neighbour cell nc of instance d, activate the
 // outcome of the test -- the scheduler's part.  c, ii, first: this lane's
 // cell, its instance and whether this is the cell's first removal.  Returns
 // false when the TMA wait gave up (abort raised).
-template <int MODE, int K, class Act>
+template <int MODE, int K, bool CVAL, class Act>
 __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDesc* inst, Ctl* gctl,
                                             unsigned long long deadline, int c, int ii, int first,
                                             const int* cg, const int* ig, int prof_on,
@@ -734,7 +768,7 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
         if (rl == 0 && has_nb) {
             const int nc = sd == 0 ? c - 1 : sd == 1 ? c + 1 : sd == 2 ? c - cxn : c + cxn;
             double vt = inf_of<double>();
-            if (bmax >= 0) {
+            if (CVAL && bmax >= 0) {
                 // eq. cell_value: V_i + ((h + h^c)/2) / F(y_i) with
                 // (h + h^c)/2 = (k+1) h/2; h/F(y_i) read at the node across
                 // the boundary from x_i (the box in shared memory carries a
@@ -751,7 +785,7 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
             // HCM: update the neighbour's cell value whether or not it is
             // activated
             unsigned long long old = KEY_UNSET, kk = KEY_UNSET;
-            if (vt < inf_of<double>()) {
+            if (CVAL && vt < inf_of<double>()) {
                 kk = key_of(vt);
                 old = atomicMin(&d.cval[nc], kk);
             }
@@ -951,7 +985,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
             PROF_MARK(2);
             pacc[7] += 1;
 
-            const bool ok = visit_cells<MODE, K>(
+            const bool ok = visit_cells<MODE, K, true>(
                 w, inst, gctl, deadline, c, ii_, first, cg, ig, prof_on, pacc, pt,
                 [&](const InstDesc& dn, int nc, unsigned long long kk, unsigned long long old, bool activate) {
                     const int was = activate ? atomicExch(&dn.qflag[nc], 1) : 1;
@@ -1133,7 +1167,12 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
     }
     if (!grid_sync(gctl, deadline, &s_flag)) return;
 
-    // ---- each warp: take a cell, solve it, hand on its activations
+    // ---- each warp: take a cell, solve it, hand on its activations.  (A
+    // warp that kept one of the neighbours it requested and ran it next,
+    // skipping the ring, was measured slower: running ahead depth first
+    // reaches cells before their other upstream neighbours settle, and the
+    // revisits outweigh the saved round trips.  First in, first out keeps the
+    // wave together.)
     for (;;) {
         int e = 0;
         if (lane == 0) e = ring_pop(p, gctl, deadline);
@@ -1156,7 +1195,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
         PROF_MARK(2);
         pacc[7] += 1;
         const int cg[1] = {c}, ig[1] = {ii};
-        const bool ok = visit_cells<MODE, K>(
+        const bool ok = visit_cells<MODE, K, false>(
             w, inst, gctl, deadline, c, ii, first, cg, ig, prof_on, pacc, pt,
             [&](const InstDesc& dn, int nc, unsigned long long, unsigned long long, bool activate) {
                 if (activate && atomicOr(&dn.qflag[nc], 1) == 0) {
