@@ -160,8 +160,8 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     // block prefixes carry their owner tables (one int per block) behind them
     size_t nb_int = 0, nb_full = 0;
     for (int i = 0; i < n; ++i) {
-        nb_int += (size_t)((hj->L[i].nyp + 7) / 8) * ((hj->L[i].nxp + 31) / 32);
-        nb_full += (size_t)((hj->L[i].urows + 7) / 8) * ((hj->L[i].upitch + 31) / 32);
+        nb_int += (size_t)aux_blocks(hj->L[i].nyp, hj->L[i].nxp);
+        nb_full += (size_t)aux_blocks(hj->L[i].urows, hj->L[i].upitch);
     }
     const size_t t_own_int = a256((size_t)(n + 1) * 4 + nb_int * 4);
     const size_t t_own_full = a256((size_t)(n + 1) * 4 + nb_full * 4);
@@ -170,10 +170,11 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     const size_t image_bytes = 2 * t_desc + t_aux + t_own_int + t_pre + t_own_full + t_src;
     const size_t z_ctl = a256((size_t)(2 * n + 2) * sizeof(Ctl) + (size_t)n * sizeof(ResidualOut));
     const size_t zero_bytes = z_ctl + a256(Jtot * 4) * 2;
-    // ring of the round-free schedule: a power of two >= twice the job's
-    // cells and the warps of a launch, behind its three counters
+    // ring of the round-free schedule: a power of two >= 16 times the job's
+    // cells (a launch rarely pushes more, so pushes seldom wait for a slot)
+    // and the warps of a launch, behind its three counters
     size_t Q = 8192;
-    while (Q < 2 * Jtot) Q <<= 1;
+    while (Q < 16 * Jtot) Q <<= 1;
     const size_t hist_bytes = a256((3 * 8192 + 1) * 4);
     const size_t ring_bytes = a256(384 + hist_bytes + Q * 8);
     const size_t total = image_bytes + zero_bytes + a256(Jtot * 8) + ring_bytes + ibytes + 256;
@@ -232,9 +233,9 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
         desc_main_h[i].cell_base = (int)coff;
         if (fp32) desc_f32_h[i].cell_base = (int)coff;
         blk_pre_h[i] = boff;
-        boff += ((L.nyp + 7) / 8) * ((L.nxp + 31) / 32);
+        boff += aux_blocks(L.nyp, L.nxp);
         blk_full_h[i] = bfull;
-        bfull += ((L.urows + 7) / 8) * ((L.upitch + 31) / 32);
+        bfull += aux_blocks(L.urows, L.upitch);
         cell_pre_h[i] = (int)coff;
         coff += (size_t)L.J;
         for (size_t e = 0; e < hs[i].node.size(); ++e, ++so) {
@@ -393,7 +394,7 @@ extern "C" size_t eik_plan_workspace_bytes(const eik_plan_desc* d) {
     const Layout L = make_layout(d->nx, d->ny, default_k(d));
     const bool fp32 = d->precision == EIK_FP32_REFINE;
     size_t Q = 8192;
-    while (Q < 2 * (size_t)L.J) Q <<= 1;
+    while (Q < 16 * (size_t)L.J) Q <<= 1;
     return inst_bytes(L, fp32, true, true) + (size_t)L.J * 16 + Q * 8 + 128 * 1024;
 }
 

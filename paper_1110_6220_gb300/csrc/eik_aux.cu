@@ -10,7 +10,8 @@ namespace eik {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int ROWS = 8;  // rows per block (256 threads = 8 rows x 32 columns)
+constexpr int ROWS = AUX_ROWS;      // rows per block (256 threads = 8 rows x 32 lanes)
+constexpr int SPAN = AUX_COLS / 32;  // nodes per thread, 32 columns apart
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
 #pragma unroll
@@ -30,12 +31,12 @@ __device__ __forceinline__ float2 df_of(double v) {
 
 // A positive double as a double-float pair without the FP64 pipe: hi keeps
 // the leading 24 significand bits (exact in a float), lo the next 24 of the
-// remaining 29 (rounded; 2^-53 relative).  False outside [2^-74, 2^127]
+// remaining 29 (rounded; 2^-53 relative).  False outside [2^-74, 2^126)
 // (the caller takes the FP64 route there).
 __device__ __forceinline__ bool split_pos(double v, float2* out) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int e = (int)((b >> 52) & 0x7ff);
-    if (e < 1023 - 74 || e > 1023 + 127) return false;
+    if (e < 1023 - 74 || e > 1023 + 125) return false;
     const float hi = __uint_as_float(((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff));
     const float lo = __int2float_rn((int)(b & 0x1fffffffull)) * __uint_as_float((unsigned)(e - 1075 + 127) << 23);
     *out = make_float2(hi, lo);
@@ -59,7 +60,8 @@ __device__ __forceinline__ float2 f_pair(float hx, float hy, double h, double F)
     return df_of(h / F);
 }
 
-// The instance and the (row, column) of this thread's node in its padded grid.
+// The instance and the (row, first column) of this thread's nodes in its
+// padded grid: columns i, i + 32, ..., i + 32 (SPAN - 1).
 struct Where {
     int inst, i, j;
 };
@@ -68,10 +70,10 @@ __device__ __forceinline__ Where locate(const AuxInst* a, const int* blk_pre, in
     // blk_pre[n + 1 + b] holds the instance of block b (see k_block_owner)
     const int lo = blk_pre[n + 1 + b];
     const int local = b - blk_pre[lo];
-    const int tx = (a[lo].nxp + 31) / 32;
+    const int tx = (a[lo].nxp + AUX_COLS - 1) / AUX_COLS;
     Where w;
     w.inst = lo;
-    w.i = (local % tx) * 32 + (threadIdx.x & 31);
+    w.i = (local % tx) * AUX_COLS + (threadIdx.x & 31);
     w.j = (local / tx) * ROWS + (threadIdx.x >> 5);
     return w;
 }
@@ -93,52 +95,64 @@ __global__ void k_init_grid(const AuxInst* A, const int* blk_full, int n) {
     const int lo = blk_full[n + 1 + b];
     const AuxInst& p = A[lo];
     const int local = b - blk_full[lo];
-    const int tx = (p.upitch + 31) / 32;
-    const int c = (local % tx) * 32 + (threadIdx.x & 31);   // column in the padded array
-    const int r = (local / tx) * ROWS + (threadIdx.x >> 5); // row in the padded array
-    const int i = c - 1, j = r - 1;                          // grid node (ring: outside)
-    const bool in = c < p.upitch && r < p.nyp + 2;
+    const int tx = (p.upitch + AUX_COLS - 1) / AUX_COLS;
+    const int c0 = (local % tx) * AUX_COLS + (threadIdx.x & 31);  // first column in the padded array
+    const int r = (local / tx) * ROWS + (threadIdx.x >> 5);        // row in the padded array
+    const int j = r - 1;                                            // grid row (ring: outside)
     const double INF = inf_of<double>();
     const float FINF = inf_of<float>();
-    bool bad = false;
-    double F = 0.0;
-    if (in && i >= 0 && j >= 0 && i < p.nx && j < p.ny) {
-        F = p.F[(size_t)j * p.nx + i];
-        if (!(F >= 0.0) || F == INF) bad = true;
-    }
-    const bool finite_f = !bad && F > 0.0;  // a grid node with a positive speed
-    if (p.f64) {
-        // FP64 mode: f = h/F in FP64
-        const double fv = finite_f ? p.h / F : INF;
-        if (in) {
-            const size_t q = (size_t)r * p.upitch + c;
-            p.f64[q] = fv;
-            p.U64[q] = INF;
-        }
-        unsigned long long k = (fv < INF) ? key_of(fv) : KEY_UNSET;
-        k = warp_min_u64(k);  // a warp lies in one row of one instance
-        if ((threadIdx.x & 31) == 0 && k != KEY_UNSET) atomicMin(&p.ctl->fmin_f, k);
-    } else {
-        // pair modes: f = h/F as a double-float quotient on the FP32 pipe;
-        // beyond 1e18 the FP32 quadratic would overflow: an obstacle
-        float2 fp = make_float2(FINF, 0.0f);
-        if (finite_f) {
-            fp = f_pair(p.hx, p.hy, p.h, F);
-            if (!(fp.x < 1e18f)) fp = make_float2(FINF, 0.0f);
-        }
-        if (in) {
-            const size_t q = (size_t)r * p.upitch + c;
-            p.fdf[q] = fp;
-            p.Udf[q] = make_float2(FINF, 0.0f);
-            if (p.f32) p.f32[q] = fp.x;
-            if (p.U32) p.U32[q] = FINF;
-        }
-        // smallest f of the row, then (one lane) a lower bound of it as a key
-        unsigned m = fp.x < FINF ? __float_as_uint(fp.x) : 0xffffffffu;
+    // the speeds first, all at once
+    double F[SPAN];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(FULL, m, o));
-        if ((threadIdx.x & 31) == 0 && m != 0xffffffffu) {
-            const unsigned long long k = key_of(widen(__uint_as_float(m)) * (1.0 - 0x1p-20));
+    for (int s = 0; s < SPAN; ++s) {
+        const int i = c0 + 32 * s - 1;
+        F[s] = (i >= 0 && j >= 0 && i < p.nx && j < p.ny) ? p.F[(size_t)j * p.nx + i] : 0.0;
+    }
+    bool bad = false;
+    unsigned long long kmin = KEY_UNSET;
+    unsigned mmin = 0xffffffffu;
+#pragma unroll
+    for (int s = 0; s < SPAN; ++s) {
+        const int c = c0 + 32 * s;
+        const bool in = c < p.upitch && r < p.nyp + 2;
+        if (!(F[s] >= 0.0) || F[s] == INF) bad = true;
+        const bool finite_f = F[s] > 0.0 && F[s] < INF;  // a grid node with a positive speed
+        const size_t q = (size_t)r * p.upitch + c;
+        if (p.f64) {
+            // FP64 mode: f = h/F in FP64
+            const double fv = finite_f ? p.h / F[s] : INF;
+            if (in) {
+                p.f64[q] = fv;
+                p.U64[q] = INF;
+            }
+            if (fv < INF) kmin = min(kmin, key_of(fv));
+        } else {
+            // pair modes: f = h/F as a double-float quotient on the FP32
+            // pipe; beyond 1e18 the FP32 quadratic would overflow: an obstacle
+            float2 fp = make_float2(FINF, 0.0f);
+            if (finite_f) {
+                fp = f_pair(p.hx, p.hy, p.h, F[s]);
+                if (!(fp.x < 1e18f)) fp = make_float2(FINF, 0.0f);
+            }
+            if (in) {
+                p.fdf[q] = fp;
+                p.Udf[q] = make_float2(FINF, 0.0f);
+                if (p.f32) p.f32[q] = fp.x;
+                if (p.U32) p.U32[q] = FINF;
+            }
+            if (fp.x < FINF) mmin = min(mmin, __float_as_uint(fp.x));
+        }
+    }
+    // the smallest f of the warp's row, one atomic per warp (pair modes: a
+    // lower bound of it, from the leading float)
+    if (p.f64) {
+        kmin = warp_min_u64(kmin);
+        if ((threadIdx.x & 31) == 0 && kmin != KEY_UNSET) atomicMin(&p.ctl->fmin_f, kmin);
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mmin = min(mmin, __shfl_xor_sync(FULL, mmin, o));
+        if ((threadIdx.x & 31) == 0 && mmin != 0xffffffffu) {
+            const unsigned long long k = key_of(widen(__uint_as_float(mmin)) * (1.0 - 0x1p-20));
             atomicMin(&p.ctl->fmin_f, k);
             if (p.ctl2) atomicMin(&p.ctl2->fmin_f, k);
         }
@@ -210,31 +224,35 @@ __global__ void k_ctl_init(Ctl* ctl, int count) {
 __global__ void k_seed(const AuxInst* A, const int* blk_pre, int n, float beta) {
     const Where w = locate(A, blk_pre, n);
     const AuxInst& p = A[w.inst];
-    const int i = w.i, j = w.j;
-    const bool in = i < p.nx && j < p.ny;
-    unsigned long long k = KEY_UNSET;
-    if (in) {
-        const size_t q = (size_t)(j + 1) * p.upitch + (i + 1);
-        const float2 fv = p.fdf[q];
-        float2 v;
-        if (fv.x < 0.0f) {
-            v = p.Udf[q];  // source: keeps q
-        } else {
-            const float u = p.U32[q];
-            v = (fv.x < inf_of<float>() && u < inf_of<float>()) ? make_float2(u * (1.0f + beta), 0.0f)
-                                                                 : make_float2(inf_of<float>(), 0.0f);
-            p.Udf[q] = v;
+    const int j = w.j;
+#pragma unroll
+    for (int s = 0; s < SPAN; ++s) {
+        const int i = w.i + 32 * s;
+        const bool in = i < p.nx && j < p.ny;
+        unsigned long long k = KEY_UNSET;
+        if (in) {
+            const size_t q = (size_t)(j + 1) * p.upitch + (i + 1);
+            const float2 fv = p.fdf[q];
+            float2 v;
+            if (fv.x < 0.0f) {
+                v = p.Udf[q];  // source: keeps q
+            } else {
+                const float u = p.U32[q];
+                v = (fv.x < inf_of<float>() && u < inf_of<float>()) ? make_float2(u * (1.0f + beta), 0.0f)
+                                                                     : make_float2(inf_of<float>(), 0.0f);
+                p.Udf[q] = v;
+            }
+            if (v.x < inf_of<float>()) k = key_of((double)v.x + (double)v.y);
         }
-        if (v.x < inf_of<float>()) k = key_of((double)v.x + (double)v.y);
-    }
-    // min over the k-wide segment of the row that lies in one cell
-    for (int o = 1; o < p.k && o < 32; o <<= 1) {
-        const unsigned long long x = __shfl_xor_sync(FULL, k, o);
-        k = x < k ? x : k;
-    }
-    if (in && (i % (p.k < 32 ? p.k : 32)) == 0 && k != KEY_UNSET) {
-        const int c = (j / p.k) * p.cxn + (i / p.k);
-        atomicMin(&p.cval[c], k);
+        // min over the k-wide segment of the row that lies in one cell
+        for (int o = 1; o < p.k && o < 32; o <<= 1) {
+            const unsigned long long x = __shfl_xor_sync(FULL, k, o);
+            k = x < k ? x : k;
+        }
+        if (in && (i % (p.k < 32 ? p.k : 32)) == 0 && k != KEY_UNSET) {
+            const int c = (j / p.k) * p.cxn + (i / p.k);
+            atomicMin(&p.cval[c], k);
+        }
     }
 }
 
@@ -249,8 +267,10 @@ __global__ void k_seed_cells(const AuxInst* A, const int* cell_pre, int n, int n
     }
     const AuxInst& p = A[lo];
     const int c = e - cell_pre[lo];
+    // the FP32 pass may leave flags behind (its removal marks): a cell not
+    // queued here starts idle
+    p.qflag[c] = p.cval[c] != KEY_UNSET ? 1 : 0;
     if (p.cval[c] != KEY_UNSET) {
-        p.qflag[c] = 1;
         p.visits[c] = 0;
         const int pos = atomicAdd(&p.ctl2->fcnt[0], 1);
         if (pos < p.J) p.far0[pos] = c;
@@ -270,45 +290,48 @@ __global__ void k_seed_cells(const AuxInst* A, const int* cell_pre, int n, int n
 __global__ void k_residual(const AuxInst* A, const int* blk_pre, int n) {
     const Where w = locate(A, blk_pre, n);
     const AuxInst& p = A[w.inst];
-    const int i = w.i, j = w.j;
+    const int j = w.j;
+    const int up = p.upitch;
     const float FINF = inf_of<float>();
     float r = 0.0f, umax = 0.0f;
     unsigned long long bad = 0;
-    if (i < p.nx && j < p.ny) {
-        const size_t q = (size_t)(j + 1) * p.upitch + (i + 1);
-        const int up = p.upitch;
+#pragma unroll
+    for (int s = 0; s < SPAN; ++s) {
+        const int i = w.i + 32 * s;
+        if (i >= p.nx || j >= p.ny) continue;
+        const size_t q = (size_t)(j + 1) * up + (i + 1);
         const float2 V = p.Udf[q];
+        const float2 fs = p.fdf[q];
+        const double Fv = p.F[(size_t)j * p.nx + i];
+        const float2 W = p.Udf[q - 1], E = p.Udf[q + 1], S = p.Udf[q - up], N = p.Udf[q + up];
         const bool vfin = V.x < FINF;
-        if (vfin) umax = V.x;
+        if (vfin) umax = fmaxf(umax, V.x);
         p.out[(size_t)j * p.nx + i] = vfin ? widen(V.x) + widen(V.y) + p.shift : inf_of<double>();
-        if (!(p.fdf[q].x < 0.0f)) {  // not a source
-            const double Fv = p.F[(size_t)j * p.nx + i];
-            float2 f = make_float2(FINF, 0.0f);
-            if (Fv > 0.0) {
-                f = f_pair(p.hx, p.hy, p.h, Fv);
-                if (!(f.x < 1e18f)) f = make_float2(FINF, 0.0f);
+        if (fs.x < 0.0f) continue;  // a source
+        float2 f = make_float2(FINF, 0.0f);
+        if (Fv > 0.0) {
+            f = f_pair(p.hx, p.hy, p.h, Fv);
+            if (!(f.x < 1e18f)) f = make_float2(FINF, 0.0f);
+        }
+        const float2 a = lt(E, W) ? E : W, b = lt(N, S) ? N : S;
+        const bool ab = lt(a, b);
+        const float2 lo = ab ? a : b, hi = ab ? b : a;
+        const bool tfin = f.x < FINF && lo.x < FINF;
+        if (vfin && tfin) {
+            const float2 d = hi.x < FINF ? df_sub(hi, lo) : make_float2(FINF, 0.0f);
+            float2 R;  // T(V) - V
+            if (lt(d, f)) {
+                const float2 x = df_sub(df_add(df_mul(f, f), df_mul(f, f)), df_mul(d, d));
+                const float2 inc = df_div(df_mul(df_sub(f, d), df_add(f, d)), df_add(d, df_sqrt(x)));
+                R = df_add(df_sub(hi, V), inc);
+            } else {
+                R = df_add(df_sub(lo, V), f);
             }
-            const float2 W = p.Udf[q - 1], E = p.Udf[q + 1], S = p.Udf[q - up], N = p.Udf[q + up];
-            const float2 a = lt(E, W) ? E : W, b = lt(N, S) ? N : S;
-            const bool ab = lt(a, b);
-            const float2 lo = ab ? a : b, hi = ab ? b : a;
-            const bool tfin = f.x < FINF && lo.x < FINF;
-            if (vfin && tfin) {
-                const float2 d = hi.x < FINF ? df_sub(hi, lo) : make_float2(FINF, 0.0f);
-                float2 R;  // T(V) - V
-                if (lt(d, f)) {
-                    const float2 x = df_sub(df_add(df_mul(f, f), df_mul(f, f)), df_mul(d, d));
-                    const float2 inc = df_div(df_mul(df_sub(f, d), df_add(f, d)), df_add(d, df_sqrt(x)));
-                    R = df_add(df_sub(hi, V), inc);
-                } else {
-                    R = df_add(df_sub(lo, V), f);
-                }
-                const float allow = 0x1p-40f * (V.x + lo.x + 4.0f * f.x);
-                r = (fabsf(R.x) + fabsf(R.y) + allow) * (1.0f + 0x1p-20f);
-            } else if (vfin || tfin) {
-                r = FINF;
-                bad = 1;
-            }
+            const float allow = 0x1p-40f * (V.x + lo.x + 4.0f * f.x);
+            r = fmaxf(r, (fabsf(R.x) + fabsf(R.y) + allow) * (1.0f + 0x1p-20f));
+        } else if (vfin || tfin) {
+            r = FINF;
+            bad += 1;
         }
     }
     // maxima of the warp on the float images (all >= 0), one atomic per warp
@@ -331,17 +354,21 @@ __global__ void k_residual(const AuxInst* A, const int* blk_pre, int n) {
 __global__ void k_output(const AuxInst* A, const int* blk_pre, int n) {
     const Where w = locate(A, blk_pre, n);
     const AuxInst& p = A[w.inst];
-    const int i = w.i, j = w.j;
-    if (i < p.nx && j < p.ny) {
-        const size_t q = (size_t)(j + 1) * p.upitch + (i + 1);
-        double v;
-        if (p.U64) {
-            v = p.U64[q];
-        } else {
-            const float2 a = p.Udf[q];
-            v = a.x < inf_of<float>() ? (double)a.x + (double)a.y : inf_of<double>();
+    const int j = w.j;
+#pragma unroll
+    for (int s = 0; s < SPAN; ++s) {
+        const int i = w.i + 32 * s;
+        if (i < p.nx && j < p.ny) {
+            const size_t q = (size_t)(j + 1) * p.upitch + (i + 1);
+            double v;
+            if (p.U64) {
+                v = p.U64[q];
+            } else {
+                const float2 a = p.Udf[q];
+                v = a.x < inf_of<float>() ? widen(a.x) + widen(a.y) : inf_of<double>();
+            }
+            p.out[(size_t)j * p.nx + i] = v + p.shift;
         }
-        p.out[(size_t)j * p.nx + i] = v + p.shift;
     }
 }
 

@@ -146,6 +146,14 @@ struct ResidualOut {              // reduced with atomics on ordered keys
     unsigned long long n_bad;     // finite/infinite mismatches
 };
 
+// Node-wise kernels (eik_aux.cu) map blocks of AUX_ROWS x AUX_COLS nodes
+// onto each instance's padded array; a thread handles AUX_COLS / 32 nodes of
+// its row, 32 columns apart.
+constexpr int AUX_ROWS = 8, AUX_COLS = 128;
+__host__ __device__ inline int aux_blocks(int rows, int cols) {
+    return ((rows + AUX_ROWS - 1) / AUX_ROWS) * ((cols + AUX_COLS - 1) / AUX_COLS);
+}
+
 struct AuxInst {
     const double* F;              // nx*ny row-major speeds (device)
     double* out;                  // nx*ny result (device; the caller's or staging)

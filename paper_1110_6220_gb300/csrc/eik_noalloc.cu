@@ -170,8 +170,8 @@ extern "C" int eik_solve_noalloc(const eik_plan_desc* d, const eik_instance* in,
     std::memset((void*)&tb, 0, sizeof(tb));
     Tables* tdev = (Tables*)take(sizeof(Tables));
     // block prefixes, each followed by its owner table (filled on the device)
-    const int nbi = ((L.nyp + 7) / 8) * ((L.nxp + 31) / 32);
-    const int nbf = ((L.urows + 7) / 8) * ((L.upitch + 31) / 32);
+    const int nbi = aux_blocks(L.nyp, L.nxp);
+    const int nbf = aux_blocks(L.urows, L.upitch);
     int* blk_pre_dev = (int*)take((size_t)(2 + nbi) * 4);
     int* blk_full_dev = (int*)take((size_t)(2 + nbf) * 4);
     const int blk_pre_h[2] = {0, nbi};

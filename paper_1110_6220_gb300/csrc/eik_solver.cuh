@@ -193,19 +193,22 @@ __device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
     p.y = fmaf(a.x, b.y, fmaf(a.y, b.x, p.y));
     return fast_two_sum(p.x, p.y);
 }
-__device__ __forceinline__ float2 df_div(float2 a, float2 b) {  // b > 0 finite
-    const float q0 = a.x / b.x;
+// The first approximations come from the fast reciprocal / inverse-root
+// units (a couple of ulps); the correction squares that error away.
+__device__ __forceinline__ float2 df_div(float2 a, float2 b) {  // 0 < b < 2^126
+    const float q0 = __fdividef(a.x, b.x);
     const float2 p = two_prod(q0, b.x);  // q0 b.x exactly
-    // a - q0 b: a.x - p.x is exact (the two agree to within a rounding)
+    // a - q0 b: a.x - p.x is exact (the two agree to within a few roundings)
     const float r = ((a.x - p.x) - p.y) + fmaf(-q0, b.y, a.y);
-    return fast_two_sum(q0, r / b.x);
+    return fast_two_sum(q0, __fdividef(r, b.x));
 }
-__device__ __forceinline__ float2 df_sqrt(float2 a) {  // a >= 0 finite
+__device__ __forceinline__ float2 df_sqrt(float2 a) {  // 0 <= a < 2^126
     if (!(a.x > 0.0f)) return make_float2(0.0f, 0.0f);
-    const float y0 = sqrtf(a.x);
+    const float ri = rsqrtf(a.x);
+    const float y0 = a.x * ri;
     const float2 p = two_prod(y0, y0);
     const float r = ((a.x - p.x) - p.y) + a.y;  // a - y0^2
-    return fast_two_sum(y0, r / (2.0f * y0));
+    return fast_two_sum(y0, 0.5f * r * ri);
 }
 
 // order, finiteness and conversion of a stored value, for each representation
@@ -1028,7 +1031,8 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
 // the slot's previous lap, a consumer for the producer of its own ticket, so
 // an idle warp holds a ticket and watches only its own slot, and every push
 // goes straight to the warp that has waited longest.  Each cell's flag has
-// two bits: requested (bit 0) and running (bit 1).
+// two bits: requested (bit 0) and running (bit 1); bit 2 records that the
+// cell was removed before.
 //   activate: set bit 0; the caller that set it on an idle cell pushes it.
 //   claim:    flag := running (the request is consumed) before the halo load.
 //   finish:   clear bit 1; if bit 0 came back meanwhile, push the cell again.
@@ -1055,7 +1059,9 @@ __device__ __forceinline__ bool ring_push(const SolveParams& p, Ctl* gctl, unsig
     const unsigned t = atomicAdd(&p.qctl[Q_TAIL], 1u);
     unsigned long long* sl = p.ring + (t & p.ring_mask);
     unsigned spins = 0;
-    while ((unsigned)(ld_vol64(sl) >> 32) != t) {  // the previous lap's consumer is still reading
+    // the first lap finds every slot free (seeded so); later laps wait for
+    // the previous lap's consumer to have read the slot
+    while (t > p.ring_mask && (unsigned)(ld_vol64(sl) >> 32) != t) {
         if ((++spins & 255u) == 0 && (gtimer() > deadline || ld_vol(&gctl->abort))) {
             fail(gctl, EIK_ETIMEDOUT, 0x6000000ull);
             return false;
@@ -1181,12 +1187,11 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
         const int ii = find_inst(p.cell_pre, NI, e);
         const InstDesc& d = inst[ii];
         const int c = e - d.cell_base;
-        // ---- claim: running, the request consumed, before the halo load
+        // ---- claim: running, the request consumed, before the halo load;
+        // bit 2 marks a cell removed before (its first removal activates
+        // across source boundaries)
         int first = 0;
-        if (lane == 0) {
-            atomicExch(&d.qflag[c], 2);
-            first = atomicAdd(&d.visits[c], 1) == 0;
-        }
+        if (lane == 0) first = (atomicExch(&d.qflag[c], 6) & 4) == 0;
         first = __shfl_sync(FULL, first, 0);
         __threadfence();
         fence_proxy_async_global();
@@ -1198,7 +1203,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
         const bool ok = visit_cells<MODE, K, false>(
             w, inst, gctl, deadline, c, ii, first, cg, ig, prof_on, pacc, pt,
             [&](const InstDesc& dn, int nc, unsigned long long, unsigned long long, bool activate) {
-                if (activate && atomicOr(&dn.qflag[nc], 1) == 0) {
+                if (activate && (atomicOr(&dn.qflag[nc], 1) & 3) == 0) {
                     atomicAdd(&p.qctl[Q_PENDING], 1u);
                     ring_push(p, gctl, (unsigned)(dn.cell_base + nc), deadline);
                 }
