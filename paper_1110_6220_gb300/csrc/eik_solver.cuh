@@ -68,6 +68,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
         "l"((unsigned long long)tm), "r"(x), "r"(y), "r"(smem_addr(bar))
         : "memory");
 }
+// Release / acquire at GPU scope.  Every hand-off of tile values between
+// warps goes through read-modify-writes of the receiving cell's flag, which
+// are totally ordered: the writer's fence orders its value stores before its
+// flag update, the reader's fence orders its flag update before its loads,
+// so whichever update comes second sees the other side's work.  No
+// sequentially consistent fence is needed.
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
@@ -629,7 +636,7 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
     int gsweeps = 0;
     bool gdone = c < 0;
     int s = 0;
-    for (; s < C::MAX_PASSES; ++s) {
+    for (; s < C::MAX_PASSES && __ballot_sync(FULL, !gdone) != 0u; ++s) {
         bool changed = false;
         for (int t2 = 0; t2 < 2 * K - 1; ++t2) {
 #pragma unroll
@@ -718,7 +725,7 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
                 gU[(j + 1) * C::BW + (i + 1)];
         }
     }
-    __threadfence();  // release the new values before any activation
+    fence_acq_rel_gpu();  // release the new values before any activation
     fence_proxy_async_global();
     __syncwarp();
     PROF_MARK(5);
@@ -981,7 +988,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
                 first = atomicAdd(&d.visits[c], 1) == 0;
             }
             first = __shfl_sync(FULL, first, g * C::LPC);
-            __threadfence();
+            fence_acq_rel_gpu();
             fence_proxy_async_global();
             fence_proxy_async_shared();
             __syncwarp();
@@ -1193,7 +1200,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
         int first = 0;
         if (lane == 0) first = (atomicExch(&d.qflag[c], 6) & 4) == 0;
         first = __shfl_sync(FULL, first, 0);
-        __threadfence();
+        fence_acq_rel_gpu();
         fence_proxy_async_global();
         fence_proxy_async_shared();
         __syncwarp();

@@ -30,10 +30,12 @@ static void shape_of(int num_sms, int n_inst, int sm_cap, bool async, LaunchShap
         cudaGetLastError();
         per_sm = 0;
     }
-    // a single grid: at most two blocks per SM (a round rarely has more cells
-    // than that, and every extra block makes each grid barrier slower); a
-    // batch keeps every SM full, so it takes the occupancy limit
-    int cap = n_inst > 1 ? per_sm : 2;
+    // a single grid in rounds: at most two blocks per SM (a round rarely has
+    // more cells than that, and every extra block makes each grid barrier
+    // slower); a batch keeps every SM full, and the round-free schedule has no
+    // barrier and gains from more warps waiting for cells (1025^2: 1.82 ms at
+    // three blocks per SM, 1.94 ms at two), so both take the occupancy limit
+    int cap = n_inst > 1 || async ? per_sm : 2;
     if (sm_cap > 0 && sm_cap < cap) cap = sm_cap;  // leave room for other jobs
     s->blocks = (per_sm < cap ? per_sm : cap) * num_sms;
     s->per_sm = per_sm;
