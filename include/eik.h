@@ -110,7 +110,8 @@ typedef struct {
     int32_t launches;       /* kernels this solve launched */
     int32_t cell_k;         /* cell size used */
     int32_t schedule;       /* bit 0: FP32 pass round-free; bit 1: FP64 / double-float pass
-                               round-free; bit 2: FP32_REFINE as one double-float pass */
+                               round-free; bit 2: FP32_REFINE as one double-float pass;
+                               bit 3: replayed from a captured CUDA graph */
     int32_t status;         /* EIK_OK or the error of this solve */
 } eik_stats;
 
@@ -149,6 +150,27 @@ int eik_solve(eik_plan p, const eik_instance* in, eik_stats* st);
  * status of each instance is in st[i].status. */
 int eik_solve_batch(const eik_plan_desc* d, const eik_instance* in, int32_t n_inst,
                     eik_stats* st, void* cuda_stream);
+
+/* ------------------------------------------------------- fixed batches
+ * A batch solved again and again (the same grids with new speeds, a time
+ * loop, a benchmark).  eik_batch_create builds everything eik_solve_batch
+ * builds -- layouts, tables, sources, device workspace, the tuned cell size
+ * and schedule -- once, and captures each job's launch sequence in a CUDA
+ * graph; eik_batch_run replays it.  The instances' sizes, pointers and
+ * sources are fixed at creation: their F values may change between runs
+ * (speeds in host memory are copied in at each run) and their U buffers
+ * receive each run's result.  cuda_stream: NULL, or a stream whose queued
+ * work each run waits for.  Where a graph cannot be captured the jobs are
+ * queued directly (eik_stats.schedule bit 3 tells which).
+ *
+ * eik_batch_run blocks until every U is written; st: NULL or n_inst entries
+ * (ms is the device time of the job that holds the instance).  Returns
+ * EIK_OK if every instance succeeded, else the first error. */
+typedef struct eik_batch_s* eik_batch;
+int eik_batch_create(eik_batch* out, const eik_plan_desc* d, const eik_instance* in, int32_t n_inst,
+                     void* cuda_stream);
+int eik_batch_run(eik_batch b, eik_stats* st);
+void eik_batch_destroy(eik_batch b);
 
 /* ------------------------------------------------------- autotuning
  * The cell size k (Sec. 4) and the width of the value buckets (Sec. 2's

@@ -74,22 +74,26 @@ int grow(DevBuf* b, size_t bytes) {
 
 // ---------------------------------------------------------------- sources
 int prepare_sources(const Layout& L, const eik_instance* in, HostSources* hs) {
+    const int n = in->nsrc;
+    if (n < 0) return EIK_EINVAL;
+    if (n > 0 && (!in->src_ij || !in->src_q)) return EIK_EINVAL;
+    std::vector<int32_t> ij(2 * (size_t)n);
+    std::vector<double> q((size_t)n);
+    if (n > 0 && (cudaMemcpy(ij.data(), in->src_ij, ij.size() * 4, cudaMemcpyDefault) != cudaSuccess ||
+                  cudaMemcpy(q.data(), in->src_q, q.size() * 8, cudaMemcpyDefault) != cudaSuccess)) {
+        cudaGetLastError();
+        return EIK_EINVAL;
+    }
+    return prepare_sources_host(L, n, ij.data(), q.data(), hs);
+}
+
+int prepare_sources_host(const Layout& L, int n, const int32_t* ij, const double* q, HostSources* hs) {
     hs->node.clear();
     hs->q.clear();
     hs->cell.clear();
     hs->cell_key.clear();
     hs->q_min = 0.0;
-    const int n = in->nsrc;
-    if (n < 0) return EIK_EINVAL;
-    if (n == 0) return EIK_OK;
-    if (!in->src_ij || !in->src_q) return EIK_EINVAL;
-    std::vector<int32_t> ij(2 * (size_t)n);
-    std::vector<double> q((size_t)n);
-    if (cudaMemcpy(ij.data(), in->src_ij, ij.size() * 4, cudaMemcpyDefault) != cudaSuccess ||
-        cudaMemcpy(q.data(), in->src_q, q.size() * 8, cudaMemcpyDefault) != cudaSuccess) {
-        cudaGetLastError();
-        return EIK_EINVAL;
-    }
+    if (n <= 0) return n < 0 ? EIK_EINVAL : EIK_OK;
     std::vector<std::pair<int, double>> s((size_t)n);
     for (int e = 0; e < n; ++e) {
         const int i = ij[2 * e], j = ij[2 * e + 1];
@@ -138,10 +142,60 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     hj->out_user.resize(n);
     size_t nsrc = 0, ncs = 0, Jtot = 0, ibytes = 0;
     std::vector<size_t> inst_off((size_t)n);
+    // ---- the sources of every instance into one pinned staging buffer:
+    // one asynchronous copy per array that lives on the device, one wait
+    size_t sbytes = 0;
+    std::vector<size_t> soff((size_t)n);
     for (int i = 0; i < n; ++i) {
         if (!in[i].F || !in[i].U || in[i].nsrc < 0) return EIK_EINVAL;
+        if (in[i].nsrc > 0 && (!in[i].src_ij || !in[i].src_q)) return EIK_EINVAL;
+        soff[i] = sbytes;
+        sbytes += (size_t)in[i].nsrc * 16;  // 2 ints + 1 double per source
+    }
+    if (hj->src_cap < sbytes) {
+        if (hj->src_host) cudaFreeHost(hj->src_host);
+        hj->src_host = nullptr;
+        hj->src_cap = 0;
+        if (cudaMallocHost((void**)&hj->src_host, sbytes) != cudaSuccess) {
+            cudaGetLastError();
+            return EIK_ENOMEM;
+        }
+        hj->src_cap = sbytes;
+    }
+    bool waited = true;
+    for (int i = 0; i < n; ++i) {
+        const size_t m = (size_t)in[i].nsrc;
+        if (!m) continue;
+        char* dst = hj->src_host + soff[i];
+        const bool dij = is_device_ptr(in[i].src_ij), dq = is_device_ptr(in[i].src_q);
+        if (dij) {
+            if (cudaMemcpyAsync(dst, in[i].src_ij, m * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+                cudaGetLastError();
+                return EIK_EINVAL;
+            }
+            waited = false;
+        } else {
+            std::memcpy(dst, in[i].src_ij, m * 8);
+        }
+        if (dq) {
+            if (cudaMemcpyAsync(dst + m * 8, in[i].src_q, m * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+                cudaGetLastError();
+                return EIK_EINVAL;
+            }
+            waited = false;
+        } else {
+            std::memcpy(dst + m * 8, in[i].src_q, m * 8);
+        }
+    }
+    if (!waited && cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return EIK_ECUDA;
+    }
+    for (int i = 0; i < n; ++i) {
         hj->L[i] = make_layout(descs[i].nx, descs[i].ny, k);
-        const int rc = prepare_sources(hj->L[i], &in[i], &hs[i]);
+        const char* sp = hj->src_host + soff[i];
+        const int rc = prepare_sources_host(hj->L[i], in[i].nsrc, (const int32_t*)sp,
+                                            (const double*)(sp + (size_t)in[i].nsrc * 8), &hs[i]);
         if (rc) return rc;
         stageF[i] = !is_device_ptr(in[i].F);
         hj->out_host[i] = !is_device_ptr(in[i].U);
@@ -352,6 +406,9 @@ void free_job(HostJob* hj) {
     if (hj->zero_host) cudaFreeHost(hj->zero_host);
     hj->zero_host = nullptr;
     hj->zero_cap = 0;
+    if (hj->src_host) cudaFreeHost(hj->src_host);
+    hj->src_host = nullptr;
+    hj->src_cap = 0;
 }
 
 int run_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance* in, const JobParams& P,

@@ -57,6 +57,9 @@ struct Ctl {
     unsigned long long rounds;
     unsigned long long advances;  // bucket threshold moves
     unsigned long long err_info;  // first failing site (debugging aid)
+    // launch-wide control blocks: first start and last end of the persistent
+    // pass (%globaltimer, ns), kept where events cannot be (graph replay)
+    unsigned long long t_start, t_end;
     // per-phase clock cycles summed over warps, filled only when profiling
     // (EIK_PROFILE=1): 0 split, 1 barrier, 2 list+pop, 3 TMA wait, 4 sweeps,
     // 5 write-back, 6 activation, 7 warp-rounds with work

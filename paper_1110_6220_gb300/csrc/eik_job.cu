@@ -179,7 +179,8 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
     const int n = j.n;
     cudaMemsetAsync(j.zero_base, 0, j.zero_bytes, st);
     cudaMemsetAsync(j.cval_all, 0xff, j.ncval * 8, st);
-    if (launch_ctl_init(j.ictl, 2 * n, st) != cudaSuccess) return EIK_ECUDA;
+    // the instances' control blocks and the two launch-wide ones behind them
+    if (launch_ctl_init(j.ictl, 2 * n + 2, st) != cudaSuccess) return EIK_ECUDA;
     if (launch_block_owner(j.blk_pre, n, st) != cudaSuccess ||
         launch_block_owner(j.blk_full, n, st) != cudaSuccess)
         return EIK_ECUDA;
@@ -320,6 +321,13 @@ void job_stats(const Layout& L, const eik_plan_desc* d, bool fp32, const Ctl* ic
     s.rounds = rounds;
     s.buckets = adv;
     s.cell_k = L.k;
+    // pass times from the kernels' own timers (callers with events on the
+    // launching stream replace them)
+    auto span = [](const Ctl* g) {
+        return g->t_end > g->t_start && g->t_start != ~0ull ? (double)(g->t_end - g->t_start) * 1e-6 : 0.0;
+    };
+    s.pass_ms[0] = fp32 ? span(g_first) : 0.0;
+    s.pass_ms[1] = span(g_main);
     const double fmin = dval(ictl_main->fmin_f);
     s.bucket_width = bw_main > 0 ? bw_main : (bw_main < 0 ? -bw_main : 4.0) * L.k * fmin;
     if (fp32) {

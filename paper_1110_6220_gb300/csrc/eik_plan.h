@@ -43,6 +43,8 @@ bool desc_valid(const eik_plan_desc* d);
 JobParams choose_params(const eik_plan_desc* d, int n);
 int default_k(const eik_plan_desc* d);  // choose_params(d, 1).k
 int prepare_sources(const Layout& L, const eik_instance* in, HostSources* hs);
+// the same from host copies of the n sources (ij: 2n ints, q: n doubles)
+int prepare_sources_host(const Layout& L, int n, const int32_t* ij, const double* q, HostSources* hs);
 bool is_device_ptr(const void* p);
 int grow(DevBuf* b, size_t bytes);
 int profiling();
@@ -60,6 +62,8 @@ struct HostJob {
     std::vector<double> bw_main;  // per instance: bucket width of the main pass
     char* zero_host = nullptr;   // readback buffer (pinned) of the zero region
     size_t zero_cap = 0;
+    char* src_host = nullptr;    // pinned staging of the instances' sources
+    size_t src_cap = 0;
 };
 
 // Lay out and upload a job of n instances (one k and precision); descs[i]

@@ -850,6 +850,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
     Ctl* gctl = p.gctl;
     const InstDesc* inst = p.inst;
     const unsigned long long deadline = gtimer() + (unsigned long long)p.deadline_ns;
+    if (threadIdx.x == 0) atomicMin(&gctl->t_start, gtimer());
 
     for (int i = threadIdx.x; i < NI; i += blockDim.x) {
         S.theta[i] = 0;
@@ -1028,6 +1029,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
     if (p.profile && lane == 0)
         for (int i = 0; i < 8; ++i) atomicAdd(&gctl->prof[i], pacc[i]);
     if (gtid == 0) gctl->rounds = st_rounds;
+    if (lane == 0) atomicMax(&gctl->t_end, gtimer());
 }
 
 // ---------------------------------------------------------------- async
@@ -1126,6 +1128,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
     const int gthreads = gridDim.x * blockDim.x;
     unsigned long long pacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long long pt = clock64();
+    if (threadIdx.x == 0) atomicMin(&gctl->t_start, gtimer());
 
     // ---- seed the ring with every instance's initially queued cells (their
     // flags are already 1: requested).  When many cells start queued (the
@@ -1229,6 +1232,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
     if (w.st_lane) atomicAdd(&gctl->lane_updates, w.st_lane);
     if (p.profile && lane == 0)
         for (int i = 0; i < 8; ++i) atomicAdd(&gctl->prof[i], pacc[i]);
+    if (lane == 0) atomicMax(&gctl->t_end, gtimer());
 }
 
 }  // namespace eik

@@ -74,6 +74,7 @@ class eik_tune_result(ctypes.Structure):
 
 eik_plan = ctypes.c_void_p
 eik_server = ctypes.c_void_p
+eik_batch = ctypes.c_void_p
 _P = ctypes.POINTER
 
 _lib.eik_strerror.argtypes = [ctypes.c_int]
@@ -92,6 +93,13 @@ _lib.eik_solve_noalloc.restype = ctypes.c_int
 _lib.eik_solve_batch.argtypes = [_P(eik_plan_desc), _P(eik_instance), ctypes.c_int32,
                                  _P(eik_stats), ctypes.c_void_p]
 _lib.eik_solve_batch.restype = ctypes.c_int
+_lib.eik_batch_create.argtypes = [_P(eik_batch), _P(eik_plan_desc), _P(eik_instance), ctypes.c_int32,
+                                  ctypes.c_void_p]
+_lib.eik_batch_create.restype = ctypes.c_int
+_lib.eik_batch_run.argtypes = [eik_batch, _P(eik_stats)]
+_lib.eik_batch_run.restype = ctypes.c_int
+_lib.eik_batch_destroy.argtypes = [eik_batch]
+_lib.eik_batch_destroy.restype = None
 _lib.eik_tune.argtypes = [_P(eik_plan_desc), _P(eik_instance), ctypes.c_int32, ctypes.c_void_p,
                           _P(eik_tune_result)]
 _lib.eik_tune.restype = ctypes.c_int
@@ -112,7 +120,8 @@ _lib.eik_server_destroy.argtypes = [eik_server]
 _lib.eik_server_destroy.restype = None
 
 SYMBOLS = ["eik_strerror", "eik_plan_create", "eik_plan_destroy", "eik_plan_workspace_bytes",
-           "eik_solve", "eik_solve_noalloc", "eik_solve_batch", "eik_tune", "eik_tune_save",
+           "eik_solve", "eik_solve_noalloc", "eik_solve_batch", "eik_batch_create", "eik_batch_run",
+           "eik_batch_destroy", "eik_tune", "eik_tune_save",
            "eik_tune_load", "eik_tune_reset", "eik_server_create", "eik_submit", "eik_poll",
            "eik_server_destroy"]
 
@@ -166,6 +175,29 @@ def eik_solve_batch(descs, insts, cuda_stream=None):
     S = (eik_stats * n)()
     rc = _lib.eik_solve_batch(D, I, n, S, _stream_ptr(cuda_stream))
     return rc, list(S)
+
+
+def eik_batch_create(descs, insts, cuda_stream=None) -> eik_batch:
+    n = len(descs)
+    D = (eik_plan_desc * n)(*descs)
+    I = (eik_instance * n)(*insts)
+    b = eik_batch()
+    rc = _lib.eik_batch_create(ctypes.byref(b), D, I, n, _stream_ptr(cuda_stream))
+    if rc:
+        raise EikError(rc, "eik_batch_create")
+    b.n_inst = n
+    return b
+
+
+def eik_batch_run(batch: eik_batch, n_inst: int = None):
+    n = n_inst if n_inst is not None else batch.n_inst
+    S = (eik_stats * n)()
+    rc = _lib.eik_batch_run(batch, S)
+    return rc, list(S)
+
+
+def eik_batch_destroy(batch: eik_batch) -> None:
+    _lib.eik_batch_destroy(batch)
 
 
 def eik_tune(descs, insts, cuda_stream=None):
