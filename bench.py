@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-grid batch measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the Poisson serving measurement")
     ap.add_argument("--no-sweep", action="store_true", help="skip the cell-size sweep")
+    ap.add_argument("--no-configs", action="store_true", help="skip the C1 / C2-FP64 / C3 solves")
     ap.add_argument("--serving-requests", type=int, default=128)
     return ap.parse_args()
 
@@ -223,6 +224,33 @@ def k_sweep(eik, torch, I, F, src, q, V, reps=3):
                         "unit": UNIT, "max_rel_err": err, "rounds": st.rounds, "avhr": st.avhr,
                         "pass_ms": list(st.pass_ms)})
     return out
+
+
+def config_measure(eik, torch, I, prec, steps=5, k=0):
+    """One more configuration: device-resident inputs, median device time of
+    whole solves through a plan, and the error against the oracle."""
+    import oracle
+    F = torch.from_numpy(I.F).cuda()
+    src = torch.from_numpy(I.src_ij).cuda()
+    q = torch.from_numpy(np.ascontiguousarray(I.sq)).cuda()
+    U = torch.empty_like(F)
+    ms = []
+    with eik.Plan(I.nx, I.ny, I.h, k, prec) as p:
+        for r in range(steps + 2):
+            rc, st = p.solve(F, src, q, U)
+            if rc:
+                raise RuntimeError(f"eik_solve {I.name}: {eik.eik_strerror(rc)}")
+            if r >= 2:
+                ms.append(st.ms)
+    V = oracle.fmm(I.F, I.h, I.si, I.sj, I.sq)
+    Ug = U.cpu().numpy()
+    fin = np.isfinite(V)
+    err = float(np.abs(Ug[fin] - V[fin]).max() / np.abs(V[fin]).max())
+    med = statistics.median(ms)
+    return {"grid": f"{I.nx}x{I.ny}", "precision": "fp64" if prec == eik.EIK_FP64 else "fp32ref",
+            "cell_k": st.cell_k, "ms": med, "value": I.npts / med / 1e3, "unit": UNIT,
+            "max_rel_err": err, "inf_pattern_exact": bool((np.isfinite(Ug) == fin).all()),
+            "err_bound": st.err_bound, "avhr": st.avhr, "schedule": st.schedule}
 
 
 def batch_measure(eik, torch, steps=5, warmup=2, k=0):
@@ -523,6 +551,13 @@ def run_ours(args):
                                       "one_double_float_pass": bool(s0.schedule & 4)}
         if not args.no_sweep:
             line["k_sweep"] = k_sweep(eik, torch, I, F, src, q, V)
+        if not args.no_configs:
+            from paper_1110_6220_gb300 import workloads as W
+            line["configs"] = {
+                "c1_const129_fp64": config_measure(eik, torch, W.const_point(129), eik.EIK_FP64),
+                "c2_sin1025_fp64": config_measure(eik, torch, I, eik.EIK_FP64),
+                "c3_checker_maze4097_fp32ref": config_measure(eik, torch, W.checker_maze(4097), eik.EIK_FP32_REFINE),
+            }
         if not args.no_batch:
             line["batch"] = batch_measure(eik, torch)
         if not args.no_serving:

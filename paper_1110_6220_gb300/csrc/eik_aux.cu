@@ -29,29 +29,6 @@ __device__ __forceinline__ float2 df_of(double v) {
     return make_float2(hi, __double2float_rn(v - (double)hi));
 }
 
-// A positive double as a double-float pair without the FP64 pipe: hi keeps
-// the leading 24 significand bits (exact in a float), lo the next 24 of the
-// remaining 29 (rounded; 2^-53 relative).  False outside [2^-74, 2^126)
-// (the caller takes the FP64 route there).
-__device__ __forceinline__ bool split_pos(double v, float2* out) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const int e = (int)((b >> 52) & 0x7ff);
-    if (e < 1023 - 74 || e > 1023 + 125) return false;
-    const float hi = __uint_as_float(((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff));
-    const float lo = __int2float_rn((int)(b & 0x1fffffffull)) * __uint_as_float((unsigned)(e - 1075 + 127) << 23);
-    *out = make_float2(hi, lo);
-    return true;
-}
-// A float as a double without the FP64 pipe (exponent rebias); subnormals,
-// infinities and NaN take the ordinary conversion.
-__device__ __forceinline__ double widen(float x) {
-    const unsigned u = __float_as_uint(x);
-    const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 255u) return (u & 0x7fffffffu) == 0u ? (u ? -0.0 : 0.0) : (double)x;
-    return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
-                                            ((unsigned long long)(e + 896u) << 52) |
-                                            ((unsigned long long)(u & 0x7fffffu) << 29)));
-}
 // h / F for the pair modes: a double-float quotient from the split F, or the
 // FP64 quotient where F cannot be split
 __device__ __forceinline__ float2 f_pair(float hx, float hy, double h, double F) {

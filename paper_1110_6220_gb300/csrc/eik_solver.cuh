@@ -121,20 +121,6 @@ __device__ __forceinline__ bool updatable(float f) {
 // (eq. two_sided_update), else the one-sided min(a, b) + f
 // (eq. one_sided_update).  Neighbours are >= 0 (possibly +inf); f is finite.
 
-// FP64 (g = 2 f^2 precomputed): U = hi + (sqrt(g - d^2) - d) / 2, d = hi - lo.
-__device__ __forceinline__ double update_f64(double W, double E, double S, double N, double f,
-                                             double g) {
-    const long long a = min(ob(W), ob(E)), b = min(ob(S), ob(N));
-    const long long lob = min(a, b), hib = max(a, b);
-    const double lo = from_ob(lob), hi = from_ob(hib);
-    const double one = lo + f;
-    const double d = hi - lo;  // finite whenever hi is
-    const bool two_sided = hib < INF_BITS64 && ob(d) < ob(f);
-    const double s = sqrt(two_sided ? fma(-d, d, g) : g);
-    const double two = fma(0.5, s - d, hi);
-    return two_sided ? two : one;
-}
-
 // FP32, with the quadratic in the cancellation-free form
 //   hi + (f^2 - d^2) / (d + sqrt(2 f^2 - d^2))
 // whose small increment carries all the rounding; its quotient and root need
@@ -256,6 +242,69 @@ __device__ __forceinline__ float2 update_df(float2 W, float2 E, float2 S, float2
     return lo.x < INF ? r : make_float2(INF, 0.0f);
 }
 
+// Exact conversions without the FP64 pipe (GB300 runs conversions there).
+// split_pos: a positive double as a pair -- hi keeps the leading 24
+// significand bits (exact in a float), lo the next 24 of the remaining 29
+// (rounded, 2^-53 relative); false outside [2^-74, 2^126).  widen: a float as
+// a double by exponent rebias (subnormals, infinities and NaN take the
+// ordinary conversion).
+__device__ __forceinline__ bool split_pos(double v, float2* out) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e < 1023 - 74 || e > 1023 + 125) return false;
+    const float hi = __uint_as_float(((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff));
+    const float lo = __int2float_rn((int)(b & 0x1fffffffull)) * __uint_as_float((unsigned)(e - 1075 + 127) << 23);
+    *out = make_float2(hi, lo);
+    return true;
+}
+__device__ __forceinline__ double widen(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 255u) return (u & 0x7fffffffu) == 0u ? (u ? -0.0 : 0.0) : (double)x;
+    return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                            ((unsigned long long)(e + 896u) << 52) |
+                                            ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+// The two-sided increment (f^2 - d^2) / (d + sqrt(2 f^2 - d^2)) in
+// double-float arithmetic, 0 <= d < f.
+__device__ __forceinline__ float2 df_increment(float2 d, float2 f) {
+    const float2 f2 = df_mul(f, f);
+    const float2 x = df_sub(df_add(f2, f2), df_mul(d, d));  // >= f^2 > 0
+    return df_div(df_mul(df_sub(f, d), df_add(f, d)), df_add(d, df_sqrt(x)));
+}
+
+// FP64: U = hi + increment, with the increment -- at most sqrt 2 f, so a
+// few units of 2^-46 relative to it are ~1e-14 f -- in double-float
+// arithmetic on the FP32 pipe.  Only the base, the difference d = hi - lo
+// and the sums run on the FP64 pipe (four adds, no square root or division),
+// which on GB300 runs at 1/64 of the FP32 rate.  fp: f as a pair, (0, 0)
+// where f lies outside [2^-40, 2^40] (the pair products would leave the
+// float range): the update then takes the FP64 root.
+__device__ __forceinline__ double update_f64(double W, double E, double S, double N, double f, float2 fp) {
+    const long long a = min(ob(W), ob(E)), b = min(ob(S), ob(N));
+    const long long lob = min(a, b), hib = max(a, b);
+    const double lo = from_ob(lob), hi = from_ob(hib);
+    const double one = lo + f;
+    const double d = hi - lo;  // finite whenever hi is
+    const bool two_sided = hib < INF_BITS64 && ob(d) < ob(f);
+    float2 dp;
+    if (!split_pos(d, &dp)) dp = make_float2(0.0f, 0.0f);  // d < 2^-74 (or not two-sided)
+    const float2 inc = df_increment(dp, fp);
+    double two = hi + (widen(inc.x) + widen(inc.y));
+    if (two_sided && fp.x == 0.0f) {
+        const double s = sqrt(fma(-d, d, 2.0 * f * f));
+        two = fma(0.5, s - d, hi);
+    }
+    return two_sided ? two : one;
+}
+// f as the pair update_f64 takes
+__device__ __forceinline__ float2 f64_pair(double f) {
+    float2 r;
+    if (f >= 0x1p-40 && f <= 0x1p40 && split_pos(f, &r)) return r;
+    return make_float2(0.0f, 0.0f);
+}
+
 // ---------------------------------------------------------------- modes
 enum { MODE_F64 = 0, MODE_F32 = 1, MODE_DF = 2 };
 
@@ -286,7 +335,7 @@ struct TileCfg {
     static constexpr int BH = K + 2;
     static constexpr int UBYTES = BW * BH * ES;
     static constexpr int FBYTES = BW * BH * (int)sizeof(FT);        // f box incl. halo (TMA)
-    static constexpr int XBYTES = MODE == MODE_F64 ? K * K * 8 : 0;  // 2 f^2 (computed)
+    static constexpr int XBYTES = MODE == MODE_F64 ? K * K * 8 : 0;  // f as pairs (computed)
     static constexpr int TX_BYTES = UBYTES + FBYTES;
     static constexpr int A128(int b) { return (b + 127) / 128 * 128; }
     static constexpr int F_OFF = A128(UBYTES);
@@ -315,7 +364,8 @@ __device__ __forceinline__ bool node_candidate(const typename TileCfg<MODE, K>::
     if (!updatable(fv)) return false;
     old = tU[q];
     if constexpr (MODE == MODE_F64)
-        cand = update_f64(tU[q - 1], tU[q + 1], tU[q - C::BW], tU[q + C::BW], fv, tG[j * K + i]);
+        cand = update_f64(tU[q - 1], tU[q + 1], tU[q - C::BW], tU[q + C::BW], fv,
+                          reinterpret_cast<const float2*>(tG)[j * K + i]);
     else if constexpr (MODE == MODE_F32)
         cand = update_f32(tU[q - 1], tU[q + 1], tU[q - C::BW], tU[q + C::BW], fv);
     else
@@ -617,13 +667,13 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
     w.phase ^= 1u;
     PROF_MARK(3);
     if constexpr (MODE == MODE_F64) {
-        // 2 f^2 per node, once per visit (saves two FP64 ops per update)
+        // f as a pair per node, once per visit (the update's increment)
         for (int e = lane; e < C::CPW * K * K; e += 32) {
             const int gg = e / (K * K), r = e - gg * (K * K);
             const int jj = r / K, i2 = r - jj * K;
             unsigned char* gb = wbase + gg * C::GROUP_BYTES;
             const double fv = reinterpret_cast<const double*>(gb + C::F_OFF)[(jj + 1) * C::BW + i2 + 1];
-            reinterpret_cast<double*>(gb + C::X_OFF)[r] = 2.0 * fv * fv;
+            reinterpret_cast<float2*>(gb + C::X_OFF)[r] = f64_pair(fv);
         }
         __syncwarp();
     }
