@@ -417,6 +417,19 @@ def serving_measure(eik, torch, count=128, seed=5, budget=64 << 30):
         eik.eik_server_destroy(srv)
 
 
+def replica_rate(local_ms, npts, steps, world, device):
+    """Replicas: every rank solved `steps` grids of `npts` points in local_ms.
+    The job took the slowest rank's time (max over ranks); the rate is all
+    ranks' points over it, in Mpts/s.  Returns (max ms, rate)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        local_ms = float(t.item())
+    return local_ms, world * steps * npts / (local_ms / 1e3) / 1e6
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -465,13 +478,9 @@ def run_ours(args):
             e1.record(stream)
         torch.cuda.synchronize()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    tot_ms = sum(step_ms)
+    tot_ms, value = replica_rate(sum(step_ms), I.npts, args.steps, world, dev)
     if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
         dist.barrier()
-    value = world * args.steps * I.npts / (tot_ms / 1e3) / 1e6
 
     # ---- end to end through the public API with host (pinned) buffers
     Fh = torch.from_numpy(I.F).pin_memory()
@@ -491,12 +500,7 @@ def run_ours(args):
         if rc:
             raise RuntimeError(f"eik_solve (host buffers): {eik.eik_strerror(rc)}")
         e2e_ms.append(a.elapsed_time(b))
-    e2e_tot = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_tot], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_tot = float(t.item())
-    e2e_value = world * args.steps * I.npts / (e2e_tot / 1e3) / 1e6
+    e2e_tot, e2e_value = replica_rate(sum(e2e_ms), I.npts, args.steps, world, dev)
 
     if rank == 0:
         Ug = U.cpu().numpy()
