@@ -561,6 +561,8 @@ def run_ours(args):
                 "c1_const129_fp64": config_measure(eik, torch, W.const_point(129), eik.EIK_FP64),
                 "c2_sin1025_fp64": config_measure(eik, torch, I, eik.EIK_FP64),
                 "c3_checker_maze4097_fp32ref": config_measure(eik, torch, W.checker_maze(4097), eik.EIK_FP32_REFINE),
+                "q_boundary_sin1025_fp32ref": config_measure(eik, torch, W.sin_boundary(1025), eik.EIK_FP32_REFINE),
+                "q_boundary_sin1025_fp64": config_measure(eik, torch, W.sin_boundary(1025), eik.EIK_FP64),
             }
         if not args.no_batch:
             line["batch"] = batch_measure(eik, torch)

@@ -271,7 +271,7 @@ __global__ void k_residual(const AuxInst* A, const int* blk_pre, int n) {
     const int j = w.j;
     const int up = p.upitch;
     const float FINF = inf_of<float>();
-    float r = 0.0f, umax = 0.0f;
+    float r = 0.0f, rrel = 0.0f, umax = 0.0f;
     unsigned long long bad = 0;
 #pragma unroll
     for (int s = 0; s < SPAN; ++s) {
@@ -306,23 +306,28 @@ __global__ void k_residual(const AuxInst* A, const int* blk_pre, int n) {
                 R = df_add(df_sub(lo, V), f);
             }
             const float allow = 0x1p-40f * (V.x + lo.x + 4.0f * f.x);
-            r = fmaxf(r, (fabsf(R.x) + fabsf(R.y) + allow) * (1.0f + 0x1p-20f));
+            const float rn = (fabsf(R.x) + fabsf(R.y) + allow) * (1.0f + 0x1p-20f);
+            r = fmaxf(r, rn);
+            // relative to this node's f (rounded up; f.y < ulp(f.x))
+            rrel = fmaxf(rrel, __fdiv_ru(rn, f.x * (1.0f - 0x1p-22f)));
         } else if (vfin || tfin) {
-            r = FINF;
+            r = rrel = FINF;
             bad += 1;
         }
     }
     // maxima of the warp on the float images (all >= 0), one atomic per warp
-    unsigned rb = __float_as_uint(r), ub = __float_as_uint(umax);
+    unsigned rb = __float_as_uint(r), ub = __float_as_uint(umax), eb = __float_as_uint(rrel);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         rb = max(rb, __shfl_xor_sync(FULL, rb, o));
+        eb = max(eb, __shfl_xor_sync(FULL, eb, o));
         ub = max(ub, __shfl_xor_sync(FULL, ub, o));
         bad += __shfl_xor_sync(FULL, bad, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        const float rf = __uint_as_float(rb);
+        const float rf = __uint_as_float(rb), ef = __uint_as_float(eb);
         atomicMax(&p.res->r_max, key_of(rf < FINF ? widen(rf) : inf_of<double>()));
+        atomicMax(&p.res->r_rel, key_of(ef < FINF ? widen(ef) : inf_of<double>()));
         // V.y < ulp(V.x): a bound of max V
         atomicMax(&p.res->u_max, key_of(widen(__uint_as_float(ub)) * (1.0 + 0x1p-20)));
         if (bad) atomicAdd(&p.res->n_bad, bad);

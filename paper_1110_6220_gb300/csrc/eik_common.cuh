@@ -145,6 +145,7 @@ cudaError_t launch_solver_df(int k, bool async, const SolveParams& p, const Laun
 //                    refinement pass).  All share the layout of SolveParams.
 struct ResidualOut {              // reduced with atomics on ordered keys
     unsigned long long r_max;     // max |V - T(V)| over non-source nodes
+    unsigned long long r_rel;     // max |V - T(V)| / f over the same nodes
     unsigned long long u_max;     // max finite V
     unsigned long long n_bad;     // finite/infinite mismatches
 };

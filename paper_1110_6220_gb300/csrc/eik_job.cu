@@ -332,15 +332,17 @@ void job_stats(const Layout& L, const eik_plan_desc* d, bool fp32, const Ctl* ic
     s.bucket_width = bw_main > 0 ? bw_main : (bw_main < 0 ? -bw_main : 4.0) * L.k * fmin;
     if (fp32) {
         // values on the device are U - q_min >= 0
-        const double rr = dval(r->r_max), umax = dval(r->u_max);
+        const double rr = dval(r->r_max), rrel = dval(r->r_rel), umax = dval(r->u_max);
         s.max_residual = rr;
         // Certificate (comparison principle for the monotone scheme): for
-        // lam > 1, lam * (U - q_min) is a strict supersolution with margin
-        // (lam - 1) f_min / sqrt 2, and likewise a strict subsolution for
-        // lam < 1; so |V - U| <= sqrt 2 * r / f_min * max(U - q_min).
+        // lam > 1, lam * (U - q_min) is a strict supersolution whose margin
+        // at node x is (lam - 1) f(x) / sqrt 2, and likewise a strict
+        // subsolution for lam < 1; a residual r(x) <= that margin at every x
+        // keeps V between them, so
+        //   |V - U| <= sqrt 2 * max_x (r(x) / f(x)) * max(U - q_min).
         double bound = 0.0;
         if (r->n_bad) bound = std::numeric_limits<double>::infinity();
-        else if (rr > 0 && umax > 0) bound = std::sqrt(2.0) * rr / fmin * umax;
+        else if (rrel > 0 && umax > 0) bound = std::sqrt(2.0) * rrel * umax;
         const double scale = std::max(std::fabs(umax + q_min), std::fabs(q_min));
         s.err_bound = scale > 0 ? bound / scale : bound;
         const double tol = d->tol > 0 ? d->tol : 1e-5;

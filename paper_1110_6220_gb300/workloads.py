@@ -75,6 +75,23 @@ def sin_point(n: int = 1025, omega: float = 20.0, amp: float = 0.5) -> Instance:
                     np.array([c], np.int32), np.zeros(1), name=f"sin{int(omega)}_{n}")
 
 
+def boundary_nodes(n: int):
+    """(i, j) of every node on the boundary of an n x n grid, each once."""
+    k = np.arange(n)
+    i = np.concatenate([k, k, np.zeros(n - 2, int), np.full(n - 2, n - 1)])
+    j = np.concatenate([np.zeros(n, int), np.full(n, n - 1), k[1:-1], k[1:-1]])
+    return i.astype(np.int32), j.astype(np.int32)
+
+
+def sin_boundary(n: int = 1025, omega: float = 20.0, amp: float = 0.5) -> Instance:
+    """Sec. 5's general boundary conditions: F = 1 + amp sin(omega pi x)
+    sin(omega pi y) with q = 0 on the whole boundary of the square (Q = dOmega)."""
+    h, _ = _grid(n)
+    si, sj = boundary_nodes(n)
+    return Instance(n, n, h, sin_field(n, omega, amp), si, sj, np.zeros(si.size),
+                    name=f"sin{int(omega)}_gbc_{n}")
+
+
 def checker_field(n: int, checkers: int = 64, lo: float = 1.0, hi: float = 2.0) -> np.ndarray:
     _, x = _grid(n)
     b = np.minimum(np.floor(checkers * x).astype(np.int64), checkers - 1)

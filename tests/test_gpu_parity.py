@@ -130,6 +130,20 @@ def test_fp32_refine_certified(eik, orc, k):
         assert rel <= 5e-8, f"fp32ref {I.name}: {rel:.3e} above the observed accuracy floor"
 
 
+@pytest.mark.parametrize("omega,amp", [(20.0, 0.5), (2.0, 0.99)])
+def test_boundary_sources(eik, orc, omega, amp):
+    """Q = the whole boundary with q = 0 (Sec. 5's general boundary
+    conditions): every boundary cell starts queued."""
+    I = W.sin_boundary(257, omega, amp)
+    V = oracle_U(orc, I)
+    for k in (8, 16):
+        U, st = solve(eik, I, k)
+        compare(U, V, TOL64, f"{I.name} fp64 k={k}")
+        U, st = solve(eik, I, k, precision=eik.EIK_FP32_REFINE)
+        rel = compare(U, V, TOL32, f"{I.name} fp32ref k={k}")
+        assert st.status == 0 and rel <= max(st.err_bound, 1e-15) * 1.0001
+
+
 def test_device_pointers_match_host_pointers(eik, orc):
     import torch
     I = W.sin_point(300)

@@ -142,22 +142,25 @@ def test_distance_function_converges_first_order(orc):
 
 @pytest.mark.slow
 def test_paper_printed_errors(orc):
-    """Tab. const and Tab. sinu_1 print the L_inf error of the 1408 x 1408
-    solution against Fast Marching on an h/4 grid (Sec. 5).  Reading the grid
-    as 1408 intervals (h = 1/1408) the oracle reproduces both to 0.5%."""
+    """Tab. const, Tab. sinu_1 (point source) and Tabs. sinu_1_gbc /
+    sinu_2_gbc (q = 0 on the whole boundary) print the L_inf and L1 errors of
+    the 1408 x 1408 solution against Fast Marching on an h/4 grid (Sec. 5).
+    Reading the grid as 1408 intervals (h = 1/1408) the oracle reproduces
+    them within the tolerance each case states (0.5% but for one L_inf)."""
     with open(os.path.join(GOLD, "paper_errors.json")) as fh:
         gold = json.load(fh)
     for case in gold["cases"]:
         n = case["n"]
         mk = getattr(W, case["workload"])
-        I = mk(n)
-        J = mk(4 * (n - 1) + 1)
+        args = case.get("args", [])
+        I = mk(n, *args)
+        J = mk(4 * (n - 1) + 1, *args)
         U = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
         V = orc.fmm(J.F, J.h, J.si, J.sj, J.sq)[::4, ::4]
         linf = np.abs(U - V).max()
-        assert abs(linf / case["Linf"] - 1) < 5e-3, (case["name"], linf)
+        assert abs(linf / case["Linf"] - 1) < case["linf_tol"], (case["name"], linf)
         l1 = np.abs(U - V).mean()
-        assert abs(l1 / case["L1"] - 1) < 0.1, (case["name"], l1)
+        assert abs(l1 / case["L1"] - 1) < case["l1_tol"], (case["name"], l1)
 
 
 def test_fsm_sweep_count_constant_speed(orc):
