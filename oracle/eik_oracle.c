@@ -414,3 +414,246 @@ int orc_apply_T(int nx, int ny, double h, const double *F, int nsrc, const int32
     problem_free(&p);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Heap-Cell Methods, Sec. 4.2 (HCM) and Sec. 4.3 (FHCM), serially:    */
+/* Alg. generic_LC_cells over k x k cells kept in a binary heap by     */
+/* cell value, with four directional flags per cell.                   */
+/*   HCM:  a removed cell is swept until a sweep changes nothing; its  */
+/*         flagged directions come first, then the other two of the    */
+/*         first four, then the cycle of Alg. FSM_order (Remark        */
+/*         HCM_preferred_sweeps and the list before it).  An           */
+/*         activation across a side raises both flags that point away  */
+/*         from that side.                                             */
+/*   FHCM: a removed cell is swept once in each flagged direction and  */
+/*         no more (Alg. FHCM); an activation raises one of the two    */
+/*         flags when the boundary values on that side are monotone    */
+/*         (the Monotonicity Check), both otherwise.                   */
+/* The activation test and the cell values follow Alg. generic_LC_cells */
+/* and eq. cell_value: a node x_i on the border that changed during the */
+/* removal (or a source, on the cell's first removal) with V_i < V_j    */
+/* across the border, x_j not a source, adds the neighbour cell; the    */
+/* neighbour's cell value becomes min(itself, max finite V on the       */
+/* border + (k+1)/2 * h / F(y)), F read at the node across the border   */
+/* from the largest value (the smallest h/F of the grid where that node */
+/* is an obstacle).  Sweep directions are numbered as in Alg. FSM_order: */
+/* 0 (i up, j up), 1 (i up, j down), 2 (i down, j down), 3 (i down, j up). */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t *cell;
+    int32_t *pos;
+    int32_t size;
+    const double *key;
+} cell_heap;
+
+static int ch_less(const cell_heap *H, int a, int b) { return H->key[H->cell[a]] < H->key[H->cell[b]]; }
+static void ch_swap(cell_heap *H, int a, int b)
+{
+    int32_t ca = H->cell[a], cb = H->cell[b];
+    H->cell[a] = cb;
+    H->cell[b] = ca;
+    H->pos[cb] = a;
+    H->pos[ca] = b;
+}
+static void ch_up(cell_heap *H, int k)
+{
+    while (k > 0) {
+        int parent = (k - 1) / 2;
+        if (!ch_less(H, k, parent)) break;
+        ch_swap(H, k, parent);
+        k = parent;
+    }
+}
+static void ch_down(cell_heap *H, int k)
+{
+    for (;;) {
+        int l = 2 * k + 1, r = l + 1, s = k;
+        if (l < H->size && ch_less(H, l, s)) s = l;
+        if (r < H->size && ch_less(H, r, s)) s = r;
+        if (s == k) break;
+        ch_swap(H, k, s);
+        k = s;
+    }
+}
+
+/* one Gauss-Seidel sweep of the cell's nodes in direction dir; 1 if a value changed */
+static int sweep_cell(const problem *p, double *V, int i0, int i1, int j0, int j1, int dir)
+{
+    int i_up = (dir == 0 || dir == 1), j_up = (dir == 0 || dir == 3);
+    int changed = 0;
+    for (int ii = i0; ii < i1; ++ii) {
+        int i = i_up ? ii : i1 - 1 - (ii - i0);
+        for (int jj = j0; jj < j1; ++jj) {
+            int j = j_up ? jj : j1 - 1 - (jj - j0);
+            size_t k = (size_t)j * p->nx + i;
+            if (p->src[k]) continue;
+            double t = T_at(p, V, i, j);
+            if (t < V[k]) {
+                V[k] = t;
+                changed = 1;
+            }
+        }
+    }
+    return changed;
+}
+
+/* stats: [0] cell removals, [1] sweeps, [2] monotone checks passed, [3] checks */
+int orc_cells(int nx, int ny, double h, const double *F, int nsrc, const int32_t *si, const int32_t *sj,
+              const double *sq, int k, int fast, double *U, int64_t *stats)
+{
+    if (k < 1) return ORC_EINVAL;
+    problem p;
+    int rc = problem_init(&p, nx, ny, h, F, nsrc, si, sj, sq);
+    if (rc) return rc;
+    init_values(&p, U);
+    const int cxn = (nx + k - 1) / k, cyn = (ny + k - 1) / k, J = cxn * cyn;
+    double *cval = (double *)malloc((size_t)J * sizeof(double));
+    unsigned char *flags = (unsigned char *)calloc((size_t)J, 1);
+    unsigned char *removed = (unsigned char *)calloc((size_t)J, 1);
+    int32_t *hcell = (int32_t *)malloc((size_t)J * sizeof(int32_t));
+    int32_t *hpos = (int32_t *)malloc((size_t)J * sizeof(int32_t));
+    double *old = (double *)malloc((size_t)k * k * sizeof(double));
+    if (!cval || !flags || !removed || !hcell || !hpos || !old) {
+        free(cval); free(flags); free(removed); free(hcell); free(hpos); free(old);
+        problem_free(&p);
+        return ORC_ENOMEM;
+    }
+    double fmin = INFINITY;
+    for (size_t e = 0; e < (size_t)nx * ny; ++e)
+        if (p.f[e] < fmin) fmin = p.f[e];
+    cell_heap H = {hcell, hpos, 0, cval};
+    for (int c = 0; c < J; ++c) {
+        cval[c] = INFINITY;
+        hpos[c] = -1;
+    }
+    /* source cells: queued with all four flags, cell value max q over the cell */
+    for (size_t e = 0; e < (size_t)nx * ny; ++e) {
+        if (!p.src[e]) continue;
+        int i = (int)(e % nx), j = (int)(e / nx);
+        int c = (j / k) * cxn + i / k;
+        if (hpos[c] < 0) {
+            cval[c] = p.q[e];
+            hcell[H.size] = c;
+            hpos[c] = H.size++;
+        } else if (p.q[e] > cval[c]) {
+            cval[c] = p.q[e];
+        }
+        flags[c] = 15;
+    }
+    for (int e = H.size / 2; e >= 0; --e) ch_down(&H, e);
+    int64_t removals = 0, sweeps = 0, mono_ok = 0, mono_n = 0;
+    while (H.size > 0) {
+        int c = hcell[0];
+        H.size--;
+        if (H.size > 0) {
+            hcell[0] = hcell[H.size];
+            hpos[hcell[0]] = 0;
+            ch_down(&H, 0);
+        }
+        hpos[c] = -1;
+        ++removals;
+        const int first = !removed[c];
+        removed[c] = 1;
+        const int cx = c % cxn, cy = c / cxn;
+        const int i0 = cx * k, i1 = i0 + k < nx ? i0 + k : nx, j0 = cy * k, j1 = j0 + k < ny ? j0 + k : ny;
+        const int w = i1 - i0;
+        for (int j = j0; j < j1; ++j)
+            for (int i = i0; i < i1; ++i) old[(j - j0) * w + (i - i0)] = U[(size_t)j * nx + i];
+        /* the sweeps */
+        const int fl = flags[c];
+        flags[c] = 0;
+        if (fast) {
+            for (int d = 0; d < 4; ++d)
+                if (fl >> d & 1) {
+                    sweep_cell(&p, U, i0, i1, j0, j1, d);
+                    ++sweeps;
+                }
+        } else {
+            int order[4], no = 0;
+            for (int d = 0; d < 4; ++d) if (fl >> d & 1) order[no++] = d;
+            for (int d = 0; d < 4; ++d) if (!(fl >> d & 1)) order[no++] = d;
+            int s = 0, changed;
+            do {
+                int d = s < 4 ? order[s] : s % 4;
+                changed = sweep_cell(&p, U, i0, i1, j0, j1, d);
+                ++s;
+            } while (changed);
+            sweeps += s;
+        }
+        /* the four borders: W, E, S, N */
+        for (int sd = 0; sd < 4; ++sd) {
+            int ncx = cx + (sd == 0 ? -1 : sd == 1 ? 1 : 0), ncy = cy + (sd == 2 ? -1 : sd == 3 ? 1 : 0);
+            if (ncx < 0 || ncy < 0 || ncx >= cxn || ncy >= cyn) continue;
+            const int nc = ncy * cxn + ncx;
+            const int len = sd < 2 ? j1 - j0 : i1 - i0;
+            int act = 0, bmax = -1;
+            double vmax = 0.0;
+            int nondec = 1, noninc = 1;
+            double prev = 0.0;
+            for (int b = 0; b < len; ++b) {
+                int bi, bj, ai, aj;
+                if (sd == 0) { bi = i0; bj = j0 + b; ai = bi - 1; aj = bj; }
+                else if (sd == 1) { bi = i1 - 1; bj = j0 + b; ai = i1; aj = bj; }
+                else if (sd == 2) { bi = i0 + b; bj = j0; ai = bi; aj = j0 - 1; }
+                else { bi = i0 + b; bj = j1 - 1; ai = bi; aj = j1; }
+                const size_t qb = (size_t)bj * nx + bi, qa = (size_t)aj * nx + ai;
+                const double vb = U[qb];
+                const int ch = vb < old[(bj - j0) * w + (bi - i0)];
+                if ((ch || (first && p.src[qb])) && vb < U[qa] && !p.src[qa]) act = 1;
+                if (isfinite(vb) && (bmax < 0 || vb >= vmax)) { vmax = vb; bmax = b; }
+                if (b > 0) {
+                    if (vb < prev) nondec = 0;
+                    if (vb > prev) noninc = 0;
+                }
+                prev = vb;
+            }
+            if (bmax >= 0) {
+                int ai, aj;
+                if (sd == 0) { ai = i0 - 1; aj = j0 + bmax; }
+                else if (sd == 1) { ai = i1; aj = j0 + bmax; }
+                else if (sd == 2) { ai = i0 + bmax; aj = j0 - 1; }
+                else { ai = i0 + bmax; aj = j1; }
+                double fy = p.f[(size_t)aj * nx + ai];
+                if (!isfinite(fy)) fy = fmin;
+                const double v = vmax + 0.5 * (k + 1) * fy;
+                if (v < cval[nc]) {
+                    cval[nc] = v;
+                    if (hpos[nc] >= 0) ch_up(&H, hpos[nc]);
+                }
+            }
+            if (!act) continue;
+            /* the flags pointing away from side sd, and along the border
+             * the direction from its smaller values (the Monotonicity Check) */
+            int up, down;  /* flag for increasing / decreasing along-border coordinate */
+            if (sd == 0) { up = 3; down = 2; }       /* neighbour west: i down */
+            else if (sd == 1) { up = 0; down = 1; }  /* neighbour east: i up */
+            else if (sd == 2) { up = 1; down = 2; }  /* neighbour south: j down */
+            else { up = 0; down = 3; }               /* neighbour north: j up */
+            int set;
+            if (!fast) {
+                set = (1 << up) | (1 << down);
+            } else {
+                ++mono_n;
+                if (noninc) { set = 1 << down; ++mono_ok; }
+                else if (nondec) { set = 1 << up; ++mono_ok; }
+                else set = (1 << up) | (1 << down);
+            }
+            flags[nc] |= (unsigned char)set;
+            if (hpos[nc] < 0) {
+                hcell[H.size] = nc;
+                hpos[nc] = H.size++;
+                ch_up(&H, hpos[nc]);
+            }
+        }
+    }
+    if (stats) {
+        stats[0] = removals;
+        stats[1] = sweeps;
+        stats[2] = mono_ok;
+        stats[3] = mono_n;
+    }
+    free(cval); free(flags); free(removed); free(hcell); free(hpos); free(old);
+    problem_free(&p);
+    return ORC_OK;
+}

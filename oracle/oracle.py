@@ -95,7 +95,8 @@ class Oracle:
         lib.orc_apply_T.argtypes = common + [P(d), P(d)]
         lib.orc_node_update.argtypes = [d, d, d, d, d]
         lib.orc_node_update.restype = d
-        for fn in (lib.orc_fmm, lib.orc_fsm, lib.orc_jacobi, lib.orc_apply_T):
+        lib.orc_cells.argtypes = common + [ctypes.c_int, ctypes.c_int, P(d), P(i64)]
+        for fn in (lib.orc_fmm, lib.orc_fsm, lib.orc_jacobi, lib.orc_apply_T, lib.orc_cells):
             fn.restype = ctypes.c_int
         self.lib = lib
         self.path = lib_path
@@ -131,6 +132,21 @@ class Oracle:
                                 ctypes.byref(ns)), "fsm")
         del keep
         return (U, ns.value) if return_sweeps else U
+
+    def cells(self, F, h, si, sj, sq, k, fast=False):
+        """Heap-Cell Method (Sec. 4.2; fast=False, exact) or Fast Heap-Cell
+        Method (Sec. 4.3, Alg. FHCM; fast=True, inexact) on k x k cells.
+        Returns U and {'avhr', 'avs', 'mon_pct', 'removals', 'sweeps'}."""
+        keep, args, shape = _args(F, h, si, sj, sq)
+        U = np.empty(shape, dtype=np.float64)
+        st = np.zeros(4, dtype=np.int64)
+        _check(self.lib.orc_cells(*args, int(k), int(bool(fast)), _ptr(U, ctypes.c_double),
+                                  _ptr(st, ctypes.c_int64)), "cells")
+        del keep
+        ny, nx = shape
+        J = ((nx + k - 1) // k) * ((ny + k - 1) // k)
+        return U, {"removals": int(st[0]), "sweeps": int(st[1]), "avhr": st[0] / J, "avs": st[1] / J,
+                   "mon_pct": 100.0 * st[2] / st[3] if st[3] else 100.0}
 
     def jacobi(self, F, h, si, sj, sq, max_iters=1_000_000, return_iters=False):
         """Jacobi value iteration from +inf; only sensible on tiny grids."""
@@ -178,6 +194,10 @@ def fsm(*a, **k):
 
 def jacobi(*a, **k):
     return default().jacobi(*a, **k)
+
+
+def cells(*a, **k):
+    return default().cells(*a, **k)
 
 
 def apply_T(*a, **k):

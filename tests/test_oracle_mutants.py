@@ -68,3 +68,51 @@ def test_unmutated_source_passes_the_same_pins():
     clean = oracle.Oracle.from_source(_source())
     for pin in PINS:
         pin(clean)
+
+
+# ---------------------------------------------------------------- cell methods
+CELL_MUTANTS = {
+    # HCM that stops after one sweep is no longer exact
+    "hcm_single_sweep": ("            } while (changed);", "            } while (0);"),
+    # a source on a cell border that never activates across it leaves cells unreached
+    "no_first_removal_activation": ("if ((ch || (first && p.src[qb])) && vb < U[qa] && !p.src[qa]) act = 1;",
+                                    "if (ch && vb < U[qa] && !p.src[qa]) act = 1;"),
+}
+# mistakes that keep HCM exact and FHCM an upper bound, caught by the
+# paper's printed cell-method statistics (slow)
+CELL_MUTANTS_TABLE = {
+    "fhcm_one_flag_when_not_monotone": ("                else set = (1 << up) | (1 << down);",
+                                        "                else set = 1 << up;"),
+    "sweep_i_order_swapped": ("    int i_up = (dir == 0 || dir == 1), j_up = (dir == 0 || dir == 3);",
+                              "    int i_up = (dir == 2 || dir == 3), j_up = (dir == 0 || dir == 3);"),
+    "monotone_flags_swapped": ("                if (noninc) { set = 1 << down; ++mono_ok; }",
+                               "                if (noninc) { set = 1 << up; ++mono_ok; }"),
+}
+
+
+def _caught_by(mutant, pin_fns):
+    for pin in pin_fns:
+        try:
+            pin(mutant)
+        except (AssertionError, oracle.OracleError):
+            return True
+    return False
+
+
+@pytest.mark.parametrize("name", sorted(CELL_MUTANTS))
+def test_cell_pins_catch_planted_mistake(name):
+    old, new = CELL_MUTANTS[name]
+    src = _source()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    mutant = oracle.Oracle.from_source(src.replace(old, new))
+    assert _caught_by(mutant, [pins.test_hcm_is_exact_and_fhcm_an_upper_bound]), name
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(CELL_MUTANTS_TABLE))
+def test_cell_table_pin_catches_planted_mistake(name):
+    old, new = CELL_MUTANTS_TABLE[name]
+    src = _source()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    mutant = oracle.Oracle.from_source(src.replace(old, new))
+    assert _caught_by(mutant, [pins.test_cell_methods_reproduce_tab_sinu_1]), name

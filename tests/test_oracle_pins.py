@@ -308,3 +308,57 @@ def test_causality(orc):
         src[I.sj, I.si] = True
         fin = np.isfinite(U) & ~src
         assert (m[fin] < U[fin]).all()
+
+
+# ---------------------------------------------------------------- cell methods
+def test_hcm_is_exact_and_fhcm_an_upper_bound(orc):
+    """HCM sweeps every removed cell to convergence, so by Theorem
+    convergence it reaches the solution of eq. Eik_discr (FMM's) whatever the
+    cell size; FHCM stops early but only ever applies the local update to
+    upper bounds, so it never goes below that solution (Sec. 4.3)."""
+    rng = np.random.default_rng(11)
+    for t in range(60):
+        I = W.tiny_random(rng, n_max=24)
+        V = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+        fin = np.isfinite(V)
+        scale = max(np.abs(V[fin]).max(), 1e-300) if fin.any() else 1.0
+        for k in (1, 2, 3, 5, 8):
+            U, _ = orc.cells(I.F, I.h, I.si, I.sj, I.sq, k, fast=False)
+            assert (np.isfinite(U) == fin).all()
+            assert np.abs(U[fin] - V[fin]).max(initial=0) <= 1e-13 * scale
+            Uf, _ = orc.cells(I.F, I.h, I.si, I.sj, I.sq, k, fast=True)
+            assert (Uf[fin] >= V[fin] - 1e-13 * scale).all()
+            if k == 1:  # one-node cells: one update per removal is exact
+                assert np.abs(Uf[fin] - V[fin]).max(initial=0) <= 1e-13 * scale
+
+
+@pytest.mark.slow
+def test_cell_methods_reproduce_tab_sinu_1(orc):
+    """Tab. sinu_1 prints HCM's and FHCM's removals per cell, FHCM's sweeps
+    per cell and Monotonicity Check rate, and FHCM's error ratios (errors
+    against Fast Marching on an h/4 grid, Sec. 5), for four cell sizes; the
+    oracle's cell methods reproduce them: AvHR and AvS within 3%, Mon %
+    within 1.5 points, the average error ratio within 5% and the ratio of
+    maximum errors within 1%."""
+    with open(os.path.join(GOLD, "paper_cells.json")) as fh:
+        gold = json.load(fh)
+    n = gold["n"]
+    I = W.sin_point(n)
+    J = W.sin_point(4 * (n - 1) + 1)
+    V = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+    truth = orc.fmm(J.F, J.h, J.si, J.sj, J.sq)[::4, ::4]
+    e = np.abs(V - truth)
+    m = e > 0
+    for row in gold["rows"]:
+        k = row["k"]
+        _, sh = orc.cells(I.F, I.h, I.si, I.sj, I.sq, k, fast=False)
+        Uf, sf = orc.cells(I.F, I.h, I.si, I.sj, I.sq, k, fast=True)
+        assert abs(sh["avhr"] / row["hcm_avhr"] - 1) < 0.03, (row, sh)
+        assert abs(sf["avhr"] / row["fhcm_avhr"] - 1) < 0.03, (row, sf)
+        assert abs(sf["avs"] / row["fhcm_avs"] - 1) < 0.03, (row, sf)
+        assert abs(sf["mon_pct"] - row["mon_pct"]) < 1.5, (row, sf)
+        E = np.abs(Uf - truth)
+        rho = (E[m] / e[m]).mean()
+        rmax = E.max() / e.max()
+        assert abs(rho / row["rho"] - 1) < 0.05, (row, rho)
+        assert abs(rmax / row["Rmax"] - 1) < 0.01, (row, rmax)
