@@ -253,6 +253,55 @@ def config_measure(eik, torch, I, prec, steps=5, k=0):
             "err_bound": st.err_bound, "avhr": st.avhr, "schedule": st.schedule}
 
 
+def fhcm_measure(eik, torch, I, steps=5):
+    """The Fast Heap-Cell Method (Sec. 4.3) on the single 1025^2 grid, FP64:
+    device time beside the exact method (HCM), and Sec. 5's error ratios
+    against Fast Marching on an h/4 grid, beside the serial FHCM of the
+    oracle and the paper's Tab. sinu_1 row for its closest cell size."""
+    import oracle
+    from paper_1110_6220_gb300 import workloads as W
+    F = torch.from_numpy(I.F).cuda()
+    src = torch.from_numpy(I.src_ij).cuda()
+    q = torch.from_numpy(np.ascontiguousarray(I.sq)).cuda()
+    U = torch.empty_like(F)
+    out = {}
+    for name, method in (("hcm", eik.EIK_METHOD_HCM), ("fhcm", eik.EIK_METHOD_FHCM)):
+        ms = []
+        with eik.Plan(I.nx, I.ny, I.h, 0, eik.EIK_FP64, method=method) as p:
+            for r in range(steps + 2):
+                rc, st = p.solve(F, src, q, U)
+                if rc:
+                    raise RuntimeError(f"eik_solve ({name}): {eik.eik_strerror(rc)}")
+                if r >= 2:
+                    ms.append(st.ms)
+        med = statistics.median(ms)
+        out[name] = {"ms": med, "value": I.npts / med / 1e3, "unit": UNIT, "cell_k": st.cell_k,
+                     "avhr": st.avhr, "avs": st.avs}
+        if method == eik.EIK_METHOD_FHCM:
+            out[name]["mono_pct"] = st.mono_pct
+            Ug = U.cpu().numpy()
+    n = I.nx
+    J = W.sin_point(4 * (n - 1) + 1)
+    orc = oracle.default()
+    V = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+    truth = orc.fmm(J.F, J.h, J.si, J.sj, J.sq)[::4, ::4]
+    e = np.abs(V - truth)
+    m = e > 0
+
+    def ratios(X):
+        E = np.abs(X - truth)
+        return {"R": float((E[m] / e[m]).max()), "rho": float((E[m] / e[m]).mean()),
+                "R_max_errors": float(E.max() / e.max())}
+    out["fhcm"].update(ratios(Ug))
+    out["fhcm"]["below_exact"] = int((Ug < V - 1e-12 * V.max()).sum())
+    Uo, so = orc.cells(I.F, I.h, I.si, I.sj, I.sq, out["fhcm"]["cell_k"], fast=True)
+    out["oracle_serial_fhcm"] = dict(ratios(Uo), avhr=so["avhr"], avs=so["avs"], mono_pct=so["mon_pct"])
+    out["paper_tab_sinu_1_fhcm_176_cells"] = {"R": 1.0560, "rho": 1.0022, "R_max_errors": 1.0000,
+                                               "avhr": 1.125, "avs": 1.262, "mono_pct": 94.5,
+                                               "note": "1408^2 grid, 8-node cells; context"}
+    return out
+
+
 def batch_measure(eik, torch, steps=5, warmup=2, k=0):
     """The batched workload: 512 grids with side lengths log-uniform in
     [65, 1025] (sin-product or random-block speeds, 1-8 sources), FP32 +
@@ -564,6 +613,8 @@ def run_ours(args):
                 "q_boundary_sin1025_fp32ref": config_measure(eik, torch, W.sin_boundary(1025), eik.EIK_FP32_REFINE),
                 "q_boundary_sin1025_fp64": config_measure(eik, torch, W.sin_boundary(1025), eik.EIK_FP64),
             }
+        if not args.no_configs:
+            line["fhcm"] = fhcm_measure(eik, torch, I)
         if not args.no_batch:
             line["batch"] = batch_measure(eik, torch)
         if not args.no_serving:

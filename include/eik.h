@@ -62,11 +62,22 @@ enum {
     EIK_ECUDA = -7           /* a CUDA runtime call failed */
 };
 
-/* Precision modes.  EIK_FP64: every local update in FP64.  EIK_FP32_REFINE:
- * cell solves in FP32 with the cancellation-free quadratic, then an FP64
- * refinement pass seeded by the FP32 result, then an FP64 residual check
- * whose bound (eik_stats.err_bound) certifies the tolerance. */
+/* Precision modes.  EIK_FP64: FP64 values; the two-sided increment is
+ * evaluated in double-float arithmetic (~1e-14 of it), the sums in FP64.
+ * EIK_FP32_REFINE: every update on the FP32 pipe with the cancellation-free
+ * quadratic, values carried as double-float pairs -- either one pass from
+ * the sources, or an FP32 pass and a refinement pass seeded from it (see
+ * autotuning) -- then a residual check whose bound (eik_stats.err_bound)
+ * certifies the tolerance. */
 enum { EIK_FP64 = 0, EIK_FP32_REFINE = 1 };
+
+/* Methods.  EIK_METHOD_HCM: every removed cell is solved to convergence
+ * (Sec. 4.2): the exact solution of eq. Eik_discr.  EIK_METHOD_FHCM: the
+ * Fast Heap-Cell Method (Sec. 4.3, Alg. FHCM): a removed cell is swept once
+ * in each of its flagged directions, and an activation flags one or two
+ * directions by the Monotonicity Check of the cell border; faster, never
+ * below the exact solution, but not exact (FP64 only). */
+enum { EIK_METHOD_HCM = 0, EIK_METHOD_FHCM = 1 };
 
 /* Problem-shape description (Sec. 3 problem statement plus the method's
  * cell size).  All fields are read at eik_plan_create. */
@@ -80,6 +91,7 @@ typedef struct {
     int32_t precision;     /* EIK_FP64 or EIK_FP32_REFINE */
     double tol;            /* FP32_REFINE: certified max error / max|u|; <= 0: 1e-5 */
     int64_t deadline_ns;   /* device wall-clock limit per solve; <= 0: 20 s */
+    int32_t method;        /* EIK_METHOD_HCM or EIK_METHOD_FHCM */
 } eik_plan_desc;
 
 /* One problem instance (Sec. 3: speed F, exit set Q with values q). */
@@ -99,20 +111,23 @@ typedef struct {
     double updates_per_pt;  /* local updates evaluated / (nx*ny) */
     double avhr;            /* cell visits / number of cells */
     double avs;             /* cell sweeps / number of cells */
-    double max_residual;    /* FP64 max |V - T(V)| over finite non-source nodes */
+    double max_residual;    /* max |V - T(V)| over finite non-source nodes (FP32_REFINE; an
+                               upper bound, evaluated in double-float with an allowance) */
     double err_bound;       /* certified max |V - U| / max|U| (FP32_REFINE); 0 for FP64 */
     double bucket_width;    /* bucket width used */
     int64_t cell_visits;    /* total cell removals (all passes) */
     int64_t rounds;         /* grid-wide rounds (barrier-separated bucket releases) */
     int64_t buckets;        /* bucket advances (threshold moves) */
-    double pass_ms[2];      /* device time of the persistent FP32 pass [0] and FP64 pass [1]
-                               (CUDA events on the plan's stream; 0 if not run) */
+    double pass_ms[2];      /* device time of the persistent FP32 pass [0] and main pass [1]
+                               (events on the launching stream; the kernels' own timers when
+                               replayed from a graph; 0 if not run) */
     int32_t launches;       /* kernels this solve launched */
     int32_t cell_k;         /* cell size used */
     int32_t schedule;       /* bit 0: FP32 pass round-free; bit 1: FP64 / double-float pass
                                round-free; bit 2: FP32_REFINE as one double-float pass;
                                bit 3: replayed from a captured CUDA graph */
     int32_t status;         /* EIK_OK or the error of this solve */
+    double mono_pct;        /* FHCM: Monotonicity Checks that found the border monotone, % */
 } eik_stats;
 
 typedef struct eik_plan_s* eik_plan;

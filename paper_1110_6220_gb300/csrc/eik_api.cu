@@ -42,6 +42,8 @@ bool desc_valid(const eik_plan_desc* d) {
         d->cell_k != 64)
         return false;
     if (d->precision != EIK_FP64 && d->precision != EIK_FP32_REFINE) return false;
+    if (d->method != EIK_METHOD_HCM && d->method != EIK_METHOD_FHCM) return false;
+    if (d->method == EIK_METHOD_FHCM && d->precision != EIK_FP64) return false;
     if ((long long)d->nx * d->ny > (1ll << 31) - 1) return false;
     return true;
 }
@@ -223,7 +225,7 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     const size_t t_src = a256(nsrc * 8 + 8) + a256(ncs * 8 + 8) + 4 * ns4;
     const size_t image_bytes = 2 * t_desc + t_aux + t_own_int + t_pre + t_own_full + t_src;
     const size_t z_ctl = a256((size_t)(2 * n + 2) * sizeof(Ctl) + (size_t)n * sizeof(ResidualOut));
-    const size_t zero_bytes = z_ctl + a256(Jtot * 4) * 2;
+    const size_t zero_bytes = z_ctl + a256(Jtot * 4) * 3;  // qflag, visits, FHCM flags
     // ring of the round-free schedule: a power of two >= 16 times the job's
     // cells (a launch rarely pushes more, so pushes seldom wait for a slot)
     // and the warps of a launch, behind its three counters
@@ -260,6 +262,7 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     ResidualOut* res_dev = (ResidualOut*)(gctl_dev + 2);
     int* qflag_all = (int*)(zero_dev + z_ctl);
     int* visits_all = (int*)(zero_dev + z_ctl + a256(Jtot * 4));
+    int* dflags_all = (int*)(zero_dev + z_ctl + 2 * a256(Jtot * 4));
     unsigned long long* cval_all = (unsigned long long*)cval_dev;
 
     bool ok = true;
@@ -271,6 +274,7 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
         a.cval = cval_all + coff;
         a.qflag = qflag_all + coff;
         a.visits = visits_all + coff;
+        a.dflags = dflags_all + coff;
         hj->arr[i] = a;
         const double* F = stageF[i] ? a.Fstage : in[i].F;
         double* out = hj->out_host[i] ? a.Ostage : in[i].U;
@@ -344,6 +348,7 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     j.deadline_ns = deadline_ns;
     j.sm_cap = 0;
     j.one_pass = fp32 && P.one_pass;
+    j.fhcm = descs[0].method == EIK_METHOD_FHCM;
     j.async_first = P.async_first;
     j.async_main = P.async_main;
     j.qctl = (unsigned*)ring_dev;
@@ -585,13 +590,14 @@ extern "C" int eik_solve_batch(const eik_plan_desc* d, const eik_instance* in, i
     // the group; each group runs as jobs of at most MAX_BATCH instances, one
     // persistent launch per pass
     std::map<std::pair<int, int>, std::vector<int>> groups;
-    for (int i = 0; i < n_inst; ++i) groups[{d[i].cell_k, d[i].precision}].push_back(i);
+    for (int i = 0; i < n_inst; ++i)
+        groups[{d[i].cell_k, d[i].precision + 2 * d[i].method}].push_back(i);
     int first_err = EIK_OK;
     std::vector<eik_plan_desc> gd;
     std::vector<eik_instance> gi;
     std::vector<eik_stats> gs;
     for (auto& kv : groups) {
-        const bool fp32 = kv.first.second == EIK_FP32_REFINE;
+        const bool fp32 = kv.first.second % 2 == EIK_FP32_REFINE;
         const std::vector<int>& idx = kv.second;
         for (size_t b0 = 0; b0 < idx.size(); b0 += MAX_BATCH) {
             const int m = (int)std::min<size_t>(MAX_BATCH, idx.size() - b0);

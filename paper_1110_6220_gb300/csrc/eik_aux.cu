@@ -180,6 +180,7 @@ __global__ void k_init_source_cells(const AuxInst* A, const SourceTable s) {
         const int c = s.cell[e];
         p.cval[c] = s.cell_key[e];
         p.qflag[c] = 1;
+        if (p.dflags) p.dflags[c] = 15;  // FHCM: source cells sweep in all four directions
         const int pos = atomicAdd(&p.ctl->fcnt[0], 1);
         if (pos < p.J) p.far0[pos] = c;
     }

@@ -108,7 +108,7 @@ extern "C" int eik_batch_create(eik_batch* out, const eik_plan_desc* d, const ei
     // groups as eik_solve_batch forms them: (cell_k as given, precision), at
     // most MAX_BATCH instances per job
     std::map<std::pair<int, int>, std::vector<int>> by;
-    for (int i = 0; i < n_inst; ++i) by[{d[i].cell_k, d[i].precision}].push_back(i);
+    for (int i = 0; i < n_inst; ++i) by[{d[i].cell_k, d[i].precision + 2 * d[i].method}].push_back(i);
     int rc = EIK_OK;
     for (auto& kv : by) {
         const std::vector<int>& idx = kv.second;
@@ -127,7 +127,7 @@ extern "C" int eik_batch_create(eik_batch* out, const eik_plan_desc* d, const ei
             }
             g->P = choose_params(g->d.data(), (int)m);
             for (auto& x : g->d) x.cell_k = g->P.k;
-            g->fp32 = kv.first.second == EIK_FP32_REFINE;
+            g->fp32 = kv.first.second % 2 == EIK_FP32_REFINE;
             for (auto& e : g->ev)
                 if (cudaEventCreate(&e) != cudaSuccess) rc = EIK_ECUDA;
             if (!rc)

@@ -60,6 +60,8 @@ struct Ctl {
     // launch-wide control blocks: first start and last end of the persistent
     // pass (%globaltimer, ns), kept where events cannot be (graph replay)
     unsigned long long t_start, t_end;
+    // FHCM Monotonicity Checks: monotone borders / checks made
+    unsigned long long mono_ok, mono_n;
     // per-phase clock cycles summed over warps, filled only when profiling
     // (EIK_PROFILE=1): 0 split, 1 barrier, 2 list+pop, 3 TMA wait, 4 sweeps,
     // 5 write-back, 6 activation, 7 warp-rounds with work
@@ -87,6 +89,7 @@ struct __align__(64) InstDesc {
     unsigned long long* cval;     // ordered cell-value keys
     int* qflag;                   // rounds: 1 while queued; async: bit 0 requested, bit 1 running
     int* visits;                  // removals so far
+    int* dflags;                  // FHCM: directional flags (bit d: sweep direction d)
     int* lists;                   // 5 * J ints: near[3], far[2]
     Ctl* ctl;                     // this instance's lists, counters and status
     int upitch;
@@ -103,6 +106,7 @@ struct SolveParams {
     Ctl* gctl;                    // grid barrier, abort flag, launch status, rounds
     long long deadline_ns;        // relative to kernel start
     int profile;                  // accumulate gctl->prof
+    int fhcm;                     // Fast Heap-Cell Method: one sweep per flagged direction
     // asynchronous scheduling only: ring of (sequence << 32 | global cell)
     // words, ring_mask + 1 (a power of two) >= twice the job's cells and the
     // launch's warps; the global
@@ -125,9 +129,9 @@ struct LaunchShape {
 };
 
 // one per arithmetic mode (eik_solver_f64.cu, eik_solver_f32.cu, eik_solver_df.cu)
-int solver_shape_f64(int k, int num_sms, int n_inst, int sm_cap, bool async, LaunchShape* out);
-int solver_shape_f32(int k, int num_sms, int n_inst, int sm_cap, bool async, LaunchShape* out);
-int solver_shape_df(int k, int num_sms, int n_inst, int sm_cap, bool async, LaunchShape* out);
+int solver_shape_f64(int k, int num_sms, int n_inst, int sm_cap, bool async, bool fhcm, LaunchShape* out);
+int solver_shape_f32(int k, int num_sms, int n_inst, int sm_cap, bool async, bool fhcm, LaunchShape* out);
+int solver_shape_df(int k, int num_sms, int n_inst, int sm_cap, bool async, bool fhcm, LaunchShape* out);
 // async: the round-free kernel (k_solve_async, cell sizes >= 8) instead of
 // the bucketed rounds (k_solve)
 cudaError_t launch_solver_f64(int k, bool async, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
@@ -168,7 +172,7 @@ struct AuxInst {
     double* U64; double* f64;
     float* U32; float* f32;
     float2* Udf; float2* fdf;
-    unsigned long long* cval; int* qflag; int* visits; int* far0;
+    unsigned long long* cval; int* qflag; int* visits; int* far0; int* dflags;
     Ctl* ctl;                     // the instance's control block of the first pass
     Ctl* ctl2;                    // ... of the refinement pass (FP32+refinement)
     ResidualOut* res;

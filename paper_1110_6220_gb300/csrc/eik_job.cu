@@ -110,6 +110,7 @@ static void fill_desc(InstDesc* d, const Layout& L, void* U, const void* f, bool
     d->cval = a.cval;
     d->qflag = a.qflag;
     d->visits = a.visits;
+    d->dflags = a.dflags;
     d->lists = a.lists;
     d->ctl = ctl;
     d->upitch = L.upitch;
@@ -157,6 +158,7 @@ void fill_inst_tables(const Layout& L, const InstArrays& a, bool fp32, double h,
     aux->cval = a.cval;
     aux->qflag = a.qflag;
     aux->visits = a.visits;
+    aux->dflags = a.dflags;
     aux->far0 = a.lists + 3 * L.J;
     aux->ctl = fp32 ? ictl_first : ictl_main;
     aux->ctl2 = fp32 ? ictl_main : nullptr;
@@ -195,6 +197,7 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
     p.n_inst = n;
     p.deadline_ns = j.deadline_ns > 0 ? j.deadline_ns : 20000000000ll;
     p.profile = profiling();
+    p.fhcm = j.fhcm ? 1 : 0;
     p.ring = j.ring;
     p.ring_mask = j.ring_mask;
     p.cell_pre = j.cell_pre;
@@ -206,7 +209,7 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
         // FP32_REFINE in one double-float pass from the sources (every
         // update on the FP32 pipe), certified like the two-pass form
         if (ev) cudaEventRecord(ev[0], st), cudaEventRecord(ev[1], st);
-        if (solver_shape_df(j.k, num_sms, n, j.sm_cap, am, &shape)) return EIK_ECUDA;
+        if (solver_shape_df(j.k, num_sms, n, j.sm_cap, am, false, &shape)) return EIK_ECUDA;
         p.inst = j.desc_main;
         p.gctl = j.gctl + 1;
         if (ev) cudaEventRecord(ev[2], st);
@@ -216,7 +219,7 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
         if (launch_residual(j.aux, j.blk_pre, n, j.nblocks, st) != cudaSuccess) return EIK_ECUDA;
         ++nl;
     } else if (j.fp32) {
-        if (solver_shape_f32(j.k, num_sms, n, j.sm_cap, af, &shape)) return EIK_ECUDA;
+        if (solver_shape_f32(j.k, num_sms, n, j.sm_cap, af, false, &shape)) return EIK_ECUDA;
         p.inst = j.desc_f32;
         p.gctl = j.gctl;
         if (ev) cudaEventRecord(ev[0], st);
@@ -229,7 +232,7 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
             cudaSuccess)
             return EIK_ECUDA;
         nl += 2;
-        if (solver_shape_df(j.k, num_sms, n, j.sm_cap, am, &shape)) return EIK_ECUDA;
+        if (solver_shape_df(j.k, num_sms, n, j.sm_cap, am, false, &shape)) return EIK_ECUDA;
         p.inst = j.desc_main;
         p.gctl = j.gctl + 1;
         if (ev) cudaEventRecord(ev[2], st);
@@ -239,7 +242,7 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
         if (launch_residual(j.aux, j.blk_pre, n, j.nblocks, st) != cudaSuccess) return EIK_ECUDA;
         ++nl;
     } else {
-        if (solver_shape_f64(j.k, num_sms, n, j.sm_cap, am, &shape)) return EIK_ECUDA;
+        if (solver_shape_f64(j.k, num_sms, n, j.sm_cap, am, j.fhcm, &shape)) return EIK_ECUDA;
         p.inst = j.desc_main;
         p.gctl = j.gctl + 1;
         if (ev) cudaEventRecord(ev[2], st);
@@ -258,16 +261,16 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
 bool job_pairable(const JobDev& j, int num_sms) {
     LaunchShape a{}, b{};
     if (j.fp32 && j.one_pass) {
-        if (solver_shape_df(j.k, num_sms, j.n, 1, j.async_main, &b)) return false;
+        if (solver_shape_df(j.k, num_sms, j.n, 1, j.async_main, false, &b)) return false;
         return b.per_sm >= 2;
     }
     if (j.fp32) {
-        if (solver_shape_f32(j.k, num_sms, j.n, 1, j.async_first, &a) ||
-            solver_shape_df(j.k, num_sms, j.n, 1, j.async_main, &b))
+        if (solver_shape_f32(j.k, num_sms, j.n, 1, j.async_first, false, &a) ||
+            solver_shape_df(j.k, num_sms, j.n, 1, j.async_main, false, &b))
             return false;
         return a.per_sm >= 2 && b.per_sm >= 2;
     }
-    if (solver_shape_f64(j.k, num_sms, j.n, 1, j.async_main, &a)) return false;
+    if (solver_shape_f64(j.k, num_sms, j.n, 1, j.async_main, j.fhcm, &a)) return false;
     return a.per_sm >= 2;
 }
 
@@ -328,6 +331,7 @@ void job_stats(const Layout& L, const eik_plan_desc* d, bool fp32, const Ctl* ic
     };
     s.pass_ms[0] = fp32 ? span(g_first) : 0.0;
     s.pass_ms[1] = span(g_main);
+    s.mono_pct = g_main->mono_n ? 100.0 * (double)g_main->mono_ok / (double)g_main->mono_n : 0.0;
     const double fmin = dval(ictl_main->fmin_f);
     s.bucket_width = bw_main > 0 ? bw_main : (bw_main < 0 ? -bw_main : 4.0) * L.k * fmin;
     if (fp32) {

@@ -27,6 +27,7 @@ struct InstArrays {
     unsigned long long* cval;
     int* qflag;
     int* visits;
+    int* dflags;                // FHCM: directional flags per cell
     int* lists;                 // 5 J
     double* Fstage;             // device copy of a host F (null if F is on the device)
     double* Ostage;             // result staging for a host U (null if U is on the device)
@@ -58,6 +59,7 @@ struct JobDev {
     int sm_cap;                 // > 0: at most this many blocks per SM (room for other jobs)
     bool async_first, async_main;  // round-free schedule (k_solve_async) for the FP32 / main pass
     bool one_pass;              // fp32: no FP32 pass; the double-float pass solves from the sources
+    bool fhcm;                  // Fast Heap-Cell Method (one sweep per flagged direction)
     unsigned long long* ring;   // async: ring of ring_mask + 1 words
     unsigned ring_mask;
     unsigned* qctl;             // async: head, tail, pending (384 bytes before the ring)

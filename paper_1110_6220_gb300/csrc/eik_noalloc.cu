@@ -129,7 +129,7 @@ extern "C" int eik_solve_noalloc(const eik_plan_desc* d, const eik_instance* in,
                                  void* cuda_stream) {
     const auto t0 = std::chrono::steady_clock::now();
     if (!desc_valid(d) || !in || !in->F || !in->U) return EIK_EINVAL;
-    if (d->precision != EIK_FP64) return EIK_EINVAL;
+    if (d->precision != EIK_FP64 || d->method != EIK_METHOD_HCM) return EIK_EINVAL;
     if (!is_device_ptr(in->F) || !is_device_ptr(in->U)) return EIK_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {

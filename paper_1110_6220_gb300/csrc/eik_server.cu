@@ -129,7 +129,7 @@ bool launch_slot(eik_server_s* s, Slot& sl, size_t held_by_others) {
     sl.reqs.clear();
     for (auto it = s->waiting.begin(); it != s->waiting.end() && (int)sl.reqs.size() < MAX_BATCH;) {
         Request* r = *it;
-        if (r->d.cell_k == kreq && r->d.precision == prec) {
+        if (r->d.cell_k == kreq && r->d.precision == prec && r->d.method == head->d.method) {
             if (held_by_others + bytes + r->bytes > s->budget) break;  // keep FIFO order
             bytes += r->bytes;
             sl.reqs.push_back(r);

@@ -572,6 +572,7 @@ struct WarpState {
     // per instance change instead of three atomics per visit on one address)
     int acc_inst;
     unsigned long long acc_visits, acc_sweeps, acc_lane, st_lane;
+    unsigned long long mono_ok, mono_n;  // FHCM Monotonicity Checks
 
     __device__ __forceinline__ void init(unsigned char* smem) {
         lane = threadIdx.x & 31;
@@ -593,6 +594,7 @@ struct WarpState {
         phase = 0;
         acc_inst = -1;
         acc_visits = acc_sweeps = acc_lane = st_lane = 0;
+        mono_ok = mono_n = 0;
         if (lane == 0) {
             mbar_init(bar, 1);
             fence_mbar_init();
@@ -612,7 +614,7 @@ struct WarpState {
 // outcome of the test -- the scheduler's part.  c, ii, first: this lane's
 // cell, its instance and whether this is the cell's first removal.  Returns
 // false when the TMA wait gave up (abort raised).
-template <int MODE, int K, bool CVAL, class Act>
+template <int MODE, int K, bool CVAL, bool FAST, class Act>
 __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDesc* inst, Ctl* gctl,
                                             unsigned long long deadline, int c, int ii, int first,
                                             const int* cg, const int* ig, int prof_on,
@@ -678,8 +680,20 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
         __syncwarp();
     }
 
+    // ---- FHCM (Alg. FHCM): the cell's directional flags, taken and cleared
+    // now (after the claim); only the flagged directions sweep, once
+    int fl = 15;
+    if constexpr (FAST) {
+        int mine = 0;
+        if (dl == 0 && c >= 0) mine = atomicExch(&d.dflags[c], 0);
+        fl = __shfl_sync(FULL, mine, g * C::LPC);
+        if (fl == 0) fl = 15;  // a cell queued without flags: sweep all four
+    }
+    const bool dir_on = (fl >> dir) & 1;
+
     // ---- passes of four concurrent directional sweeps until a pass
     // changes nothing or the fixed-point check finds nothing to improve
+    // (FHCM: one pass of the flagged directions)
     unsigned long long chg[C::RPL];
 #pragma unroll
     for (int m = 0; m < C::RPL; ++m) chg[m] = 0ull;
@@ -694,7 +708,7 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
                 const int j = rl + C::LPD * m;
                 const int jj = sy ? j : K - 1 - j;
                 const int ii2 = t2 - jj;
-                if (c >= 0 && ii2 >= 0 && ii2 < K) {
+                if (c >= 0 && (!FAST || dir_on) && ii2 >= 0 && ii2 < K) {
                     const int i = sx ? ii2 : K - 1 - ii2;
                     T cand, old;
                     if (node_candidate<MODE, K>(tU, tF, tG, i, j, cand, old) && lt(cand, old)) {
@@ -707,6 +721,10 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
             __syncwarp();
         }
         const unsigned any = __ballot_sync(FULL, changed);
+        if constexpr (FAST) {
+            if (!gdone) gsweeps += __popc(fl);
+            gdone = true;
+        }
         if (!gdone) {
             gsweeps += 4;
             if (!(any & w.gmask)) gdone = true;
@@ -825,6 +843,33 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
                 bmax = obm;
             }
         }
+        // FHCM: the neighbour's flags, from the Monotonicity Check of this
+        // border (its values along the border coordinate: non-increasing ->
+        // the sweep that runs against it, non-decreasing -> the one that runs
+        // with it, neither -> both), released before the activation
+        if (FAST && rl == 0 && has_nb && activate) {
+            bool nondec = true, noninc = true;
+            T prev = zero_v<T>();
+            for (int b = 0; b < K; ++b) {
+                const int bi = sd == 0 ? 0 : sd == 1 ? K - 1 : b;
+                const int bj = sd == 2 ? 0 : sd == 3 ? K - 1 : b;
+                const T v = tU[(bj + 1) * C::BW + (bi + 1)];
+                if (b > 0) {
+                    if (lt(v, prev)) nondec = false;
+                    if (lt(prev, v)) noninc = false;
+                }
+                prev = v;
+            }
+            // neighbour W: i down; E: i up; S: j down; N: j up
+            const int up = sd == 0 ? 3 : sd == 1 ? 0 : sd == 2 ? 1 : 0;
+            const int down = sd == 0 ? 2 : sd == 1 ? 1 : sd == 2 ? 2 : 3;
+            const int bits = noninc ? 1 << down : nondec ? 1 << up : (1 << up) | (1 << down);
+            w.mono_n += 1;
+            w.mono_ok += (noninc || nondec) ? 1 : 0;
+            const int nc = sd == 0 ? c - 1 : sd == 1 ? c + 1 : sd == 2 ? c - cxn : c + cxn;
+            atomicOr(&d.dflags[nc], bits);
+            fence_acq_rel_gpu();
+        }
         if (rl == 0 && has_nb) {
             const int nc = sd == 0 ? c - 1 : sd == 1 ? c + 1 : sd == 2 ? c - cxn : c + cxn;
             double vt = inf_of<double>();
@@ -862,7 +907,7 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
 // instances, the warps process them, re-activations go to the next near list
 // (key <= theta) or to the far list, and a grid barrier ends the round; when
 // an instance's near list runs dry its next bucket is split off the far list.
-template <int MODE, int K>
+template <int MODE, int K, bool FAST>
 __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
     k_solve(const __grid_constant__ SolveParams p) {
     using C = TileCfg<MODE, K>;
@@ -1046,7 +1091,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
             PROF_MARK(2);
             pacc[7] += 1;
 
-            const bool ok = visit_cells<MODE, K, true>(
+            const bool ok = visit_cells<MODE, K, true, FAST>(
                 w, inst, gctl, deadline, c, ii_, first, cg, ig, prof_on, pacc, pt,
                 [&](const InstDesc& dn, int nc, unsigned long long kk, unsigned long long old, bool activate) {
                     const int was = activate ? atomicExch(&dn.qflag[nc], 1) : 1;
@@ -1076,6 +1121,10 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
 
     flush_counters(inst, w.acc_inst, w.acc_visits, w.acc_sweeps, w.acc_lane);
     if (w.st_lane) atomicAdd(&gctl->lane_updates, w.st_lane);
+    if (FAST && w.mono_n) {
+        atomicAdd(&gctl->mono_n, w.mono_n);
+        atomicAdd(&gctl->mono_ok, w.mono_ok);
+    }
     if (p.profile && lane == 0)
         for (int i = 0; i < 8; ++i) atomicAdd(&gctl->prof[i], pacc[i]);
     if (gtid == 0) gctl->rounds = st_rounds;
@@ -1152,7 +1201,7 @@ __device__ __forceinline__ int ring_pop(const SolveParams& p, Ctl* gctl, unsigne
     return (int)(unsigned)v;
 }
 
-template <int MODE, int K>
+template <int MODE, int K, bool FAST>
 __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
     k_solve_async(const __grid_constant__ SolveParams p) {
     using C = TileCfg<MODE, K>;
@@ -1260,7 +1309,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
         PROF_MARK(2);
         pacc[7] += 1;
         const int cg[1] = {c}, ig[1] = {ii};
-        const bool ok = visit_cells<MODE, K, false>(
+        const bool ok = visit_cells<MODE, K, false, FAST>(
             w, inst, gctl, deadline, c, ii, first, cg, ig, prof_on, pacc, pt,
             [&](const InstDesc& dn, int nc, unsigned long long, unsigned long long, bool activate) {
                 if (activate && (atomicOr(&dn.qflag[nc], 1) & 3) == 0) {
@@ -1280,6 +1329,10 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
 
     flush_counters(inst, w.acc_inst, w.acc_visits, w.acc_sweeps, w.acc_lane);
     if (w.st_lane) atomicAdd(&gctl->lane_updates, w.st_lane);
+    if (FAST && w.mono_n) {
+        atomicAdd(&gctl->mono_n, w.mono_n);
+        atomicAdd(&gctl->mono_ok, w.mono_ok);
+    }
     if (p.profile && lane == 0)
         for (int i = 0; i < 8; ++i) atomicAdd(&gctl->prof[i], pacc[i]);
     if (lane == 0) atomicMax(&gctl->t_end, gtimer());

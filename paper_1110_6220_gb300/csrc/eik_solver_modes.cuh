@@ -6,17 +6,26 @@
 
 namespace eik {
 
+// The Fast Heap-Cell variant (FAST) is built for FP64 only (the only mode
+// that offers it); the exact kernels carry none of its code.
 template <int MODE, int K>
-static const void* solver_fn(bool async) {
+static const void* solver_fn(bool async, bool fhcm) {
+    if constexpr (MODE == MODE_F64) {
+        if (fhcm) {
+            if constexpr (TileCfg<MODE, K>::CPW == 1)
+                if (async) return (const void*)k_solve_async<MODE, K, true>;
+            return (const void*)k_solve<MODE, K, true>;
+        }
+    }
     if constexpr (TileCfg<MODE, K>::CPW == 1)
-        if (async) return (const void*)k_solve_async<MODE, K>;
-    return (const void*)k_solve<MODE, K>;
+        if (async) return (const void*)k_solve_async<MODE, K, false>;
+    return (const void*)k_solve<MODE, K, false>;
 }
 
 template <int MODE, int K>
-static void shape_of(int num_sms, int n_inst, int sm_cap, bool async, LaunchShape* s) {
+static void shape_of(int num_sms, int n_inst, int sm_cap, bool async, bool fhcm, LaunchShape* s) {
     using C = TileCfg<MODE, K>;
-    const void* fn = solver_fn<MODE, K>(async);
+    const void* fn = solver_fn<MODE, K>(async, fhcm);
     s->threads = C::WPB * 32;
     s->smem = (size_t)C::WPB * C::WARP_BYTES + 128 + (size_t)inst_state_bytes(n_inst);
     s->blocks = 0;
@@ -42,35 +51,36 @@ static void shape_of(int num_sms, int n_inst, int sm_cap, bool async, LaunchShap
 }
 
 template <int MODE>
-static int solver_shape_mode(int k, int num_sms, int n_inst, int sm_cap, bool async, LaunchShape* out) {
+static int solver_shape_mode(int k, int num_sms, int n_inst, int sm_cap, bool async, bool fhcm,
+                             LaunchShape* out) {
     out->blocks = 0;
     switch (k) {
-    case 4: shape_of<MODE, 4>(num_sms, n_inst, sm_cap, async, out); break;
-    case 8: shape_of<MODE, 8>(num_sms, n_inst, sm_cap, async, out); break;
-    case 16: shape_of<MODE, 16>(num_sms, n_inst, sm_cap, async, out); break;
-    case 32: shape_of<MODE, 32>(num_sms, n_inst, sm_cap, async, out); break;
-    case 64: shape_of<MODE, 64>(num_sms, n_inst, sm_cap, async, out); break;
+    case 4: shape_of<MODE, 4>(num_sms, n_inst, sm_cap, async, fhcm, out); break;
+    case 8: shape_of<MODE, 8>(num_sms, n_inst, sm_cap, async, fhcm, out); break;
+    case 16: shape_of<MODE, 16>(num_sms, n_inst, sm_cap, async, fhcm, out); break;
+    case 32: shape_of<MODE, 32>(num_sms, n_inst, sm_cap, async, fhcm, out); break;
+    case 64: shape_of<MODE, 64>(num_sms, n_inst, sm_cap, async, fhcm, out); break;
     default: return -1;
     }
     return out->blocks > 0 ? 0 : -1;
 }
 
 template <int MODE, int K>
-static cudaError_t launch_one(bool async, const SolveParams& p, const LaunchShape& s, cudaStream_t st) {
+static cudaError_t launch_one(bool async, bool fhcm, const SolveParams& p, const LaunchShape& s, cudaStream_t st) {
     void* args[] = {(void*)&p};
-    return cudaLaunchCooperativeKernel(solver_fn<MODE, K>(async), dim3(s.blocks), dim3(s.threads), args, s.smem,
-                                       st);
+    return cudaLaunchCooperativeKernel(solver_fn<MODE, K>(async, fhcm), dim3(s.blocks), dim3(s.threads), args,
+                                       s.smem, st);
 }
 
 template <int MODE>
 static cudaError_t launch_solver_mode(int k, bool async, const SolveParams& p, const LaunchShape& s,
                                       cudaStream_t st) {
     switch (k) {
-    case 4: return launch_one<MODE, 4>(async, p, s, st);
-    case 8: return launch_one<MODE, 8>(async, p, s, st);
-    case 16: return launch_one<MODE, 16>(async, p, s, st);
-    case 32: return launch_one<MODE, 32>(async, p, s, st);
-    case 64: return launch_one<MODE, 64>(async, p, s, st);
+    case 4: return launch_one<MODE, 4>(async, p.fhcm != 0, p, s, st);
+    case 8: return launch_one<MODE, 8>(async, p.fhcm != 0, p, s, st);
+    case 16: return launch_one<MODE, 16>(async, p.fhcm != 0, p, s, st);
+    case 32: return launch_one<MODE, 32>(async, p.fhcm != 0, p, s, st);
+    case 64: return launch_one<MODE, 64>(async, p.fhcm != 0, p, s, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -34,13 +34,15 @@ EIK_ENOTCONVERGED = -6
 EIK_ECUDA = -7
 EIK_FP64 = 0
 EIK_FP32_REFINE = 1
+EIK_METHOD_HCM = 0
+EIK_METHOD_FHCM = 1
 
 
 class eik_plan_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("h", ctypes.c_double),
                 ("cell_k", ctypes.c_int32), ("bucket_width", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("tol", ctypes.c_double),
-                ("deadline_ns", ctypes.c_int64)]
+                ("deadline_ns", ctypes.c_int64), ("method", ctypes.c_int32)]
 
 
 class eik_instance(ctypes.Structure):
@@ -56,7 +58,8 @@ class eik_stats(ctypes.Structure):
                 ("cell_visits", ctypes.c_int64), ("rounds", ctypes.c_int64),
                 ("buckets", ctypes.c_int64), ("pass_ms", ctypes.c_double * 2),
                 ("launches", ctypes.c_int32), ("cell_k", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("status", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("mono_pct", ctypes.c_double)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
@@ -271,9 +274,9 @@ def _ptr(a, dtype):
 
 
 def make_desc(nx, ny, h, cell_k=8, precision=EIK_FP64, bucket_width=0.0, tol=0.0,
-              deadline_ns=0) -> eik_plan_desc:
+              deadline_ns=0, method=0) -> eik_plan_desc:
     return eik_plan_desc(int(nx), int(ny), float(h), int(cell_k), float(bucket_width),
-                         int(precision), float(tol), int(deadline_ns))
+                         int(precision), float(tol), int(deadline_ns), int(method))
 
 
 def make_instance(F, src_ij, src_q, U) -> eik_instance:
@@ -286,8 +289,8 @@ class Plan:
     """Owns an ``eik_plan`` for one grid shape."""
 
     def __init__(self, nx, ny, h, cell_k=8, precision=EIK_FP64, bucket_width=0.0, tol=0.0,
-                 deadline_ns=0, stream=None):
-        self.desc = make_desc(nx, ny, h, cell_k, precision, bucket_width, tol, deadline_ns)
+                 deadline_ns=0, stream=None, method=EIK_METHOD_HCM):
+        self.desc = make_desc(nx, ny, h, cell_k, precision, bucket_width, tol, deadline_ns, method)
         self.handle = eik_plan_create(self.desc, stream)
 
     def solve(self, F, src_ij, src_q, U):
@@ -315,7 +318,7 @@ class Plan:
 
 
 def solve(F, h, si, sj, sq, cell_k=8, precision=EIK_FP64, bucket_width=0.0, tol=0.0,
-          deadline_ns=0):
+          deadline_ns=0, method=EIK_METHOD_HCM):
     """Convenience: host arrays in, host U out, (U, stats); raises on error."""
     F = np.ascontiguousarray(F, dtype=np.float64)
     ny, nx = F.shape
@@ -323,7 +326,7 @@ def solve(F, h, si, sj, sq, cell_k=8, precision=EIK_FP64, bucket_width=0.0, tol=
                                   .reshape(-1), dtype=np.int32)
     sq = np.ascontiguousarray(np.atleast_1d(sq), dtype=np.float64)
     U = np.empty((ny, nx), dtype=np.float64)
-    with Plan(nx, ny, h, cell_k, precision, bucket_width, tol, deadline_ns) as p:
+    with Plan(nx, ny, h, cell_k, precision, bucket_width, tol, deadline_ns, method=method) as p:
         rc, st = p.solve(F, src_ij, sq, U)
     if rc:
         raise EikError(rc, "eik_solve")
