@@ -224,6 +224,8 @@ typedef struct {
     int32_t async_main;    /* 1: the FP64 / refinement pass runs round-free */
     int32_t one_pass;      /* FP32_REFINE: 1 = one double-float pass from the sources, 0 = an
                               FP32 pass, then a refinement pass seeded from it */
+    int32_t hold_ns;       /* round-free: a taken cell waits until this long after its latest
+                              request, so that several upstream changes merge into one visit */
     double ms;             /* device time of the job with the chosen values */
     double ms_before;      /* device time with the choice in force before */
     int32_t trials;        /* solves run */
@@ -231,7 +233,7 @@ typedef struct {
 
 int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t n_inst, void* cuda_stream,
              eik_tune_result* out);
-/* Write / merge the table as text ("eik-tune 3" then one line per class).
+/* Write / merge the table as text ("eik-tune 4" then one line per class).
  * EIK_EINVAL if the file cannot be written / read or is malformed (nothing
  * merged then). */
 int eik_tune_save(const char* path);

@@ -225,7 +225,7 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     const size_t t_src = a256(nsrc * 8 + 8) + a256(ncs * 8 + 8) + 4 * ns4;
     const size_t image_bytes = 2 * t_desc + t_aux + t_own_int + t_pre + t_own_full + t_src;
     const size_t z_ctl = a256((size_t)(2 * n + 2) * sizeof(Ctl) + (size_t)n * sizeof(ResidualOut));
-    const size_t zero_bytes = z_ctl + a256(Jtot * 4) * 3;  // qflag, visits, FHCM flags
+    const size_t zero_bytes = z_ctl + a256(Jtot * 4) * 3 + a256(Jtot * 8);  // qflag, visits, FHCM flags, request times
     // ring of the round-free schedule: a power of two >= 16 times the job's
     // cells (a launch rarely pushes more, so pushes seldom wait for a slot)
     // and the warps of a launch, behind its three counters
@@ -263,6 +263,7 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     int* qflag_all = (int*)(zero_dev + z_ctl);
     int* visits_all = (int*)(zero_dev + z_ctl + a256(Jtot * 4));
     int* dflags_all = (int*)(zero_dev + z_ctl + 2 * a256(Jtot * 4));
+    unsigned long long* req_all = (unsigned long long*)(zero_dev + z_ctl + 3 * a256(Jtot * 4));
     unsigned long long* cval_all = (unsigned long long*)cval_dev;
 
     bool ok = true;
@@ -349,6 +350,8 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     j.sm_cap = 0;
     j.one_pass = fp32 && P.one_pass;
     j.fhcm = descs[0].method == EIK_METHOD_FHCM;
+    j.hold_ns = P.hold_ns;
+    j.req_time = req_all;
     j.async_first = P.async_first;
     j.async_main = P.async_main;
     j.qctl = (unsigned*)ring_dev;

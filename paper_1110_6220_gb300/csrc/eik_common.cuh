@@ -107,6 +107,11 @@ struct SolveParams {
     long long deadline_ns;        // relative to kernel start
     int profile;                  // accumulate gctl->prof
     int fhcm;                     // Fast Heap-Cell Method: one sweep per flagged direction
+    // round-free schedule: a taken cell waits until hold_ns after its latest
+    // request before it runs, so that requests from several upstream
+    // neighbours merge into one visit (req_time: request times, per cell)
+    unsigned hold_ns;
+    unsigned long long* req_time;
     // asynchronous scheduling only: ring of (sequence << 32 | global cell)
     // words, ring_mask + 1 (a power of two) >= twice the job's cells and the
     // launch's warps; the global

@@ -198,6 +198,8 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
     p.deadline_ns = j.deadline_ns > 0 ? j.deadline_ns : 20000000000ll;
     p.profile = profiling();
     p.fhcm = j.fhcm ? 1 : 0;
+    p.hold_ns = j.hold_ns;
+    p.req_time = j.req_time;
     p.ring = j.ring;
     p.ring_mask = j.ring_mask;
     p.cell_pre = j.cell_pre;

@@ -60,6 +60,8 @@ struct JobDev {
     bool async_first, async_main;  // round-free schedule (k_solve_async) for the FP32 / main pass
     bool one_pass;              // fp32: no FP32 pass; the double-float pass solves from the sources
     bool fhcm;                  // Fast Heap-Cell Method (one sweep per flagged direction)
+    unsigned hold_ns;           // round-free: minimum age of a request before its cell runs
+    unsigned long long* req_time;  // request times per cell (job-wide index), %globaltimer ns
     unsigned long long* ring;   // async: ring of ring_mask + 1 words
     unsigned ring_mask;
     unsigned* qctl;             // async: head, tail, pending (384 bytes before the ring)

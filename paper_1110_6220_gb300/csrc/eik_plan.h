@@ -33,6 +33,7 @@ struct JobParams {
     double w_first, w_main;
     bool async_first = false, async_main = false;  // round-free schedule per pass (k >= 8)
     bool one_pass = false;  // FP32_REFINE as one double-float pass from the sources
+    unsigned hold_ns = 0;   // round-free: minimum age of a request before its cell runs
 };
 
 bool desc_valid(const eik_plan_desc* d);

@@ -1293,6 +1293,14 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
         if (lane == 0) e = ring_pop(p, gctl, deadline);
         e = __shfl_sync(FULL, e, 0);
         if (e < 0) break;
+        if (p.hold_ns && lane == 0) {
+            // hold the cell until hold_ns after its latest request (0: none
+            // recorded, no hold); the wait ends by that time whatever else
+            const unsigned long long until = __ldcg(&p.req_time[e]) + p.hold_ns;
+            for (unsigned long long now = gtimer(); now < until && until - now <= p.hold_ns; now = gtimer())
+                __nanosleep(100);
+        }
+        __syncwarp();
         const int ii = find_inst(p.cell_pre, NI, e);
         const InstDesc& d = inst[ii];
         const int c = e - d.cell_base;
@@ -1313,6 +1321,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
             w, inst, gctl, deadline, c, ii, first, cg, ig, prof_on, pacc, pt,
             [&](const InstDesc& dn, int nc, unsigned long long, unsigned long long, bool activate) {
                 if (activate && (atomicOr(&dn.qflag[nc], 1) & 3) == 0) {
+                    if (p.hold_ns) p.req_time[dn.cell_base + nc] = gtimer();
                     atomicAdd(&p.qctl[Q_PENDING], 1u);
                     ring_push(p, gctl, (unsigned)(dn.cell_base + nc), deadline);
                 }

@@ -71,7 +71,7 @@ class eik_tune_result(ctypes.Structure):
     _fields_ = [("cell_k", ctypes.c_int32), ("bucket_first", ctypes.c_double),
                 ("bucket_main", ctypes.c_double), ("async_first", ctypes.c_int32),
                 ("async_main", ctypes.c_int32), ("one_pass", ctypes.c_int32),
-                ("ms", ctypes.c_double),
+                ("hold_ns", ctypes.c_int32), ("ms", ctypes.c_double),
                 ("ms_before", ctypes.c_double), ("trials", ctypes.c_int32)]
 
 

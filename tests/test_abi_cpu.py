@@ -73,7 +73,7 @@ def test_tune_table_round_trip_and_use_without_gpu(tmp_path):
     assert w_auto == w8 and w32 != w8  # built-in: k = 8 for one FP64 grid
     f = tmp_path / "tune.txt"
     # class: FP64, single grid, side 2^10
-    f.write_text("eik-tune 3\n0 0 10 32 8 8 0 1 0 1.5\n")
+    f.write_text("eik-tune 4\n0 0 10 32 8 8 0 1 0 0 1.5\n")
     assert eik.eik_tune_load(str(f)) == 0
     assert eik.eik_plan_workspace_bytes(d0) == w32
     # another side class keeps the built-in choice
@@ -82,10 +82,10 @@ def test_tune_table_round_trip_and_use_without_gpu(tmp_path):
     g = tmp_path / "out.txt"
     assert eik.eik_tune_save(str(g)) == 0
     lines = g.read_text().splitlines()
-    assert lines[0] == "eik-tune 3"
-    assert [float(x) for x in lines[1].split()] == [0, 0, 10, 32, 8, 8, 0, 1, 0, 1.5]
+    assert lines[0] == "eik-tune 4"
+    assert [float(x) for x in lines[1].split()] == [0, 0, 10, 32, 8, 8, 0, 1, 0, 0, 1.5]
     bad = tmp_path / "bad.txt"
-    bad.write_text("eik-tune 3\n1 0 10 12 8 8 0 0 0 1.0\n")  # k = 12 is not a cell size
+    bad.write_text("eik-tune 4\n1 0 10 12 8 8 0 0 0 0 1.0\n")  # k = 12 is not a cell size
     assert eik.eik_tune_load(str(bad)) == eik.EIK_EINVAL
     bad.write_text("something else\n")
     assert eik.eik_tune_load(str(bad)) == eik.EIK_EINVAL

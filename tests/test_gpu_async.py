@@ -34,7 +34,7 @@ def _side_class(sizes):
 def _force(eik, tmp_path, rows):
     """rows: (precision, batch, side class, k, async_first, async_main, one_pass)."""
     f = tmp_path / "sched.txt"
-    lines = ["eik-tune 3"] + [f"{p} {b} {s} {k} 4 4 {a1} {a2} {op} 1.0" for p, b, s, k, a1, a2, op in rows]
+    lines = ["eik-tune 4"] + [f"{p} {b} {s} {k} 4 4 {a1} {a2} {op} 0 1.0" for p, b, s, k, a1, a2, op in rows]
     f.write_text("\n".join(lines) + "\n")
     eik.eik_tune_reset()
     assert eik.eik_tune_load(str(f)) == 0

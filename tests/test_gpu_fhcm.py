@@ -32,7 +32,7 @@ def eik():
 def _force(eik, tmp_path, I, k, async_main):
     cls = int(round(0.5 * math.log2(I.nx * I.ny)))
     f = tmp_path / "sched.txt"
-    f.write_text(f"eik-tune 3\n0 0 {cls} {k} 256 256 0 {async_main} 0 1.0\n")
+    f.write_text(f"eik-tune 4\n0 0 {cls} {k} 256 256 0 {async_main} 0 0 1.0\n")
     eik.eik_tune_reset()
     assert eik.eik_tune_load(str(f)) == 0
 
