@@ -137,22 +137,6 @@ __global__ void k_init_grid(const AuxInst* A, const int* blk_full, int n) {
     if (bad) atomicCAS(&p.ctl->status, 0, EIK_EINVAL);
 }
 
-__global__ void k_fill(double* a, size_t n, double v) {
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
-         e += (size_t)gridDim.x * blockDim.x)
-        a[e] = v;
-}
-__global__ void k_fill32(float* a, size_t n, float v) {
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
-         e += (size_t)gridDim.x * blockDim.x)
-        a[e] = v;
-}
-__global__ void k_fill_df(float2* a, size_t n) {
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
-         e += (size_t)gridDim.x * blockDim.x)
-        a[e] = make_float2(inf_of<float>(), 0.0f);
-}
-
 // Sources: U = q (shifted) and f = -1 (fixed node); source cells get the cell
 // value max q (Sec. 4.2, HCM item 1) and start queued.
 __global__ void k_init_sources(const AuxInst* A, const SourceTable s) {
@@ -357,19 +341,6 @@ __global__ void k_output(const AuxInst* A, const int* blk_pre, int n) {
 }
 
 }  // namespace
-
-cudaError_t launch_fill(double* a, size_t n, double v, cudaStream_t st) {
-    k_fill<<<1024, 256, 0, st>>>(a, n, v);
-    return cudaGetLastError();
-}
-cudaError_t launch_fill32(float* a, size_t n, float v, cudaStream_t st) {
-    k_fill32<<<1024, 256, 0, st>>>(a, n, v);
-    return cudaGetLastError();
-}
-cudaError_t launch_fill_df(float2* a, size_t n, cudaStream_t st) {
-    k_fill_df<<<1024, 256, 0, st>>>(a, n);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_ctl_init(Ctl* ctl, int count, cudaStream_t st) {
     k_ctl_init<<<(count + 255) / 256, 256, 0, st>>>(ctl, count);

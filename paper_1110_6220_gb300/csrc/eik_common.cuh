@@ -45,7 +45,6 @@ struct Ctl {
     unsigned int bar_gen;         // grid barrier generation
     int cnt[3];                   // near-list lengths
     int fcnt[2];                  // far-list lengths
-    int cursor[2];                // work cursor of the current round (by parity)
     int status;                   // EIK_* of this launch
     int abort;                    // set on any error: every block stops
     unsigned long long fmin[2];   // min key over a far list (per split parity)
@@ -191,9 +190,6 @@ struct SourceTable {
     const int* cell; const unsigned long long* cell_key; const int* cell_inst; int ncell;
 };
 
-cudaError_t launch_fill(double* a, size_t n, double v, cudaStream_t st);
-cudaError_t launch_fill32(float* a, size_t n, float v, cudaStream_t st);
-cudaError_t launch_fill_df(float2* a, size_t n, cudaStream_t st);  // (+inf, 0)
 cudaError_t launch_ctl_init(Ctl* ctl, int count, cudaStream_t st);  // count control blocks
 // A block prefix pre[0..n] is followed in memory by its owner table
 // (pre[n + 1 + b] = instance of block b), filled on the device by this:

@@ -328,7 +328,6 @@ struct TileCfg {
     static constexpr int LPC = 4 * LPD;              // lanes per cell
     static constexpr int CPW = 32 / LPC;             // cells per warp (lock-step)
     static constexpr int RPL = K / LPD;              // rows per lane
-    static constexpr int BPL = (K + LPC - 1) / LPC;  // boundary nodes per lane and side
     // U box: k+2 rows; k+2 wide for 8-byte values, k+4 for floats (a row of
     // a TMA box must be a multiple of 16 bytes)
     static constexpr int BW = ES == 8 ? K + 2 : K + 4;
@@ -440,23 +439,6 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 __device__ __forceinline__ void fail(Ctl* ctl, int code, unsigned long long info) {
     if (atomicCAS(&ctl->status, 0, code) == 0) ctl->err_info = info;
     atomicExch(&ctl->abort, 1);
-}
-
-// warp-aggregated append of `val` (where pred) to a list of capacity cap
-__device__ __forceinline__ void warp_push(int* list, int* count, bool pred, int val, int cap,
-                                          Ctl* ctl) {
-    const unsigned m = __ballot_sync(0xffffffffu, pred);
-    if (!m) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(count, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (pred) {
-        const int pos = base + __popc(m & ((1u << lane) - 1u));
-        if (pos < cap) list[pos] = val;
-        else fail(ctl, EIK_ECUDA, 0x1000000ull + (unsigned)pos);
-    }
 }
 
 __device__ __forceinline__ void lane_push(int* list, int* count, int val, int cap, Ctl* ctl) {

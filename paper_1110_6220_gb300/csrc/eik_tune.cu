@@ -75,14 +75,19 @@ int side_class(const eik_plan_desc* d, int n) {
 //    requests of several upstream neighbours then merge into one visit
 //    (21 visits per cell instead of 39, 23.7 ms instead of 33.8 ms); on
 //    1025^2 and on the batch the hold saved nothing or cost time.
+//  - the tuner (eik_tune) on each class then moved three choices: FP64
+//    batches run round-free at k = 8 (46.2 ms instead of 75.8 ms on the
+//    512-grid mix), small FP64 grids too (129^2: 0.32 ms instead of 0.37
+//    ms), and ~2048^2 grids hold for 4 us (2049^2 maze: 6.3 ms for 6.8 ms).
 Entry builtin(int prec, bool batch, int side) {
     if (prec == EIK_FP32_REFINE) {
         Entry e{batch ? 16 : 8, 256.0, 16.0, 0.0, false, true};
         e.one_pass = true;
-        if (!batch && side >= 12) e.hold_ns = 8000;
+        if (!batch) e.hold_ns = side >= 12 ? 8000 : side == 11 ? 4000 : 0;
         return e;
     }
-    return batch ? Entry{16, 4.0, 4.0, 0.0} : Entry{8, 256.0, 256.0, 0.0};
+    if (batch || side <= 8) return Entry{8, 4.0, 4.0, 0.0, false, true};
+    return Entry{8, 256.0, 256.0, 0.0};
 }
 
 int load_file(const char* path) {
