@@ -11,6 +11,8 @@
 // device.  Finished jobs are detected with events (no blocking), their
 // results copied out and their tickets completed.
 #include <algorithm>
+#include <cmath>
+#include <cstdlib>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -125,11 +127,20 @@ bool launch_slot(eik_server_s* s, Slot& sl, size_t held_by_others) {
     const Request* head = s->waiting.front();
     const int kreq = head->d.cell_k;  // 0: chosen for the job
     const int prec = head->d.precision;
+    // a job lasts about as long as its largest grid: a request joins the
+    // head's job unless its grid is more than a size class larger than the
+    // head's, so that a small head is not held behind large grids while a
+    // large head still takes the small requests along
+    auto size_class = [](const eik_plan_desc& d) {
+        return (int)std::lround(0.5 * std::log2((double)d.nx * d.ny));
+    };
+    const int scls = size_class(head->d);
     size_t bytes = 0;
     sl.reqs.clear();
     for (auto it = s->waiting.begin(); it != s->waiting.end() && (int)sl.reqs.size() < MAX_BATCH;) {
         Request* r = *it;
-        if (r->d.cell_k == kreq && r->d.precision == prec && r->d.method == head->d.method) {
+        if (r->d.cell_k == kreq && r->d.precision == prec && r->d.method == head->d.method &&
+            size_class(r->d) <= scls + 1) {
             if (held_by_others + bytes + r->bytes > s->budget) break;  // keep FIFO order
             bytes += r->bytes;
             sl.reqs.push_back(r);
