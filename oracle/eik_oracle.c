@@ -167,11 +167,15 @@ typedef struct {
     int32_t *pos;  /* pos[node] = index in heap, -1 if absent */
     int32_t size;
     const double *V;
+    int by_index;  /* equal values: smaller node id first (else any order) */
 } heap;
 
 static inline int heap_less(const heap *H, int a, int b)
 {
-    return H->V[H->node[a]] < H->V[H->node[b]];
+    const double va = H->V[H->node[a]], vb = H->V[H->node[b]];
+    if (H->by_index && va == vb)
+        return H->node[a] < H->node[b];
+    return va < vb;
 }
 
 static inline void heap_swap(heap *H, int a, int b)
@@ -253,13 +257,27 @@ static void fmm_touch(const problem *p, double *V, unsigned char *label, heap *H
     }
 }
 
-int orc_fmm(int nx, int ny, double h, const double *F, int nsrc, const int32_t *si,
-            const int32_t *sj, const double *sq, double *U, int64_t *n_accepted)
+/* Source order of the acceptance record: smaller q first, then node id. */
+static const problem *g_src_problem;
+static int src_cmp(const void *a, const void *b)
 {
-    problem p;
-    int rc = problem_init(&p, nx, ny, h, F, nsrc, si, sj, sq);
-    if (rc)
-        return rc;
+    const int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    const double qx = g_src_problem->q[x], qy = g_src_problem->q[y];
+    if (qx != qy)
+        return qx < qy ? -1 : 1;
+    return x < y ? -1 : x > y;
+}
+
+/*
+ * Alg. FMM on problem p.  order (may be null): the nodes in the order they
+ * become Accepted -- the exit set first (it is Accepted in the
+ * initialisation; listed by q, then id), then each node as the main loop
+ * removes it from the heap.  by_index: equal values leave the heap in node
+ * order.  Returns the number of Accepted nodes, or a negative error code.
+ */
+static int64_t fmm_run(const problem *p, double *U, int32_t *order, int by_index)
+{
+    const int nx = p->nx, ny = p->ny;
     size_t m = (size_t)nx * ny;
     unsigned char *label = (unsigned char *)calloc(m, 1);
     heap H;
@@ -267,44 +285,71 @@ int orc_fmm(int nx, int ny, double h, const double *F, int nsrc, const int32_t *
     H.pos = (int32_t *)malloc(m * sizeof(int32_t));
     H.size = 0;
     H.V = U;
+    H.by_index = by_index;
     if (!label || !H.node || !H.pos) {
-        free(label); free(H.node); free(H.pos); problem_free(&p);
+        free(label); free(H.node); free(H.pos);
         return ORC_ENOMEM;
     }
     for (size_t k = 0; k < m; ++k)
         H.pos[k] = -1;
     /* Initialisation: Q is Accepted with V = q, everything else Far, +inf. */
-    init_values(&p, U);
+    init_values(p, U);
+    int64_t acc = 0;
     for (size_t k = 0; k < m; ++k)
-        if (p.src[k])
+        if (p->src[k]) {
             label[k] = ACCEPTED;
+            if (order)
+                order[acc] = (int32_t)k;
+            ++acc;
+        }
+    if (order && acc > 1) {
+        g_src_problem = p;
+        qsort(order, (size_t)acc, sizeof(int32_t), src_cmp);
+    }
     /* Far neighbours of Accepted nodes become Considered. */
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i)
-            if (p.src[(size_t)j * nx + i]) {
-                fmm_touch(&p, U, label, &H, i + 1, j);
-                fmm_touch(&p, U, label, &H, i - 1, j);
-                fmm_touch(&p, U, label, &H, i, j + 1);
-                fmm_touch(&p, U, label, &H, i, j - 1);
+            if (p->src[(size_t)j * nx + i]) {
+                fmm_touch(p, U, label, &H, i + 1, j);
+                fmm_touch(p, U, label, &H, i - 1, j);
+                fmm_touch(p, U, label, &H, i, j + 1);
+                fmm_touch(p, U, label, &H, i, j - 1);
             }
-    int64_t acc = 0;
     /* Main loop: accept the smallest Considered node, update its neighbours. */
     while (H.size > 0) {
         int32_t k = heap_pop(&H);
         label[k] = ACCEPTED;
+        if (order)
+            order[acc] = k;
         ++acc;
         int i = k % nx, j = k / nx;
-        fmm_touch(&p, U, label, &H, i + 1, j);
-        fmm_touch(&p, U, label, &H, i - 1, j);
-        fmm_touch(&p, U, label, &H, i, j + 1);
-        fmm_touch(&p, U, label, &H, i, j - 1);
+        fmm_touch(p, U, label, &H, i + 1, j);
+        fmm_touch(p, U, label, &H, i - 1, j);
+        fmm_touch(p, U, label, &H, i, j + 1);
+        fmm_touch(p, U, label, &H, i, j - 1);
     }
-    if (n_accepted)
-        *n_accepted = acc;
     free(label);
     free(H.node);
     free(H.pos);
+    return acc;
+}
+
+int orc_fmm(int nx, int ny, double h, const double *F, int nsrc, const int32_t *si,
+            const int32_t *sj, const double *sq, double *U, int64_t *n_accepted)
+{
+    problem p;
+    int rc = problem_init(&p, nx, ny, h, F, nsrc, si, sj, sq);
+    if (rc)
+        return rc;
+    int64_t acc = fmm_run(&p, U, NULL, 0);
+    int64_t nq = 0; /* the exit set, Accepted before the main loop */
+    for (size_t k = 0; k < (size_t)nx * ny; ++k)
+        nq += p.src[k];
     problem_free(&p);
+    if (acc < 0)
+        return (int)acc;
+    if (n_accepted)
+        *n_accepted = acc - nq; /* removals from the heap */
     return ORC_OK;
 }
 
@@ -656,4 +701,169 @@ int orc_cells(int nx, int ny, double h, const double *F, int nsrc, const int32_t
     free(cval); free(flags); free(removed); free(hcell); free(hpos); free(old);
     problem_free(&p);
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Fast Marching-Sweeping Method, Sec. 4.1 (Alg. FMSM, Remark          */
+/* sweeping_in_FMSM, Fig. coarse_sweep_choice), serially.              */
+/*   Part I: Alg. FMM on the coarse grid X^c of cell centres: spacing  */
+/*   k h, speed F at the centre (the mean of the one, two or four nodes */
+/*   nearest to it, clamped to the grid), and as its exit set           */
+/*   Q^c the cells that hold sources, each with the smallest q among    */
+/*   them.  The acceptance order is the permutation P: Q^c first (by q, */
+/*   then index), then the heap's removals, equal values by index; the  */
+/*   cells Fast Marching never accepts (infinite coarse value) follow   */
+/*   by index.                                                           */
+/*   Part II: every cell once, in the order P, on its domain c with the */
+/*   current values of N^f(c) as boundary data.  A cell of Q^c is swept */
+/*   by Alg. FSM unchanged: the directions of Alg. FSM_order in turn,    */
+/*   the full local update, until a sweep changes nothing.  Any other    */
+/*   cell gets at most four sweeps, each with the sweep-directional      */
+/*   update (the quadrant of the two neighbours behind the sweep): the   */
+/*   directions both of whose sides border cells accepted before it, or */
+/*   -- when no direction has both -- every direction with one such      */
+/*   side, taken in Alg. FSM_order's order.  Directions are numbered as  */
+/*   in Alg. FSM_order: 0 (i up, j up: from the SW corner, behind it W   */
+/*   and S), 1 (i up, j down: NW; W, N), 2 (i down, j down: NE; E, N),   */
+/*   3 (i down, j up: SE; E, S).                                          */
+/* ------------------------------------------------------------------ */
+
+/* one sweep of the cell's nodes in direction dir with the sweep-directional update */
+static int sweep_cell_directional(const problem *p, double *V, int i0, int i1, int j0, int j1, int dir)
+{
+    const int i_up = (dir == 0 || dir == 1), j_up = (dir == 0 || dir == 3);
+    const int nx = p->nx, ny = p->ny;
+    int changed = 0;
+    for (int ii = i0; ii < i1; ++ii) {
+        int i = i_up ? ii : i1 - 1 - (ii - i0);
+        for (int jj = j0; jj < j1; ++jj) {
+            int j = j_up ? jj : j1 - 1 - (jj - j0);
+            size_t k = (size_t)j * nx + i;
+            if (p->src[k]) continue;
+            double ux = nb(V, nx, ny, i_up ? i - 1 : i + 1, j);
+            double uy = nb(V, nx, ny, i, j_up ? j - 1 : j + 1);
+            double t = quadrant_update(ux, uy, p->f[k]);
+            if (t < V[k]) {
+                V[k] = t;
+                changed = 1;
+            }
+        }
+    }
+    return changed;
+}
+
+/*
+ * Uc (may be null): the coarse values, cyn x cxn.  order (may be null): the
+ * cells in processing order.  dirs_out (may be null): per cell, the sweep
+ * directions taken (bit d: direction d), or 16 for a cell swept by Alg. FSM.
+ * stats: [0] cells processed, [1] sweeps, [2] coarse nodes Accepted by Fast
+ * Marching (the exit set included).
+ */
+int orc_fmsm(int nx, int ny, double h, const double *F, int nsrc, const int32_t *si, const int32_t *sj,
+             const double *sq, int k, double *U, double *Uc, int32_t *order, int32_t *dirs_out,
+             int64_t *stats)
+{
+    if (k < 1) return ORC_EINVAL;
+    problem p;
+    int rc = problem_init(&p, nx, ny, h, F, nsrc, si, sj, sq);
+    if (rc) return rc;
+    const int cxn = (nx + k - 1) / k, cyn = (ny + k - 1) / k, J = cxn * cyn;
+    double *Fc = (double *)malloc((size_t)J * sizeof(double));
+    double *Vc = (double *)malloc((size_t)J * sizeof(double));
+    int32_t *ord = (int32_t *)malloc((size_t)J * sizeof(int32_t));
+    int32_t *rank = (int32_t *)malloc((size_t)J * sizeof(int32_t));
+    int32_t *csi = (int32_t *)malloc((size_t)(nsrc > 0 ? nsrc : 1) * sizeof(int32_t));
+    int32_t *csj = (int32_t *)malloc((size_t)(nsrc > 0 ? nsrc : 1) * sizeof(int32_t));
+    double *csq = (double *)malloc((size_t)(nsrc > 0 ? nsrc : 1) * sizeof(double));
+    problem pc;
+    memset(&pc, 0, sizeof(pc));
+    if (!Fc || !Vc || !ord || !rank || !csi || !csj || !csq) {
+        rc = ORC_ENOMEM;
+        goto done;
+    }
+    /* ---- Part I: the coarse grid and its Fast Marching */
+    for (int cy = 0; cy < cyn; ++cy)
+        for (int cx = 0; cx < cxn; ++cx) {
+            /* F at the centre, as the mean of the nodes nearest to it (one,
+             * two or four of them; exact for a bilinear F) */
+            int i0 = cx * k + (k - 1) / 2, i1 = cx * k + k / 2;
+            int j0 = cy * k + (k - 1) / 2, j1 = cy * k + k / 2;
+            if (i0 > nx - 1) i0 = nx - 1;
+            if (i1 > nx - 1) i1 = nx - 1;
+            if (j0 > ny - 1) j0 = ny - 1;
+            if (j1 > ny - 1) j1 = ny - 1;
+            const double a = F[(size_t)j0 * nx + i0], b = F[(size_t)j0 * nx + i1];
+            const double c = F[(size_t)j1 * nx + i0], d = F[(size_t)j1 * nx + i1];
+            Fc[cy * cxn + cx] = 0.25 * (((a + b) + c) + d);
+        }
+    for (int s = 0; s < nsrc; ++s) { /* problem_init keeps the smallest q per coarse node */
+        csi[s] = si[s] / k;
+        csj[s] = sj[s] / k;
+        csq[s] = sq[s];
+    }
+    rc = problem_init(&pc, cxn, cyn, (double)k * h, Fc, nsrc, csi, csj, csq);
+    if (rc) { /* problem_init has freed its arrays already */
+        memset(&pc, 0, sizeof(pc));
+        goto done;
+    }
+    {
+        int64_t acc = fmm_run(&pc, Vc, ord, 1);
+        if (acc < 0) {
+            rc = (int)acc;
+            goto done;
+        }
+        for (int c = 0; c < J; ++c) rank[c] = -1;
+        for (int64_t e = 0; e < acc; ++e) rank[ord[e]] = (int32_t)e;
+        int64_t e = acc;
+        for (int c = 0; c < J; ++c)
+            if (rank[c] < 0) {
+                ord[e] = c;
+                rank[c] = (int32_t)e++;
+            }
+        if (stats) stats[2] = acc;
+    }
+    /* ---- Part II: the cells in order */
+    init_values(&p, U);
+    int64_t sweeps = 0;
+    for (int e = 0; e < J; ++e) {
+        const int c = ord[e];
+        const int cx = c % cxn, cy = c / cxn;
+        const int i0 = cx * k, i1 = i0 + k < nx ? i0 + k : nx, j0 = cy * k, j1 = j0 + k < ny ? j0 + k : ny;
+        if (pc.src[c]) {
+            /* Alg. FSM on the cell: sweep until a sweep changes nothing */
+            for (int s = 0;; ++s) {
+                ++sweeps;
+                if (!sweep_cell(&p, U, i0, i1, j0, j1, s % 4)) break;
+            }
+            if (dirs_out) dirs_out[c] = 16;
+            continue;
+        }
+        /* sides W, E, S, N bordering a cell accepted before this one */
+        const int w = cx > 0 && rank[c - 1] < e, ea = cx + 1 < cxn && rank[c + 1] < e;
+        const int so = cy > 0 && rank[c - cxn] < e, no = cy + 1 < cyn && rank[c + cxn] < e;
+        const int xs[4] = {w, w, ea, ea}, ys[4] = {so, no, no, so};
+        int dirs = 0;
+        for (int d = 0; d < 4; ++d)
+            if (xs[d] && ys[d]) dirs |= 1 << d;
+        if (!dirs)
+            for (int d = 0; d < 4; ++d)
+                if (xs[d] || ys[d]) dirs |= 1 << d;
+        for (int d = 0; d < 4; ++d)
+            if (dirs >> d & 1) {
+                sweep_cell_directional(&p, U, i0, i1, j0, j1, d);
+                ++sweeps;
+            }
+        if (dirs_out) dirs_out[c] = dirs;
+    }
+    if (stats) {
+        stats[0] = J;
+        stats[1] = sweeps;
+    }
+    if (Uc) memcpy(Uc, Vc, (size_t)J * sizeof(double));
+    if (order) memcpy(order, ord, (size_t)J * sizeof(int32_t));
+done:
+    free(Fc); free(Vc); free(ord); free(rank); free(csi); free(csj); free(csq);
+    problem_free(&pc);
+    problem_free(&p);
+    return rc;
 }

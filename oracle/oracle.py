@@ -6,6 +6,8 @@ Functions follow the paper (Chacon & Vladimirsky, "Fast two-scale methods for
 Eikonal equations"):
   * ``fmm``      -- Alg. FMM (Sec. 3.1), binary heap;
   * ``fsm``      -- Algs. FSM_order / FSM (Sec. 3.2), Gauss-Seidel in 4 directions;
+  * ``cells``    -- the Heap-Cell Methods HCM / FHCM (Secs. 4.2, 4.3);
+  * ``fmsm``     -- the Fast Marching-Sweeping Method (Sec. 4.1, Alg. FMSM);
   * ``jacobi``   -- value iteration from +inf (eq. generic_value_it) on eq. Eik_discr;
   * ``apply_T``  -- one application of the local update operator of eq. Eik_discr;
   * ``node_update`` -- the local update at one node (eqs. one_sided_update,
@@ -96,7 +98,8 @@ class Oracle:
         lib.orc_node_update.argtypes = [d, d, d, d, d]
         lib.orc_node_update.restype = d
         lib.orc_cells.argtypes = common + [ctypes.c_int, ctypes.c_int, P(d), P(i64)]
-        for fn in (lib.orc_fmm, lib.orc_fsm, lib.orc_jacobi, lib.orc_apply_T, lib.orc_cells):
+        lib.orc_fmsm.argtypes = common + [ctypes.c_int, P(d), P(d), P(i32), P(i32), P(i64)]
+        for fn in (lib.orc_fmm, lib.orc_fsm, lib.orc_jacobi, lib.orc_apply_T, lib.orc_cells, lib.orc_fmsm):
             fn.restype = ctypes.c_int
         self.lib = lib
         self.path = lib_path
@@ -148,6 +151,27 @@ class Oracle:
         return U, {"removals": int(st[0]), "sweeps": int(st[1]), "avhr": st[0] / J, "avs": st[1] / J,
                    "mon_pct": 100.0 * st[2] / st[3] if st[3] else 100.0}
 
+    def fmsm(self, F, h, si, sj, sq, k):
+        """Fast Marching-Sweeping Method (Sec. 4.1, Alg. FMSM) on k x k cells
+        (inexact).  Returns U and {'avs', 'sweeps', 'cells', 'accepted',
+        'order' (cell indices in processing order), 'Uc' (coarse values,
+        (cyn, cxn)), 'dirs' (per cell the sweep directions, bit d for
+        direction d of Alg. FSM_order, 16 for a cell swept by Alg. FSM)}."""
+        keep, args, shape = _args(F, h, si, sj, sq)
+        ny, nx = shape
+        cxn, cyn = (nx + k - 1) // k, (ny + k - 1) // k
+        U = np.empty(shape, dtype=np.float64)
+        Uc = np.empty((cyn, cxn), dtype=np.float64)
+        order = np.empty(cxn * cyn, dtype=np.int32)
+        dirs = np.zeros((cyn, cxn), dtype=np.int32)
+        st = np.zeros(3, dtype=np.int64)
+        _check(self.lib.orc_fmsm(*args, int(k), _ptr(U, ctypes.c_double), _ptr(Uc, ctypes.c_double),
+                                 _ptr(order, ctypes.c_int32), _ptr(dirs, ctypes.c_int32),
+                                 _ptr(st, ctypes.c_int64)), "fmsm")
+        del keep
+        return U, {"cells": int(st[0]), "sweeps": int(st[1]), "avs": st[1] / max(int(st[0]), 1),
+                   "accepted": int(st[2]), "order": order, "Uc": Uc, "dirs": dirs}
+
     def jacobi(self, F, h, si, sj, sq, max_iters=1_000_000, return_iters=False):
         """Jacobi value iteration from +inf; only sensible on tiny grids."""
         keep, args, shape = _args(F, h, si, sj, sq)
@@ -190,6 +214,10 @@ def fmm(*a, **k):
 
 def fsm(*a, **k):
     return default().fsm(*a, **k)
+
+
+def fmsm(*a, **k):
+    return default().fmsm(*a, **k)
 
 
 def jacobi(*a, **k):

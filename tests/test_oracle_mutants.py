@@ -116,3 +116,46 @@ def test_cell_table_pin_catches_planted_mistake(name):
     assert src.count(old) == 1, f"mutation site for {name} not unique"
     mutant = oracle.Oracle.from_source(src.replace(old, new))
     assert _caught_by(mutant, [pins.test_cell_methods_reproduce_tab_sinu_1]), name
+
+
+# ---------------------------------------------------------------- FMSM
+FMSM_MUTANTS = {
+    # sweep-directional update from the neighbours ahead of the sweep
+    "fmsm_front_neighbour": ("double ux = nb(V, nx, ny, i_up ? i - 1 : i + 1, j);",
+                             "double ux = nb(V, nx, ny, i_up ? i + 1 : i - 1, j);"),
+    # a direction whenever one of its sides was accepted before
+    "fmsm_either_side": ("            if (xs[d] && ys[d]) dirs |= 1 << d;",
+                         "            if (xs[d] || ys[d]) dirs |= 1 << d;"),
+    # exit-set cells treated like the others (no Alg. FSM)
+    "fmsm_exit_cells_not_swept": ("        if (pc.src[c]) {\n            /* Alg. FSM on the cell",
+                                  "        if (0 && pc.src[c]) {\n            /* Alg. FSM on the cell"),
+    # earlier and later neighbours swapped
+    "fmsm_later_as_earlier": ("const int w = cx > 0 && rank[c - 1] < e,",
+                              "const int w = cx > 0 && rank[c - 1] > e,"),
+    # the coarse speed from the node k/2 into the cell, not the centre
+    "fmsm_coarse_speed_corner": ("Fc[cy * cxn + cx] = 0.25 * (((a + b) + c) + d);",
+                                 "Fc[cy * cxn + cx] = d;"),
+}
+FMSM_PINS = [pins.test_fmsm_checkerboard_acceptance_order, pins.test_fmsm_one_node_cells_are_fast_marching,
+             pins.test_fmsm_is_an_upper_bound, pins.test_fmsm_reproduces_tab_const]
+# caught only by the paper's sin20 table (slow)
+FMSM_MUTANTS_TABLE = {"fmsm_coarse_speed_corner"}
+
+
+@pytest.mark.parametrize("name", sorted(set(FMSM_MUTANTS) - FMSM_MUTANTS_TABLE))
+def test_fmsm_pins_catch_planted_mistake(name):
+    old, new = FMSM_MUTANTS[name]
+    src = _source()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    mutant = oracle.Oracle.from_source(src.replace(old, new))
+    assert _caught_by(mutant, FMSM_PINS), name
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(FMSM_MUTANTS_TABLE))
+def test_fmsm_table_pin_catches_planted_mistake(name):
+    old, new = FMSM_MUTANTS[name]
+    src = _source()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    mutant = oracle.Oracle.from_source(src.replace(old, new))
+    assert _caught_by(mutant, [pins.test_fmsm_reproduces_tab_sinu_1]), name

@@ -362,3 +362,123 @@ def test_cell_methods_reproduce_tab_sinu_1(orc):
         rmax = E.max() / e.max()
         assert abs(rho / row["rho"] - 1) < 0.05, (row, rho)
         assert abs(rmax / row["Rmax"] - 1) < 0.01, (row, rmax)
+
+
+# ---------------------------------------------------------------- FMSM (Sec. 4.1)
+
+
+def _fmsm_gold():
+    with open(os.path.join(GOLD, "paper_fmsm.json")) as fh:
+        return json.load(fh)
+
+
+# sweep directions as numbered in Alg. FSM_order, by the corner they start from
+_DIR_BIT = {"SW": 1, "NW": 2, "NE": 4, "SE": 8}
+
+
+def test_fmsm_checkerboard_acceptance_order(orc):
+    """Fig. checkers_FMSM: Part I of FMSM (Fast Marching on the coarse grid)
+    accepts the 25 cells of a 5 x 5 checkerboard in the printed order, and
+    the text after it gives the sweeps of cells #1 (NW and SW) and #14 (NE
+    only).  With one-node cells the oracle's coarse grid is that board.  The
+    printed order must be one that Fast Marching can take: the coarse values
+    are non-decreasing along it, equal within the groups the printed order
+    leaves free (the four edge neighbours, the four diagonals, ...) and rise
+    between them; and the two cells get the printed directions."""
+    g = _fmsm_gold()["checkers"]
+    order = np.array(g["order"])  # [j][i]
+    F = np.array([[1.0 if (i + j) % 2 == 0 else 2.0 for i in range(5)] for j in range(5)])
+    _, st = orc.fmsm(F, 1.0, [2], [2], [0.0], 1)
+    Uc = st["Uc"]
+    seq = np.array([Uc[np.argwhere(order == m)[0][0], np.argwhere(order == m)[0][1]] for m in range(25)])
+    groups = [(0, 0), (1, 4), (5, 8), (9, 12), (13, 20), (21, 24)]
+    for a, b in groups:
+        assert np.ptp(seq[a:b + 1]) <= 1e-12, (a, b, seq[a:b + 1])
+    for (_, b), (a2, _) in zip(groups, groups[1:]):
+        assert seq[b] < seq[a2] - 1e-9, (b, a2)
+    assert np.isfinite(seq).all()
+    for num, names in g["directions"].items():
+        j, i = np.argwhere(order == int(num))[0]
+        assert st["dirs"][j, i] == sum(_DIR_BIT[n] for n in names), (num, st["dirs"][j, i])
+    # the oracle's own acceptance record lists the cells by non-decreasing value
+    assert (np.diff(Uc.ravel()[st["order"]]) >= 0).all()
+
+
+def test_fmsm_one_node_cells_are_fast_marching(orc):
+    """With k = 1 the coarse grid is the grid itself: Part I is Fast Marching
+    on it, and Part II updates each node once, after the neighbours Fast
+    Marching accepted before it, from the quadrants behind the chosen sweeps
+    -- which hold the upwind neighbours.  FMSM then reproduces FMM (eq.
+    Eik_discr's solution)."""
+    rng = np.random.default_rng(21)
+    for _ in range(60):
+        I = W.tiny_random(rng, n_max=20)
+        V = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+        U, st = orc.fmsm(I.F, I.h, I.si, I.sj, I.sq, 1)
+        fin = np.isfinite(V)
+        assert (np.isfinite(U) == fin).all()
+        scale = max(np.abs(V[fin]).max(), 1e-300)
+        assert np.abs(U[fin] - V[fin]).max(initial=0) <= 1e-13 * scale
+        assert st["cells"] == I.nx * I.ny
+
+
+def test_fmsm_is_an_upper_bound(orc):
+    """Every FMSM value comes from the local update applied to values that
+    are themselves upper bounds (Sec. 4.1: the method only adds errors), so
+    FMSM never goes below eq. Eik_discr's solution, and nodes that solution
+    leaves unreachable stay +inf."""
+    rng = np.random.default_rng(22)
+    for _ in range(40):
+        I = W.tiny_random(rng, n_max=26)
+        V = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+        fin = np.isfinite(V)
+        scale = max(np.abs(V[fin]).max(), 1e-300) if fin.any() else 1.0
+        for k in (2, 3, 5, 8):
+            U, st = orc.fmsm(I.F, I.h, I.si, I.sj, I.sq, k)
+            assert (U[fin] >= V[fin] - 1e-13 * scale).all()
+            assert np.isinf(U[~fin]).all()
+            assert st["cells"] == ((I.nx + k - 1) // k) * ((I.ny + k - 1) // k)
+
+
+def test_fmsm_reproduces_tab_const(orc):
+    """Tab. const: with F = 1 and a point source at the centre FMSM adds no
+    error at any cell size (all three error ratios 1.0000), and its sweeps
+    per cell are as printed: one for most cells, two for the cells on the
+    axes through the source (one neighbour accepted before them, Fig.
+    coarse_sweep_choice).  AvS within 2% (the paper's cells divide 1408
+    nodes exactly; here the 1409th row and column form cells of their own)."""
+    g = _fmsm_gold()["const"]
+    n = g["n"]
+    c = (n - 1) // 2
+    F = np.ones((n, n))
+    h = 1.0 / (n - 1)
+    V = orc.fmm(F, h, [c], [c], [0.0])
+    for row in g["rows"]:
+        U, st = orc.fmsm(F, h, [c], [c], [0.0], row["k"])
+        assert np.abs(U - V).max() <= 1e-13 * V.max(), row
+        assert abs(st["avs"] / row["avs"] - 1) < 0.02, (row, st["avs"])
+
+
+@pytest.mark.slow
+def test_fmsm_reproduces_tab_sinu_1(orc):
+    """Tab. sinu_1's FMSM rows (errors against Fast Marching on an h/4 grid,
+    Sec. 5): the ratio of maximum errors within 5% at 88, 176 and 352 cells
+    and within 10% at 44, the average error ratio within 1% at 88, 176 and
+    352 cells, and the sweeps per cell within 1.5% at all four sizes."""
+    g = _fmsm_gold()["sinu_1"]
+    n = g["n"]
+    I = W.sin_point(n)
+    J = W.sin_point(4 * (n - 1) + 1)
+    V = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+    truth = orc.fmm(J.F, J.h, J.si, J.sj, J.sq)[::4, ::4]
+    e = np.abs(V - truth)
+    m = e > 0
+    for row in g["rows"]:
+        U, st = orc.fmsm(I.F, I.h, I.si, I.sj, I.sq, row["k"])
+        E = np.abs(U - truth)
+        rmax = E.max() / e.max()
+        rho = (E[m] / e[m]).mean()
+        assert abs(rmax / row["Rmax"] - 1) < (0.10 if row["k"] == 32 else 0.05), (row, rmax)
+        if row["k"] != 32:
+            assert abs(rho / row["rho"] - 1) < 0.01, (row, rho)
+        assert abs(st["avs"] / row["avs"] - 1) < 0.015, (row, st["avs"])
