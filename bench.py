@@ -254,10 +254,12 @@ def config_measure(eik, torch, I, prec, steps=5, k=0):
 
 
 def fhcm_measure(eik, torch, I, steps=5):
-    """The Fast Heap-Cell Method (Sec. 4.3) on the single 1025^2 grid, FP64:
-    device time beside the exact method (HCM), and Sec. 5's error ratios
-    against Fast Marching on an h/4 grid, beside the serial FHCM of the
-    oracle and the paper's Tab. sinu_1 row for its closest cell size."""
+    """The inexact methods on the single 1025^2 grid, FP64: the Fast
+    Heap-Cell Method (Sec. 4.3) beside the exact one (HCM), and the Fast
+    Marching-Sweeping Method (Sec. 4.1) at three cell sizes; device times and
+    Sec. 5's error ratios against Fast Marching on an h/4 grid, beside the
+    oracle's serial FHCM / FMSM and the paper's Tab. sinu_1 rows for the
+    closest cell size.  Returns (fhcm, fmsm) dictionaries."""
     import oracle
     from paper_1110_6220_gb300 import workloads as W
     F = torch.from_numpy(I.F).cuda()
@@ -299,7 +301,33 @@ def fhcm_measure(eik, torch, I, steps=5):
     out["paper_tab_sinu_1_fhcm_176_cells"] = {"R": 1.0560, "rho": 1.0022, "R_max_errors": 1.0000,
                                                "avhr": 1.125, "avs": 1.262, "mono_pct": 94.5,
                                                "note": "1408^2 grid, 8-node cells; context"}
-    return out
+    fm = {}
+    for k in (8, 16, 32):
+        ms, coarse, main = [], [], []
+        with eik.Plan(I.nx, I.ny, I.h, k, eik.EIK_FP64, method=eik.EIK_METHOD_FMSM) as p:
+            for r in range(steps + 2):
+                rc, st = p.solve(F, src, q, U)
+                if rc:
+                    raise RuntimeError(f"eik_solve (fmsm): {eik.eik_strerror(rc)}")
+                if r >= 2:
+                    ms.append(st.ms)
+                    coarse.append(st.pass_ms[0])
+                    main.append(st.pass_ms[1])
+        med = statistics.median(ms)
+        Ug = U.cpu().numpy()
+        Uo, so = orc.fmsm(I.F, I.h, I.si, I.sj, I.sq, k)
+        fm[f"k{k}"] = dict({"ms": med, "value": I.npts / med / 1e3, "unit": UNIT,
+                            "coarse_solve_ms": statistics.median(coarse), "cell_pass_ms": statistics.median(main),
+                            "avs": st.avs, "launches": st.launches,
+                            "max_rel_diff_vs_oracle_fmsm": float(np.abs(Ug - Uo)[np.isfinite(Uo)].max() /
+                                                                 np.abs(Uo[np.isfinite(Uo)]).max()),
+                            "oracle_avs": so["avs"]}, **ratios(Ug))
+    fm["paper_tab_sinu_1_fmsm"] = {
+        "k8_176_cells": {"R": 3.4828, "rho": 1.0074, "R_max_errors": 1.3705, "avs": 1.126},
+        "k16_88_cells": {"R": 4.6801, "rho": 1.0515, "R_max_errors": 1.9504, "avs": 1.213},
+        "k32_44_cells": {"R": 6.0892, "rho": 1.3657, "R_max_errors": 2.2889, "avs": 1.200},
+        "note": "1408^2 grid; context"}
+    return out, fm
 
 
 def batch_measure(eik, torch, steps=5, warmup=2, k=0):
@@ -614,7 +642,7 @@ def run_ours(args):
                 "q_boundary_sin1025_fp64": config_measure(eik, torch, W.sin_boundary(1025), eik.EIK_FP64),
             }
         if not args.no_configs:
-            line["fhcm"] = fhcm_measure(eik, torch, I)
+            line["fhcm"], line["fmsm"] = fhcm_measure(eik, torch, I)
         if not args.no_batch:
             line["batch"] = batch_measure(eik, torch)
         if not args.no_serving:

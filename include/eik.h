@@ -76,8 +76,18 @@ enum { EIK_FP64 = 0, EIK_FP32_REFINE = 1 };
  * Fast Heap-Cell Method (Sec. 4.3, Alg. FHCM): a removed cell is swept once
  * in each of its flagged directions, and an activation flags one or two
  * directions by the Monotonicity Check of the cell border; faster, never
- * below the exact solution, but not exact (FP64 only). */
-enum { EIK_METHOD_HCM = 0, EIK_METHOD_FHCM = 1 };
+ * below the exact solution, but not exact (FP64 only).  EIK_METHOD_FMSM:
+ * the Fast Marching-Sweeping Method (Sec. 4.1, Alg. FMSM): Fast Marching on
+ * the coarse grid of cell centres (speed F at each centre, as the mean of
+ * the nodes nearest to it; the cells holding sources as its exit set, each
+ * with its smallest q) orders the cells; each cell is then processed once in
+ * that order -- a cell holding a source by Fast Sweeping to convergence, any
+ * other by at most four sweeps with sweep-directional updates in the
+ * directions set by its neighbours accepted before it (Remark
+ * sweeping_in_FMSM, Fig. coarse_sweep_choice).  Never below the exact
+ * solution, not exact; FP64 and cell sizes >= 8 only (cell_k 0 picks 8 or
+ * more). */
+enum { EIK_METHOD_HCM = 0, EIK_METHOD_FHCM = 1, EIK_METHOD_FMSM = 2 };
 
 /* Problem-shape description (Sec. 3 problem statement plus the method's
  * cell size).  All fields are read at eik_plan_create. */
@@ -91,7 +101,7 @@ typedef struct {
     int32_t precision;     /* EIK_FP64 or EIK_FP32_REFINE */
     double tol;            /* FP32_REFINE: certified max error / max|u|; <= 0: 1e-5 */
     int64_t deadline_ns;   /* device wall-clock limit per solve; <= 0: 20 s */
-    int32_t method;        /* EIK_METHOD_HCM or EIK_METHOD_FHCM */
+    int32_t method;        /* EIK_METHOD_HCM, EIK_METHOD_FHCM or EIK_METHOD_FMSM */
 } eik_plan_desc;
 
 /* One problem instance (Sec. 3: speed F, exit set Q with values q). */
@@ -118,14 +128,16 @@ typedef struct {
     int64_t cell_visits;    /* total cell removals (all passes) */
     int64_t rounds;         /* grid-wide rounds (barrier-separated bucket releases) */
     int64_t buckets;        /* bucket advances (threshold moves) */
-    double pass_ms[2];      /* device time of the persistent FP32 pass [0] and main pass [1]
+    double pass_ms[2];      /* device time of the persistent FP32 pass (FMSM: the coarse solve) [0]
+                               and main pass [1]
                                (events on the launching stream; the kernels' own timers when
                                replayed from a graph; 0 if not run) */
     int32_t launches;       /* kernels this solve launched */
     int32_t cell_k;         /* cell size used */
     int32_t schedule;       /* bit 0: FP32 pass round-free; bit 1: FP64 / double-float pass
                                round-free; bit 2: FP32_REFINE as one double-float pass;
-                               bit 3: replayed from a captured CUDA graph */
+                               bit 3: replayed from a captured CUDA graph; bit 4: FMSM (a
+                               coarse solve, then every cell once as its predecessors finish) */
     int32_t status;         /* EIK_OK or the error of this solve */
     double mono_pct;        /* FHCM: Monotonicity Checks that found the border monotone, % */
 } eik_stats;
@@ -212,7 +224,8 @@ void eik_batch_destroy(eik_batch b);
  * timing each pass on its own; record
  * the fastest choice for the job's class (never one slower than the choice
  * in force before) and return it.  Blocks; about twenty solves.  Each U
- * receives a valid result.  All descriptors must have one precision;
+ * receives a valid result.  All descriptors must have one precision and a
+ * heap-cell method (EIK_METHOD_FMSM is refused with EIK_EINVAL);
  * their cell_k and bucket_width are ignored.  The table is per process and
  * shared by all threads and devices.  EIK_TUNE_FILE, if set, names a file
  * loaded on first use. */

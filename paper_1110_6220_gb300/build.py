@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libeik.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["eik_solver_f64.cu", "eik_solver_f32.cu", "eik_solver_df.cu", "eik_aux.cu", "eik_job.cu", "eik_api.cu", "eik_noalloc.cu", "eik_server.cu", "eik_tune.cu", "eik_batch.cu"]
+SOURCES = ["eik_solver_f64.cu", "eik_solver_f32.cu", "eik_solver_df.cu", "eik_aux.cu", "eik_job.cu", "eik_api.cu", "eik_noalloc.cu", "eik_server.cu", "eik_tune.cu", "eik_batch.cu", "eik_fmsm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(HERE, "..", "include")]

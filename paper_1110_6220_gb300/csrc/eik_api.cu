@@ -42,8 +42,10 @@ bool desc_valid(const eik_plan_desc* d) {
         d->cell_k != 64)
         return false;
     if (d->precision != EIK_FP64 && d->precision != EIK_FP32_REFINE) return false;
-    if (d->method != EIK_METHOD_HCM && d->method != EIK_METHOD_FHCM) return false;
-    if (d->method == EIK_METHOD_FHCM && d->precision != EIK_FP64) return false;
+    if (d->method != EIK_METHOD_HCM && d->method != EIK_METHOD_FHCM && d->method != EIK_METHOD_FMSM)
+        return false;
+    if (d->method != EIK_METHOD_HCM && d->precision != EIK_FP64) return false;
+    if (d->method == EIK_METHOD_FMSM && d->cell_k != 0 && d->cell_k < 8) return false;
     if ((long long)d->nx * d->ny > (1ll << 31) - 1) return false;
     return true;
 }
@@ -233,7 +235,10 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     while (Q < 16 * Jtot) Q <<= 1;
     const size_t hist_bytes = a256((3 * 8192 + 1) * 4);
     const size_t ring_bytes = a256(384 + hist_bytes + Q * 8);
-    const size_t total = image_bytes + zero_bytes + a256(Jtot * 8) + ring_bytes + ibytes + 256;
+    // FMSM: coarse speeds and coarse values, one of each per cell
+    const bool fmsm = descs[0].method == EIK_METHOD_FMSM;
+    const size_t fm_bytes = fmsm ? 2 * a256(Jtot * 8) : 0;
+    const size_t total = image_bytes + zero_bytes + a256(Jtot * 8) + ring_bytes + fm_bytes + ibytes + 256;
     int rc = grow(&hj->arena, total);
     if (rc) return rc;
     char* base = (char*)hj->arena.p;
@@ -241,7 +246,8 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     char* zero_dev = base + image_bytes;
     char* cval_dev = zero_dev + zero_bytes;
     char* ring_dev = cval_dev + a256(Jtot * 8);
-    char* inst_dev = ring_dev + ring_bytes;
+    char* fm_dev = ring_dev + ring_bytes;
+    char* inst_dev = fm_dev + fm_bytes;
 
     hj->image.assign(image_bytes, 0);
     char* img = hj->image.data();
@@ -289,6 +295,8 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
             aux_h[i].ctl = &ictl_dev[n + i];
             aux_h[i].ctl2 = nullptr;
         }
+        aux_h[i].Fc = fmsm ? (double*)fm_dev + coff : nullptr;
+        aux_h[i].Uc = fmsm ? (double*)(fm_dev + a256(Jtot * 8)) + coff : nullptr;
         desc_main_h[i].cell_base = (int)coff;
         if (fp32) desc_f32_h[i].cell_base = (int)coff;
         blk_pre_h[i] = boff;
@@ -350,6 +358,8 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     j.sm_cap = 0;
     j.one_pass = fp32 && P.one_pass;
     j.fhcm = descs[0].method == EIK_METHOD_FHCM;
+    j.fmsm = fmsm;
+    j.coarse = nullptr;
     j.hold_ns = P.hold_ns;
     j.req_time = req_all;
     j.async_first = P.async_first;
@@ -375,6 +385,43 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
         }
         hj->zero_cap = z_ctl;
     }
+    if (fmsm) {
+        // Part I's problem: per instance the grid of cell centres (spacing
+        // k h, speeds from k_fmsm_coarse_speed), with the cells that hold
+        // sources as its exit set at their sources' q (the job keeps the
+        // smallest per node); solved exactly, its values land in Uc
+        if (!hj->coarse) hj->coarse = new (std::nothrow) HostJob();
+        if (!hj->coarse) return EIK_ENOMEM;
+        std::vector<eik_plan_desc> cd((size_t)n);
+        std::vector<eik_instance> ci((size_t)n);
+        std::vector<std::vector<int32_t>> cij((size_t)n);
+        for (int i = 0; i < n; ++i) {
+            const Layout& L = hj->L[i];
+            cd[i] = descs[i];
+            cd[i].nx = L.cxn;
+            cd[i].ny = L.cyn;
+            cd[i].h = descs[i].h * k;
+            cd[i].cell_k = 0;
+            cd[i].bucket_width = 0.0;
+            cd[i].precision = EIK_FP64;
+            cd[i].method = EIK_METHOD_HCM;
+            const int m = in[i].nsrc;
+            const int32_t* ij = (const int32_t*)(hj->src_host + soff[i]);
+            cij[i].resize((size_t)2 * m + 2);
+            for (int s = 0; s < 2 * m; ++s) cij[i][s] = ij[s] / k;
+            ci[i] = in[i];
+            ci[i].F = aux_h[i].Fc;
+            ci[i].U = aux_h[i].Uc;
+            ci[i].src_ij = cij[i].data();
+            ci[i].src_q = (const double*)(hj->src_host + soff[i] + (size_t)m * 8);
+        }
+        // the coarse sources' q are read from this job's staging buffer
+        // (pinned host memory) while the coarse job copies them into its own
+        const JobParams Pc = choose_params(cd.data(), n);
+        rc = build_job(hj->coarse, n, cd.data(), ci.data(), Pc, false, deadline_ns, st);
+        if (rc) return rc;
+        j.coarse = &hj->coarse->j;
+    }
     return EIK_OK;
 }
 
@@ -387,6 +434,8 @@ int finish_job(HostJob* hj, const eik_plan_desc* descs, cudaStream_t st, double 
                             cudaMemcpyDeviceToHost, st);
     const size_t rb = (size_t)(2 * n + 2) * sizeof(Ctl) + (size_t)n * sizeof(ResidualOut);
     cudaMemcpyAsync(hj->zero_host, j.zero_base, rb, cudaMemcpyDeviceToHost, st);
+    const bool fmsm = j.fmsm && hj->coarse;
+    if (fmsm) cudaMemcpyAsync(hj->coarse->zero_host, hj->coarse->j.zero_base, rb, cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) {
         cudaGetLastError();
         return EIK_ECUDA;
@@ -400,7 +449,13 @@ int finish_job(HostJob* hj, const eik_plan_desc* descs, cudaStream_t st, double 
         job_stats(hj->L[i], &descs[i], j.fp32, &ic[i], &ic[n + i], &g[0], &g[1], &r[i], hj->shift[i],
                   hj->bw_main[i], ms, &s);
         s.schedule = (j.fp32 && !j.one_pass && j.async_first && j.k >= 8 ? 1 : 0) |
-                     (j.async_main && j.k >= 8 ? 2 : 0) | (j.one_pass ? 4 : 0);
+                     (j.async_main && j.k >= 8 && !j.fmsm ? 2 : 0) | (j.one_pass ? 4 : 0) | (j.fmsm ? 16 : 0);
+        if (fmsm && !s.status) {
+            // a failed coarse solve fails the instance
+            const Ctl* cc = (const Ctl*)hj->coarse->zero_host;
+            const int cs = cc[2 * n + 1].status ? cc[2 * n + 1].status : cc[n + i].status;
+            if (cs) s.status = cs;
+        }
         if (st_out) st_out[i] = s;
         if (s.status && !first_err) first_err = s.status;
     }
@@ -408,6 +463,11 @@ int finish_job(HostJob* hj, const eik_plan_desc* descs, cudaStream_t st, double 
 }
 
 void free_job(HostJob* hj) {
+    if (hj->coarse) {
+        free_job(hj->coarse);
+        delete hj->coarse;
+        hj->coarse = nullptr;
+    }
     if (hj->arena.p) cudaFree(hj->arena.p);
     hj->arena.p = nullptr;
     hj->arena.cap = 0;
@@ -437,7 +497,7 @@ int run_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance* 
     rc = finish_job(hj, descs, s, 0.0, st_out);
     float ms = 0.f, p0 = 0.f, p1 = 0.f;
     cudaEventElapsedTime(&ms, ev[0], ev[1]);
-    if (fp32) cudaEventElapsedTime(&p0, ev[2], ev[3]);
+    if (fp32 || hj->j.fmsm) cudaEventElapsedTime(&p0, ev[2], ev[3]);
     cudaEventElapsedTime(&p1, ev[4], ev[5]);
     if (st_out)
         for (int e = 0; e < n; ++e) {
@@ -541,7 +601,7 @@ extern "C" int eik_solve(eik_plan p, const eik_instance* in, eik_stats* st) {
     cudaEventElapsedTime(&ms, p->ev0, p->ev1);
     local.ms = ms;
     local.mpts_per_s = ms > 0 ? (double)p->d.nx * p->d.ny / ms / 1000.0 : 0.0;
-    if (fp32) cudaEventElapsedTime(&ms, p->pev[0], p->pev[1]), local.pass_ms[0] = ms;
+    if (fp32 || p->job.j.fmsm) cudaEventElapsedTime(&ms, p->pev[0], p->pev[1]), local.pass_ms[0] = ms;
     cudaEventElapsedTime(&ms, p->pev[2], p->pev[3]);
     local.pass_ms[1] = ms;
     local.launches = nl;

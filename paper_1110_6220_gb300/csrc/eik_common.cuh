@@ -181,6 +181,8 @@ struct AuxInst {
     Ctl* ctl2;                    // ... of the refinement pass (FP32+refinement)
     ResidualOut* res;
     int J;
+    double* Fc;                   // FMSM: coarse speeds, J (cyn x cxn)
+    double* Uc;                   // FMSM: coarse values, J
 };
 
 // Sources of all instances: node (j*nx + i) and shifted q, with instance id;
@@ -201,6 +203,16 @@ cudaError_t launch_init_sources(const AuxInst* a, const SourceTable& s, cudaStre
 cudaError_t launch_seed_refine(const AuxInst* a, const int* blk_pre, int n, int nblocks,
                                const int* cell_pre, int ncells, float beta, cudaStream_t st);
 cudaError_t launch_residual(const AuxInst* a, const int* blk_pre, int n, int nblocks, cudaStream_t st);
+
+// Fast Marching-Sweeping Method (eik_fmsm.cu), FP64, cell sizes >= 8:
+// coarse speeds Fc of every cell; then, from the coarse values Uc, each
+// cell's sweeps, later neighbours and count of earlier ones, the ready cells
+// queued (ring and qctl zeroed before); then the persistent pass.
+cudaError_t launch_fmsm_coarse_speed(const AuxInst* a, const int* cell_pre, int n, int ncells, cudaStream_t st);
+cudaError_t launch_fmsm_prep(const AuxInst* a, const int* cell_pre, int n, int ncells, unsigned long long* ring,
+                             unsigned* qctl, cudaStream_t st);
+int fmsm_shape(int k, int num_sms, int sm_cap, LaunchShape* out);
+cudaError_t launch_fmsm(int k, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
 cudaError_t launch_output(const AuxInst* a, const int* blk_pre, int n, int nblocks, cudaStream_t st);
 
 }  // namespace eik

@@ -243,6 +243,32 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
         ++nl;
         if (launch_residual(j.aux, j.blk_pre, n, j.nblocks, st) != cudaSuccess) return EIK_ECUDA;
         ++nl;
+    } else if (j.fmsm) {
+        // Fast Marching-Sweeping: the coarse speeds, the coarse grids solved
+        // by their own job (Part I), the order and the ready cells, then
+        // every cell once (Part II)
+        if (!j.coarse) return EIK_EINVAL;
+        if (launch_fmsm_coarse_speed(j.aux, j.cell_pre, n, j.ncells, st) != cudaSuccess) return EIK_ECUDA;
+        ++nl;
+        int nlc = 0;
+        if (ev) cudaEventRecord(ev[0], st);
+        const int rc = enqueue_job(*j.coarse, num_sms, st, nullptr, &nlc);
+        if (rc) return rc;
+        if (ev) cudaEventRecord(ev[1], st);
+        nl += nlc;
+        if (cudaMemsetAsync(j.qctl, 0, 384, st) != cudaSuccess ||
+            cudaMemsetAsync(j.ring, 0, ((size_t)j.ring_mask + 1) * 8, st) != cudaSuccess)
+            return EIK_ECUDA;
+        if (launch_fmsm_prep(j.aux, j.cell_pre, n, j.ncells, j.ring, j.qctl, st) != cudaSuccess)
+            return EIK_ECUDA;
+        ++nl;
+        if (fmsm_shape(j.k, num_sms, j.sm_cap, &shape)) return EIK_ECUDA;
+        p.inst = j.desc_main;
+        p.gctl = j.gctl + 1;
+        if (ev) cudaEventRecord(ev[2], st);
+        if (launch_fmsm(j.k, p, shape, st) != cudaSuccess) return EIK_ECUDA;
+        if (ev) cudaEventRecord(ev[3], st);
+        ++nl;
     } else {
         if (solver_shape_f64(j.k, num_sms, n, j.sm_cap, am, j.fhcm, &shape)) return EIK_ECUDA;
         p.inst = j.desc_main;
@@ -262,6 +288,10 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
 
 bool job_pairable(const JobDev& j, int num_sms) {
     LaunchShape a{}, b{};
+    if (j.fmsm) {
+        if (fmsm_shape(j.k, num_sms, 1, &a) || !j.coarse || !job_pairable(*j.coarse, num_sms)) return false;
+        return a.per_sm >= 2;
+    }
     if (j.fp32 && j.one_pass) {
         if (solver_shape_df(j.k, num_sms, j.n, 1, j.async_main, false, &b)) return false;
         return b.per_sm >= 2;

@@ -60,6 +60,8 @@ struct JobDev {
     bool async_first, async_main;  // round-free schedule (k_solve_async) for the FP32 / main pass
     bool one_pass;              // fp32: no FP32 pass; the double-float pass solves from the sources
     bool fhcm;                  // Fast Heap-Cell Method (one sweep per flagged direction)
+    bool fmsm;                  // Fast Marching-Sweeping Method (coarse solve, then one visit per cell)
+    const JobDev* coarse;       // FMSM: the job of the instances' coarse grids
     unsigned hold_ns;           // round-free: minimum age of a request before its cell runs
     unsigned long long* req_time;  // request times per cell (job-wide index), %globaltimer ns
     unsigned long long* ring;   // async: ring of ring_mask + 1 words
@@ -87,7 +89,8 @@ void fill_inst_tables(const Layout& L, const InstArrays& a, bool fp32, double h,
                       bool* ok);
 
 // Queue the whole solve of a job on st (tables and sources already uploaded).
-// ev: null or 4 events around the FP32 pass [0,1] and the main pass [2,3].
+// ev: null or 4 events around the FP32 pass (FMSM: the coarse solve) [0,1]
+// and the main pass [2,3].
 int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, int* launches);
 
 // True when every solver launch of j, capped to one block per SM, takes at

@@ -65,6 +65,7 @@ struct HostJob {
     size_t zero_cap = 0;
     char* src_host = nullptr;    // pinned staging of the instances' sources
     size_t src_cap = 0;
+    HostJob* coarse = nullptr;   // FMSM: the job of the coarse grids (owned)
 };
 
 // Lay out and upload a job of n instances (one k and precision); descs[i]

@@ -146,6 +146,7 @@ JobParams choose_params(const eik_plan_desc* d, int n) {
     }
     JobParams P;
     P.k = d[0].cell_k ? d[0].cell_k : e.k;
+    if (d[0].method == EIK_METHOD_FMSM && P.k < 8) P.k = 8;  // one cell per warp
     P.w_first = -e.m_first;
     P.w_main = -e.m_main;
     P.async_first = e.async_first;
@@ -174,7 +175,8 @@ extern "C" int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t 
                         eik_tune_result* out) {
     if (!d || !in || n_inst < 1 || n_inst > MAX_BATCH) return EIK_EINVAL;
     for (int i = 0; i < n_inst; ++i)
-        if (!desc_valid(&d[i]) || d[i].precision != d[0].precision) return EIK_EINVAL;
+        if (!desc_valid(&d[i]) || d[i].precision != d[0].precision || d[i].method == EIK_METHOD_FMSM)
+            return EIK_EINVAL;  // the table holds the cell solver's schedules
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {

@@ -36,6 +36,7 @@ EIK_FP64 = 0
 EIK_FP32_REFINE = 1
 EIK_METHOD_HCM = 0
 EIK_METHOD_FHCM = 1
+EIK_METHOD_FMSM = 2
 
 
 class eik_plan_desc(ctypes.Structure):

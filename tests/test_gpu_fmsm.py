@@ -1,0 +1,111 @@
+"""Fast Marching-Sweeping Method on the GPU (Sec. 4.1, Alg. FMSM).  The GPU
+runs each cell as soon as the neighbours accepted before it are done.  A
+cell's result depends only on which of its neighbours ran before it, so the
+GPU's result is that of the serial loop over the acceptance order, and it is
+compared with the oracle's serial FMSM node by node (FP64: 1e-12 of max |U|,
++inf exactly) and by its number of sweeps."""
+import numpy as np
+import pytest
+
+from paper_1110_6220_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+FMSM = 2
+
+
+@pytest.fixture(scope="module")
+def eik():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1110_6220_gb300 import build
+    build.build()
+    from paper_1110_6220_gb300 import eik as e
+    return e
+
+
+def _instances():
+    rng = np.random.default_rng(9)
+    insts = [W.sin_point(257), W.const_point(129),
+             W.random_instance(rng, 150, 260, kinds=("blocks",)), W.random_instance(rng, 150, 260, kinds=("sin",)),
+             W.checker_maze(385, seed=3, n_walls=6, n_src=3)]
+    c = W.sin_point(257)
+    c.F = W.checker_field(257, 16)  # checkerboard speeds, centre source
+    insts.append(c)
+    return insts
+
+
+def _compare(I, k, U, st, Uo, so):
+    fin = np.isfinite(Uo)
+    assert (np.isfinite(U) == fin).all(), I.name
+    scale = np.abs(Uo[fin]).max()
+    err = np.abs(U[fin] - Uo[fin]).max(initial=0.0)
+    assert err <= 1e-12 * scale, (I.name, k, err / scale)
+    assert abs(st.avhr - 1.0) < 1e-12, (I.name, st.avhr)  # every cell once
+    # the sweeps of each cell are the oracle's; a cell holding a source
+    # sweeps to convergence, which rounding may end one sweep apart
+    src_cells = len({(int(i) // k, int(j) // k) for i, j in zip(I.si, I.sj)})
+    assert abs(round(st.avs * so["cells"]) - so["sweeps"]) <= src_cells, (I.name, st.avs * so["cells"], so["sweeps"])
+
+
+@pytest.mark.parametrize("k", [8, 16, 32])
+def test_fmsm_matches_serial_oracle(eik, orc, k):
+    for I in _instances():
+        U, st = eik.solve(I.F, I.h, I.si, I.sj, I.sq, cell_k=k, method=FMSM)
+        assert st.status == 0 and st.cell_k == k and st.schedule & 16
+        Uo, so = orc.fmsm(I.F, I.h, I.si, I.sj, I.sq, k)
+        _compare(I, k, U, st, Uo, so)
+
+
+@pytest.mark.parametrize("k", [8, 16])
+def test_fmsm_full_size_sin1025(eik, orc, k):
+    """The 1025^2 sin20 grid with a centre source, element by element."""
+    I = W.sin_point(1025)
+    U, st = eik.solve(I.F, I.h, I.si, I.sj, I.sq, cell_k=k, method=FMSM)
+    assert st.status == 0
+    Uo, so = orc.fmsm(I.F, I.h, I.si, I.sj, I.sq, k)
+    _compare(I, k, U, st, Uo, so)
+    V = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+    assert (U >= V - 1e-12 * V.max()).all()  # never below the exact solution
+
+
+def test_fmsm_k64_and_ragged(eik, orc):
+    rng = np.random.default_rng(4)
+    I = W.random_instance(rng, 300, 330, kinds=("sin",))
+    U, st = eik.solve(I.F, I.h, I.si, I.sj, I.sq, cell_k=64, method=FMSM)
+    assert st.status == 0
+    Uo, so = orc.fmsm(I.F, I.h, I.si, I.sj, I.sq, 64)
+    _compare(I, 64, U, st, Uo, so)
+
+
+def test_fmsm_batch(eik, orc):
+    """Several grids as one job: one coarse job for all of them, one
+    persistent pass; each grid's result is its serial FMSM."""
+    import torch
+    rng = np.random.default_rng(12)
+    insts = [W.random_instance(rng, 70, 300) for _ in range(6)] + [W.sin_point(129)]
+    descs, ins, keep = [], [], []
+    for I in insts:
+        F = torch.from_numpy(I.F).cuda()
+        U = torch.empty_like(F)
+        ij = torch.from_numpy(np.stack([I.si, I.sj], 1).reshape(-1).astype(np.int32)).cuda()
+        q = torch.from_numpy(I.sq.astype(np.float64)).cuda()
+        keep.append((F, U, ij, q))
+        descs.append(eik.make_desc(I.nx, I.ny, I.h, 8, eik.EIK_FP64, method=FMSM))
+        ins.append(eik.make_instance(F, ij, q, U))
+    rc, sts = eik.eik_solve_batch(descs, ins)
+    assert rc == 0
+    for I, (F, U, _, _), st in zip(insts, keep, sts):
+        Uo, so = orc.fmsm(I.F, I.h, I.si, I.sj, I.sq, 8)
+        _compare(I, 8, U.cpu().numpy(), st, Uo, so)
+
+
+def test_fmsm_rejected_forms(eik):
+    I = W.const_point(65)
+    for prec, k in ((eik.EIK_FP32_REFINE, 8), (eik.EIK_FP64, 4)):
+        d = eik.make_desc(65, 65, I.h, k, prec, method=FMSM)
+        assert eik.eik_plan_workspace_bytes(d) == 0  # the descriptor is refused
+    d = eik.make_desc(65, 65, I.h, 0, eik.EIK_FP64, method=FMSM)
+    U = np.empty_like(I.F)
+    rc, _ = eik.eik_tune([d], [eik.make_instance(I.F, I.src_ij, I.sq, U)])
+    assert rc == eik.EIK_EINVAL  # the tuning table holds the cell solver's schedules
