@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the cell-size sweep")
     ap.add_argument("--no-configs", action="store_true", help="skip the C1 / C2-FP64 / C3 solves")
     ap.add_argument("--serving-requests", type=int, default=128)
+    ap.add_argument("--batch-count", type=int, default=512,
+                    help="grids in the batch measurement (512: the 512-grid workload; fewer for profiling)")
     return ap.parse_args()
 
 
@@ -330,7 +332,7 @@ def fhcm_measure(eik, torch, I, steps=5):
     return out, fm
 
 
-def batch_measure(eik, torch, steps=5, warmup=2, k=0):
+def batch_measure(eik, torch, steps=5, warmup=2, k=0, count=512):
     """The batched workload: 512 grids with side lengths log-uniform in
     [65, 1025] (sin-product or random-block speeds, 1-8 sources), FP32 +
     refinement, inputs resident on the device.  Timed as a fixed batch
@@ -338,7 +340,7 @@ def batch_measure(eik, torch, steps=5, warmup=2, k=0):
     replayed), wall clock per run including the result read-back; the one-off
     eik_solve_batch call (which builds the job each time) is timed beside it."""
     from paper_1110_6220_gb300 import workloads as W
-    insts = W.batch_mix(512, seed=1)
+    insts = W.batch_mix(count, seed=1)
     npts = sum(I.npts for I in insts)
     dev = []
     for I in insts:
@@ -370,7 +372,7 @@ def batch_measure(eik, torch, steps=5, warmup=2, k=0):
         if r:
             one_off.append(1e3 * (time.perf_counter() - t0))
     med = statistics.median(wall)
-    return {"workload": "512 grids, n log-uniform in [65, 1025], sin-product or random-block F, "
+    return {"workload": f"{count} grids, n log-uniform in [65, 1025], sin-product or random-block F, "
                         "1-8 sources, seed 1", "precision": "fp32ref", "cell_k_used": st[0].cell_k,
             "points": npts, "ms_per_batch": med, "value": npts / (med / 1e3) / 1e6, "unit": UNIT,
             "timing": "wall clock per eik_batch_run (graph replay + read-back), median of 5",
@@ -644,7 +646,7 @@ def run_ours(args):
         if not args.no_configs:
             line["fhcm"], line["fmsm"] = fhcm_measure(eik, torch, I)
         if not args.no_batch:
-            line["batch"] = batch_measure(eik, torch)
+            line["batch"] = batch_measure(eik, torch, count=args.batch_count)
         if not args.no_serving:
             line["serving"] = serving_measure(eik, torch, count=args.serving_requests)
         if world == 1 and not args.no_cpu_baseline:

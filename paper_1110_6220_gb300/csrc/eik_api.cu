@@ -291,9 +291,12 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
                          &ictl_dev[n + i],
                          &res_dev[i], F, out, hj->shift[i], &aux_h[i], &desc_main_h[i], &desc_f32_h[i], &ok);
         if (fp32 && P.one_pass) {
-            // the source cells are queued for the double-float pass itself
+            // the source cells are queued for the double-float pass itself,
+            // and nothing reads the FP32 pass's arrays
             aux_h[i].ctl = &ictl_dev[n + i];
             aux_h[i].ctl2 = nullptr;
+            aux_h[i].f32 = nullptr;
+            aux_h[i].U32 = nullptr;
         }
         aux_h[i].Fc = fmsm ? (double*)fm_dev + coff : nullptr;
         aux_h[i].Uc = fmsm ? (double*)(fm_dev + a256(Jtot * 8)) + coff : nullptr;

@@ -55,6 +55,18 @@ __device__ __forceinline__ Where locate(const AuxInst* a, const int* blk_pre, in
     return w;
 }
 
+// Tests of a speed on its bit pattern (the integer pipe; GB300 runs double
+// comparisons on its FP64 pipe).  valid: 0 <= F < +inf (either zero, no NaN);
+// positive: 0 < F < +inf.
+__device__ __forceinline__ bool speed_valid(double F) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(F);
+    return b < 0x7ff0000000000000ull || b == 0x8000000000000000ull;
+}
+__device__ __forceinline__ bool speed_positive(double F) {
+    const long long b = __double_as_longlong(F);
+    return b > 0 && b < 0x7ff0000000000000ll;
+}
+
 // owner[b] = instance of block b, for the prefix pre[0..n]: one block per
 // instance fills its range
 __global__ void k_block_owner(const int* pre, int n, int* owner) {
@@ -92,8 +104,8 @@ __global__ void k_init_grid(const AuxInst* A, const int* blk_full, int n) {
     for (int s = 0; s < SPAN; ++s) {
         const int c = c0 + 32 * s;
         const bool in = c < p.upitch && r < p.nyp + 2;
-        if (!(F[s] >= 0.0) || F[s] == INF) bad = true;
-        const bool finite_f = F[s] > 0.0 && F[s] < INF;  // a grid node with a positive speed
+        if (!speed_valid(F[s])) bad = true;
+        const bool finite_f = speed_positive(F[s]);  // a grid node with a positive speed
         const size_t q = (size_t)r * p.upitch + c;
         if (p.f64) {
             // FP64 mode: f = h/F in FP64
@@ -243,7 +255,9 @@ __global__ void k_seed_cells(const AuxInst* A, const int* cell_pre, int n, int n
 // Certificate data of the pair modes, and the output.  At every non-source
 // node, an upper bound of r = |V - T(V)|: T the exact local update (eqs.
 // one_sided_update / two_sided_update with the relevant-quadrant shortcut)
-// with f = h/F recomputed from F.  T(V) - V is evaluated relative to V in
+// with f = h/F as k_init_grid stored it: the double-float quotient of h by
+// the split F (the solvers never write f except on sources, which this
+// skips).  T(V) - V is evaluated relative to V in
 // double-float arithmetic on the FP32 pipe -- the upwind offsets, 2 f^2 - d^2,
 // its root and the quotient of the cancellation-free form all carry ~46 bits
 // -- and an allowance of 2^-40 (V + min(a, b) + 4 f) covers every rounding of
@@ -258,6 +272,7 @@ __global__ void k_residual(const AuxInst* A, const int* blk_pre, int n) {
     const float FINF = inf_of<float>();
     float r = 0.0f, rrel = 0.0f, umax = 0.0f;
     unsigned long long bad = 0;
+    const bool shifted = __double_as_longlong(p.shift) != 0;  // min q != 0: add it back
 #pragma unroll
     for (int s = 0; s < SPAN; ++s) {
         const int i = w.i + 32 * s;
@@ -265,17 +280,17 @@ __global__ void k_residual(const AuxInst* A, const int* blk_pre, int n) {
         const size_t q = (size_t)(j + 1) * up + (i + 1);
         const float2 V = p.Udf[q];
         const float2 fs = p.fdf[q];
-        const double Fv = p.F[(size_t)j * p.nx + i];
         const float2 W = p.Udf[q - 1], E = p.Udf[q + 1], S = p.Udf[q - up], N = p.Udf[q + up];
         const bool vfin = V.x < FINF;
         if (vfin) umax = fmaxf(umax, V.x);
-        p.out[(size_t)j * p.nx + i] = vfin ? widen(V.x) + widen(V.y) + p.shift : inf_of<double>();
-        if (fs.x < 0.0f) continue;  // a source
-        float2 f = make_float2(FINF, 0.0f);
-        if (Fv > 0.0) {
-            f = f_pair(p.hx, p.hy, p.h, Fv);
-            if (!(f.x < 1e18f)) f = make_float2(FINF, 0.0f);
+        double o = inf_of<double>();
+        if (vfin) {
+            o = widen(V.x) + widen(V.y);
+            if (shifted) o += p.shift;
         }
+        p.out[(size_t)j * p.nx + i] = o;
+        if (fs.x < 0.0f) continue;  // a source
+        const float2 f = fs;  // +inf on obstacles
         const float2 a = lt(E, W) ? E : W, b = lt(N, S) ? N : S;
         const bool ab = lt(a, b);
         const float2 lo = ab ? a : b, hi = ab ? b : a;
@@ -293,8 +308,11 @@ __global__ void k_residual(const AuxInst* A, const int* blk_pre, int n) {
             const float allow = 0x1p-40f * (V.x + lo.x + 4.0f * f.x);
             const float rn = (fabsf(R.x) + fabsf(R.y) + allow) * (1.0f + 0x1p-20f);
             r = fmaxf(r, rn);
-            // relative to this node's f (rounded up; f.y < ulp(f.x))
-            rrel = fmaxf(rrel, __fdiv_ru(rn, f.x * (1.0f - 0x1p-22f)));
+            // relative to this node's f, rounded up (f.y < ulp(f.x)): the fast
+            // quotient is within 2 ulps for divisors in [2^-100, 1e18], and the
+            // factor adds 8; tinier f take the directed-rounding quotient
+            const float fd = f.x * (1.0f - 0x1p-22f);
+            rrel = fmaxf(rrel, fd >= 0x1p-100f ? __fdividef(rn, fd) * (1.0f + 0x1p-20f) : __fdiv_ru(rn, fd));
         } else if (vfin || tfin) {
             r = rrel = FINF;
             bad += 1;

@@ -133,10 +133,10 @@ __device__ __forceinline__ bool fmsm_sweep(double* tU, const double* tF, const f
 }
 
 // Part II.  Each warp takes a ready cell from the ring, loads its tile and
-// halo, sweeps it, writes it back and counts down its later neighbours,
-// queueing each whose count reaches zero.  `pending` counts the cells not yet
-// done; a waiting warp that sees it at zero leaves.  Every wait is bounded by
-// the launch deadline.
+// halo, sweeps it, writes it back and counts down its later neighbours; of
+// those whose count reaches zero it keeps one to run next and queues the
+// rest.  `pending` counts the cells not yet done; a waiting warp that sees it
+// at zero leaves.  Every wait is bounded by the launch deadline.
 template <int K>
 __global__ void __launch_bounds__(TileCfg<MODE_F64, K>::WPB * 32)
     k_solve_fmsm(const __grid_constant__ SolveParams p) {
@@ -162,11 +162,15 @@ __global__ void __launch_bounds__(TileCfg<MODE_F64, K>::WPB * 32)
     unsigned long long pacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long long pt = clock64();
 
+    int next = -1;  // a cell this warp released itself and runs next
     for (;;) {
-        int e = 0;
-        if (lane == 0) e = ring_pop(p, gctl, deadline);
-        e = __shfl_sync(FULLM, e, 0);
-        if (e < 0) break;
+        int e = next;
+        if (e < 0) {
+            if (lane == 0) e = ring_pop(p, gctl, deadline);
+            e = __shfl_sync(FULLM, e, 0);
+            if (e < 0) break;
+        }
+        next = -1;
         const int ii = find_inst(p.cell_pre, NI, e);
         const InstDesc& d = inst[ii];
         const int c = e - d.cell_base;
@@ -251,13 +255,24 @@ __global__ void __launch_bounds__(TileCfg<MODE_F64, K>::WPB * 32)
         fence_proxy_async_global();
         __syncwarp();
         PROF_MARK(5);
-        // ---- count down the later neighbours (lane s: side s)
+        // ---- count down the later neighbours (lane s: side s).  Of those
+        // that become ready, this warp keeps the first and runs it next (no
+        // round trip through the ring on the chain of dependent cells); the
+        // others are queued.
+        bool ready = false;
+        int nc = -1;
         if (lane < 4 && ((fl >> (FMSM_LATER + lane)) & 1)) {
-            const int nc = lane == 0 ? c - 1 : lane == 1 ? c + 1 : lane == 2 ? c - d.cxn : c + d.cxn;
-            if (atomicSub(&d.visits[nc], 1) == 1) {
+            nc = lane == 0 ? c - 1 : lane == 1 ? c + 1 : lane == 2 ? c - d.cxn : c + d.cxn;
+            ready = atomicSub(&d.visits[nc], 1) == 1;
+        }
+        const unsigned rmask = __ballot_sync(FULLM, ready);
+        if (rmask) {
+            const int keep = __ffs(rmask) - 1;
+            if (ready && lane != keep) {
                 fence_acq_rel_gpu();  // pass on what this neighbour's other predecessors released
                 ring_push(p, gctl, (unsigned)(d.cell_base + nc), deadline);
             }
+            next = __shfl_sync(FULLM, d.cell_base + nc, keep);
         }
         __syncwarp();
         if (lane == 0) {

@@ -246,8 +246,8 @@ __device__ __forceinline__ float2 update_df(float2 W, float2 E, float2 S, float2
 // split_pos: a positive double as a pair -- hi keeps the leading 24
 // significand bits (exact in a float), lo the next 24 of the remaining 29
 // (rounded, 2^-53 relative); false outside [2^-74, 2^126).  widen: a float as
-// a double by exponent rebias (subnormals, infinities and NaN take the
-// ordinary conversion).
+// a double, exactly, from its bits alone (exponent rebias; a subnormal is
+// normalised by its leading-zero count).
 __device__ __forceinline__ bool split_pos(double v, float2* out) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int e = (int)((b >> 52) & 0x7ff);
@@ -259,11 +259,20 @@ __device__ __forceinline__ bool split_pos(double v, float2* out) {
 }
 __device__ __forceinline__ double widen(float x) {
     const unsigned u = __float_as_uint(x);
-    const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 255u) return (u & 0x7fffffffu) == 0u ? (u ? -0.0 : 0.0) : (double)x;
-    return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
-                                            ((unsigned long long)(e + 896u) << 52) |
-                                            ((unsigned long long)(u & 0x7fffffu) << 29)));
+    const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned long long b;
+    if (e == 255u) {
+        b = 0x7ff0000000000000ull | ((unsigned long long)m << 29);  // inf, NaN
+    } else if (e != 0u) {
+        b = ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+    } else if (m == 0u) {
+        b = 0ull;  // zero
+    } else {
+        // m 2^-149: the leading one moved to bit 23, exponent 2^(23 - lz - 149)
+        const int lz = __clz(m) - 8;
+        b = ((unsigned long long)(897 - lz) << 52) | ((unsigned long long)((m << lz) & 0x7fffffu) << 29);
+    }
+    return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) | b));
 }
 
 // The two-sided increment (f^2 - d^2) / (d + sqrt(2 f^2 - d^2)) in
