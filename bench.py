@@ -97,6 +97,43 @@ def cpu_baseline(I, seconds):
                       f"(binary heap), 1 thread, {el:.1f} s"}
 
 
+def _oracle_solve(args):
+    """One grid with the oracle FMM (a worker of oracle_parallel)."""
+    F, h, si, sj, sq = args
+    import oracle
+    oracle.fmm(F, h, si, sj, sq)
+    return int(F.size)
+
+
+def oracle_parallel(insts, seconds, cores=8):
+    """The oracle FMM, as it stands, one grid per process on up to `cores`
+    host cores (a pool started by spawn: the parent has initialised CUDA),
+    each process taking the next grid when it is free.  The sample is the
+    workload's first grids, as many as make about `seconds` of work per core
+    at the oracle's single-core rate (~7 Mpts/s)."""
+    import multiprocessing as mp
+    import oracle
+    from paper_1110_6220_gb300 import workloads as W
+    oracle.build()
+    cores = max(1, min(cores, os.cpu_count() or 1))
+    sample, pts = [], 0
+    for I in insts:
+        sample.append(I)
+        pts += I.npts
+        if pts >= seconds * cores * 7e6:
+            break
+    tiny = W.const_point(17)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_solve, [(tiny.F, tiny.h, tiny.si, tiny.sj, tiny.sq)] * cores)  # start and load
+        t0 = time.perf_counter()
+        done = sum(pool.imap_unordered(_oracle_solve, [(I.F, I.h, I.si, I.sj, I.sq) for I in sample]))
+        el = time.perf_counter() - t0
+    return {"value": done / el / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the first {len(sample)} grids of the workload ({done} points), FP64 Fast Marching "
+                      f"oracle, one grid per process on {cores} cores, {el:.1f} s"}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -332,7 +369,7 @@ def fhcm_measure(eik, torch, I, steps=5):
     return out, fm
 
 
-def batch_measure(eik, torch, steps=5, warmup=2, k=0, count=512):
+def batch_measure(eik, torch, steps=5, warmup=2, k=0, count=512, cpu_seconds=0.0):
     """The batched workload: 512 grids with side lengths log-uniform in
     [65, 1025] (sin-product or random-block speeds, 1-8 sources), FP32 +
     refinement, inputs resident on the device.  Timed as a fixed batch
@@ -372,15 +409,18 @@ def batch_measure(eik, torch, steps=5, warmup=2, k=0, count=512):
         if r:
             one_off.append(1e3 * (time.perf_counter() - t0))
     med = statistics.median(wall)
-    return {"workload": f"{count} grids, n log-uniform in [65, 1025], sin-product or random-block F, "
-                        "1-8 sources, seed 1", "precision": "fp32ref", "cell_k_used": st[0].cell_k,
-            "points": npts, "ms_per_batch": med, "value": npts / (med / 1e3) / 1e6, "unit": UNIT,
-            "timing": "wall clock per eik_batch_run (graph replay + read-back), median of 5",
-            "device_ms": statistics.median(dms), "pass_ms": list(st[0].pass_ms),
-            "graph_replay": bool(st[0].schedule & 8),
-            "max_err_bound": max(s.err_bound for s in st), "launches_per_batch": st[0].launches,
-            "one_off_eik_solve_batch_ms": statistics.median(one_off),
-            "one_off_value": npts / (statistics.median(one_off) / 1e3) / 1e6}
+    out = {"workload": f"{count} grids, n log-uniform in [65, 1025], sin-product or random-block F, "
+                       "1-8 sources, seed 1", "precision": "fp32ref", "cell_k_used": st[0].cell_k,
+           "points": npts, "ms_per_batch": med, "value": npts / (med / 1e3) / 1e6, "unit": UNIT,
+           "timing": "wall clock per eik_batch_run (graph replay + read-back), median of 5",
+           "device_ms": statistics.median(dms), "pass_ms": list(st[0].pass_ms),
+           "graph_replay": bool(st[0].schedule & 8),
+           "max_err_bound": max(s.err_bound for s in st), "launches_per_batch": st[0].launches,
+           "one_off_eik_solve_batch_ms": statistics.median(one_off),
+           "one_off_value": npts / (statistics.median(one_off) / 1e3) / 1e6}
+    if cpu_seconds > 0:
+        out["cpu_baseline_parallel"] = oracle_parallel(insts, cpu_seconds)
+    return out
 
 def _pct(xs, p):
     xs = sorted(xs)
@@ -390,7 +430,7 @@ def _pct(xs, p):
     return xs[i]
 
 
-def serving_measure(eik, torch, count=128, seed=5, budget=64 << 30):
+def serving_measure(eik, torch, count=128, seed=5, budget=64 << 30, cpu_seconds=0.0):
     """The serving workload: a seeded Poisson stream of FP32 + refinement
     solves, side lengths log-uniform in [129, 2049], sin-product, random-block
     and checkerboard+maze speeds in equal shares, served through
@@ -491,6 +531,8 @@ def serving_measure(eik, torch, count=128, seed=5, budget=64 << 30):
                 "p50_ms": 1e3 * _pct(lat, 50), "p99_ms": 1e3 * _pct(lat, 99),
                 "serial_p50_ms": 1e3 * _pct(sl, 50), "serial_p99_ms": 1e3 * _pct(sl, 99),
                 "value": npts / span / 1e6, "unit": UNIT})
+        if cpu_seconds > 0:
+            out["cpu_baseline_parallel"] = oracle_parallel(insts, cpu_seconds)
         return out
     finally:
         eik.eik_server_destroy(srv)
@@ -646,9 +688,11 @@ def run_ours(args):
         if not args.no_configs:
             line["fhcm"], line["fmsm"] = fhcm_measure(eik, torch, I)
         if not args.no_batch:
-            line["batch"] = batch_measure(eik, torch, count=args.batch_count)
+            line["batch"] = batch_measure(eik, torch, count=args.batch_count,
+                                          cpu_seconds=0.0 if args.no_cpu_baseline else 10.0)
         if not args.no_serving:
-            line["serving"] = serving_measure(eik, torch, count=args.serving_requests)
+            line["serving"] = serving_measure(eik, torch, count=args.serving_requests,
+                                              cpu_seconds=0.0 if args.no_cpu_baseline else 10.0)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(I, args.cpu_seconds)
         print(json.dumps(line), flush=True)
