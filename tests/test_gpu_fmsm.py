@@ -109,3 +109,63 @@ def test_fmsm_rejected_forms(eik):
     U = np.empty_like(I.F)
     rc, _ = eik.eik_tune([d], [eik.make_instance(I.F, I.src_ij, I.sq, U)])
     assert rc == eik.EIK_EINVAL  # the tuning table holds the cell solver's schedules
+
+
+def test_fmsm_in_fixed_batch_and_server(eik, orc):
+    """FMSM grids mixed with HCM grids: a fixed batch replayed from its
+    captured graph (run twice) and the serving loop each give every FMSM grid
+    its serial FMSM result and every HCM grid the exact solution."""
+    import time
+    insts = W.batch_mix(8, seed=43, n_lo=65, n_hi=220)
+    methods = [FMSM if e % 2 == 0 else eik.EIK_METHOD_HCM for e in range(len(insts))]
+    descs, ins, keep = [], [], []
+    for I, m in zip(insts, methods):
+        U = np.empty_like(I.F)
+        src = I.src_ij
+        keep.append((src, U))
+        descs.append(eik.make_desc(I.nx, I.ny, I.h, 8, eik.EIK_FP64, method=m))
+        ins.append(eik.make_instance(I.F, src, I.sq, U))
+
+    def verify(what):
+        for I, m, (_, U) in zip(insts, methods, keep):
+            if m == FMSM:
+                Uo, _ = orc.fmsm(I.F, I.h, I.si, I.sj, I.sq, 8)
+            else:
+                Uo = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+            fin = np.isfinite(Uo)
+            assert (np.isfinite(U) == fin).all(), (what, I.name)
+            assert np.abs(U[fin] - Uo[fin]).max(initial=0.0) <= 1e-12 * np.abs(Uo[fin]).max(), (what, I.name, m)
+
+    b = eik.eik_batch_create(descs, ins)
+    try:
+        for r in range(2):
+            for _, U in keep:
+                U[...] = np.nan
+            rc, sts = eik.eik_batch_run(b)
+            assert rc == 0
+            assert all(s.schedule & 8 for s in sts)  # replayed from the captured graph
+            assert all(bool(s.schedule & 16) == (m == FMSM) for s, m in zip(sts, methods))
+            verify(f"fixed batch run {r}")
+    finally:
+        eik.eik_batch_destroy(b)
+    for _, U in keep:
+        U[...] = np.nan
+    srv = eik.eik_server_create(1 << 30, 0)
+    try:
+        tickets = []
+        for d, i in zip(descs, ins):
+            rc, t = eik.eik_submit(srv, d, i)
+            assert rc == 0
+            tickets.append(t)
+        for t in tickets:
+            t0 = time.perf_counter()
+            while True:
+                rc, _ = eik.eik_poll(srv, t)
+                if rc != eik.EIK_EAGAIN:
+                    break
+                assert time.perf_counter() - t0 < 60
+                time.sleep(2e-4)
+            assert rc == 0
+    finally:
+        eik.eik_server_destroy(srv)
+    verify("server")
