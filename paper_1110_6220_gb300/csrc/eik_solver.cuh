@@ -323,11 +323,16 @@ template <> struct ModeTypes<MODE_F32> { using T = float; using FT = float; };
 template <> struct ModeTypes<MODE_DF> { using T = float2; using FT = float2; };
 
 // One warp works on one cell (two cells for k = 4).  Its lanes sweep the four
-// directions of Alg. FSM_order at the same time: LPD lanes per direction, each
-// lane owning k/LPD rows of the tile.  At wavefront step t the lanes of a
-// direction update the nodes of anti-diagonal t of that direction; lanes that
-// reach the same node in one step read the same inputs and write the same
-// value, so a pass of 2k-1 steps is four Gauss-Seidel sweeps, race free.
+// directions of Alg. FSM_order at the same time, LPD lanes per direction.  At
+// wavefront step t the lanes of a direction update the nodes of anti-diagonal
+// t of that direction.  For k <= 8 each lane owns one row of the tile (and
+// keeps that row's changed-node mask in a register); for k >= 16 lane u takes
+// the diagonal's nodes u, u + LPD, ...: every direction's diagonal t has the
+// same length, so a slot no lane needs is skipped by the whole warp (k = 16:
+// 46 slots a pass instead of 62), and changed nodes are marked by a byte
+// each.  Lanes that reach the same node in one step read the same inputs and
+// write the same value, so a pass of 2k-1 steps is four Gauss-Seidel sweeps,
+// race free.
 template <int MODE, int K>
 struct TileCfg {
     using T = typename ModeTypes<MODE>::T;    // a value of U
@@ -348,7 +353,8 @@ struct TileCfg {
     static constexpr int A128(int b) { return (b + 127) / 128 * 128; }
     static constexpr int F_OFF = A128(UBYTES);
     static constexpr int X_OFF = F_OFF + A128(FBYTES);
-    static constexpr int GROUP_BYTES = X_OFF + A128(XBYTES);
+    static constexpr int FL_OFF = X_OFF + A128(XBYTES);               // k >= 16: a changed flag per node
+    static constexpr int GROUP_BYTES = FL_OFF + A128(RPL > 1 ? K * K : 0);
     static constexpr int MASK_OFF = CPW * GROUP_BYTES;
     static constexpr int BAR_OFF = MASK_OFF + CPW * K * 8;
     static constexpr int WARP_BYTES = A128(BAR_OFF + 16);
@@ -685,18 +691,24 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
     // ---- passes of four concurrent directional sweeps until a pass
     // changes nothing or the fixed-point check finds nothing to improve
     // (FHCM: one pass of the flagged directions)
-    unsigned long long chg[C::RPL];
-#pragma unroll
-    for (int m = 0; m < C::RPL; ++m) chg[m] = 0ull;
+    // k <= 8: this lane's row mask of changed nodes; k >= 16: a byte per node
+    // of this visit, 1 once the node has changed (lanes of several directions
+    // that change one node in one step all store 1)
+    constexpr bool DIAG = C::RPL > 1;
+    unsigned long long chg = 0ull;
+    unsigned char* flags = wbase + g * C::GROUP_BYTES + C::FL_OFF;
+    if constexpr (DIAG) {
+        for (int e = 4 * dl; e < K * K; e += 4 * C::LPC) *reinterpret_cast<unsigned*>(flags + e) = 0u;
+        __syncwarp();
+    }
     int gsweeps = 0;
     bool gdone = c < 0;
     int s = 0;
     for (; s < C::MAX_PASSES && __ballot_sync(FULL, !gdone) != 0u; ++s) {
         bool changed = false;
         for (int t2 = 0; t2 < 2 * K - 1; ++t2) {
-#pragma unroll
-            for (int m = 0; m < C::RPL; ++m) {
-                const int j = rl + C::LPD * m;
+            if constexpr (!DIAG) {
+                const int j = rl;
                 const int jj = sy ? j : K - 1 - j;
                 const int ii2 = t2 - jj;
                 if (c >= 0 && (!FAST || dir_on) && ii2 >= 0 && ii2 < K) {
@@ -704,8 +716,28 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
                     T cand, old;
                     if (node_candidate<MODE, K>(tU, tF, tG, i, j, cand, old) && lt(cand, old)) {
                         tU[(j + 1) * C::BW + (i + 1)] = cand;
-                        chg[m] |= 1ull << i;
+                        chg |= 1ull << i;
                         changed = true;
+                    }
+                }
+            } else {
+                // anti-diagonal t2 (in sweep order): rows lo .. lo + len - 1
+                const int lo = t2 < K ? 0 : t2 - (K - 1);
+                const int len = (t2 < K ? t2 : K - 1) - lo + 1;
+#pragma unroll
+                for (int m = 0; m < C::RPL; ++m) {
+                    if (m * C::LPD < len) {  // the same for every lane
+                        const int u = rl + C::LPD * m;
+                        if (u < len && c >= 0 && (!FAST || dir_on)) {
+                            const int jj = lo + u, ii2 = t2 - jj;
+                            const int j = sy ? jj : K - 1 - jj, i = sx ? ii2 : K - 1 - ii2;
+                            T cand, old;
+                            if (node_candidate<MODE, K>(tU, tF, tG, i, j, cand, old) && lt(cand, old)) {
+                                tU[(j + 1) * C::BW + (i + 1)] = cand;
+                                flags[j * K + i] = 1;
+                                changed = true;
+                            }
+                        }
                     }
                 }
             }
@@ -759,12 +791,27 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
     PROF_MARK(4);
 
     // ---- changed-node masks per row: union over the four directions
-#pragma unroll
-    for (int m = 0; m < C::RPL; ++m) {
-        unsigned long long v = chg[m];
+    if constexpr (!DIAG) {
+        // the four directions' lanes of a row hold its masks
+        unsigned long long v = chg;
         v |= __shfl_xor_sync(FULL, v, C::LPD);
         v |= __shfl_xor_sync(FULL, v, 2 * C::LPD);
-        if (dir == 0) masks[g * K + rl + C::LPD * m] = v;
+        if (dir == 0) masks[g * K + rl] = v;
+    } else {
+        // from the flag bytes (0 or 1 each): eight bytes folded into their
+        // low eight bits by OR-ing shifted copies
+        for (int j = dl; j < K; j += C::LPC) {
+            unsigned long long v = 0ull;
+#pragma unroll
+            for (int i0 = 0; i0 < K; i0 += 8) {
+                unsigned long long x = *reinterpret_cast<const unsigned long long*>(flags + j * K + i0);
+                x |= x >> 7;
+                x |= x >> 14;
+                x |= x >> 28;
+                v |= (x & 0xffull) << i0;
+            }
+            masks[g * K + j] = v;
+        }
     }
     __syncwarp();
     // ---- write back the nodes that changed (coalesced across lanes)
