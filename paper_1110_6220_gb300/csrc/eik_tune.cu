@@ -81,7 +81,9 @@ int side_class(const eik_plan_desc* d, int n) {
 //    ms), and ~2048^2 grids hold for 4 us (2049^2 maze: 6.3 ms for 6.8 ms).
 Entry builtin(int prec, bool batch, int side) {
     if (prec == EIK_FP32_REFINE) {
-        Entry e{batch ? 16 : 8, 256.0, 16.0, 0.0, false, true};
+        // cells of 16 from ~4096^2 (4097^2 sin20: 18.3 vs 29.1 ms at k = 8;
+        // checkerboard+maze 23.6 vs 25.3 ms); at ~2048^2 k = 8 and 16 split
+        Entry e{batch || side >= 12 ? 16 : 8, 256.0, 16.0, 0.0, false, true};
         e.one_pass = true;
         if (!batch) e.hold_ns = side >= 12 ? 8000 : side == 11 ? 4000 : 0;
         return e;
