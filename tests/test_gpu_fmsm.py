@@ -169,3 +169,38 @@ def test_fmsm_in_fixed_batch_and_server(eik, orc):
     finally:
         eik.eik_server_destroy(srv)
     verify("server")
+
+
+def test_fmsm_degenerate_cases(eik, orc):
+    """Edge cases of the order and of the cells, each against the oracle:
+    a grid smaller than one cell, no sources (everything stays +inf), a
+    source on an obstacle, a source walled in (most of the grid unreachable,
+    its cells ordered last by index), and a grid one cell high."""
+    rng = np.random.default_rng(17)
+    cases = []
+    F = rng.uniform(0.5, 2.0, size=(5, 6))
+    cases.append(("one cell", F, 1.0 / 5, [2], [1], [0.0]))
+    F = rng.uniform(0.5, 2.0, size=(40, 33))
+    cases.append(("no sources", F, 1.0 / 39, [], [], []))
+    F = rng.uniform(0.5, 2.0, size=(60, 70))
+    F[30, 20] = 0.0
+    cases.append(("source on an obstacle", F, 1.0 / 69, [20, 50], [30, 10], [0.0, 0.25]))
+    F = rng.uniform(0.5, 2.0, size=(64, 64))
+    F[20:31, 20] = 0.0
+    F[20:31, 30] = 0.0
+    F[20, 20:31] = 0.0
+    F[30, 20:31] = 0.0
+    cases.append(("walled-in source", F, 1.0 / 63, [25], [25], [0.0]))
+    F = rng.uniform(0.5, 2.0, size=(7, 200))
+    cases.append(("one cell high", F, 1.0 / 199, [0, 199], [3, 6], [0.0, 0.0]))
+    for name, F, h, si, sj, sq in cases:
+        si, sj = np.array(si, np.int32), np.array(sj, np.int32)
+        sq = np.array(sq, np.float64)
+        U, st = eik.solve(F, h, si, sj, sq, cell_k=8, method=FMSM)
+        assert st.status == 0, name
+        Uo, so = orc.fmsm(F, h, si, sj, sq, 8)
+        fin = np.isfinite(Uo)
+        assert (np.isfinite(U) == fin).all(), name
+        if fin.any():
+            assert np.abs(U[fin] - Uo[fin]).max() <= 1e-12 * np.abs(Uo[fin]).max(), name
+        assert abs(round(st.avs * so["cells"]) - so["sweeps"]) <= max(len(si), 1), name
