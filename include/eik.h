@@ -157,7 +157,8 @@ int eik_plan_create(eik_plan* out, const eik_plan_desc* d, void* cuda_stream);
 /* Release a plan and its device workspace.  NULL is ignored. */
 void eik_plan_destroy(eik_plan p);
 
-/* Bytes of device workspace a plan for *d would hold (0 if *d is invalid). */
+/* Bytes of device workspace a plan for *d would hold (0 if *d is invalid);
+ * for EIK_METHOD_FMSM this includes the coarse grid's solve. */
 size_t eik_plan_workspace_bytes(const eik_plan_desc* d);
 
 /* Solve one instance on the plan's grid shape; blocks until U is written.

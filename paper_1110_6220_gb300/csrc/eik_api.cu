@@ -517,13 +517,41 @@ int run_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance* 
 }  // namespace eik
 
 // ================================================================= plans
-extern "C" size_t eik_plan_workspace_bytes(const eik_plan_desc* d) {
-    if (!desc_valid(d)) return 0;
+namespace {
+// Arena bytes of a one-instance job for *d (build_job's layout, rounded up)
+size_t job_bytes(const eik_plan_desc* d) {
     const Layout L = make_layout(d->nx, d->ny, default_k(d));
     const bool fp32 = d->precision == EIK_FP32_REFINE;
     size_t Q = 8192;
     while (Q < 16 * (size_t)L.J) Q <<= 1;
-    return inst_bytes(L, fp32, true, true) + (size_t)L.J * 16 + Q * 8 + 128 * 1024;
+    size_t b = inst_bytes(L, fp32, true, true) + (size_t)L.J * 16 + Q * 8 + 128 * 1024;
+    if (d->method == EIK_METHOD_FMSM) b += (size_t)L.J * 16 + 512;  // coarse speeds and values
+    return b;
+}
+// FMSM: the descriptor of the coarse grid's job (as build_job forms it)
+eik_plan_desc coarse_desc(const eik_plan_desc* d) {
+    const int k = default_k(d);
+    const Layout L = make_layout(d->nx, d->ny, k);
+    eik_plan_desc c = *d;
+    c.nx = L.cxn;
+    c.ny = L.cyn;
+    c.h = d->h * k;
+    c.cell_k = 0;
+    c.bucket_width = 0.0;
+    c.precision = EIK_FP64;
+    c.method = EIK_METHOD_HCM;
+    return c;
+}
+}  // namespace
+
+extern "C" size_t eik_plan_workspace_bytes(const eik_plan_desc* d) {
+    if (!desc_valid(d)) return 0;
+    size_t b = job_bytes(d);
+    if (d->method == EIK_METHOD_FMSM) {
+        const eik_plan_desc c = coarse_desc(d);
+        b += job_bytes(&c);
+    }
+    return b;
 }
 
 extern "C" int eik_plan_create(eik_plan* out, const eik_plan_desc* d, void* cuda_stream) {
@@ -555,8 +583,14 @@ extern "C" int eik_plan_create(eik_plan* out, const eik_plan_desc* d, void* cuda
     if (cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess) rc = EIK_ECUDA;
     for (int e = 0; e < 4 && !rc; ++e)
         if (cudaEventCreate(&p->pev[e]) != cudaSuccess) rc = EIK_ECUDA;
-    // reserve the workspace now, so that solves do not allocate
-    if (!rc) rc = grow(&p->job.arena, eik_plan_workspace_bytes(&p->d));
+    // reserve the workspace now, so that solves do not allocate (FMSM: the
+    // coarse grid's job too)
+    if (!rc) rc = grow(&p->job.arena, job_bytes(&p->d));
+    if (!rc && p->d.method == EIK_METHOD_FMSM) {
+        p->job.coarse = new (std::nothrow) HostJob();
+        const eik_plan_desc c = coarse_desc(&p->d);
+        rc = p->job.coarse ? grow(&p->job.coarse->arena, job_bytes(&c)) : EIK_ENOMEM;
+    }
     if (rc) {
         cudaGetLastError();
         eik_plan_destroy(p);
