@@ -234,11 +234,12 @@ __device__ __forceinline__ float2 update_df(float2 W, float2 E, float2 S, float2
     const bool ab = lt(a, b);
     const float2 lo = ab ? a : b, hi = ab ? b : a;
     const float INF = inf_of<float>();
-    const float2 one = df_add(lo, f);
     const float d = (hi.x - lo.x) + (hi.y - lo.y);
     const bool two_sided = hi.x < INF && d < f.x;
-    const float2 two = df_add_f(hi, increment_f32(two_sided ? d : 0.0f, f.x));
-    const float2 r = two_sided ? two : one;
+    // one pair sum for both branches: hi + increment (two-sided), lo + f
+    // (one-sided); adding a pair whose low part is 0 equals df_add_f
+    const float inc = increment_f32(two_sided ? d : 0.0f, f.x);
+    const float2 r = df_add(two_sided ? hi : lo, two_sided ? make_float2(inc, 0.0f) : f);
     return lo.x < INF ? r : make_float2(INF, 0.0f);
 }
 
@@ -695,7 +696,10 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
     // of this visit, 1 once the node has changed (lanes of several directions
     // that change one node in one step all store 1)
     constexpr bool DIAG = C::RPL > 1;
-    unsigned long long chg = 0ull;
+    unsigned chg = 0u;  // k <= 8: bit i of this lane's row
+    // k <= 8: this lane's row, in sweep order (live at steps jr .. jr + K - 1)
+    const int jr = sy ? rl : K - 1 - rl;
+    const bool lane_on = c >= 0 && (!FAST || dir_on);
     unsigned char* flags = wbase + g * C::GROUP_BYTES + C::FL_OFF;
     if constexpr (DIAG) {
         for (int e = 4 * dl; e < K * K; e += 4 * C::LPC) *reinterpret_cast<unsigned*>(flags + e) = 0u;
@@ -708,15 +712,13 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
         bool changed = false;
         for (int t2 = 0; t2 < 2 * K - 1; ++t2) {
             if constexpr (!DIAG) {
-                const int j = rl;
-                const int jj = sy ? j : K - 1 - j;
-                const int ii2 = t2 - jj;
-                if (c >= 0 && (!FAST || dir_on) && ii2 >= 0 && ii2 < K) {
-                    const int i = sx ? ii2 : K - 1 - ii2;
+                const unsigned ii2 = (unsigned)(t2 - jr);
+                if (lane_on && ii2 < (unsigned)K) {
+                    const int j = rl, i = sx ? (int)ii2 : K - 1 - (int)ii2;
                     T cand, old;
                     if (node_candidate<MODE, K>(tU, tF, tG, i, j, cand, old) && lt(cand, old)) {
                         tU[(j + 1) * C::BW + (i + 1)] = cand;
-                        chg |= 1ull << i;
+                        chg |= 1u << i;
                         changed = true;
                     }
                 }
@@ -793,7 +795,7 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
     // ---- changed-node masks per row: union over the four directions
     if constexpr (!DIAG) {
         // the four directions' lanes of a row hold its masks
-        unsigned long long v = chg;
+        unsigned v = chg;
         v |= __shfl_xor_sync(FULL, v, C::LPD);
         v |= __shfl_xor_sync(FULL, v, 2 * C::LPD);
         if (dir == 0) masks[g * K + rl] = v;
