@@ -238,8 +238,9 @@ typedef struct {
     int32_t async_main;    /* 1: the FP64 / refinement pass runs round-free */
     int32_t one_pass;      /* FP32_REFINE: 1 = one double-float pass from the sources, 0 = an
                               FP32 pass, then a refinement pass seeded from it */
-    int32_t hold_ns;       /* round-free: a taken cell waits until this long after its latest
-                              request, so that several upstream changes merge into one visit */
+    int32_t hold_ns;       /* round-free: a taken cell younger than this (since its latest
+                              request) goes back to the ring's tail and the warp takes the
+                              next, so that several upstream changes merge into one visit */
     double ms;             /* device time of the job with the chosen values */
     double ms_before;      /* device time with the choice in force before */
     int32_t trials;        /* solves run */

@@ -106,8 +106,8 @@ struct SolveParams {
     long long deadline_ns;        // relative to kernel start
     int profile;                  // accumulate gctl->prof
     int fhcm;                     // Fast Heap-Cell Method: one sweep per flagged direction
-    // round-free schedule: a taken cell waits until hold_ns after its latest
-    // request before it runs, so that requests from several upstream
+    // round-free schedule: a taken cell requested less than hold_ns ago goes
+    // back to the ring's tail, so that requests from several upstream
     // neighbours merge into one visit (req_time: request times, per cell)
     unsigned hold_ns;
     unsigned long long* req_time;

@@ -1333,12 +1333,18 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
         if (lane == 0) e = ring_pop(p, gctl, deadline);
         e = __shfl_sync(FULL, e, 0);
         if (e < 0) break;
-        if (p.hold_ns && lane == 0) {
-            // hold the cell until hold_ns after its latest request (0: none
-            // recorded, no hold); the wait ends by that time whatever else
-            const unsigned long long until = __ldcg(&p.req_time[e]) + p.hold_ns;
-            for (unsigned long long now = gtimer(); now < until && until - now <= p.hold_ns; now = gtimer())
-                __nanosleep(100);
+        if (p.hold_ns) {
+            // a cell requested less than hold_ns ago (0: no time recorded)
+            // goes back to the ring's tail, still requested, and the warp
+            // takes the next one: requests from several upstream neighbours
+            // merge into one visit without the warp idling
+            int young = 0;
+            if (lane == 0) {
+                const unsigned long long t = __ldcg(&p.req_time[e]), now = gtimer();
+                young = t != 0ull && now < t + p.hold_ns && t + p.hold_ns - now <= p.hold_ns;
+                if (young) ring_push(p, gctl, (unsigned)e, deadline);
+            }
+            if (__shfl_sync(FULL, young, 0)) continue;
         }
         __syncwarp();
         const int ii = find_inst(p.cell_pre, NI, e);
