@@ -482,3 +482,44 @@ def test_fmsm_reproduces_tab_sinu_1(orc):
         if row["k"] != 32:
             assert abs(rho / row["rho"] - 1) < 0.01, (row, rho)
         assert abs(st["avs"] / row["avs"] - 1) < 0.015, (row, st["avs"])
+
+
+@pytest.mark.slow
+def test_cell_methods_reproduce_tab_checker_11(orc):
+    """Tab. checker_11 (Sec. 5, Checkerboards): a discontinuous speed, where
+    the cell methods' statistics are reproduced: HCM's removals per cell
+    within 1%; FHCM's removals and sweeps per cell within 2%, its
+    Monotonicity Check rate within 1 point and its error ratios (average and
+    ratio of maximum errors) at 1 like the paper's; FMSM's sweeps per cell
+    within 1% and its average error ratio within 1% for cells of 16 and 8."""
+    with open(os.path.join(GOLD, "paper_checker11.json")) as fh:
+        gold = json.load(fh)
+    n = gold["n"]
+
+    def inst(m):
+        I = W.sin_point(m)
+        I.F = W.checker_field(m, 11)
+        return I
+    I, J = inst(n), inst(4 * (n - 1) + 1)
+    V = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+    truth = orc.fmm(J.F, J.h, J.si, J.sj, J.sq)[::4, ::4]
+    e = np.abs(V - truth)
+    m = e > 0
+
+    def ratios(X):
+        E = np.abs(X - truth)
+        return (E[m] / e[m]).mean(), E.max() / e.max()
+    for row in gold["rows"]:
+        k = row["k"]
+        _, sh = orc.cells(I.F, I.h, I.si, I.sj, I.sq, k, fast=False)
+        Uf, sf = orc.cells(I.F, I.h, I.si, I.sj, I.sq, k, fast=True)
+        Um, sm = orc.fmsm(I.F, I.h, I.si, I.sj, I.sq, k)
+        assert abs(sh["avhr"] / row["hcm_avhr"] - 1) < 0.01, (row, sh)
+        assert abs(sf["avhr"] / row["fhcm_avhr"] - 1) < 0.02, (row, sf)
+        assert abs(sf["avs"] / row["fhcm_avs"] - 1) < 0.02, (row, sf)
+        assert abs(sf["mon_pct"] - row["mon_pct"]) < 1.0, (row, sf)
+        rho, rmax = ratios(Uf)
+        assert abs(rho - row["fhcm_rho"]) < 1e-3 and abs(rmax - row["fhcm_Rmax"]) < 1e-3, (row, rho, rmax)
+        assert abs(sm["avs"] / row["fmsm_avs"] - 1) < 0.01, (row, sm["avs"])
+        if k in (16, 8):
+            assert abs(ratios(Um)[0] / row["fmsm_rho"] - 1) < 0.01, (row, ratios(Um))
