@@ -85,7 +85,9 @@ Entry builtin(int prec, bool batch, int side) {
         // checkerboard+maze 23.6 vs 25.3 ms); at ~2048^2 k = 8 and 16 split
         Entry e{batch || side >= 12 ? 16 : 8, 256.0, 16.0, 0.0, false, true};
         e.one_pass = true;
-        if (!batch) e.hold_ns = side >= 12 ? 8000 : side == 11 ? 4000 : 0;
+        // holds (a young cell goes back to the ring): 4097^2 20 us (maze
+        // 21.9 -> 20.4 ms, sin20 17.3 -> 14.3 ms against 8 us), 2049^2 4 us
+        if (!batch) e.hold_ns = side >= 12 ? 20000 : side == 11 ? 4000 : 0;
         return e;
     }
     if (batch || side <= 8) return Entry{8, 4.0, 4.0, 0.0, false, true};
