@@ -70,11 +70,12 @@ int side_class(const eik_plan_desc* d, int n) {
 //    a refinement pass seeded everywhere revisits it on every upstream change;
 //  - FP64 stays on rounds: round-free, it visits each cell 4-5x as often, and
 //    FP64 visits are the costly ones.
-//  - single grids of about 4096^2 and more hold each round-free cell until
-//    8 us after its latest request: on the 4097^2 checkerboard + maze the
-//    requests of several upstream neighbours then merge into one visit
-//    (21 visits per cell instead of 39, 23.7 ms instead of 33.8 ms); on
-//    1025^2 and on the batch the hold saved nothing or cost time.
+//  - single grids of about 4096^2 and more hold each round-free cell: a
+//    cell requested less than the hold ago goes back to the ring, so the
+//    requests of several upstream neighbours merge into one visit (first
+//    measured with the warp waiting instead: 8 us took the 4097^2
+//    checkerboard + maze from 39 visits per cell to 21, 33.8 ms to 23.7 ms);
+//    on 1025^2 and on the batch a hold saves nothing or costs time.
 //  - the tuner (eik_tune) on each class then moved three choices: FP64
 //    batches run round-free at k = 8 (46.2 ms instead of 75.8 ms on the
 //    512-grid mix), small FP64 grids too (129^2: 0.32 ms instead of 0.37
@@ -276,7 +277,7 @@ extern "C" int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t 
         H.async_first = chosen.async_first;
         H.async_main = true;
         H.one_pass = chosen.one_pass;
-        for (unsigned hold : {4000u, 8000u, 16000u}) {
+        for (unsigned hold : {4000u, 8000u, 16000u, 24000u}) {
             H.hold_ns = hold;
             float t[3];
             if (trial(H, t) == EIK_OK && t[0] < chosen.ms) {
