@@ -68,8 +68,9 @@ int side_class(const eik_plan_desc* d, int n) {
 //    A double-float visit costs about a quarter of an FP64 one (the FP64 pipe
 //    is slow), and a pass from the sources visits each cell a few times where
 //    a refinement pass seeded everywhere revisits it on every upstream change;
-//  - FP64 stays on rounds: round-free, it visits each cell 4-5x as often, and
-//    FP64 visits are the costly ones.
+//  - FP64 first stayed on rounds: round-free, it visits each cell 4-5x as
+//    often, and FP64 visits are the costly ones; once a hold could merge
+//    requests without idling warps, round-free won from ~1024^2 (below).
 //  - single grids of about 4096^2 and more hold each round-free cell: a
 //    cell requested less than the hold ago goes back to the ring, so the
 //    requests of several upstream neighbours merge into one visit (first
@@ -80,7 +81,7 @@ int side_class(const eik_plan_desc* d, int n) {
 //    batches run round-free at k = 8 (46.2 ms instead of 75.8 ms on the
 //    512-grid mix), small FP64 grids too (129^2: 0.32 ms instead of 0.37
 //    ms), and ~2048^2 grids hold for 4 us (2049^2 maze: 6.3 ms for 6.8 ms).
-Entry builtin(int prec, bool batch, int side) {
+Entry builtin(int prec, bool batch, int side, bool fhcm) {
     if (prec == EIK_FP32_REFINE) {
         // cells of 16 from ~4096^2 (4097^2 sin20: 18.3 vs 29.1 ms at k = 8;
         // checkerboard+maze 23.6 vs 25.3 ms); at ~2048^2 k = 8 and 16 split
@@ -92,7 +93,17 @@ Entry builtin(int prec, bool batch, int side) {
         return e;
     }
     if (batch || side <= 8) return Entry{8, 4.0, 4.0, 0.0, false, true};
-    return Entry{8, 256.0, 256.0, 0.0};
+    // one FP64 grid: with a hold (a young cell goes back to the ring) the
+    // round-free schedule beats rounds from ~1024^2 (1025^2 sin20 3.68 ->
+    // 3.35 ms at 4 us; 2049^2 sin20 10.9 -> 9.3 ms and maze 14.0 -> 11.9 ms at
+    // 16 us; 4097^2 sin20 43.7 -> 36.7 ms, maze 40.9 -> 41.8 ms); at ~512^2 it
+    // splits (sin20 1.79 -> 1.66 ms, maze 5.33 -> 5.49 ms), rounds stay
+    // FHCM's one-sweep visits gain less from merged requests: rounds
+    // (1025^2 sin20 2.72 ms, against 2.92 ms round-free with a 4 us hold)
+    if (side == 9 || fhcm) return Entry{8, 256.0, 256.0, 0.0};
+    Entry e{8, 256.0, 256.0, 0.0, false, true};
+    e.hold_ns = side == 10 ? 4000 : 16000;
+    return e;
 }
 
 int load_file(const char* path) {
@@ -142,7 +153,7 @@ JobParams choose_params(const eik_plan_desc* d, int n) {
     const int prec = d[0].precision;
     const bool batch = n > 1;
     const int side = side_class(d, n);
-    Entry e = builtin(prec, batch, side);
+    Entry e = builtin(prec, batch, side, d[0].method == EIK_METHOD_FHCM);
     {
         std::lock_guard<std::mutex> lock(g_mu);
         maybe_load_env();
