@@ -286,27 +286,27 @@ __device__ __forceinline__ float2 df_increment(float2 d, float2 f) {
 
 // FP64: U = hi + increment, with the increment -- at most sqrt 2 f, so a
 // few units of 2^-46 relative to it are ~1e-14 f -- in double-float
-// arithmetic on the FP32 pipe.  Only the base, the difference d = hi - lo
-// and the sums run on the FP64 pipe (four adds, no square root or division),
-// which on GB300 runs at 1/64 of the FP32 rate.  fp: f as a pair, (0, 0)
+// arithmetic on the FP32 pipe.  Only the difference d = hi - lo and the
+// sums run on the FP64 pipe (three adds, no square root or division; one
+// final add serves both branches), which on GB300 runs at 1/64 of the FP32
+// rate.  fp: f as a pair, (0, 0)
 // where f lies outside [2^-40, 2^40] (the pair products would leave the
 // float range): the update then takes the FP64 root.
 __device__ __forceinline__ double update_f64(double W, double E, double S, double N, double f, float2 fp) {
     const long long a = min(ob(W), ob(E)), b = min(ob(S), ob(N));
     const long long lob = min(a, b), hib = max(a, b);
     const double lo = from_ob(lob), hi = from_ob(hib);
-    const double one = lo + f;
     const double d = hi - lo;  // finite whenever hi is
     const bool two_sided = hib < INF_BITS64 && ob(d) < ob(f);
     float2 dp;
     if (!split_pos(d, &dp)) dp = make_float2(0.0f, 0.0f);  // d < 2^-74 (or not two-sided)
     const float2 inc = df_increment(dp, fp);
-    double two = hi + (widen(inc.x) + widen(inc.y));
     if (two_sided && fp.x == 0.0f) {
         const double s = sqrt(fma(-d, d, 2.0 * f * f));
-        two = fma(0.5, s - d, hi);
+        return fma(0.5, s - d, hi);
     }
-    return two_sided ? two : one;
+    // hi + increment (two-sided), lo + f (one-sided)
+    return (two_sided ? hi : lo) + (two_sided ? widen(inc.x) + widen(inc.y) : f);
 }
 // f as the pair update_f64 takes
 __device__ __forceinline__ float2 f64_pair(double f) {
