@@ -1241,8 +1241,12 @@ __device__ __forceinline__ int ring_pop(const SolveParams& p, Ctl* gctl, unsigne
     return (int)(unsigned)v;
 }
 
+// The double-float kernels at k = 8 and 16 are held to three blocks per SM:
+// left alone, the compiler fits them into 64 registers (four blocks) with
+// spills, which measured slower (1025^2: 1.86 against 1.73 ms per pass; the
+// 512-grid batch 14.1 against 13.9 ms).  0 leaves the others to the compiler.
 template <int MODE, int K, bool FAST>
-__global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
+__global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32, (MODE == MODE_DF && (K == 8 || K == 16)) ? 3 : 0)
     k_solve_async(const __grid_constant__ SolveParams p) {
     using C = TileCfg<MODE, K>;
     static_assert(C::CPW == 1, "one cell per warp");
