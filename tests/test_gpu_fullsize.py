@@ -1,0 +1,89 @@
+"""The benchmark's own workloads at full size, in the launch configuration
+bench.py times (cell_k = 0: the built-in choice of k, form, schedule and
+hold), against the oracle: the 1025^2 sin20 grid and the 4097^2
+checkerboard+maze grid in FP32 + refinement node by node, and the 512-grid
+batch as a fixed batch replayed from its graph, every 32nd grid node by
+node.  FP32 + refinement: within 1e-5 of max |U| (the stated tolerance),
+within the solve's own certificate, and below 5e-8 (the accuracy the
+double-float pass reaches, so a wrong f or update would show); +inf
+exactly."""
+import numpy as np
+import pytest
+
+from paper_1110_6220_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def eik():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1110_6220_gb300 import build
+    build.build()
+    from paper_1110_6220_gb300 import eik as e
+    e.eik_tune_reset()
+    return e
+
+
+def _check(U, V, bound, what):
+    fin = np.isfinite(V)
+    assert (np.isfinite(U) == fin).all(), f"{what}: +inf pattern differs"
+    rel = np.abs(U[fin] - V[fin]).max() / np.abs(V[fin]).max()
+    assert rel <= TOL32, (what, rel)
+    assert rel <= max(bound, 1e-15) * 1.0001, (what, rel, bound)
+    assert rel <= 5e-8, (what, rel)
+    return rel
+
+
+def _solve_device(eik, I, prec):
+    import torch
+    F = torch.from_numpy(I.F).cuda()
+    src = torch.from_numpy(I.src_ij).cuda()
+    q = torch.from_numpy(np.ascontiguousarray(I.sq)).cuda()
+    U = torch.empty_like(F)
+    with eik.Plan(I.nx, I.ny, I.h, 0, prec) as p:
+        rc, st = p.solve(F, src, q, U)
+    assert rc == 0, eik.eik_strerror(rc)
+    return U.cpu().numpy(), st
+
+
+def test_sin1025_fp32ref_as_benchmarked(eik, orc):
+    I = W.sin_point(1025)
+    U, st = _solve_device(eik, I, eik.EIK_FP32_REFINE)
+    assert st.cell_k == 8 and st.schedule & 2 and st.schedule & 4  # one round-free double-float pass
+    _check(U, orc.fmm(I.F, I.h, I.si, I.sj, I.sq), st.err_bound, "sin1025")
+
+
+def test_checker_maze4097_fp32ref_as_benchmarked(eik, orc):
+    I = W.checker_maze(4097)
+    U, st = _solve_device(eik, I, eik.EIK_FP32_REFINE)
+    assert st.cell_k == 16 and st.schedule & 2
+    V = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+    assert np.isinf(V).any()  # the maze leaves pockets unreachable
+    _check(U, V, st.err_bound, "checkermaze4097")
+
+
+def test_batch512_fixed_batch_as_benchmarked(eik, orc):
+    import torch
+    insts = W.batch_mix(512, seed=1)
+    dev, descs = [], []
+    for I in insts:
+        F = torch.from_numpy(I.F).cuda()
+        ij = torch.from_numpy(I.src_ij).cuda()
+        q = torch.from_numpy(np.ascontiguousarray(I.sq)).cuda()
+        dev.append((F, ij, q, torch.empty_like(F)))
+        descs.append(eik.make_desc(I.nx, I.ny, I.h, 0, eik.EIK_FP32_REFINE))
+    b = eik.eik_batch_create(descs, [eik.make_instance(*d) for d in dev])
+    try:
+        for _ in range(2):  # the second run replays the captured graph on the same buffers
+            rc, sts = eik.eik_batch_run(b)
+            assert rc == 0, eik.eik_strerror(rc)
+    finally:
+        eik.eik_batch_destroy(b)
+    assert all(s.schedule & 8 for s in sts) and sts[0].cell_k == 16
+    for e in range(0, len(insts), 32):
+        I = insts[e]
+        _check(dev[e][3].cpu().numpy(), orc.fmm(I.F, I.h, I.si, I.sj, I.sq), sts[e].err_bound, f"batch[{e}] {I.name}")
