@@ -87,3 +87,45 @@ def test_batch512_fixed_batch_as_benchmarked(eik, orc):
     for e in range(0, len(insts), 32):
         I = insts[e]
         _check(dev[e][3].cpu().numpy(), orc.fmm(I.F, I.h, I.si, I.sj, I.sq), sts[e].err_bound, f"batch[{e}] {I.name}")
+
+
+def test_serving_stream_as_benchmarked(eik, orc):
+    """The serving workload: the 128-request Poisson stream (sides
+    log-uniform in [129, 2049], three speed kinds) submitted at once to a
+    server with a 64 GB budget; every request completes, and every 16th is
+    compared node by node with the oracle."""
+    import time
+    import torch
+    stream = W.poisson_stream(128, 1.0, seed=5)
+    insts = [I for _, I in stream]
+    dev = []
+    for I in insts:
+        F = torch.from_numpy(I.F).cuda()
+        dev.append((F, torch.from_numpy(I.src_ij).cuda(), torch.from_numpy(np.ascontiguousarray(I.sq)).cuda(),
+                    torch.empty_like(F)))
+    descs = [eik.make_desc(I.nx, I.ny, I.h, 0, eik.EIK_FP32_REFINE) for I in insts]
+    ins = [eik.make_instance(*d) for d in dev]
+    torch.cuda.synchronize()
+    srv = eik.eik_server_create(64 << 30, len(insts))
+    sts = {}
+    try:
+        tickets = []
+        for d, i in zip(descs, ins):
+            rc, t = eik.eik_submit(srv, d, i)
+            assert rc == 0, eik.eik_strerror(rc)
+            tickets.append(t)
+        t0 = time.perf_counter()
+        for e, t in enumerate(tickets):
+            while True:
+                rc, st = eik.eik_poll(srv, t)
+                if rc != eik.EIK_EAGAIN:
+                    break
+                assert time.perf_counter() - t0 < 120
+                time.sleep(2e-4)
+            assert rc == 0, eik.eik_strerror(rc)
+            sts[e] = st
+    finally:
+        eik.eik_server_destroy(srv)
+    for e in range(0, len(insts), 16):
+        I = insts[e]
+        _check(dev[e][3].cpu().numpy(), orc.fmm(I.F, I.h, I.si, I.sj, I.sq), sts[e].err_bound, f"request {e} {I.name}")
