@@ -211,7 +211,7 @@ cudaError_t launch_residual(const AuxInst* a, const int* blk_pre, int n, int nbl
 cudaError_t launch_fmsm_coarse_speed(const AuxInst* a, const int* cell_pre, int n, int ncells, cudaStream_t st);
 cudaError_t launch_fmsm_prep(const AuxInst* a, const int* cell_pre, int n, int ncells, unsigned long long* ring,
                              unsigned* qctl, cudaStream_t st);
-int fmsm_shape(int k, int num_sms, int sm_cap, LaunchShape* out);
+int fmsm_shape(int k, int num_sms, int n_inst, int sm_cap, LaunchShape* out);
 cudaError_t launch_fmsm(int k, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
 cudaError_t launch_output(const AuxInst* a, const int* blk_pre, int n, int nblocks, cudaStream_t st);
 

@@ -297,8 +297,12 @@ __global__ void __launch_bounds__(TileCfg<MODE_F64, K>::WPB * 32)
     }
 }
 
+// One grid: a block per SM.  Only about a hundred cells are ready at a time,
+// and the waiting warps' polling slowed the working ones (1025^2 sin20 at
+// k = 8: 3.46 ms at the occupancy limit, 3.30 ms at two blocks per SM, 3.27
+// ms at one).  A batch keeps the occupancy limit.
 template <int K>
-void shape_fmsm(int num_sms, int sm_cap, LaunchShape* s) {
+void shape_fmsm(int num_sms, int n_inst, int sm_cap, LaunchShape* s) {
     using C = TileCfg<MODE_F64, K>;
     const void* fn = (const void*)k_solve_fmsm<K>;
     s->threads = C::WPB * 32;
@@ -314,7 +318,7 @@ void shape_fmsm(int num_sms, int sm_cap, LaunchShape* s) {
         cudaGetLastError();
         per_sm = 0;
     }
-    int cap = per_sm;
+    int cap = n_inst > 1 || per_sm < 1 ? per_sm : 1;
     if (sm_cap > 0 && sm_cap < cap) cap = sm_cap;
     s->blocks = cap * num_sms;
     s->per_sm = per_sm;
@@ -333,13 +337,13 @@ cudaError_t launch_fmsm_prep(const AuxInst* a, const int* cell_pre, int n, int n
     return cudaGetLastError();
 }
 
-int fmsm_shape(int k, int num_sms, int sm_cap, LaunchShape* out) {
+int fmsm_shape(int k, int num_sms, int n_inst, int sm_cap, LaunchShape* out) {
     out->blocks = 0;
     switch (k) {
-    case 8: shape_fmsm<8>(num_sms, sm_cap, out); break;
-    case 16: shape_fmsm<16>(num_sms, sm_cap, out); break;
-    case 32: shape_fmsm<32>(num_sms, sm_cap, out); break;
-    case 64: shape_fmsm<64>(num_sms, sm_cap, out); break;
+    case 8: shape_fmsm<8>(num_sms, n_inst, sm_cap, out); break;
+    case 16: shape_fmsm<16>(num_sms, n_inst, sm_cap, out); break;
+    case 32: shape_fmsm<32>(num_sms, n_inst, sm_cap, out); break;
+    case 64: shape_fmsm<64>(num_sms, n_inst, sm_cap, out); break;
     default: return -1;
     }
     return out->blocks > 0 ? 0 : -1;

@@ -262,7 +262,7 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
         if (launch_fmsm_prep(j.aux, j.cell_pre, n, j.ncells, j.ring, j.qctl, st) != cudaSuccess)
             return EIK_ECUDA;
         ++nl;
-        if (fmsm_shape(j.k, num_sms, j.sm_cap, &shape)) return EIK_ECUDA;
+        if (fmsm_shape(j.k, num_sms, n, j.sm_cap, &shape)) return EIK_ECUDA;
         p.inst = j.desc_main;
         p.gctl = j.gctl + 1;
         if (ev) cudaEventRecord(ev[2], st);
@@ -289,7 +289,7 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
 bool job_pairable(const JobDev& j, int num_sms) {
     LaunchShape a{}, b{};
     if (j.fmsm) {
-        if (fmsm_shape(j.k, num_sms, 1, &a) || !j.coarse || !job_pairable(*j.coarse, num_sms)) return false;
+        if (fmsm_shape(j.k, num_sms, j.n, 1, &a) || !j.coarse || !job_pairable(*j.coarse, num_sms)) return false;
         return a.per_sm >= 2;
     }
     if (j.fp32 && j.one_pass) {
