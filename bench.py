@@ -286,10 +286,19 @@ def config_measure(eik, torch, I, prec, steps=5, k=0):
     fin = np.isfinite(V)
     err = float(np.abs(Ug[fin] - V[fin]).max() / np.abs(V[fin]).max())
     med = statistics.median(ms)
-    return {"grid": f"{I.nx}x{I.ny}", "precision": "fp64" if prec == eik.EIK_FP64 else "fp32ref",
-            "cell_k": st.cell_k, "ms": med, "value": I.npts / med / 1e3, "unit": UNIT,
-            "max_rel_err": err, "inf_pattern_exact": bool((np.isfinite(Ug) == fin).all()),
-            "err_bound": st.err_bound, "avhr": st.avhr, "schedule": st.schedule}
+    out = {"grid": f"{I.nx}x{I.ny}", "precision": "fp64" if prec == eik.EIK_FP64 else "fp32ref",
+           "cell_k": st.cell_k, "ms": med, "value": I.npts / med / 1e3, "unit": UNIT,
+           "max_rel_err": err, "inf_pattern_exact": bool((np.isfinite(Ug) == fin).all()),
+           "err_bound": st.err_bound, "avhr": st.avhr, "schedule": st.schedule}
+    if prec == eik.EIK_FP64:
+        # the FP64 pipe: three FP64 adds per node evaluation (the library's
+        # count of evaluations, lock-step passes included) against GB300's
+        # nominal FP64 rate, 1.25 TFLOP/s = 0.625 T instructions/s
+        adds = 3.0 * st.updates_per_pt * I.npts
+        out["fp64_pipe"] = {"bound": "alu", "achieved": adds / (med / 1e3) / 1e9, "peak": 625.0,
+                            "unit": "G FP64 instructions/s", "frac": adds / (med / 1e3) / 625e9,
+                            "peak_source": "of nominal", "updates_per_pt": st.updates_per_pt}
+    return out
 
 
 def fhcm_measure(eik, torch, I, steps=5):
