@@ -397,6 +397,101 @@ int orc_fsm(int nx, int ny, double h, const double *F, int nsrc, const int32_t *
 }
 
 /* ------------------------------------------------------------------ */
+/* Locking Sweeping, Sec. 3.2, Remark locking_FSM: Alg. FSM with a     */
+/* locking flag per node.                                              */
+/* ------------------------------------------------------------------ */
+
+/*
+ * One sweep in direction dir (Alg. FSM_order's numbering) over the nodes of
+ * the box [i0,i1) x [j0,j1) that are unlocked (unl[k] != 0).  Every node the
+ * sweep processes is locked; if its value decreases, each neighbour inside
+ * the box whose value is larger (the only ones whose update can use it) is
+ * unlocked.  Sources are never unlocked.  Returns 1 if a value changed; adds
+ * the local updates computed to *evals and keeps *n_unl, the number of
+ * unlocked nodes, current.
+ */
+static int sweep_locked(const problem *p, double *V, unsigned char *unl, int i0, int i1, int j0, int j1,
+                        int dir, int64_t *evals, int64_t *n_unl)
+{
+    const int i_up = dir <= 1, j_up = dir == 0 || dir == 3;
+    int changed = 0;
+    for (int ii = i0; ii < i1; ++ii) {
+        int i = i_up ? ii : i1 - 1 - (ii - i0);
+        for (int jj = j0; jj < j1; ++jj) {
+            int j = j_up ? jj : j1 - 1 - (jj - j0);
+            size_t k = (size_t)j * p->nx + i;
+            if (!unl[k]) continue;
+            unl[k] = 0;
+            --*n_unl;
+            double t = T_at(p, V, i, j);
+            ++*evals;
+            if (!(t < V[k])) continue;
+            V[k] = t;
+            changed = 1;
+            const int ni[4] = {i - 1, i + 1, i, i}, nj[4] = {j, j, j - 1, j + 1};
+            for (int e = 0; e < 4; ++e) {
+                if (ni[e] < i0 || ni[e] >= i1 || nj[e] < j0 || nj[e] >= j1) continue;
+                size_t kn = (size_t)nj[e] * p->nx + ni[e];
+                if (V[kn] > V[k] && !unl[kn] && !p->src[kn]) {
+                    unl[kn] = 1;
+                    ++*n_unl;
+                }
+            }
+        }
+    }
+    return changed;
+}
+
+/*
+ * LSM on the whole grid: every node starts locked except the non-source
+ * neighbours of sources; sweeps in the directions of Alg. FSM_order run
+ * while some node is unlocked.  The count of unlocked nodes stands in for
+ * the final sweep that would find them all locked, so *n_sweeps is one less
+ * than Alg. FSM's count or equal to it.  *n_evals: local updates computed.
+ */
+int orc_lsm(int nx, int ny, double h, const double *F, int nsrc, const int32_t *si,
+            const int32_t *sj, const double *sq, double *U, int32_t max_sweeps,
+            int32_t *n_sweeps, int64_t *n_evals)
+{
+    problem p;
+    int rc = problem_init(&p, nx, ny, h, F, nsrc, si, sj, sq);
+    if (rc)
+        return rc;
+    unsigned char *unl = (unsigned char *)calloc((size_t)nx * ny, 1);
+    if (!unl) {
+        problem_free(&p);
+        return ORC_ENOMEM;
+    }
+    init_values(&p, U);
+    int64_t n_unl = 0, evals = 0;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            if (!p.src[(size_t)j * nx + i]) continue;
+            const int ni[4] = {i - 1, i + 1, i, i}, nj[4] = {j, j, j - 1, j + 1};
+            for (int e = 0; e < 4; ++e) {
+                if (ni[e] < 0 || ni[e] >= nx || nj[e] < 0 || nj[e] >= ny) continue;
+                size_t kn = (size_t)nj[e] * nx + ni[e];
+                if (!p.src[kn] && !unl[kn]) {
+                    unl[kn] = 1;
+                    ++n_unl;
+                }
+            }
+        }
+    int32_t sweep = 0;
+    while (n_unl > 0 && sweep < max_sweeps) {
+        sweep_locked(&p, U, unl, 0, nx, 0, ny, sweep % 4, &evals, &n_unl);
+        ++sweep;
+    }
+    if (n_sweeps)
+        *n_sweeps = sweep;
+    if (n_evals)
+        *n_evals = evals;
+    free(unl);
+    problem_free(&p);
+    return n_unl ? ORC_ENOTCONVERGED : ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* Jacobi "value iteration" from +inf (Sec. 2, eq. generic_value_it,   */
 /* applied to the system of eq. Eik_discr): every node is updated from */
 /* the previous iterate simultaneously, until nothing changes.         */
@@ -474,6 +569,15 @@ int orc_apply_T(int nx, int ny, double h, const double *F, int nsrc, const int32
 /*         no more (Alg. FHCM); an activation raises one of the two    */
 /*         flags when the boundary values on that side are monotone    */
 /*         (the Monotonicity Check), both otherwise.                   */
+/*   HCM with locking (Sec. 4.2, the Locking Sweeping version inside   */
+/*         cells): the sweeps of HCM, each processing only the cell's  */
+/*         unlocked nodes (Remark locking_FSM, as in orc_lsm), until   */
+/*         none is left.  At a removal the nodes next to another cell  */
+/*         start unlocked (their boundary data may have changed since  */
+/*         the cell's last removal; the rest of the cell was left at    */
+/*         its fixed point), and on the first removal also the nodes    */
+/*         next to a source of the cell.  The values, and hence the     */
+/*         removals, are those of HCM bit for bit.                      */
 /* The activation test and the cell values follow Alg. generic_LC_cells */
 /* and eq. cell_value: a node x_i on the border that changed during the */
 /* removal (or a source, on the cell's first removal) with V_i < V_j    */
@@ -543,11 +647,15 @@ static int sweep_cell(const problem *p, double *V, int i0, int i1, int j0, int j
     return changed;
 }
 
-/* stats: [0] cell removals, [1] sweeps, [2] monotone checks passed, [3] checks */
+/* stats: [0] cell removals, [1] sweeps, [2] monotone checks passed, [3] checks,
+ * [4] local updates computed (every non-source node of a cell per sweep, or
+ * the unlocked ones with locking) */
 int orc_cells(int nx, int ny, double h, const double *F, int nsrc, const int32_t *si, const int32_t *sj,
-              const double *sq, int k, int fast, double *U, int64_t *stats)
+              const double *sq, int k, int method, double *U, int64_t *stats)
 {
-    if (k < 1) return ORC_EINVAL;
+    /* method: 0 HCM, 1 FHCM, 2 HCM with locking */
+    if (k < 1 || method < 0 || method > 2) return ORC_EINVAL;
+    const int fast = method == 1, lsm = method == 2;
     problem p;
     int rc = problem_init(&p, nx, ny, h, F, nsrc, si, sj, sq);
     if (rc) return rc;
@@ -559,8 +667,9 @@ int orc_cells(int nx, int ny, double h, const double *F, int nsrc, const int32_t
     int32_t *hcell = (int32_t *)malloc((size_t)J * sizeof(int32_t));
     int32_t *hpos = (int32_t *)malloc((size_t)J * sizeof(int32_t));
     double *old = (double *)malloc((size_t)k * k * sizeof(double));
-    if (!cval || !flags || !removed || !hcell || !hpos || !old) {
-        free(cval); free(flags); free(removed); free(hcell); free(hpos); free(old);
+    unsigned char *unl = lsm ? (unsigned char *)calloc((size_t)nx * ny, 1) : NULL;
+    if (!cval || !flags || !removed || !hcell || !hpos || !old || (lsm && !unl)) {
+        free(cval); free(flags); free(removed); free(hcell); free(hpos); free(old); free(unl);
         problem_free(&p);
         return ORC_ENOMEM;
     }
@@ -587,7 +696,7 @@ int orc_cells(int nx, int ny, double h, const double *F, int nsrc, const int32_t
         flags[c] = 15;
     }
     for (int e = H.size / 2; e >= 0; --e) ch_down(&H, e);
-    int64_t removals = 0, sweeps = 0, mono_ok = 0, mono_n = 0;
+    int64_t removals = 0, sweeps = 0, mono_ok = 0, mono_n = 0, evals = 0;
     while (H.size > 0) {
         int c = hcell[0];
         H.size--;
@@ -606,6 +715,9 @@ int orc_cells(int nx, int ny, double h, const double *F, int nsrc, const int32_t
         for (int j = j0; j < j1; ++j)
             for (int i = i0; i < i1; ++i) old[(j - j0) * w + (i - i0)] = U[(size_t)j * nx + i];
         /* the sweeps */
+        int64_t free_nodes = 0;
+        for (int j = j0; j < j1; ++j)
+            for (int i = i0; i < i1; ++i) free_nodes += !p.src[(size_t)j * nx + i];
         const int fl = flags[c];
         flags[c] = 0;
         if (fast) {
@@ -613,7 +725,34 @@ int orc_cells(int nx, int ny, double h, const double *F, int nsrc, const int32_t
                 if (fl >> d & 1) {
                     sweep_cell(&p, U, i0, i1, j0, j1, d);
                     ++sweeps;
+                    evals += free_nodes;
                 }
+        } else if (lsm) {
+            int order[4], no = 0;
+            for (int d = 0; d < 4; ++d) if (fl >> d & 1) order[no++] = d;
+            for (int d = 0; d < 4; ++d) if (!(fl >> d & 1)) order[no++] = d;
+            int64_t n_unl = 0;
+            for (int j = j0; j < j1; ++j)
+                for (int i = i0; i < i1; ++i) {
+                    const size_t q = (size_t)j * nx + i;
+                    if (p.src[q]) continue;
+                    int u = (i == i0 && i > 0) || (i == i1 - 1 && i1 < nx) || (j == j0 && j > 0) ||
+                            (j == j1 - 1 && j1 < ny);
+                    if (!u && first)
+                        u = (i > i0 && p.src[q - 1]) || (i + 1 < i1 && p.src[q + 1]) ||
+                            (j > j0 && p.src[q - nx]) || (j + 1 < j1 && p.src[q + nx]);
+                    if (u) {
+                        unl[q] = 1;
+                        ++n_unl;
+                    }
+                }
+            int s = 0;
+            while (n_unl > 0) {
+                int d = s < 4 ? order[s] : s % 4;
+                sweep_locked(&p, U, unl, i0, i1, j0, j1, d, &evals, &n_unl);
+                ++s;
+            }
+            sweeps += s;
         } else {
             int order[4], no = 0;
             for (int d = 0; d < 4; ++d) if (fl >> d & 1) order[no++] = d;
@@ -625,6 +764,7 @@ int orc_cells(int nx, int ny, double h, const double *F, int nsrc, const int32_t
                 ++s;
             } while (changed);
             sweeps += s;
+            evals += s * free_nodes;
         }
         /* the four borders: W, E, S, N */
         for (int sd = 0; sd < 4; ++sd) {
@@ -697,8 +837,9 @@ int orc_cells(int nx, int ny, double h, const double *F, int nsrc, const int32_t
         stats[1] = sweeps;
         stats[2] = mono_ok;
         stats[3] = mono_n;
+        stats[4] = evals;
     }
-    free(cval); free(flags); free(removed); free(hcell); free(hpos); free(old);
+    free(cval); free(flags); free(removed); free(hcell); free(hpos); free(old); free(unl);
     problem_free(&p);
     return ORC_OK;
 }

@@ -6,7 +6,9 @@ Functions follow the paper (Chacon & Vladimirsky, "Fast two-scale methods for
 Eikonal equations"):
   * ``fmm``      -- Alg. FMM (Sec. 3.1), binary heap;
   * ``fsm``      -- Algs. FSM_order / FSM (Sec. 3.2), Gauss-Seidel in 4 directions;
-  * ``cells``    -- the Heap-Cell Methods HCM / FHCM (Secs. 4.2, 4.3);
+  * ``lsm``      -- the Locking Sweeping Method (Remark locking_FSM);
+  * ``cells``    -- the Heap-Cell Methods HCM / FHCM (Secs. 4.2, 4.3), HCM also
+    with locking inside cells;
   * ``fmsm``     -- the Fast Marching-Sweeping Method (Sec. 4.1, Alg. FMSM);
   * ``jacobi``   -- value iteration from +inf (eq. generic_value_it) on eq. Eik_discr;
   * ``apply_T``  -- one application of the local update operator of eq. Eik_discr;
@@ -93,13 +95,14 @@ class Oracle:
         common = [ctypes.c_int, ctypes.c_int, d, P(d), ctypes.c_int, P(i32), P(i32), P(d)]
         lib.orc_fmm.argtypes = common + [P(d), P(i64)]
         lib.orc_fsm.argtypes = common + [P(d), i32, P(i32)]
+        lib.orc_lsm.argtypes = common + [P(d), i32, P(i32), P(i64)]
         lib.orc_jacobi.argtypes = common + [P(d), i32, P(i32)]
         lib.orc_apply_T.argtypes = common + [P(d), P(d)]
         lib.orc_node_update.argtypes = [d, d, d, d, d]
         lib.orc_node_update.restype = d
         lib.orc_cells.argtypes = common + [ctypes.c_int, ctypes.c_int, P(d), P(i64)]
         lib.orc_fmsm.argtypes = common + [ctypes.c_int, P(d), P(d), P(i32), P(i32), P(i64)]
-        for fn in (lib.orc_fmm, lib.orc_fsm, lib.orc_jacobi, lib.orc_apply_T, lib.orc_cells, lib.orc_fmsm):
+        for fn in (lib.orc_fmm, lib.orc_fsm, lib.orc_lsm, lib.orc_jacobi, lib.orc_apply_T, lib.orc_cells, lib.orc_fmsm):
             fn.restype = ctypes.c_int
         self.lib = lib
         self.path = lib_path
@@ -136,20 +139,35 @@ class Oracle:
         del keep
         return (U, ns.value) if return_sweeps else U
 
-    def cells(self, F, h, si, sj, sq, k, fast=False):
-        """Heap-Cell Method (Sec. 4.2; fast=False, exact) or Fast Heap-Cell
-        Method (Sec. 4.3, Alg. FHCM; fast=True, inexact) on k x k cells.
-        Returns U and {'avhr', 'avs', 'mon_pct', 'removals', 'sweeps'}."""
+    def lsm(self, F, h, si, sj, sq, max_sweeps=100000):
+        """Locking Sweeping (Remark locking_FSM).  Returns U and
+        {'sweeps', 'evals' (local updates computed)}."""
         keep, args, shape = _args(F, h, si, sj, sq)
         U = np.empty(shape, dtype=np.float64)
-        st = np.zeros(4, dtype=np.int64)
-        _check(self.lib.orc_cells(*args, int(k), int(bool(fast)), _ptr(U, ctypes.c_double),
+        ns, ne = ctypes.c_int32(0), ctypes.c_int64(0)
+        _check(self.lib.orc_lsm(*args, _ptr(U, ctypes.c_double), int(max_sweeps), ctypes.byref(ns),
+                                ctypes.byref(ne)), "lsm")
+        del keep
+        return U, {"sweeps": ns.value, "evals": ne.value}
+
+    def cells(self, F, h, si, sj, sq, k, fast=False, lsm=False):
+        """Heap-Cell Method (Sec. 4.2; exact) on k x k cells, its cells
+        swept with locking flags (lsm=True; the same values), or the Fast
+        Heap-Cell Method (Sec. 4.3, Alg. FHCM; fast=True, inexact).  Returns U
+        and {'avhr', 'avs', 'mon_pct', 'removals', 'sweeps', 'evals'}."""
+        if fast and lsm:
+            raise ValueError("fast and lsm exclude each other")
+        keep, args, shape = _args(F, h, si, sj, sq)
+        U = np.empty(shape, dtype=np.float64)
+        st = np.zeros(5, dtype=np.int64)
+        method = 1 if fast else 2 if lsm else 0
+        _check(self.lib.orc_cells(*args, int(k), method, _ptr(U, ctypes.c_double),
                                   _ptr(st, ctypes.c_int64)), "cells")
         del keep
         ny, nx = shape
         J = ((nx + k - 1) // k) * ((ny + k - 1) // k)
         return U, {"removals": int(st[0]), "sweeps": int(st[1]), "avhr": st[0] / J, "avs": st[1] / J,
-                   "mon_pct": 100.0 * st[2] / st[3] if st[3] else 100.0}
+                   "mon_pct": 100.0 * st[2] / st[3] if st[3] else 100.0, "evals": int(st[4])}
 
     def fmsm(self, F, h, si, sj, sq, k):
         """Fast Marching-Sweeping Method (Sec. 4.1, Alg. FMSM) on k x k cells
@@ -214,6 +232,10 @@ def fmm(*a, **k):
 
 def fsm(*a, **k):
     return default().fsm(*a, **k)
+
+
+def lsm(*a, **k):
+    return default().lsm(*a, **k)
 
 
 def fmsm(*a, **k):

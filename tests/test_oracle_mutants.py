@@ -159,3 +159,28 @@ def test_fmsm_table_pin_catches_planted_mistake(name):
     assert src.count(old) == 1, f"mutation site for {name} not unique"
     mutant = oracle.Oracle.from_source(src.replace(old, new))
     assert _caught_by(mutant, [pins.test_fmsm_reproduces_tab_sinu_1]), name
+
+
+# ---------------------------------------------------------------- locking (LSM)
+LSM_MUTANTS = {
+    # a decrease unlocks the smaller neighbours instead of the larger ones
+    "lsm_unlocks_smaller": ("if (V[kn] > V[k] && !unl[kn] && !p->src[kn]) {",
+                            "if (V[kn] < V[k] && !unl[kn] && !p->src[kn]) {"),
+    # the east border of a cell is not unlocked at a removal
+    "lsm_east_border_locked": ("(i == i1 - 1 && i1 < nx)", "(i == i1 - 1 && i1 > nx)"),
+    # the source neighbours are unlocked on every removal but the first
+    "lsm_source_neighbours_later": ("if (!u && first)", "if (!u && !first)"),
+    # whole-grid LSM starts from the neighbours of the non-sources
+    "lsm_starts_at_non_sources": ("            if (!p.src[(size_t)j * nx + i]) continue;\n            const int ni[4]",
+                                  "            if (p.src[(size_t)j * nx + i]) continue;\n            const int ni[4]"),
+}
+LSM_PINS = [pins.test_lsm_matches_fsm_sweep_for_sweep, pins.test_hcm_with_locking_is_hcm]
+
+
+@pytest.mark.parametrize("name", sorted(LSM_MUTANTS))
+def test_lsm_pins_catch_planted_mistake(name):
+    old, new = LSM_MUTANTS[name]
+    src = _source()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    mutant = oracle.Oracle.from_source(src.replace(old, new))
+    assert _caught_by(mutant, LSM_PINS), name

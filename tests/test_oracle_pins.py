@@ -353,6 +353,54 @@ def test_hcm_is_exact_and_fhcm_an_upper_bound(orc):
                 assert np.abs(Uf[fin] - V[fin]).max(initial=0) <= 1e-13 * scale
 
 
+def _bits(U):
+    return np.ascontiguousarray(U).view(np.int64)
+
+
+def test_lsm_matches_fsm_sweep_for_sweep(orc):
+    """Remark locking_FSM: a locked node is one none of whose smaller
+    neighbours changed since its last update, so updating it would change
+    nothing; the Locking Sweeping Method therefore produces Alg. FSM's values
+    bit for bit after the same number of sweeps (here one fewer at most: the
+    count of unlocked nodes replaces the final sweep that finds them all
+    locked), while computing fewer local updates."""
+    rng = np.random.default_rng(5)
+    cases = [W.tiny_random(rng, n_max=24) for _ in range(150)] + [W.sin_point(65), W.checker_maze(65, 3)]
+    for I in cases:
+        U, ns = orc.fsm(I.F, I.h, I.si, I.sj, I.sq, return_sweeps=True)
+        V, st = orc.lsm(I.F, I.h, I.si, I.sj, I.sq)
+        assert (_bits(U) == _bits(V)).all()
+        assert ns - 1 <= st["sweeps"] <= ns
+        free = I.F.size - len(set(zip(I.si.tolist(), I.sj.tolist())))
+        assert st["evals"] <= ns * free
+    # on a grid with curved characteristics most of the work is saved
+    I = W.sin_point(65)
+    _, ns = orc.fsm(I.F, I.h, I.si, I.sj, I.sq, return_sweeps=True)
+    _, st = orc.lsm(I.F, I.h, I.si, I.sj, I.sq)
+    assert st["evals"] < 0.5 * ns * (I.F.size - 1)
+
+
+def test_hcm_with_locking_is_hcm(orc):
+    """Sec. 4.2: HCM processes a removed cell by the Locking Sweeping version
+    of Alg. FSM.  Within a removal the argument of Remark locking_FSM holds
+    with the cell's boundary data fixed, so HCM with locking inside cells
+    yields HCM's values bit for bit, the same removals, no more sweeps, and
+    fewer local updates."""
+    rng = np.random.default_rng(9)
+    cases = [W.tiny_random(rng, n_max=24) for _ in range(60)] + [W.sin_point(65), W.checker_maze(65, 3)]
+    for I in cases:
+        for k in (1, 2, 3, 5, 8):
+            A, sa = orc.cells(I.F, I.h, I.si, I.sj, I.sq, k)
+            B, sb = orc.cells(I.F, I.h, I.si, I.sj, I.sq, k, lsm=True)
+            assert (_bits(A) == _bits(B)).all()
+            assert sa["removals"] == sb["removals"]
+            assert sb["sweeps"] <= sa["sweeps"] and sb["evals"] <= sa["evals"]
+    I = W.sin_point(65)
+    _, sa = orc.cells(I.F, I.h, I.si, I.sj, I.sq, 8)
+    _, sb = orc.cells(I.F, I.h, I.si, I.sj, I.sq, 8, lsm=True)
+    assert sb["evals"] < 0.6 * sa["evals"]
+
+
 @pytest.mark.slow
 def test_cell_methods_reproduce_tab_sinu_1(orc):
     """Tab. sinu_1 prints HCM's and FHCM's removals per cell, FHCM's sweeps
