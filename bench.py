@@ -302,12 +302,13 @@ def config_measure(eik, torch, I, prec, steps=5, k=0):
 
 
 def fhcm_measure(eik, torch, I, steps=5):
-    """The inexact methods on the single 1025^2 grid, FP64: the Fast
-    Heap-Cell Method (Sec. 4.3) beside the exact one (HCM), and the Fast
-    Marching-Sweeping Method (Sec. 4.1) at three cell sizes; device times and
-    Sec. 5's error ratios against Fast Marching on an h/4 grid, beside the
-    oracle's serial FHCM / FMSM and the paper's Tab. sinu_1 rows for the
-    closest cell size.  Returns (fhcm, fmsm) dictionaries."""
+    """The heap-cell variants on the single 1025^2 grid, FP64: the Fast
+    Heap-Cell Method (Sec. 4.3) beside the exact one (HCM) and HCM with
+    locking inside cells (Remark locking_FSM; exact, fewer local updates),
+    and the Fast Marching-Sweeping Method (Sec. 4.1) at three cell sizes;
+    device times and Sec. 5's error ratios against Fast Marching on an h/4
+    grid, beside the oracle's serial FHCM / FMSM and the paper's Tab. sinu_1
+    rows for the closest cell size.  Returns (fhcm, fmsm) dictionaries."""
     import oracle
     from paper_1110_6220_gb300 import workloads as W
     F = torch.from_numpy(I.F).cuda()
@@ -315,7 +316,8 @@ def fhcm_measure(eik, torch, I, steps=5):
     q = torch.from_numpy(np.ascontiguousarray(I.sq)).cuda()
     U = torch.empty_like(F)
     out = {}
-    for name, method in (("hcm", eik.EIK_METHOD_HCM), ("fhcm", eik.EIK_METHOD_FHCM)):
+    for name, method in (("hcm", eik.EIK_METHOD_HCM), ("fhcm", eik.EIK_METHOD_FHCM),
+                         ("hcm_lsm", eik.EIK_METHOD_HCM_LSM)):
         ms = []
         with eik.Plan(I.nx, I.ny, I.h, 0, eik.EIK_FP64, method=method) as p:
             for r in range(steps + 2):
@@ -326,10 +328,12 @@ def fhcm_measure(eik, torch, I, steps=5):
                     ms.append(st.ms)
         med = statistics.median(ms)
         out[name] = {"ms": med, "value": I.npts / med / 1e3, "unit": UNIT, "cell_k": st.cell_k,
-                     "avhr": st.avhr, "avs": st.avs}
+                     "avhr": st.avhr, "avs": st.avs, "updates_per_pt": st.updates_per_pt}
         if method == eik.EIK_METHOD_FHCM:
             out[name]["mono_pct"] = st.mono_pct
             Ug = U.cpu().numpy()
+        if method == eik.EIK_METHOD_HCM_LSM:
+            Ul = U.cpu().numpy()
     n = I.nx
     J = W.sin_point(4 * (n - 1) + 1)
     orc = oracle.default()
@@ -343,6 +347,8 @@ def fhcm_measure(eik, torch, I, steps=5):
         return {"R": float((E[m] / e[m]).max()), "rho": float((E[m] / e[m]).mean()),
                 "R_max_errors": float(E.max() / e.max())}
     out["fhcm"].update(ratios(Ug))
+    fin = np.isfinite(V)
+    out["hcm_lsm"]["max_rel_err_vs_oracle_fmm"] = float(np.abs(Ul[fin] - V[fin]).max() / np.abs(V[fin]).max())
     out["fhcm"]["below_exact"] = int((Ug < V - 1e-12 * V.max()).sum())
     Uo, so = orc.cells(I.F, I.h, I.si, I.sj, I.sq, out["fhcm"]["cell_k"], fast=True)
     out["oracle_serial_fhcm"] = dict(ratios(Uo), avhr=so["avhr"], avs=so["avs"], mono_pct=so["mon_pct"])

@@ -86,8 +86,16 @@ enum { EIK_FP64 = 0, EIK_FP32_REFINE = 1 };
  * directions set by its neighbours accepted before it (Remark
  * sweeping_in_FMSM, Fig. coarse_sweep_choice).  Never below the exact
  * solution, not exact; FP64 and cell sizes >= 8 only (cell_k 0 picks 8 or
- * more). */
-enum { EIK_METHOD_HCM = 0, EIK_METHOD_FHCM = 1, EIK_METHOD_FMSM = 2 };
+ * more).  EIK_METHOD_HCM_LSM: HCM whose cells are swept by the Locking
+ * Sweeping version of Fast Sweeping, as Sec. 4.2 specifies (Remark
+ * locking_FSM): a sweep updates only a cell's unlocked nodes, each node it
+ * takes is locked, and a node that decreases unlocks its larger neighbours;
+ * at a removal the nodes next to a neighbouring cell start unlocked (on the
+ * first removal also those next to a source of the cell), and the removal
+ * ends when none is unlocked.  The same exact solution as EIK_METHOD_HCM with
+ * fewer local updates (eik_stats.updates_per_pt counts the ones computed);
+ * FP64 only. */
+enum { EIK_METHOD_HCM = 0, EIK_METHOD_FHCM = 1, EIK_METHOD_FMSM = 2, EIK_METHOD_HCM_LSM = 3 };
 
 /* Problem-shape description (Sec. 3 problem statement plus the method's
  * cell size).  All fields are read at eik_plan_create. */
@@ -101,7 +109,7 @@ typedef struct {
     int32_t precision;     /* EIK_FP64 or EIK_FP32_REFINE */
     double tol;            /* FP32_REFINE: certified max error / max|u|; <= 0: 1e-5 */
     int64_t deadline_ns;   /* device wall-clock limit per solve; <= 0: 20 s */
-    int32_t method;        /* EIK_METHOD_HCM, EIK_METHOD_FHCM or EIK_METHOD_FMSM */
+    int32_t method;        /* EIK_METHOD_HCM, EIK_METHOD_FHCM, EIK_METHOD_FMSM or EIK_METHOD_HCM_LSM */
 } eik_plan_desc;
 
 /* One problem instance (Sec. 3: speed F, exit set Q with values q). */

@@ -42,7 +42,8 @@ bool desc_valid(const eik_plan_desc* d) {
         d->cell_k != 64)
         return false;
     if (d->precision != EIK_FP64 && d->precision != EIK_FP32_REFINE) return false;
-    if (d->method != EIK_METHOD_HCM && d->method != EIK_METHOD_FHCM && d->method != EIK_METHOD_FMSM)
+    if (d->method != EIK_METHOD_HCM && d->method != EIK_METHOD_FHCM && d->method != EIK_METHOD_FMSM &&
+        d->method != EIK_METHOD_HCM_LSM)
         return false;
     if (d->method != EIK_METHOD_HCM && d->precision != EIK_FP64) return false;
     if (d->method == EIK_METHOD_FMSM && d->cell_k != 0 && d->cell_k < 8) return false;
@@ -360,7 +361,9 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     j.deadline_ns = deadline_ns;
     j.sm_cap = 0;
     j.one_pass = fp32 && P.one_pass;
-    j.fhcm = descs[0].method == EIK_METHOD_FHCM;
+    j.variant = descs[0].method == EIK_METHOD_FHCM      ? VAR_FHCM
+                : descs[0].method == EIK_METHOD_HCM_LSM ? VAR_LSM
+                                                        : VAR_HCM;
     j.fmsm = fmsm;
     j.coarse = nullptr;
     j.hold_ns = P.hold_ns;

@@ -99,13 +99,19 @@ struct __align__(64) InstDesc {
 
 constexpr int MAX_BATCH = 2048;   // instances per persistent launch
 
+// Variants of the persistent cell solver: HCM (Sec. 4.2, every removed cell
+// swept to convergence), FHCM (Sec. 4.3, one sweep per flagged direction)
+// and HCM whose sweeps update only the unlocked nodes of a cell (Remark
+// locking_FSM).  FHCM and locking are built for FP64 only.
+enum { VAR_HCM = 0, VAR_FHCM = 1, VAR_LSM = 2 };
+
 struct SolveParams {
     const InstDesc* inst;         // n_inst descriptors (device memory)
     int n_inst;
     Ctl* gctl;                    // grid barrier, abort flag, launch status, rounds
     long long deadline_ns;        // relative to kernel start
     int profile;                  // accumulate gctl->prof
-    int fhcm;                     // Fast Heap-Cell Method: one sweep per flagged direction
+    int variant;                  // VAR_HCM, VAR_FHCM or VAR_LSM
     // round-free schedule: a taken cell requested less than hold_ns ago goes
     // back to the ring's tail, so that requests from several upstream
     // neighbours merge into one visit (req_time: request times, per cell)
@@ -133,9 +139,9 @@ struct LaunchShape {
 };
 
 // one per arithmetic mode (eik_solver_f64.cu, eik_solver_f32.cu, eik_solver_df.cu)
-int solver_shape_f64(int k, int num_sms, int n_inst, int sm_cap, bool async, bool fhcm, LaunchShape* out);
-int solver_shape_f32(int k, int num_sms, int n_inst, int sm_cap, bool async, bool fhcm, LaunchShape* out);
-int solver_shape_df(int k, int num_sms, int n_inst, int sm_cap, bool async, bool fhcm, LaunchShape* out);
+int solver_shape_f64(int k, int num_sms, int n_inst, int sm_cap, bool async, int variant, LaunchShape* out);
+int solver_shape_f32(int k, int num_sms, int n_inst, int sm_cap, bool async, int variant, LaunchShape* out);
+int solver_shape_df(int k, int num_sms, int n_inst, int sm_cap, bool async, int variant, LaunchShape* out);
 // async: the round-free kernel (k_solve_async, cell sizes >= 8) instead of
 // the bucketed rounds (k_solve)
 cudaError_t launch_solver_f64(int k, bool async, const SolveParams& p, const LaunchShape& s, cudaStream_t st);

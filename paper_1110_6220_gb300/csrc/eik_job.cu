@@ -197,7 +197,7 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
     p.n_inst = n;
     p.deadline_ns = j.deadline_ns > 0 ? j.deadline_ns : 20000000000ll;
     p.profile = profiling();
-    p.fhcm = j.fhcm ? 1 : 0;
+    p.variant = j.variant;
     p.hold_ns = j.hold_ns;
     p.req_time = j.req_time;
     p.ring = j.ring;
@@ -211,7 +211,7 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
         // FP32_REFINE in one double-float pass from the sources (every
         // update on the FP32 pipe), certified like the two-pass form
         if (ev) cudaEventRecord(ev[0], st), cudaEventRecord(ev[1], st);
-        if (solver_shape_df(j.k, num_sms, n, j.sm_cap, am, false, &shape)) return EIK_ECUDA;
+        if (solver_shape_df(j.k, num_sms, n, j.sm_cap, am, VAR_HCM, &shape)) return EIK_ECUDA;
         p.inst = j.desc_main;
         p.gctl = j.gctl + 1;
         if (ev) cudaEventRecord(ev[2], st);
@@ -221,7 +221,7 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
         if (launch_residual(j.aux, j.blk_pre, n, j.nblocks, st) != cudaSuccess) return EIK_ECUDA;
         ++nl;
     } else if (j.fp32) {
-        if (solver_shape_f32(j.k, num_sms, n, j.sm_cap, af, false, &shape)) return EIK_ECUDA;
+        if (solver_shape_f32(j.k, num_sms, n, j.sm_cap, af, VAR_HCM, &shape)) return EIK_ECUDA;
         p.inst = j.desc_f32;
         p.gctl = j.gctl;
         if (ev) cudaEventRecord(ev[0], st);
@@ -234,7 +234,7 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
             cudaSuccess)
             return EIK_ECUDA;
         nl += 2;
-        if (solver_shape_df(j.k, num_sms, n, j.sm_cap, am, false, &shape)) return EIK_ECUDA;
+        if (solver_shape_df(j.k, num_sms, n, j.sm_cap, am, VAR_HCM, &shape)) return EIK_ECUDA;
         p.inst = j.desc_main;
         p.gctl = j.gctl + 1;
         if (ev) cudaEventRecord(ev[2], st);
@@ -270,7 +270,7 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
         if (ev) cudaEventRecord(ev[3], st);
         ++nl;
     } else {
-        if (solver_shape_f64(j.k, num_sms, n, j.sm_cap, am, j.fhcm, &shape)) return EIK_ECUDA;
+        if (solver_shape_f64(j.k, num_sms, n, j.sm_cap, am, j.variant, &shape)) return EIK_ECUDA;
         p.inst = j.desc_main;
         p.gctl = j.gctl + 1;
         if (ev) cudaEventRecord(ev[2], st);
@@ -293,16 +293,16 @@ bool job_pairable(const JobDev& j, int num_sms) {
         return a.per_sm >= 2;
     }
     if (j.fp32 && j.one_pass) {
-        if (solver_shape_df(j.k, num_sms, j.n, 1, j.async_main, false, &b)) return false;
+        if (solver_shape_df(j.k, num_sms, j.n, 1, j.async_main, VAR_HCM, &b)) return false;
         return b.per_sm >= 2;
     }
     if (j.fp32) {
-        if (solver_shape_f32(j.k, num_sms, j.n, 1, j.async_first, false, &a) ||
-            solver_shape_df(j.k, num_sms, j.n, 1, j.async_main, false, &b))
+        if (solver_shape_f32(j.k, num_sms, j.n, 1, j.async_first, VAR_HCM, &a) ||
+            solver_shape_df(j.k, num_sms, j.n, 1, j.async_main, VAR_HCM, &b))
             return false;
         return a.per_sm >= 2 && b.per_sm >= 2;
     }
-    if (solver_shape_f64(j.k, num_sms, j.n, 1, j.async_main, j.fhcm, &a)) return false;
+    if (solver_shape_f64(j.k, num_sms, j.n, 1, j.async_main, j.variant, &a)) return false;
     return a.per_sm >= 2;
 }
 

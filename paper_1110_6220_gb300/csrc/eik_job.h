@@ -59,7 +59,7 @@ struct JobDev {
     int sm_cap;                 // > 0: at most this many blocks per SM (room for other jobs)
     bool async_first, async_main;  // round-free schedule (k_solve_async) for the FP32 / main pass
     bool one_pass;              // fp32: no FP32 pass; the double-float pass solves from the sources
-    bool fhcm;                  // Fast Heap-Cell Method (one sweep per flagged direction)
+    int variant;                // main pass: VAR_HCM, VAR_FHCM or VAR_LSM
     bool fmsm;                  // Fast Marching-Sweeping Method (coarse solve, then one visit per cell)
     const JobDev* coarse;       // FMSM: the job of the instances' coarse grids
     unsigned hold_ns;           // round-free: minimum age of a request before its cell runs

@@ -362,6 +362,10 @@ struct TileCfg {
     static constexpr int WPB_SMEM = (200 * 1024) / WARP_BYTES;
     static constexpr int WPB = WPB_SMEM >= 8 ? 8 : (WPB_SMEM < 1 ? 1 : WPB_SMEM);
     static constexpr int MAX_PASSES = K * K + 8;
+    // HCM with locking: a lock byte per node of the warp's cells, after all
+    // warps' areas (the other variants leave it out)
+    static constexpr int LK_BYTES = A128(CPW * K * K);
+    static constexpr int lk_area(int var) { return var == VAR_LSM ? WPB * LK_BYTES : 0; }
 };
 
 // ---------------------------------------------------------------- one node
@@ -406,6 +410,21 @@ __device__ __forceinline__ bool tile_improvable(const typename TileCfg<MODE, K>:
         if (node_candidate<MODE, K>(tU, tF, tG, i, j, cand, old)) imp |= lt(cand, old);
     }
     return imp;
+}
+
+// Locking (Remark locking_FSM): node (i, j) of the tile has just decreased;
+// unlock each neighbour inside the cell whose value is larger -- the only
+// ones whose local update can use the new value.
+template <int MODE, int K>
+__device__ __forceinline__ void unlock_larger(const typename TileCfg<MODE, K>::T* tU, unsigned char* lk, int i,
+                                              int j) {
+    using C = TileCfg<MODE, K>;
+    const int q = (j + 1) * C::BW + (i + 1);
+    const auto v = tU[q];
+    if (i > 0 && lt(v, tU[q - 1])) lk[j * K + i - 1] = 1;
+    if (i < K - 1 && lt(v, tU[q + 1])) lk[j * K + i + 1] = 1;
+    if (j > 0 && lt(v, tU[q - C::BW])) lk[(j - 1) * K + i] = 1;
+    if (j < K - 1 && lt(v, tU[q + C::BW])) lk[(j + 1) * K + i] = 1;
 }
 
 // ---------------------------------------------------------------- grid barrier
@@ -564,6 +583,7 @@ struct WarpState {
     T* tU;
     const FT* tF;
     const double* tG;
+    unsigned char* lk;  // HCM with locking: the lock bytes of this lane's cell
     unsigned gmask;
     uint32_t phase;
     // counters gather per lane while the instance stays the same (one flush
@@ -589,6 +609,7 @@ struct WarpState {
         tF = reinterpret_cast<const FT*>(gbase + C::F_OFF);
         tG = reinterpret_cast<const double*>(gbase + C::X_OFF);
         gmask = C::LPC == 32 ? 0xffffffffu : (((1u << C::LPC) - 1u) << (g * C::LPC));
+        lk = smem + C::WPB * C::WARP_BYTES + warp * C::LK_BYTES + g * K * K;  // used by VAR_LSM only
         phase = 0;
         acc_inst = -1;
         acc_visits = acc_sweeps = acc_lane = st_lane = 0;
@@ -610,9 +631,11 @@ struct WarpState {
 // lane calls act(d, nc, key, old, activate): key/old the proposed and the
 // previous cell value of neighbour cell nc of instance d, activate the
 // outcome of the test -- the scheduler's part.  c, ii, first: this lane's
-// cell, its instance and whether this is the cell's first removal.  Returns
-// false when the TMA wait gave up (abort raised).
-template <int MODE, int K, bool CVAL, bool FAST, class Act>
+// cell, its instance and whether this is the cell's first removal.  VAR:
+// VAR_HCM, VAR_FHCM (one pass of the flagged directions) or VAR_LSM (HCM
+// whose passes update only unlocked nodes).  Returns false when the TMA wait
+// gave up (abort raised).
+template <int MODE, int K, bool CVAL, int VAR, class Act>
 __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDesc* inst, Ctl* gctl,
                                             unsigned long long deadline, int c, int ii, int first,
                                             const int* cg, const int* ig, int prof_on,
@@ -620,6 +643,7 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
     using C = TileCfg<MODE, K>;
     using T = typename C::T;
     constexpr unsigned FULL = 0xffffffffu;
+    constexpr bool FAST = VAR == VAR_FHCM, LSM = VAR == VAR_LSM;
     const int lane = w.lane, g = w.g, dl = w.dl, dir = w.dir, rl = w.rl;
     const bool sx = w.sx, sy = w.sy;
     T* tU = w.tU;
@@ -705,13 +729,105 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
         for (int e = 4 * dl; e < K * K; e += 4 * C::LPC) *reinterpret_cast<unsigned*>(flags + e) = 0u;
         __syncwarp();
     }
+    // HCM with locking (Sec. 4.2 sweeps a removed cell by the Locking
+    // Sweeping version, Remark locking_FSM): the cell was left at its fixed
+    // point by its last removal, so only the nodes next to a neighbouring
+    // cell, whose boundary data may have changed since, start unlocked --
+    // and on the first removal also the nodes next to a source of the cell.
+    // A pass updates only unlocked nodes; each node it takes is locked as it
+    // is taken, and a decrease unlocks the node's larger neighbours in the
+    // cell.  Within a step only locks are written before the barrier and
+    // only unlocks after it, so a node that read a neighbour's old value in
+    // the step the neighbour changed is unlocked again.  (Lanes of two
+    // directions that reach one node in one step: the one that finds it
+    // already locked skips it, and the other computes the same update.)  The
+    // visit ends when no node is unlocked.
+    unsigned char* lk = w.lk;
+    int nev = 0;  // local updates this lane computed
+    if constexpr (LSM) {
+        if (c >= 0) {
+            const int cx = c % cxn, cy = c / cxn;
+            for (int e = dl; e < K * K; e += C::LPC) {
+                const int j = e / K, i = e - j * K;
+                const int q = (j + 1) * C::BW + (i + 1);
+                bool u = false;
+                if (updatable(tF[q])) {
+                    u = (i == 0 && cx > 0) || (i == K - 1 && cx + 1 < cxn) || (j == 0 && cy > 0) ||
+                        (j == K - 1 && cy + 1 < cyn);
+                    if (!u && first)
+                        u = (i > 0 && is_src(tF[q - 1])) || (i < K - 1 && is_src(tF[q + 1])) ||
+                            (j > 0 && is_src(tF[q - C::BW])) || (j < K - 1 && is_src(tF[q + C::BW]));
+                }
+                lk[e] = u ? 1 : 0;
+            }
+        }
+        __syncwarp();
+    }
     int gsweeps = 0;
     bool gdone = c < 0;
     int s = 0;
     for (; s < C::MAX_PASSES && __ballot_sync(FULL, !gdone) != 0u; ++s) {
         bool changed = false;
         for (int t2 = 0; t2 < 2 * K - 1; ++t2) {
-            if constexpr (!DIAG) {
+            if constexpr (LSM) {
+                if constexpr (!DIAG) {
+                    const unsigned ii2 = (unsigned)(t2 - jr);
+                    const int j = rl, i = sx ? (int)ii2 : K - 1 - (int)ii2;
+                    bool dec = false;
+                    if (lane_on && ii2 < (unsigned)K && lk[j * K + i]) {
+                        lk[j * K + i] = 0;
+                        T cand, old;
+                        if (node_candidate<MODE, K>(tU, tF, tG, i, j, cand, old)) {
+                            ++nev;
+                            if (lt(cand, old)) {
+                                tU[(j + 1) * C::BW + (i + 1)] = cand;
+                                chg |= 1u << i;
+                                changed = true;
+                                dec = true;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    if (dec) unlock_larger<MODE, K>(tU, lk, i, j);
+                } else {
+                    const int lo = t2 < K ? 0 : t2 - (K - 1);
+                    const int len = (t2 < K ? t2 : K - 1) - lo + 1;
+                    unsigned dec = 0u;
+                    auto node = [&](int m, int& i, int& j) {
+                        const int jj = lo + rl + C::LPD * m, ii2 = t2 - jj;
+                        j = sy ? jj : K - 1 - jj;
+                        i = sx ? ii2 : K - 1 - ii2;
+                    };
+#pragma unroll
+                    for (int m = 0; m < C::RPL; ++m) {
+                        if (m * C::LPD < len && rl + C::LPD * m < len && c >= 0) {
+                            int i, j;
+                            node(m, i, j);
+                            if (lk[j * K + i]) {
+                                lk[j * K + i] = 0;
+                                T cand, old;
+                                if (node_candidate<MODE, K>(tU, tF, tG, i, j, cand, old)) {
+                                    ++nev;
+                                    if (lt(cand, old)) {
+                                        tU[(j + 1) * C::BW + (i + 1)] = cand;
+                                        flags[j * K + i] = 1;
+                                        changed = true;
+                                        dec |= 1u << m;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int m = 0; m < C::RPL; ++m)
+                        if ((dec >> m) & 1u) {
+                            int i, j;
+                            node(m, i, j);
+                            unlock_larger<MODE, K>(tU, lk, i, j);
+                        }
+                }
+            } else if constexpr (!DIAG) {
                 const unsigned ii2 = (unsigned)(t2 - jr);
                 if (lane_on && ii2 < (unsigned)K) {
                     const int j = rl, i = sx ? (int)ii2 : K - 1 - (int)ii2;
@@ -745,21 +861,34 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
             }
             __syncwarp();
         }
-        const unsigned any = __ballot_sync(FULL, changed);
-        if constexpr (FAST) {
-            if (!gdone) gsweeps += __popc(fl);
-            gdone = true;
-        }
-        if (!gdone) {
-            gsweeps += 4;
-            if (!(any & w.gmask)) gdone = true;
-        }
-        bool imp = false;
-        if (!gdone) imp = tile_improvable<MODE, K>(tU, tF, tG, dl);
-        const unsigned anyi = __ballot_sync(FULL, imp);
-        if (!gdone && !(anyi & w.gmask)) {
-            gdone = true;
-            ++gsweeps;  // counted like the confirming sweep it replaces
+        if constexpr (LSM) {
+            // done when every node of the cell is locked
+            bool left = false;
+            if (c >= 0)
+                for (int e = 4 * dl; e < K * K; e += 4 * C::LPC)
+                    left |= *reinterpret_cast<const unsigned*>(lk + e) != 0u;
+            const unsigned anyl = __ballot_sync(FULL, left);
+            if (!gdone) {
+                gsweeps += 4;
+                if (!(anyl & w.gmask)) gdone = true;
+            }
+        } else {
+            const unsigned any = __ballot_sync(FULL, changed);
+            if constexpr (FAST) {
+                if (!gdone) gsweeps += __popc(fl);
+                gdone = true;
+            }
+            if (!gdone) {
+                gsweeps += 4;
+                if (!(any & w.gmask)) gdone = true;
+            }
+            bool imp = false;
+            if (!gdone) imp = tile_improvable<MODE, K>(tU, tF, tG, dl);
+            const unsigned anyi = __ballot_sync(FULL, imp);
+            if (!gdone && !(anyi & w.gmask)) {
+                gdone = true;
+                ++gsweeps;  // counted like the confirming sweep it replaces
+            }
         }
         if (__ballot_sync(FULL, !gdone) == 0u) break;
         if ((s & 15) == 15) {
@@ -777,10 +906,16 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
         atomicCAS(&ictl->status, 0, EIK_ENOTCONVERGED);
         fail(gctl, EIK_ENOTCONVERGED, (unsigned)c);
     }
+    if constexpr (LSM) {  // the cell's lanes' local updates
+#pragma unroll
+        for (int o = C::LPC / 2; o > 0; o >>= 1) nev += __shfl_xor_sync(FULL, nev, o);
+    }
     if (dl == 0 && c >= 0) {
-        // node evaluations executed for this cell (lock-step passes included)
+        // node evaluations executed for this cell (lock-step passes included;
+        // with locking the local updates computed)
         const unsigned long long ev =
-            (unsigned long long)(s < C::MAX_PASSES ? s + 1 : C::MAX_PASSES) * 4 * K * K;
+            LSM ? (unsigned long long)nev
+                : (unsigned long long)(s < C::MAX_PASSES ? s + 1 : C::MAX_PASSES) * 4 * K * K;
         if (ii != w.acc_inst) {
             flush_counters(inst, w.acc_inst, w.acc_visits, w.acc_sweeps, w.acc_lane);
             w.acc_inst = ii;
@@ -947,11 +1082,12 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
 // instances, the warps process them, re-activations go to the next near list
 // (key <= theta) or to the far list, and a grid barrier ends the round; when
 // an instance's near list runs dry its next bucket is split off the far list.
-template <int MODE, int K, bool FAST>
+template <int MODE, int K, int VAR>
 __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
     k_solve(const __grid_constant__ SolveParams p) {
     using C = TileCfg<MODE, K>;
     constexpr unsigned FULL = 0xffffffffu;
+    constexpr bool FAST = VAR == VAR_FHCM;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_flag;
     // TMA destinations must be 128-byte aligned: the host asks for 128 spare bytes
@@ -960,7 +1096,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
     const int NI = p.n_inst;
     InstState S;
     {
-        unsigned char* sp = smem + C::WPB * C::WARP_BYTES;
+        unsigned char* sp = smem + C::WPB * C::WARP_BYTES + C::lk_area(VAR);
         S.theta = reinterpret_cast<unsigned long long*>(sp);
         sp += NI * 8;
         S.pre = reinterpret_cast<int*>(sp);
@@ -1131,7 +1267,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
             PROF_MARK(2);
             pacc[7] += 1;
 
-            const bool ok = visit_cells<MODE, K, true, FAST>(
+            const bool ok = visit_cells<MODE, K, true, VAR>(
                 w, inst, gctl, deadline, c, ii_, first, cg, ig, prof_on, pacc, pt,
                 [&](const InstDesc& dn, int nc, unsigned long long kk, unsigned long long old, bool activate) {
                     const int was = activate ? atomicExch(&dn.qflag[nc], 1) : 1;
@@ -1245,18 +1381,19 @@ __device__ __forceinline__ int ring_pop(const SolveParams& p, Ctl* gctl, unsigne
 // left alone, the compiler fits them into 64 registers (four blocks) with
 // spills, which measured slower (1025^2: 1.86 against 1.73 ms per pass; the
 // 512-grid batch 14.1 against 13.9 ms).  0 leaves the others to the compiler.
-template <int MODE, int K, bool FAST>
+template <int MODE, int K, int VAR>
 __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32, (MODE == MODE_DF && (K == 8 || K == 16)) ? 3 : 0)
     k_solve_async(const __grid_constant__ SolveParams p) {
     using C = TileCfg<MODE, K>;
     static_assert(C::CPW == 1, "one cell per warp");
     constexpr unsigned FULL = 0xffffffffu;
+    constexpr bool FAST = VAR == VAR_FHCM;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_flag;
     unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
 
     const int NI = p.n_inst;
-    int* s_cnt = reinterpret_cast<int*>(smem + C::WPB * C::WARP_BYTES);
+    int* s_cnt = reinterpret_cast<int*>(smem + C::WPB * C::WARP_BYTES + C::lk_area(VAR));
     int* s_pre = s_cnt + NI;
     int* s_scr = s_pre + NI + 1;
 
@@ -1367,7 +1504,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32, (MODE == MODE_DF &
         PROF_MARK(2);
         pacc[7] += 1;
         const int cg[1] = {c}, ig[1] = {ii};
-        const bool ok = visit_cells<MODE, K, false, FAST>(
+        const bool ok = visit_cells<MODE, K, false, VAR>(
             w, inst, gctl, deadline, c, ii, first, cg, ig, prof_on, pacc, pt,
             [&](const InstDesc& dn, int nc, unsigned long long, unsigned long long, bool activate) {
                 if (activate && (atomicOr(&dn.qflag[nc], 1) & 3) == 0) {

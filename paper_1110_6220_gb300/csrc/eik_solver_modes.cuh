@@ -6,28 +6,32 @@
 
 namespace eik {
 
-// The Fast Heap-Cell variant (FAST) is built for FP64 only (the only mode
-// that offers it); the exact kernels carry none of its code.
-template <int MODE, int K>
-static const void* solver_fn(bool async, bool fhcm) {
-    if constexpr (MODE == MODE_F64) {
-        if (fhcm) {
-            if constexpr (TileCfg<MODE, K>::CPW == 1)
-                if (async) return (const void*)k_solve_async<MODE, K, true>;
-            return (const void*)k_solve<MODE, K, true>;
-        }
-    }
+// The Fast Heap-Cell variant and HCM with locking are built for FP64 only
+// (the only mode that offers them); the plain HCM kernels carry none of
+// their code.
+template <int MODE, int K, int VAR>
+static const void* solver_fn_var(bool async) {
     if constexpr (TileCfg<MODE, K>::CPW == 1)
-        if (async) return (const void*)k_solve_async<MODE, K, false>;
-    return (const void*)k_solve<MODE, K, false>;
+        if (async) return (const void*)k_solve_async<MODE, K, VAR>;
+    return (const void*)k_solve<MODE, K, VAR>;
 }
 
 template <int MODE, int K>
-static void shape_of(int num_sms, int n_inst, int sm_cap, bool async, bool fhcm, LaunchShape* s) {
+static const void* solver_fn(bool async, int variant) {
+    if constexpr (MODE == MODE_F64) {
+        if (variant == VAR_FHCM) return solver_fn_var<MODE, K, VAR_FHCM>(async);
+        if (variant == VAR_LSM) return solver_fn_var<MODE, K, VAR_LSM>(async);
+    }
+    return solver_fn_var<MODE, K, VAR_HCM>(async);
+}
+
+template <int MODE, int K>
+static void shape_of(int num_sms, int n_inst, int sm_cap, bool async, int variant, LaunchShape* s) {
     using C = TileCfg<MODE, K>;
-    const void* fn = solver_fn<MODE, K>(async, fhcm);
+    const void* fn = solver_fn<MODE, K>(async, variant);
     s->threads = C::WPB * 32;
-    s->smem = (size_t)C::WPB * C::WARP_BYTES + 128 + (size_t)inst_state_bytes(n_inst);
+    s->smem = (size_t)C::WPB * C::WARP_BYTES + (size_t)C::lk_area(MODE == MODE_F64 ? variant : VAR_HCM) + 128 +
+              (size_t)inst_state_bytes(n_inst);
     s->blocks = 0;
     s->per_sm = 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem) != cudaSuccess) {
@@ -51,24 +55,25 @@ static void shape_of(int num_sms, int n_inst, int sm_cap, bool async, bool fhcm,
 }
 
 template <int MODE>
-static int solver_shape_mode(int k, int num_sms, int n_inst, int sm_cap, bool async, bool fhcm,
+static int solver_shape_mode(int k, int num_sms, int n_inst, int sm_cap, bool async, int variant,
                              LaunchShape* out) {
     out->blocks = 0;
     switch (k) {
-    case 4: shape_of<MODE, 4>(num_sms, n_inst, sm_cap, async, fhcm, out); break;
-    case 8: shape_of<MODE, 8>(num_sms, n_inst, sm_cap, async, fhcm, out); break;
-    case 16: shape_of<MODE, 16>(num_sms, n_inst, sm_cap, async, fhcm, out); break;
-    case 32: shape_of<MODE, 32>(num_sms, n_inst, sm_cap, async, fhcm, out); break;
-    case 64: shape_of<MODE, 64>(num_sms, n_inst, sm_cap, async, fhcm, out); break;
+    case 4: shape_of<MODE, 4>(num_sms, n_inst, sm_cap, async, variant, out); break;
+    case 8: shape_of<MODE, 8>(num_sms, n_inst, sm_cap, async, variant, out); break;
+    case 16: shape_of<MODE, 16>(num_sms, n_inst, sm_cap, async, variant, out); break;
+    case 32: shape_of<MODE, 32>(num_sms, n_inst, sm_cap, async, variant, out); break;
+    case 64: shape_of<MODE, 64>(num_sms, n_inst, sm_cap, async, variant, out); break;
     default: return -1;
     }
     return out->blocks > 0 ? 0 : -1;
 }
 
 template <int MODE, int K>
-static cudaError_t launch_one(bool async, bool fhcm, const SolveParams& p, const LaunchShape& s, cudaStream_t st) {
+static cudaError_t launch_one(bool async, int variant, const SolveParams& p, const LaunchShape& s,
+                              cudaStream_t st) {
     void* args[] = {(void*)&p};
-    return cudaLaunchCooperativeKernel(solver_fn<MODE, K>(async, fhcm), dim3(s.blocks), dim3(s.threads), args,
+    return cudaLaunchCooperativeKernel(solver_fn<MODE, K>(async, variant), dim3(s.blocks), dim3(s.threads), args,
                                        s.smem, st);
 }
 
@@ -76,11 +81,11 @@ template <int MODE>
 static cudaError_t launch_solver_mode(int k, bool async, const SolveParams& p, const LaunchShape& s,
                                       cudaStream_t st) {
     switch (k) {
-    case 4: return launch_one<MODE, 4>(async, p.fhcm != 0, p, s, st);
-    case 8: return launch_one<MODE, 8>(async, p.fhcm != 0, p, s, st);
-    case 16: return launch_one<MODE, 16>(async, p.fhcm != 0, p, s, st);
-    case 32: return launch_one<MODE, 32>(async, p.fhcm != 0, p, s, st);
-    case 64: return launch_one<MODE, 64>(async, p.fhcm != 0, p, s, st);
+    case 4: return launch_one<MODE, 4>(async, p.variant, p, s, st);
+    case 8: return launch_one<MODE, 8>(async, p.variant, p, s, st);
+    case 16: return launch_one<MODE, 16>(async, p.variant, p, s, st);
+    case 32: return launch_one<MODE, 32>(async, p.variant, p, s, st);
+    case 64: return launch_one<MODE, 64>(async, p.variant, p, s, st);
     default: return cudaErrorInvalidValue;
     }
 }

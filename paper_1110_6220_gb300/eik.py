@@ -37,6 +37,7 @@ EIK_FP32_REFINE = 1
 EIK_METHOD_HCM = 0
 EIK_METHOD_FHCM = 1
 EIK_METHOD_FMSM = 2
+EIK_METHOD_HCM_LSM = 3
 
 
 class eik_plan_desc(ctypes.Structure):

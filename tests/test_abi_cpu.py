@@ -102,18 +102,22 @@ def test_tune_table_round_trip_and_use_without_gpu(tmp_path):
 
 def test_method_descriptor_rules_without_gpu():
     """Methods and their allowed forms, seen through eik_plan_workspace_bytes
-    (0 for a refused descriptor, no GPU needed): FHCM and FMSM are FP64 only;
-    FMSM needs cells of 8 or more, and cell_k = 0 gives it 8 or more; an
-    unknown method is refused."""
+    (0 for a refused descriptor, no GPU needed): FHCM, FMSM and HCM with
+    locking are FP64 only; FMSM needs cells of 8 or more, and cell_k = 0
+    gives it 8 or more; HCM with locking takes every cell size and needs the
+    same workspace as HCM; an unknown method is refused."""
     from paper_1110_6220_gb300 import eik
     F64, R = eik.EIK_FP64, eik.EIK_FP32_REFINE
     ws = lambda k, prec, m: eik.eik_plan_workspace_bytes(eik.make_desc(257, 257, 1 / 256, k, prec, method=m))
-    for m in (eik.EIK_METHOD_HCM, eik.EIK_METHOD_FHCM, eik.EIK_METHOD_FMSM):
+    for m in (eik.EIK_METHOD_HCM, eik.EIK_METHOD_FHCM, eik.EIK_METHOD_FMSM, eik.EIK_METHOD_HCM_LSM):
         assert ws(8, F64, m) > 0
     assert ws(8, R, eik.EIK_METHOD_HCM) > 0
     assert ws(8, R, eik.EIK_METHOD_FHCM) == 0
     assert ws(8, R, eik.EIK_METHOD_FMSM) == 0
+    assert ws(8, R, eik.EIK_METHOD_HCM_LSM) == 0
     assert ws(4, F64, eik.EIK_METHOD_FMSM) == 0
     assert ws(4, F64, eik.EIK_METHOD_HCM) > 0
     assert ws(0, F64, eik.EIK_METHOD_FMSM) > 0
-    assert ws(8, F64, 3) == 0
+    for k in (4, 8, 16, 32, 64):
+        assert ws(k, F64, eik.EIK_METHOD_HCM_LSM) == ws(k, F64, eik.EIK_METHOD_HCM)
+    assert ws(8, F64, 4) == 0
