@@ -81,6 +81,18 @@ int side_class(const eik_plan_desc* d, int n) {
 //    batches run round-free at k = 8 (46.2 ms instead of 75.8 ms on the
 //    512-grid mix), small FP64 grids too (129^2: 0.32 ms instead of 0.37
 //    ms), and ~2048^2 grids hold for 4 us (2049^2 maze: 6.3 ms for 6.8 ms).
+//  - single grids of about 8192^2 and more go back to rounds, k = 16: on the
+//    round-free ring the visits per cell of the sin20 grid grow with the
+//    side (21 at 1025^2, 38 at 8193^2, 76 at 16385^2, 159 at 32769^2), while
+//    value-ordered buckets keep them at 3-5.  Double-float, sin20: 34 / 92 /
+//    274 ms at m = 16 against 76 / 558 / 4669 ms round-free; the 4097^2 tie
+//    (13.5 against 13.0 ms) keeps it round-free there.  A checkerboard +
+//    maze keeps ~21 visits per cell round-free at any size and needs more
+//    buckets (its values are longer detours), so m = 64, which costs it
+//    64 / 190 ms against 46 / 167 ms round-free at 8193^2 / 16385^2 and
+//    gives sin20 45 / 122 / 404 ms.  FP64 at m = 32: the maze 158 / 468 ms
+//    against 179 / 588 ms round-free; sin20 at m = 16 51 / 130 ms against
+//    202 / 1448 ms.
 Entry builtin(int prec, bool batch, int side, bool fhcm) {
     if (prec == EIK_FP32_REFINE) {
         // cells of 16 from ~4096^2 (4097^2 sin20: 18.3 vs 29.1 ms at k = 8;
@@ -90,6 +102,11 @@ Entry builtin(int prec, bool batch, int side, bool fhcm) {
         // holds (a young cell goes back to the ring): 4097^2 20 us (maze
         // 21.9 -> 20.4 ms, sin20 17.3 -> 14.3 ms against 8 us), 2049^2 4 us
         if (!batch) e.hold_ns = side >= 12 ? 20000 : side == 11 ? 4000 : 0;
+        if (!batch && side >= 13) {
+            e.m_main = 64.0;
+            e.async_main = false;
+            e.hold_ns = 0;
+        }
         return e;
     }
     if (batch || side <= 8) return Entry{8, 4.0, 4.0, 0.0, false, true};
@@ -101,6 +118,7 @@ Entry builtin(int prec, bool batch, int side, bool fhcm) {
     // FHCM's one-sweep visits gain less from merged requests: rounds
     // (1025^2 sin20 2.72 ms, against 2.92 ms round-free with a 4 us hold)
     if (side == 9 || fhcm) return Entry{8, 256.0, 256.0, 0.0};
+    if (side >= 13) return Entry{16, 32.0, 32.0, 0.0};
     Entry e{8, 256.0, 256.0, 0.0, false, true};
     e.hold_ns = side == 10 ? 4000 : 16000;
     return e;

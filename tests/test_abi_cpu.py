@@ -71,11 +71,15 @@ def test_tune_table_round_trip_and_use_without_gpu(tmp_path):
     w8 = eik.eik_plan_workspace_bytes(eik.make_desc(1025, 1025, 1 / 1024, 8, eik.EIK_FP64))
     w32 = eik.eik_plan_workspace_bytes(eik.make_desc(1025, 1025, 1 / 1024, 32, eik.EIK_FP64))
     assert w_auto == w8 and w32 != w8  # built-in: k = 8 for one FP64 grid
-    # FP32 + refinement: k = 8 for one grid up to ~2048^2, 16 from ~4096^2
+    # FP32 + refinement: k = 8 for one grid up to ~2048^2, 16 from ~4096^2;
+    # FP64: 8 up to ~4096^2, 16 (bucketed rounds) from ~8192^2
     R = eik.EIK_FP32_REFINE
-    for n, k in ((1025, 8), (2049, 8), (4097, 16)):
+    for n, k in ((1025, 8), (2049, 8), (4097, 16), (8193, 16)):
         assert eik.eik_plan_workspace_bytes(eik.make_desc(n, n, 1 / (n - 1), 0, R)) == \
             eik.eik_plan_workspace_bytes(eik.make_desc(n, n, 1 / (n - 1), k, R)), n
+    for n, k in ((4097, 8), (8193, 16)):
+        assert eik.eik_plan_workspace_bytes(eik.make_desc(n, n, 1 / (n - 1), 0, eik.EIK_FP64)) == \
+            eik.eik_plan_workspace_bytes(eik.make_desc(n, n, 1 / (n - 1), k, eik.EIK_FP64)), n
     f = tmp_path / "tune.txt"
     # class: FP64, single grid, side 2^10
     f.write_text("eik-tune 4\n0 0 10 32 8 8 0 1 0 0 1.5\n")
