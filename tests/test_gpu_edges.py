@@ -136,49 +136,50 @@ def test_largest_cells_and_rectangular_grids(eik, orc, prec):
         _check(U, orc.fmm(I.F, I.h, I.si, I.sj, I.sq), tol, f"{nx}x{ny} k={k}")
 
 
-def test_largest_grids_by_properties(eik, orc):
+@pytest.mark.parametrize("n,prec", [(32769, 1), (16385, 0), (8193, 1)])
+def test_largest_grids_by_properties(eik, orc, n, prec):
     """The largest grids in this suite: 32769^2 in FP32_REFINE (1.07 G nodes,
-    about half the 2^31-node limit, every array past 8 GB) and 16385^2 in
-    FP64, the sin20 speed with a centre source.  The oracle cannot solve
-    them in seconds, so they are checked by properties that hold at any
-    size: the source keeps q, every node is finite (no obstacles), and at
+    about half the 2^31-node limit, every array past 8 GB), 16385^2 in FP64
+    and 8193^2 in FP32_REFINE, the sin20 speed with a centre source; all
+    three run the bucketed schedule the library picks for such grids.  The
+    oracle cannot solve them in seconds, so they are checked by properties
+    that hold at any size: the source keeps q, every node is finite (no obstacles), and at
     20,000 sampled nodes the oracle's local update of eq. Eik_discr, applied
     to the returned neighbours, reproduces the returned value -- the
     fixed-point property that identifies the discrete solution -- within the
     solve's own certified residual (FP32_REFINE) or 1e-12 of max u (FP64)."""
     import torch
     rng = np.random.default_rng(29)
-    for n, prec in ((32769, eik.EIK_FP32_REFINE), (16385, eik.EIK_FP64)):
-        h = 1.0 / (n - 1)
-        x = torch.arange(n, device="cuda", dtype=torch.float64) * h
-        s = torch.sin(20.0 * np.pi * x)
-        F = 1.0 + 0.5 * s[:, None] * s[None, :]  # (ny, nx), symmetric
-        c = (n - 1) // 2
-        src = torch.tensor([c, c], dtype=torch.int32, device="cuda")
-        q = torch.zeros(1, dtype=torch.float64, device="cuda")
-        U = torch.empty_like(F)
-        with eik.Plan(n, n, h, 0, prec) as p:
-            rc, st = p.solve(F, src, q, U)
-        assert rc == 0, eik.eik_strerror(rc)
-        assert U[c, c].item() == 0.0
-        assert bool(torch.isfinite(U).all())
-        umax = U.max().item()
-        ii = torch.from_numpy(rng.integers(1, n - 1, 20000)).cuda()
-        jj = torch.from_numpy(rng.integers(1, n - 1, 20000)).cuda()
-        cols = torch.stack([U[jj, ii], U[jj, ii + 1], U[jj, ii - 1], U[jj + 1, ii], U[jj - 1, ii],
-                            F[jj, ii]], 1).cpu().numpy()
-        del F, U, x, s
-        torch.cuda.empty_cache()
-        worst = 0.0
-        for (u, ue, uw, un, us, fv), i, j in zip(cols, ii.tolist(), jj.tolist()):
-            if i == c and j == c:
-                continue
-            worst = max(worst, abs(orc.node_update(ue, uw, un, us, h / fv) - u))
-        if prec == eik.EIK_FP64:
-            assert worst <= 1e-12 * umax, (n, worst / umax)
-        else:
-            assert st.err_bound <= 1e-5
-            assert worst <= st.max_residual * (1 + 1e-9) + 1e-15 * umax, (n, worst, st.max_residual)
+    h = 1.0 / (n - 1)
+    x = torch.arange(n, device="cuda", dtype=torch.float64) * h
+    s = torch.sin(20.0 * np.pi * x)
+    F = 1.0 + 0.5 * s[:, None] * s[None, :]  # (ny, nx), symmetric
+    c = (n - 1) // 2
+    src = torch.tensor([c, c], dtype=torch.int32, device="cuda")
+    q = torch.zeros(1, dtype=torch.float64, device="cuda")
+    U = torch.empty_like(F)
+    with eik.Plan(n, n, h, 0, prec) as p:
+        rc, st = p.solve(F, src, q, U)
+    assert rc == 0, eik.eik_strerror(rc)
+    assert U[c, c].item() == 0.0
+    assert bool(torch.isfinite(U).all())
+    umax = U.max().item()
+    ii = torch.from_numpy(rng.integers(1, n - 1, 20000)).cuda()
+    jj = torch.from_numpy(rng.integers(1, n - 1, 20000)).cuda()
+    cols = torch.stack([U[jj, ii], U[jj, ii + 1], U[jj, ii - 1], U[jj + 1, ii], U[jj - 1, ii],
+                        F[jj, ii]], 1).cpu().numpy()
+    del F, U, x, s
+    torch.cuda.empty_cache()
+    worst = 0.0
+    for (u, ue, uw, un, us, fv), i, j in zip(cols, ii.tolist(), jj.tolist()):
+        if i == c and j == c:
+            continue
+        worst = max(worst, abs(orc.node_update(ue, uw, un, us, h / fv) - u))
+    if prec == eik.EIK_FP64:
+        assert worst <= 1e-12 * umax, (n, worst / umax)
+    else:
+        assert st.err_bound <= 1e-5
+        assert worst <= st.max_residual * (1 + 1e-9) + 1e-15 * umax, (n, worst, st.max_residual)
 
 
 @pytest.mark.parametrize("shape", [(2, 1_000_000), (1_000_000, 2)])
