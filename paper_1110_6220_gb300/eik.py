@@ -38,6 +38,8 @@ EIK_METHOD_HCM = 0
 EIK_METHOD_FHCM = 1
 EIK_METHOD_FMSM = 2
 EIK_METHOD_HCM_LSM = 3
+EIK_NOALLOC_SCRATCH_BYTES = 32 << 20
+EIK_NOALLOC_MAX_SOURCES = 256
 
 
 class eik_plan_desc(ctypes.Structure):

@@ -40,6 +40,31 @@ def test_binding_uses_the_same_names():
         assert callable(getattr(eik, name)), name
 
 
+def test_binding_constants_match_the_header():
+    """Every EIK_ enumerator and #define in include/eik.h has the same value
+    in the Python binding, and the ctypes structures have the C sizes."""
+    from paper_1110_6220_gb300 import eik
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    consts = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+        nxt = 0
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            name, _, val = item.partition("=")
+            nxt = int(val.strip(), 0) if val.strip() else nxt
+            consts[name.strip()] = nxt
+            nxt += 1
+    for name, expr in re.findall(r"#define[ \t]+(EIK_\w+)[ \t]+([^\n]+)", text):
+        expr = re.sub(r"(\d+)u\b", r"\1", expr.strip())
+        assert re.fullmatch(r"[\d\s()<]+", expr), (name, expr)  # integers and shifts only
+        consts[name] = eval(expr)
+    assert "EIK_METHOD_HCM_LSM" in consts and "EIK_NOALLOC_SCRATCH_BYTES" in consts
+    for name, val in consts.items():
+        assert getattr(eik, name) == val, name
+
+
 def test_strerror_and_workspace_size_without_gpu():
     from paper_1110_6220_gb300 import eik
     assert eik.eik_strerror(0) == "ok"
