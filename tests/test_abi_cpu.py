@@ -65,6 +65,35 @@ def test_binding_constants_match_the_header():
         assert getattr(eik, name) == val, name
 
 
+def test_structure_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the C structures have the C compiler's size and
+    field offsets (gcc compiles a probe against include/eik.h)."""
+    import shutil
+    import subprocess
+    from paper_1110_6220_gb300 import eik
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    structs = [eik.eik_plan_desc, eik.eik_instance, eik.eik_stats, eik.eik_tune_result]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "eik.h"', "int main(void) {"]
+    for s in structs:
+        n = s.__name__
+        lines.append(f'printf("{n} %zu\\n", sizeof({n}));')
+        for f, _ in s._fields_:
+            lines.append(f'printf("{n}.{f} %zu\\n", offsetof({n}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(ln.split() for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.splitlines())
+    for s in structs:
+        n = s.__name__
+        assert int(got[n]) == ctypes.sizeof(s), n
+        for f, _ in s._fields_:
+            assert int(got[f"{n}.{f}"]) == getattr(s, f).offset, f"{n}.{f}"
+
+
 def test_strerror_and_workspace_size_without_gpu():
     from paper_1110_6220_gb300 import eik
     assert eik.eik_strerror(0) == "ok"
