@@ -9,9 +9,12 @@ from .oracle import (  # noqa: F401
     OracleError,
     apply_T,
     build,
+    cells,
     default,
     fmm,
+    fmsm,
     fsm,
     jacobi,
+    lsm,
     node_update,
 )
