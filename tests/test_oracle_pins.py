@@ -164,11 +164,14 @@ def test_distance_function_converges_first_order(orc):
 
 @pytest.mark.slow
 def test_paper_printed_errors(orc):
-    """Tab. const, Tab. sinu_1 (point source) and Tabs. sinu_1_gbc /
+    """Tabs. const, sinu_1 and sinu_2 (point source) and Tabs. sinu_1_gbc /
     sinu_2_gbc (q = 0 on the whole boundary) print the L_inf and L1 errors of
     the 1408 x 1408 solution against Fast Marching on an h/4 grid (Sec. 5).
     Reading the grid as 1408 intervals (h = 1/1408) the oracle reproduces
-    them within the tolerance each case states (0.5% but for one L_inf)."""
+    them within the tolerance each case states (0.5% for most L_inf, 1% and
+    5% where the speed dips to 0.01).  Where a case gives FSM's sweep count
+    (the tables' "# Sweeps", shared by FSM and LSM) and pins it, FSM takes
+    that many sweeps and LSM that many or one fewer."""
     with open(os.path.join(GOLD, "paper_errors.json")) as fh:
         gold = json.load(fh)
     for case in gold["cases"]:
@@ -182,6 +185,11 @@ def test_paper_printed_errors(orc):
         assert abs(linf / case["Linf"] - 1) < case["linf_tol"], (case["name"], linf)
         l1 = np.abs(U - V).mean()
         assert abs(l1 / case["L1"] - 1) < case["l1_tol"], (case["name"], l1)
+        if "fsm_sweeps" in case and "fsm_sweeps_not_pinned" not in case:
+            _, ns = orc.fsm(I.F, I.h, I.si, I.sj, I.sq, return_sweeps=True)
+            assert ns == case["fsm_sweeps"], (case["name"], ns)
+            _, st = orc.lsm(I.F, I.h, I.si, I.sj, I.sq)
+            assert st["sweeps"] in (ns - 1, ns), (case["name"], st)
 
 
 def test_fsm_sweep_count_constant_speed(orc):
