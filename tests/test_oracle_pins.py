@@ -421,12 +421,26 @@ def test_cell_methods_reproduce_tab_sinu_1(orc):
     oracle's cell methods reproduce them: AvHR and AvS within 3%, Mon %
     within 1.5 points, the average error ratio within 5% and the ratio of
     maximum errors within 1%."""
-    with open(os.path.join(GOLD, "paper_cells.json")) as fh:
+    _check_cell_table(orc, "paper_cells.json")
+
+
+@pytest.mark.slow
+def test_cell_methods_reproduce_tab_sinu_2(orc):
+    """Tab. sinu_2 (F = 1 + 0.99 sin 2 pi x sin 2 pi y, a speed that dips to
+    0.01) prints the same columns at five cell sizes, and FMSM's sweeps per
+    cell; the oracle reproduces them within the same tolerances (FMSM's AvS
+    within 3%)."""
+    _check_cell_table(orc, "paper_cells_sinu2.json")
+
+
+def _check_cell_table(orc, name):
+    with open(os.path.join(GOLD, name)) as fh:
         gold = json.load(fh)
     n = gold["n"]
-    I = W.sin_point(n)
+    args = tuple(gold.get("args", ()))
+    I = W.sin_point(n, *args)
     V = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
-    truth = _h4_reference(W.sin_point, n)
+    truth = _h4_reference(W.sin_point, n, *args)
     e = np.abs(V - truth)
     m = e > 0
     for row in gold["rows"]:
@@ -442,6 +456,9 @@ def test_cell_methods_reproduce_tab_sinu_1(orc):
         rmax = E.max() / e.max()
         assert abs(rho / row["rho"] - 1) < 0.05, (row, rho)
         assert abs(rmax / row["Rmax"] - 1) < 0.01, (row, rmax)
+        if "fmsm_avs" in row:
+            _, sm = orc.fmsm(I.F, I.h, I.si, I.sj, I.sq, k)
+            assert abs(sm["avs"] / row["fmsm_avs"] - 1) < 0.03, (row, sm["avs"])
 
 
 # ---------------------------------------------------------------- FMSM (Sec. 4.1)
