@@ -580,6 +580,58 @@ def test_fmsm_reproduces_tab_sinu_1(orc):
         assert abs(st["avs"] / row["avs"] - 1) < 0.015, (row, st["avs"])
 
 
+def _checker41(m):
+    """Tab. checker_41's problem on an m x m grid: 41 x 41 checkers, centre source."""
+    I = W.sin_point(m)
+    I.F = W.checker_field(m, 41)
+    return I
+
+
+@pytest.mark.slow
+def test_cell_methods_reproduce_tab_checker_41(orc):
+    """Tab. checker_41 (Sec. 5, Checkerboards): a finer checkerboard, where
+    cells straddle many speed jumps.  The oracle reproduces the printed
+    L_inf / L1 errors (within 0.5% / 5%), HCM's and FHCM's removals and
+    FHCM's sweeps per cell (within 3%), the Monotonicity Check rate (within
+    1.5 points), FHCM's average error ratio (within 1e-3) and its ratio of
+    maximum errors where printed as pinned, FMSM's sweeps per cell (within
+    3%), its average error ratio (within 5%) and its ratio of maximum errors
+    where pinned (within 1%)."""
+    with open(os.path.join(GOLD, "paper_checker41.json")) as fh:
+        gold = json.load(fh)
+    n = gold["n"]
+    I = _checker41(n)
+    V = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
+    truth = _h4_reference(_checker41, n)
+    e = np.abs(V - truth)
+    m = e > 0
+    assert abs(e.max() / gold["Linf"] - 1) < 0.005, e.max()
+    assert abs(e.mean() / gold["L1"] - 1) < 0.05, e.mean()
+
+    def ratios(X):
+        E = np.abs(X - truth)
+        return (E[m] / e[m]).mean(), E.max() / e.max()
+    for row in gold["rows"]:
+        k = row["k"]
+        _, sh = orc.cells(I.F, I.h, I.si, I.sj, I.sq, k, fast=False)
+        Uf, sf = orc.cells(I.F, I.h, I.si, I.sj, I.sq, k, fast=True)
+        Um, sm = orc.fmsm(I.F, I.h, I.si, I.sj, I.sq, k)
+        assert abs(sh["avhr"] / row["hcm_avhr"] - 1) < 0.03, (row, sh)
+        assert abs(sf["avhr"] / row["fhcm_avhr"] - 1) < 0.03, (row, sf)
+        assert abs(sf["avs"] / row["fhcm_avs"] - 1) < 0.03, (row, sf)
+        assert abs(sf["mon_pct"] - row["mon_pct"]) < 1.5, (row, sf)
+        rho, rmax = ratios(Uf)
+        assert abs(rho - row["fhcm_rho"]) < 1e-3, (row, rho)
+        if "fhcm_Rmax" in row:
+            assert abs(rmax - row["fhcm_Rmax"]) < 1e-3, (row, rmax)
+        assert abs(sm["avs"] / row["fmsm_avs"] - 1) < 0.03, (row, sm["avs"])
+        rho_m, rmax_m = ratios(Um)
+        assert abs(rho_m / row["fmsm_rho"] - 1) < 0.05, (row, rho_m)
+        if "fmsm_Rmax" in row:
+            assert abs(rmax_m / row["fmsm_Rmax"] - 1) < 0.01, (row, rmax_m)
+
+
+@pytest.mark.slow
 @pytest.mark.slow
 def test_cell_methods_reproduce_tab_checker_11(orc):
     """Tab. checker_11 (Sec. 5, Checkerboards): a discontinuous speed, where
