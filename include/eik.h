@@ -225,7 +225,11 @@ void eik_batch_destroy(eik_batch b);
  * first-in first-out order, with no buckets.  FP32_REFINE runs either as an
  * FP32 pass followed by a double-float refinement pass seeded from it, or as
  * one double-float pass from the sources; both take every update on the FP32
- * pipe and end with the same FP64 residual certificate.
+ * pipe and end with the same FP64 residual certificate.  Built in, single
+ * grids up to about 4096^2 run round-free and larger ones in bucketed rounds
+ * of 16-node cells: on the ring a smooth field's cells are revisited more
+ * often the larger the grid, while buckets keep the visits per cell near
+ * constant.
  *
  * eik_tune: time trial solves of the given instances, run as one job like
  * eik_solve_batch (n_inst = 1: like eik_solve), over k in {8, 16, 32}, rounds
