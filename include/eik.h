@@ -97,6 +97,24 @@ enum { EIK_FP64 = 0, EIK_FP32_REFINE = 1 };
  * FP64 only. */
 enum { EIK_METHOD_HCM = 0, EIK_METHOD_FHCM = 1, EIK_METHOD_FMSM = 2, EIK_METHOD_HCM_LSM = 3 };
 
+/* Schedules of the cell solver's persistent passes (the order in which
+ * queued cells are removed; Theorem convergence makes the result the same
+ * for any order, up to rounding -- only the work and the time differ).
+ * EIK_SCHED_AUTO: the tuned or built-in choice (see autotuning).
+ * EIK_SCHED_ROUNDS: bucketed rounds -- every queued cell within one bucket
+ * width of the smallest cell value is released at once, re-activations run
+ * in the next round, a grid-wide barrier ends each round.
+ * EIK_SCHED_FIFO: round-free -- each warp takes the next requested cell from
+ * a first-in first-out device queue as soon as it is free; cell values are
+ * not used.
+ * EIK_SCHED_ORDERED: round-free in order of value -- requested cells wait in
+ * buckets of the value their activation proposes (eq. cell_value), Dial's
+ * buckets of Sec. 2 without rounds; warps take the oldest cell of the lowest
+ * bucket within `window` buckets of the lowest one still holding a queued or
+ * running cell, which moves up as its last cell finishes.  Cell sizes >= 8;
+ * EIK_METHOD_HCM only (the other methods fall back to EIK_SCHED_FIFO). */
+enum { EIK_SCHED_AUTO = 0, EIK_SCHED_ROUNDS = 1, EIK_SCHED_FIFO = 2, EIK_SCHED_ORDERED = 3 };
+
 /* Problem-shape description (Sec. 3 problem statement plus the method's
  * cell size).  All fields are read at eik_plan_create. */
 typedef struct {
@@ -110,6 +128,9 @@ typedef struct {
     double tol;            /* FP32_REFINE: certified max error / max|u|; <= 0: 1e-5 */
     int64_t deadline_ns;   /* device wall-clock limit per solve; <= 0: 20 s */
     int32_t method;        /* EIK_METHOD_HCM, EIK_METHOD_FHCM, EIK_METHOD_FMSM or EIK_METHOD_HCM_LSM */
+    int32_t schedule;      /* EIK_SCHED_*: the persistent passes' schedule; 0 = tuned / built in */
+    int32_t window;        /* EIK_SCHED_ORDERED: buckets warps take cells from, counting the
+                              lowest, 1..32; 0 = tuned / built in */
 } eik_plan_desc;
 
 /* One problem instance (Sec. 3: speed F, exit set Q with values q). */

@@ -48,6 +48,8 @@ bool desc_valid(const eik_plan_desc* d) {
     if (d->method != EIK_METHOD_HCM && d->precision != EIK_FP64) return false;
     if (d->method == EIK_METHOD_FMSM && d->cell_k != 0 && d->cell_k < 8) return false;
     if ((long long)d->nx * d->ny > (1ll << 31) - 1) return false;
+    if (d->schedule < EIK_SCHED_AUTO || d->schedule > EIK_SCHED_ORDERED) return false;
+    if (d->window < 0 || d->window > NBQ) return false;
     return true;
 }
 
@@ -235,7 +237,14 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     size_t Q = 8192;
     while (Q < 16 * Jtot) Q <<= 1;
     const size_t hist_bytes = a256((3 * 8192 + 1) * 4);
-    const size_t ring_bytes = a256(384 + hist_bytes + Q * 8);
+    // the value-ordered schedule's bucket rings: NBQ rings of a power of two
+    // >= the job's cells (a cell sits in at most one ring at a time), behind
+    // their header
+    size_t BQ = 1024;
+    while (BQ < Jtot) BQ <<= 1;
+    const bool ordered = P.ordered && P.async_main && k >= 8 && Jtot < ((size_t)1 << 26);
+    const size_t bq_bytes = ordered ? a256((size_t)BQ_WORDS * 4) + (size_t)NBQ * BQ * 8 : 0;
+    const size_t ring_bytes = a256(384 + hist_bytes + Q * 8) + bq_bytes;
     // FMSM: coarse speeds and coarse values, one of each per cell
     const bool fmsm = descs[0].method == EIK_METHOD_FMSM;
     const size_t fm_bytes = fmsm ? 2 * a256(Jtot * 8) : 0;
@@ -374,6 +383,11 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     j.hist = (int*)(ring_dev + 384);
     j.ring = (unsigned long long*)(ring_dev + 384 + hist_bytes);
     j.ring_mask = (unsigned)(Q - 1);
+    j.ordered = ordered;
+    j.window = P.window;
+    j.bq = ordered ? (unsigned*)(ring_dev + a256(384 + hist_bytes + Q * 8)) : nullptr;
+    j.bq_data = ordered ? (unsigned long long*)((char*)j.bq + a256((size_t)BQ_WORDS * 4)) : nullptr;
+    j.bq_mask = ordered ? (unsigned)(BQ - 1) : 0u;
     j.zero_base = zero_dev;
     j.zero_bytes = zero_bytes;
     j.cval_all = cval_all;
@@ -455,7 +469,8 @@ int finish_job(HostJob* hj, const eik_plan_desc* descs, cudaStream_t st, double 
         job_stats(hj->L[i], &descs[i], j.fp32, &ic[i], &ic[n + i], &g[0], &g[1], &r[i], hj->shift[i],
                   hj->bw_main[i], ms, &s);
         s.schedule = (j.fp32 && !j.one_pass && j.async_first && j.k >= 8 ? 1 : 0) |
-                     (j.async_main && j.k >= 8 && !j.fmsm ? 2 : 0) | (j.one_pass ? 4 : 0) | (j.fmsm ? 16 : 0);
+                     (j.async_main && j.k >= 8 && !j.fmsm ? 2 : 0) | (j.one_pass ? 4 : 0) | (j.fmsm ? 16 : 0) |
+                     (j.ordered && j.variant == VAR_HCM && !j.fmsm ? 32 : 0);
         if (fmsm && !s.status) {
             // a failed coarse solve fails the instance
             const Ctl* cc = (const Ctl*)hj->coarse->zero_host;
@@ -527,7 +542,11 @@ size_t job_bytes(const eik_plan_desc* d) {
     const bool fp32 = d->precision == EIK_FP32_REFINE;
     size_t Q = 8192;
     while (Q < 16 * (size_t)L.J) Q <<= 1;
+    size_t BQ = 1024;
+    while (BQ < (size_t)L.J) BQ <<= 1;
     size_t b = inst_bytes(L, fp32, true, true) + (size_t)L.J * 16 + Q * 8 + 128 * 1024;
+    const JobParams P = choose_params(d, 1);
+    if (P.ordered && P.async_main && P.k >= 8) b += (size_t)NBQ * BQ * 8 + 1024;
     if (d->method == EIK_METHOD_FMSM) b += (size_t)L.J * 16 + 512;  // coarse speeds and values
     return b;
 }

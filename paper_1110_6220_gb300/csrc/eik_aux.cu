@@ -189,6 +189,7 @@ __global__ void k_ctl_init(Ctl* ctl, int count) {
         ctl[e].fmin[1] = KEY_UNSET;
         ctl[e].fmin_f = KEY_UNSET;
         ctl[e].t_start = ~0ull;
+        ctl[e].qdelta = KEY_UNSET;
     }
 }
 

@@ -61,6 +61,14 @@ struct Ctl {
     unsigned long long t_start, t_end;
     // FHCM Monotonicity Checks: monotone borders / checks made
     unsigned long long mono_ok, mono_n;
+    // value-ordered schedule: ordered key of the launch's bucket width (the
+    // smallest of its instances'), front moves, cells handed to idle warps
+    unsigned long long qdelta, fronts, handoffs;
+    // value-ordered schedule, profiling only: 0 bucket claims, 1 tickets
+    // taken, 2 cells received on a ticket, 3 gives, 4 requests filed again
+    // (a front moved meanwhile), 5 bucket puts, 6 cells handed on by rare
+    // checks, 7 rare checks by parked warps
+    unsigned long long qev[8];
     // per-phase clock cycles summed over warps, filled only when profiling
     // (EIK_PROFILE=1): 0 split, 1 barrier, 2 list+pop, 3 TMA wait, 4 sweeps,
     // 5 write-back, 6 activation, 7 warp-rounds with work
@@ -114,7 +122,9 @@ struct SolveParams {
     int variant;                  // VAR_HCM, VAR_FHCM or VAR_LSM
     // round-free schedule: a taken cell requested less than hold_ns ago goes
     // back to the ring's tail, so that requests from several upstream
-    // neighbours merge into one visit (req_time: request times, per cell)
+    // neighbours merge into one visit (req_time: request times, per cell;
+    // the value-ordered schedule keeps there, complemented, the lowest value
+    // proposed while the cell ran)
     unsigned hold_ns;
     unsigned long long* req_time;
     // asynchronous scheduling only: ring of (sequence << 32 | global cell)
@@ -127,7 +137,18 @@ struct SolveParams {
     const int* cell_pre;
     unsigned int* qctl;           // ring head, tail and pending count, 128 bytes apart
     int* hist;                    // 3 x 8192 + 1 ints: counting sort of the initial ring
+    // value-ordered round-free schedule only: NBQ bucket rings of cell values
+    // (bq: head/tail pairs, counts of queued or running cells, the front;
+    // BQ_WORDS words), each ring bq_mask + 1 (a power of two >= the job's
+    // cells) words of bq_data; warps take cells from the buckets within
+    // bq_window of the front
+    unsigned int* bq;
+    unsigned long long* bq_data;
+    unsigned int bq_mask;
+    int bq_window;
 };
+constexpr int NBQ = 32;           // bucket rings of the value-ordered schedule (one lane of a warp each)
+constexpr int BQ_WORDS = 160;     // header words: pairs [0, 64), 64-bit counts [64, 128), front at 128
 
 // ---------------------------------------------------------------- host launchers
 // Implemented in eik_solver_f64.cu / eik_solver_f32.cu.
@@ -138,15 +159,17 @@ struct LaunchShape {
     int per_sm;        // occupancy limit: blocks of this shape one SM holds
 };
 
+// Schedules of a persistent pass: bucketed rounds (k_solve), or the
+// round-free kernel (k_solve_async, cell sizes >= 8) taking cells first in,
+// first out or by value (bucket rings with a moving front; plain HCM).
+enum { SCH_ROUNDS = 0, SCH_FIFO = 1, SCH_ORDERED = 2 };
 // one per arithmetic mode (eik_solver_f64.cu, eik_solver_f32.cu, eik_solver_df.cu)
-int solver_shape_f64(int k, int num_sms, int n_inst, int sm_cap, bool async, int variant, LaunchShape* out);
-int solver_shape_f32(int k, int num_sms, int n_inst, int sm_cap, bool async, int variant, LaunchShape* out);
-int solver_shape_df(int k, int num_sms, int n_inst, int sm_cap, bool async, int variant, LaunchShape* out);
-// async: the round-free kernel (k_solve_async, cell sizes >= 8) instead of
-// the bucketed rounds (k_solve)
-cudaError_t launch_solver_f64(int k, bool async, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
-cudaError_t launch_solver_f32(int k, bool async, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
-cudaError_t launch_solver_df(int k, bool async, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
+int solver_shape_f64(int k, int num_sms, int n_inst, int sm_cap, int sched, int variant, LaunchShape* out);
+int solver_shape_f32(int k, int num_sms, int n_inst, int sm_cap, int sched, int variant, LaunchShape* out);
+int solver_shape_df(int k, int num_sms, int n_inst, int sm_cap, int sched, int variant, LaunchShape* out);
+cudaError_t launch_solver_f64(int k, int sched, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
+cudaError_t launch_solver_f32(int k, int sched, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
+cudaError_t launch_solver_df(int k, int sched, const SolveParams& p, const LaunchShape& s, cudaStream_t st);
 
 // aux kernels (eik_aux.cu)
 // ---------------------------------------------------------------- aux kernels

@@ -205,27 +205,36 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
     p.cell_pre = j.cell_pre;
     p.qctl = j.qctl;
     p.hist = j.hist;
+    p.bq = j.bq;
+    p.bq_data = j.bq_data;
+    p.bq_mask = j.bq_mask;
+    p.bq_window = j.window < 0 ? 0 : j.window > NBQ - 1 ? NBQ - 1 : j.window;
     const bool af = j.async_first && j.ring && j.k >= 8, am = j.async_main && j.ring && j.k >= 8;
+    // the main pass's schedule (the value-ordered form for plain HCM only)
+    const int sm = !am ? SCH_ROUNDS
+                   : j.ordered && j.bq && j.variant == VAR_HCM ? SCH_ORDERED
+                                                                    : SCH_FIFO;
+    const int sf = !af ? SCH_ROUNDS : j.ordered && j.bq ? SCH_ORDERED : SCH_FIFO;
     LaunchShape shape;
     if (j.fp32 && j.one_pass) {
         // FP32_REFINE in one double-float pass from the sources (every
         // update on the FP32 pipe), certified like the two-pass form
         if (ev) cudaEventRecord(ev[0], st), cudaEventRecord(ev[1], st);
-        if (solver_shape_df(j.k, num_sms, n, j.sm_cap, am, VAR_HCM, &shape)) return EIK_ECUDA;
+        if (solver_shape_df(j.k, num_sms, n, j.sm_cap, sm, VAR_HCM, &shape)) return EIK_ECUDA;
         p.inst = j.desc_main;
         p.gctl = j.gctl + 1;
         if (ev) cudaEventRecord(ev[2], st);
-        if (launch_solver_df(j.k, am, p, shape, st) != cudaSuccess) return EIK_ECUDA;
+        if (launch_solver_df(j.k, sm, p, shape, st) != cudaSuccess) return EIK_ECUDA;
         if (ev) cudaEventRecord(ev[3], st);
         ++nl;
         if (launch_residual(j.aux, j.blk_pre, n, j.nblocks, st) != cudaSuccess) return EIK_ECUDA;
         ++nl;
     } else if (j.fp32) {
-        if (solver_shape_f32(j.k, num_sms, n, j.sm_cap, af, VAR_HCM, &shape)) return EIK_ECUDA;
+        if (solver_shape_f32(j.k, num_sms, n, j.sm_cap, sf, VAR_HCM, &shape)) return EIK_ECUDA;
         p.inst = j.desc_f32;
         p.gctl = j.gctl;
         if (ev) cudaEventRecord(ev[0], st);
-        if (launch_solver_f32(j.k, af, p, shape, st) != cudaSuccess) return EIK_ECUDA;
+        if (launch_solver_f32(j.k, sf, p, shape, st) != cudaSuccess) return EIK_ECUDA;
         if (ev) cudaEventRecord(ev[1], st);
         ++nl;
         // refinement pass (double-float) seeded from the FP32 result
@@ -234,11 +243,11 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
             cudaSuccess)
             return EIK_ECUDA;
         nl += 2;
-        if (solver_shape_df(j.k, num_sms, n, j.sm_cap, am, VAR_HCM, &shape)) return EIK_ECUDA;
+        if (solver_shape_df(j.k, num_sms, n, j.sm_cap, sm, VAR_HCM, &shape)) return EIK_ECUDA;
         p.inst = j.desc_main;
         p.gctl = j.gctl + 1;
         if (ev) cudaEventRecord(ev[2], st);
-        if (launch_solver_df(j.k, am, p, shape, st) != cudaSuccess) return EIK_ECUDA;
+        if (launch_solver_df(j.k, sm, p, shape, st) != cudaSuccess) return EIK_ECUDA;
         if (ev) cudaEventRecord(ev[3], st);
         ++nl;
         if (launch_residual(j.aux, j.blk_pre, n, j.nblocks, st) != cudaSuccess) return EIK_ECUDA;
@@ -270,11 +279,11 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
         if (ev) cudaEventRecord(ev[3], st);
         ++nl;
     } else {
-        if (solver_shape_f64(j.k, num_sms, n, j.sm_cap, am, j.variant, &shape)) return EIK_ECUDA;
+        if (solver_shape_f64(j.k, num_sms, n, j.sm_cap, sm, j.variant, &shape)) return EIK_ECUDA;
         p.inst = j.desc_main;
         p.gctl = j.gctl + 1;
         if (ev) cudaEventRecord(ev[2], st);
-        if (launch_solver_f64(j.k, am, p, shape, st) != cudaSuccess) return EIK_ECUDA;
+        if (launch_solver_f64(j.k, sm, p, shape, st) != cudaSuccess) return EIK_ECUDA;
         if (ev) cudaEventRecord(ev[3], st);
         ++nl;
     }
@@ -288,21 +297,28 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
 
 bool job_pairable(const JobDev& j, int num_sms) {
     LaunchShape a{}, b{};
+    const bool am = j.async_main && j.ring && j.k >= 8;
+    const int sm = !am ? SCH_ROUNDS
+                   : j.ordered && j.bq && j.variant == VAR_HCM ? SCH_ORDERED
+                                                                    : SCH_FIFO;
+    const int sf = !(j.async_first && j.ring && j.k >= 8) ? SCH_ROUNDS
+                   : j.ordered && j.bq                ? SCH_ORDERED
+                                                           : SCH_FIFO;
     if (j.fmsm) {
         if (fmsm_shape(j.k, num_sms, j.n, 1, &a) || !j.coarse || !job_pairable(*j.coarse, num_sms)) return false;
         return a.per_sm >= 2;
     }
     if (j.fp32 && j.one_pass) {
-        if (solver_shape_df(j.k, num_sms, j.n, 1, j.async_main, VAR_HCM, &b)) return false;
+        if (solver_shape_df(j.k, num_sms, j.n, 1, sm, VAR_HCM, &b)) return false;
         return b.per_sm >= 2;
     }
     if (j.fp32) {
-        if (solver_shape_f32(j.k, num_sms, j.n, 1, j.async_first, VAR_HCM, &a) ||
-            solver_shape_df(j.k, num_sms, j.n, 1, j.async_main, VAR_HCM, &b))
+        if (solver_shape_f32(j.k, num_sms, j.n, 1, sf, VAR_HCM, &a) ||
+            solver_shape_df(j.k, num_sms, j.n, 1, sm, VAR_HCM, &b))
             return false;
         return a.per_sm >= 2 && b.per_sm >= 2;
     }
-    if (solver_shape_f64(j.k, num_sms, j.n, 1, j.async_main, j.variant, &a)) return false;
+    if (solver_shape_f64(j.k, num_sms, j.n, 1, sm, j.variant, &a)) return false;
     return a.per_sm >= 2;
 }
 
@@ -322,8 +338,17 @@ static void print_profile(const char* what, const Ctl* c) {
     for (int i = 0; i < 7; ++i)
         std::fprintf(stderr, " %s=%.1f%%", names[i], tot > 0 ? 100.0 * c->prof[i] / tot : 0.0);
     const double v = (double)c->prof[7];
-    std::fprintf(stderr, " warp-visits=%.0f cyc/visit: sweeps=%.0f tma=%.0f act=%.0f\n", v,
-                 v ? c->prof[4] / v : 0.0, v ? c->prof[3] / v : 0.0, v ? c->prof[6] / v : 0.0);
+    std::fprintf(stderr, " warp-visits=%.0f cyc/visit: sweeps=%.0f tma=%.0f act=%.0f pop=%.0f finish=%.0f\n", v,
+                 v ? c->prof[4] / v : 0.0, v ? c->prof[3] / v : 0.0, v ? c->prof[6] / v : 0.0,
+                 v ? c->prof[2] / v : 0.0, v ? c->prof[0] / v : 0.0);
+    if (c->fronts || c->qev[1])
+        std::fprintf(stderr,
+                     "[eik queue %s] fronts=%llu handoffs=%llu claims=%llu tickets=%llu received=%llu gives=%llu "
+                     "gone-skips=%llu puts=%llu given-back=%llu rare-checks=%llu\n",
+                     what, (unsigned long long)c->fronts, (unsigned long long)c->handoffs,
+                     (unsigned long long)c->qev[0], (unsigned long long)c->qev[1], (unsigned long long)c->qev[2],
+                     (unsigned long long)c->qev[3], (unsigned long long)c->qev[4], (unsigned long long)c->qev[5],
+                     (unsigned long long)c->qev[6], (unsigned long long)c->qev[7]);
 }
 
 void job_stats(const Layout& L, const eik_plan_desc* d, bool fp32, const Ctl* ictl_first,
@@ -338,7 +363,7 @@ void job_stats(const Layout& L, const eik_plan_desc* d, bool fp32, const Ctl* ic
         else if (ictl_first->status) status = ictl_first->status;
     }
     unsigned long long visits = ictl_main->visits, sweeps = ictl_main->sweeps, lane = ictl_main->lane_updates;
-    long long rounds = (long long)g_main->rounds, adv = (long long)ictl_main->advances;
+    long long rounds = (long long)g_main->rounds, adv = (long long)(ictl_main->advances + g_main->fronts);
     if (fp32) {
         visits += ictl_first->visits;
         sweeps += ictl_first->sweeps;

@@ -68,6 +68,13 @@ struct JobDev {
     unsigned ring_mask;
     unsigned* qctl;             // async: head, tail, pending (384 bytes before the ring)
     int* hist;                  // async: 3 x 8192 + 1 ints of counting-sort scratch
+    // value-ordered main pass (plain HCM, round-free): bucket rings and their
+    // header, and the window in buckets (null bq: first in, first out)
+    bool ordered;
+    int window;
+    unsigned* bq;
+    unsigned long long* bq_data;
+    unsigned bq_mask;
     // everything that enqueue_job zeroes before a solve: [zero_base, + zero_bytes)
     void* zero_base;
     size_t zero_bytes;

@@ -34,6 +34,11 @@ struct JobParams {
     bool async_first = false, async_main = false;  // round-free schedule per pass (k >= 8)
     bool one_pass = false;  // FP32_REFINE as one double-float pass from the sources
     unsigned hold_ns = 0;   // round-free: minimum age of a request before its cell runs
+    // round-free main pass in value order (bucket rings, a front and a
+    // window of `window` buckets above it; plain HCM) instead of first in,
+    // first out
+    bool ordered = false;
+    int window = 31;
 };
 
 bool desc_valid(const eik_plan_desc* d);

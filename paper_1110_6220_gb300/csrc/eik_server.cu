@@ -80,17 +80,20 @@ namespace {
 size_t request_bytes(const eik_plan_desc& d, const eik_instance& in) {
     const bool fp32 = d.precision == EIK_FP32_REFINE;
     const bool sF = !is_device_ptr(in.F), sU = !is_device_ptr(in.U);
-    // arrays + staging for host buffers + cell state, lists, ring and tables; a
+    // arrays + staging for host buffers + cell state, lists, rings (the
+    // value-ordered schedule's bucket rings: NBQ words per cell, up to twice
+    // that once the job's cells round up to a power of two) and tables; a
     // request that leaves the cell size open is charged its largest choice
     size_t most = 0;
+    const size_t per_cell = 160 + 2 * NBQ * 8;
     for (int k : {8, 16, 32}) {
         if (d.cell_k && k != d.cell_k) continue;
         const Layout L = make_layout(d.nx, d.ny, k);
-        most = std::max(most, inst_bytes(L, fp32, sF, sU) + (size_t)L.J * 160);
+        most = std::max(most, inst_bytes(L, fp32, sF, sU) + (size_t)L.J * per_cell);
     }
     if (d.cell_k && !most) {
         const Layout L = make_layout(d.nx, d.ny, d.cell_k);
-        most = inst_bytes(L, fp32, sF, sU) + (size_t)L.J * 160;
+        most = inst_bytes(L, fp32, sF, sU) + (size_t)L.J * per_cell;
     }
     return most + 4 * sizeof(Ctl) + 4096;
 }

@@ -1377,12 +1377,336 @@ __device__ __forceinline__ int ring_pop(const SolveParams& p, Ctl* gctl, unsigne
     return (int)(unsigned)v;
 }
 
+// ---------------------------------------------------------------- value order
+// The value-ordered round-free schedule: Dial's buckets (Sec. 2) without
+// rounds.  A requested cell goes into the bucket ring of the value its
+// activation proposes (eq. cell_value) -- bucket a = floor(value / delta),
+// rings indexed by a mod NBQ, values below the front raised to it and values
+// more than NBQ - 1 buckets above it lowered to the last one.  Each ring has
+// a count word: the cells requested or running that are filed under its
+// bucket, the bucket's lap (a / NBQ) and a closed flag.  The front is the
+// lowest bucket still counted; the warp whose finish empties it closes it
+// (a compare-and-swap from "this lap, open, 0"), moves the front one up and
+// reopens the ring for the bucket NBQ higher -- no barrier.  A request whose
+// count lands on a closed ring or another lap takes it back and files the
+// cell under the new front, so a counted cell never sits below the front.
+// A warp takes the oldest cell of the lowest non-empty bucket within
+// bq_window buckets of the front (a compare-and-swap on that ring's head);
+// cells above the window wait until the front comes within reach, which
+// keeps cells from running long before their upstream neighbours settle --
+// the revisits the first-in first-out ring pays for.  A warp that finds
+// nothing to take parks on a ticket of the first-in first-out ring (as in
+// the round-free schedule above); a cell requested within the window while
+// warps are parked is handed to one of them directly, and when the front
+// moves, the bucket that enters the window is handed to parked warps in
+// batches.  Parked warps look at the buckets only rarely (thousands of them
+// polling the same lines would queue every atomic of the working warps):
+// then they move the front if its last cell finished unseen and hand on any
+// cells left within the window.  Any removal order is exact (Theorem
+// convergence), so the order only changes the work; `pending` (cells
+// requested or running) still ends the pass.
+//
+// A ring entry carries the cell and the ring it is counted under: cell |
+// ring << 26, below 2^31 (the job's cells < 2^26, which the host checks), so
+// it reads as a non-negative int and never as the ring markers 0xffffffff.
+constexpr int BQ_CW = 64, BQ_FRONT = 128;  // header word offsets (count words are 64-bit)
+constexpr int CELL_BITS = 26;
+constexpr unsigned CELL_MASK = (1u << CELL_BITS) - 1u;
+constexpr unsigned long long CW_CLOSED = 1ull << 32, CW_LAP = 1ull << 33;
+__device__ __forceinline__ unsigned long long slot_free(unsigned t) {
+    return ((unsigned long long)t << 32) | 0xffffffffull;
+}
+__device__ __forceinline__ unsigned long long slot_full(unsigned t, unsigned v) {
+    return ((unsigned long long)(t + 1u) << 32) | v;
+}
+__device__ __forceinline__ unsigned long long* bq_cw(const SolveParams& p, unsigned s) {
+    return reinterpret_cast<unsigned long long*>(p.bq + BQ_CW) + s;
+}
+// parked warps: consumer tickets handed out beyond the producers'
+__device__ __forceinline__ int ring_waiters(const SolveParams& p) {
+    return (int)(ld_vol(&p.qctl[Q_HEAD]) - ld_vol(&p.qctl[Q_TAIL]));
+}
+#define QEV(i)                                              \
+    do {                                                    \
+        if (p.profile) atomicAdd(&gctl->qev[i], 1ull);      \
+    } while (0)
+// Put entry v into the first-in first-out ring's slot of ticket t (waiting
+// for the previous lap's consumer to release it).
+__device__ __forceinline__ bool ring_fill(const SolveParams& p, Ctl* gctl, unsigned t, unsigned v,
+                                          unsigned long long deadline) {
+    unsigned long long* sl = p.ring + (t & p.ring_mask);
+    unsigned spins = 0;
+    while (t > p.ring_mask && (unsigned)(ld_vol64(sl) >> 32) != t) {
+        if ((++spins & 255u) == 0 && (gtimer() > deadline || ld_vol(&gctl->abort))) {
+            fail(gctl, EIK_ETIMEDOUT, 0x6100000ull);
+            return false;
+        }
+    }
+    st_vol64(sl, slot_full(t, v));
+    return true;
+}
+__device__ __forceinline__ bool give(const SolveParams& p, Ctl* gctl, unsigned v, unsigned long long deadline) {
+    QEV(3);
+    return ring_fill(p, gctl, atomicAdd(&p.qctl[Q_TAIL], 1u), v, deadline);
+}
+// File entry v in bucket ring s.
+__device__ __forceinline__ bool bq_put(const SolveParams& p, Ctl* gctl, unsigned s, unsigned v,
+                                       unsigned long long deadline) {
+    QEV(5);
+    const unsigned t = atomicAdd(&p.bq[2 * s + 1], 1u);
+    unsigned long long* sl = p.bq_data + (size_t)s * (p.bq_mask + 1u) + (t & p.bq_mask);
+    unsigned spins = 0;
+    // later laps wait for the previous lap's consumer to release the slot
+    while (t > p.bq_mask && (unsigned)(ld_vol64(sl) >> 32) != t) {
+        if ((++spins & 255u) == 0 && (gtimer() > deadline || ld_vol(&gctl->abort))) {
+            fail(gctl, EIK_ETIMEDOUT, 0x6200000ull);
+            return false;
+        }
+    }
+    st_vol64(sl, slot_full(t, v));
+    return true;
+}
+// The entry of ticket h of bucket ring s (already claimed), given the slot's
+// first reading w: wait for its producer, release the slot.  -2: gave up.
+__device__ __forceinline__ int bq_take(const SolveParams& p, Ctl* gctl, unsigned s, unsigned h,
+                                       unsigned long long w, unsigned long long deadline) {
+    unsigned long long* sl = p.bq_data + (size_t)s * (p.bq_mask + 1u) + (h & p.bq_mask);
+    unsigned spins = 0;
+    while ((unsigned)(w >> 32) != h + 1u) {
+        if ((++spins & 255u) == 0 && (gtimer() > deadline || ld_vol(&gctl->abort))) {
+            fail(gctl, EIK_ETIMEDOUT, 0x6300000ull);
+            return -2;
+        }
+        w = ld_vol64(sl);
+    }
+    st_vol64(sl, slot_free(h + p.bq_mask + 1u));
+    return (int)(unsigned)w;
+}
+__device__ __forceinline__ int bq_read(const SolveParams& p, Ctl* gctl, unsigned s, unsigned h,
+                                       unsigned long long deadline) {
+    return bq_take(p, gctl, s, h, ld_vol64(p.bq_data + (size_t)s * (p.bq_mask + 1u) + (h & p.bq_mask)), deadline);
+}
+// Request a cell (global index e) whose activation proposes cell-value key
+// `key`: count it under its bucket, then hand it to a parked warp (within
+// the window) or file it.
+__device__ __forceinline__ bool bq_request(const SolveParams& p, Ctl* gctl, unsigned e, unsigned long long key,
+                                           double inv_delta, unsigned long long deadline) {
+    unsigned f = ld_vol(&p.bq[BQ_FRONT]);
+    int waiters = ring_waiters(p);
+    const double v = key == KEY_UNSET ? inf_of<double>() : val_of(key) * inv_delta;
+    const unsigned a0 = v < 1073741824.0 ? (unsigned)v : 1073741824u;
+    unsigned a, s;
+    for (unsigned tries = 1;; ++tries) {
+        a = a0 < f ? f : a0;
+        a = a > f + NBQ - 1 ? f + NBQ - 1 : a;
+        s = a & (NBQ - 1);
+        const unsigned long long old = atomicAdd(bq_cw(p, s), 1ull);
+        if ((old & CW_CLOSED) == 0 && (old >> 33) == (unsigned long long)(a / NBQ)) break;
+        // the front moved past this bucket: file the cell under the new front
+        atomicAdd(bq_cw(p, s), ~0ull);
+        QEV(4);
+        if ((tries & 255u) == 0 && (gtimer() > deadline || ld_vol(&gctl->abort))) {
+            fail(gctl, EIK_ETIMEDOUT, 0x6500000ull);
+            return false;
+        }
+        f = ld_vol(&p.bq[BQ_FRONT]);
+        waiters = ring_waiters(p);
+    }
+    const unsigned ent = e | (s << CELL_BITS);
+    if (a <= f + (unsigned)p.bq_window && waiters > 0) return give(p, gctl, ent, deadline);
+    return bq_put(p, gctl, s, ent, deadline);
+}
+// Warp-wide scan of the bucket rings in one round trip (lane L reads ring
+// L's head and tail, lane 0 the front too): the mask of rings, rotated so
+// that bit i is bucket front + i, that hold cells within the window.
+struct BqScan {
+    unsigned f, rm, hd, n;
+};
+__device__ __forceinline__ BqScan bq_scan(const SolveParams& p, int lane) {
+    const unsigned f0 = lane == 0 ? ld_vol(&p.bq[BQ_FRONT]) : 0u;
+    const unsigned long long ht = ld_vol64(reinterpret_cast<const unsigned long long*>(p.bq) + lane);
+    BqScan r;
+    r.f = __shfl_sync(0xffffffffu, f0, 0);
+    r.hd = (unsigned)ht;
+    const int n = (int)((unsigned)(ht >> 32) - r.hd);
+    r.n = n > 0 ? (unsigned)n : 0u;
+    const unsigned rel = ((unsigned)lane - r.f) & (NBQ - 1);
+    const unsigned m = __ballot_sync(0xffffffffu, rel <= (unsigned)p.bq_window && n > 0);
+    r.rm = __funnelshift_r(m, m, r.f & (NBQ - 1));
+    return r;
+}
+// Warp-wide: claim the oldest cell of the lowest non-empty bucket within the
+// window.  >= 0 the entry, -3 nothing to claim (or the race for it lost
+// three times: the warp then parks rather than join a herd of warps retrying
+// on one ring's head), -2 gave up.
+__device__ __forceinline__ int bq_claim(const SolveParams& p, Ctl* gctl, unsigned long long deadline, int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    for (int tries = 0; tries < 3; ++tries) {
+        const BqScan sc = bq_scan(p, lane);
+        if (!sc.rm) return -3;
+        const int L0 = (int)((sc.f + (unsigned)(__ffs(sc.rm) - 1)) & (NBQ - 1));
+        int r = -4;
+        if (lane == L0 && atomicCAS(&p.bq[2 * L0], sc.hd, sc.hd + 1u) == sc.hd) {
+            QEV(0);
+            r = bq_read(p, gctl, (unsigned)L0, sc.hd, deadline);
+        }
+        r = __shfl_sync(FULL, r, L0);
+        if (r != -4) return r;
+    }
+    return -3;
+}
+// Warp-wide: hand up to `most` cells of bucket ring s to parked warps (up to
+// one per parked warp), HB cells a lane at a time: the ring's head moves
+// once per batch, the producers' slots are read together, and one ticket
+// draw covers the batch.  Returns the cells handed on.
+constexpr int HB = 4;
+__device__ __forceinline__ unsigned bq_handoff(const SolveParams& p, Ctl* gctl, unsigned s, unsigned most,
+                                               unsigned long long deadline, int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    unsigned total = 0;
+    for (int round = 0; round < 16 && total < most; ++round) {
+        unsigned hd = 0, n = 0;
+        if (lane == 0) {
+            const unsigned long long ht = ld_vol64(reinterpret_cast<const unsigned long long*>(p.bq) + s);
+            hd = (unsigned)ht;
+            const int avail = (int)((unsigned)(ht >> 32) - hd), wait = ring_waiters(p);
+            int want = avail < wait ? avail : wait;
+            want = want < 32 * HB ? want : 32 * HB;
+            want = (unsigned)want < most - total ? want : (int)(most - total);
+            if (want > 0) n = atomicCAS(&p.bq[2 * s], hd, hd + (unsigned)want) == hd ? (unsigned)want : ~0u;
+        }
+        n = __shfl_sync(FULL, n, 0);
+        if (n == 0u) break;
+        if (n == ~0u) continue;  // lost the race for the head: look again
+        hd = __shfl_sync(FULL, hd, 0);
+        unsigned long long* base = p.bq_data + (size_t)s * (p.bq_mask + 1u);
+        unsigned long long w[HB];
+        int v[HB];
+#pragma unroll
+        for (int q = 0; q < HB; ++q) {
+            const unsigned j = (unsigned)lane + 32u * q;
+            w[q] = j < n ? ld_vol64(base + ((hd + j) & p.bq_mask)) : 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < HB; ++q) {
+            const unsigned j = (unsigned)lane + 32u * q;
+            v[q] = j < n ? bq_take(p, gctl, s, hd + j, w[q], deadline) : -1;
+        }
+        unsigned t0 = lane == 0 ? atomicAdd(&p.qctl[Q_TAIL], n) : 0u;
+        t0 = __shfl_sync(FULL, t0, 0);
+#pragma unroll
+        for (int q = 0; q < HB; ++q) {
+            const unsigned j = (unsigned)lane + 32u * q;
+            if (j < n && v[q] >= 0) ring_fill(p, gctl, t0 + j, (unsigned)v[q], deadline);
+        }
+        if (lane == 0) atomicAdd(&gctl->handoffs, (unsigned long long)n);
+        total += n;
+        __syncwarp();
+        if (ld_vol(&gctl->abort)) break;
+    }
+    return total;
+}
+// Warp-wide: while cells remain, close the front's bucket if it counts no
+// cell, move the front one up, reopen the ring for the bucket NBQ higher,
+// and hand the cells of the bucket that enters the window to parked warps.
+__device__ __forceinline__ void bq_advance(const SolveParams& p, Ctl* gctl, unsigned long long deadline, int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    for (int step = 0; step < NBQ; ++step) {
+        int moved = 0;
+        unsigned f = 0;
+        if (lane == 0) {
+            f = ld_vol(&p.bq[BQ_FRONT]);
+            const unsigned s0 = f & (NBQ - 1);
+            const unsigned long long open0 = (unsigned long long)(f / NBQ) * CW_LAP;
+            if (ld_vol(reinterpret_cast<const int*>(&p.qctl[Q_PENDING])) != 0 &&
+                atomicCAS(bq_cw(p, s0), open0, open0 | CW_CLOSED) == open0) {
+                atomicMax(&p.bq[BQ_FRONT], f + 1u);
+                // the ring now serves bucket f + NBQ: next lap, open (counts of
+                // requests that took the closed bucket are taken back by them)
+                atomicAdd(bq_cw(p, s0), CW_LAP - CW_CLOSED);
+                atomicAdd(&gctl->fronts, 1ull);
+                moved = 1;
+            }
+        }
+        moved = __shfl_sync(FULL, moved, 0);
+        if (!moved) return;
+        f = __shfl_sync(FULL, f, 0);
+        bq_handoff(p, gctl, (f + 1u + (unsigned)p.bq_window) & (NBQ - 1), ~0u, deadline, lane);
+        if (ld_vol(&gctl->abort)) return;
+    }
+}
+// Warp-wide: a cell to run -- claimed from the buckets, or received on a
+// parked ticket.  >= 0 the entry, -1 converged, -2 gave up.
+__device__ __forceinline__ int bq_next(const SolveParams& p, Ctl* gctl, unsigned long long deadline, int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int r = bq_claim(p, gctl, deadline, lane);
+    if (r != -3) return r;
+    unsigned x = 0;
+    if (lane == 0) {
+        QEV(1);
+        x = atomicAdd(&p.qctl[Q_HEAD], 1u);
+    }
+    x = __shfl_sync(FULL, x, 0);
+    unsigned long long* sl = p.ring + (x & p.ring_mask);
+    unsigned spins = 0, ns = 16;
+    for (;;) {
+        int got = -3;
+        if (lane == 0) {
+            const unsigned long long w = ld_vol64(sl);
+            if ((unsigned)(w >> 32) == x + 1u) {
+                st_vol64(sl, slot_free(x + p.ring_mask + 1u));
+                got = (int)(unsigned)w;
+                QEV(2);
+            }
+        }
+        got = __shfl_sync(FULL, got, 0);
+        if (got >= 0) return got;
+        if ((++spins & 31u) == 0) {
+            int st = 0;
+            if (lane == 0) {
+                if (ld_vol(reinterpret_cast<const int*>(&p.qctl[Q_PENDING])) == 0) st = -1;
+                else if (ld_vol(&gctl->abort)) st = -2;
+                else if (gtimer() > deadline) {
+                    fail(gctl, EIK_ETIMEDOUT, 0x7100000ull);
+                    st = -2;
+                }
+            }
+            st = __shfl_sync(FULL, st, 0);
+            if (st) return st;
+        }
+        // Rarely (every 512 waits, ~0.1 ms): a front whose last cell
+        // finished unseen, and cells left within the window while the warps
+        // waited (filed when none was parked), handed on to parked warps --
+        // this one among them, which keeps its ticket.
+        if ((spins & 511u) == 0) {
+            if (lane == 0) QEV(7);
+            bq_advance(p, gctl, deadline, lane);
+            const BqScan sc = bq_scan(p, lane);
+            unsigned rm = sc.rm;
+            while (rm) {
+                const int i = __ffs(rm) - 1;
+                rm &= rm - 1u;
+                const unsigned sr = (sc.f + (unsigned)i) & (NBQ - 1);
+                const unsigned n = bq_handoff(p, gctl, sr, ~0u, deadline, lane);
+                if (lane == 0 && n) atomicAdd(&gctl->qev[6], (unsigned long long)n);
+            }
+        }
+        __nanosleep(ns);
+        ns = ns < 256 ? 2 * ns : 256;
+    }
+}
+
 // The double-float kernels at k = 8 and 16 are held to three blocks per SM:
 // left alone, the compiler fits them into 64 registers (four blocks) with
 // spills, which measured slower (1025^2: 1.86 against 1.73 ms per pass; the
 // 512-grid batch 14.1 against 13.9 ms).  0 leaves the others to the compiler.
-template <int MODE, int K, int VAR>
-__global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32, (MODE == MODE_DF && (K == 8 || K == 16)) ? 3 : 0)
+// ORD: the value-ordered schedule (bucket rings, a front, a window) instead
+// of first-in first-out.  Left to itself the compiler squeezes the ordered
+// FP64 and FP32 kernels into 48-64 registers with spills; they get the
+// first-in first-out kernels' two blocks per SM instead.
+template <int MODE, int K, int VAR, bool ORD>
+__global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32,
+                                  (MODE == MODE_DF && (K == 8 || K == 16)) ? 3 : (ORD ? 2 : 0))
     k_solve_async(const __grid_constant__ SolveParams p) {
     using C = TileCfg<MODE, K>;
     static_assert(C::CPW == 1, "one cell per warp");
@@ -1420,7 +1744,37 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32, (MODE == MODE_DF &
     __syncthreads();
     const int total = block_exclusive_scan(s_cnt, s_pre, NI, s_scr);
     const unsigned Q = p.ring_mask + 1u;
-    const bool sorted = total > SORT_MIN;
+    double inv_delta = 0.0;  // ORD: 1 / bucket width
+    if constexpr (ORD) {
+        // empty rings (slot j of every ring free for ticket j), the front at
+        // bucket 0, and the launch's bucket width: the smallest of its
+        // instances' (relative widths in units of k min(h/F), default 4)
+        const unsigned BQ = p.bq_mask + 1u;
+        for (unsigned e = gtid; e < Q; e += gthreads) p.ring[e] = slot_free(e);
+        for (size_t e = gtid; e < (size_t)NBQ * BQ; e += gthreads) p.bq_data[e] = slot_free((unsigned)(e & p.bq_mask));
+        for (int e = gtid; e < BQ_WORDS; e += gthreads) p.bq[e] = 0u;
+        for (int i = gtid; i < NI; i += gthreads) {
+            double delta = inst[i].delta;
+            if (!(delta > 0.0)) delta = (delta < 0.0 ? -delta : 4.0) * (double)K * val_of(ld_cg(&inst[i].ctl->fmin_f));
+            if (delta > 0.0 && delta < inf_of<double>()) atomicMin(&gctl->qdelta, key_of(delta));
+        }
+        if (gtid == 0) {
+            p.qctl[Q_HEAD] = 0;
+            p.qctl[Q_TAIL] = 0;
+            p.qctl[Q_PENDING] = (unsigned)total;
+        }
+        if (!grid_sync(gctl, deadline, &s_flag)) return;
+        const unsigned long long dk = ld_cg(&gctl->qdelta);
+        inv_delta = dk == KEY_UNSET ? 0.0 : 1.0 / val_of(dk);
+        for (int e = gtid; e < total; e += gthreads) {
+            const int i = find_inst(s_pre, NI, e);
+            const InstDesc& d = inst[i];
+            const int c = ld_cg(&d.lists[3 * d.J + (e - s_pre[i])]);
+            bq_request(p, gctl, (unsigned)(d.cell_base + c), ld_cg(&d.cval[c]), inv_delta, deadline);
+        }
+        if (!grid_sync(gctl, deadline, &s_flag)) return;
+    }
+    const bool sorted = !ORD && total > SORT_MIN;
     auto seed_cell = [&](int e, int& gcell) -> int {  // initial entry e: global cell, bucket
         const int i = find_inst(s_pre, NI, e);
         const InstDesc& d = inst[i];
@@ -1444,24 +1798,26 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32, (MODE == MODE_DF &
         if (blockIdx.x == 0) block_exclusive_scan(p.hist, p.hist + SORT_BUCKETS, SORT_BUCKETS, s_scr);
         if (!grid_sync(gctl, deadline, &s_flag)) return;
     }
-    for (unsigned e = gtid; e < Q; e += gthreads) {
-        if ((int)e < total) {
-            int gc;
-            const int b = seed_cell((int)e, gc);
-            const unsigned pos =
-                sorted ? (unsigned)(ld_cg(&p.hist[SORT_BUCKETS + b]) + atomicAdd(&p.hist[2 * SORT_BUCKETS + 1 + b], 1))
-                       : e;
-            p.ring[pos] = ((unsigned long long)(pos + 1u) << 32) | (unsigned)gc;
-        } else {
-            p.ring[e] = ((unsigned long long)e << 32) | 0xffffffffull;
+    if constexpr (!ORD) {
+        for (unsigned e = gtid; e < Q; e += gthreads) {
+            if ((int)e < total) {
+                int gc;
+                const int b = seed_cell((int)e, gc);
+                const unsigned pos =
+                    sorted ? (unsigned)(ld_cg(&p.hist[SORT_BUCKETS + b]) + atomicAdd(&p.hist[2 * SORT_BUCKETS + 1 + b], 1))
+                           : e;
+                p.ring[pos] = ((unsigned long long)(pos + 1u) << 32) | (unsigned)gc;
+            } else {
+                p.ring[e] = ((unsigned long long)e << 32) | 0xffffffffull;
+            }
         }
+        if (gtid == 0) {
+            p.qctl[Q_HEAD] = 0;
+            p.qctl[Q_TAIL] = (unsigned)total;
+            p.qctl[Q_PENDING] = (unsigned)total;
+        }
+        if (!grid_sync(gctl, deadline, &s_flag)) return;
     }
-    if (gtid == 0) {
-        p.qctl[Q_HEAD] = 0;
-        p.qctl[Q_TAIL] = (unsigned)total;
-        p.qctl[Q_PENDING] = (unsigned)total;
-    }
-    if (!grid_sync(gctl, deadline, &s_flag)) return;
 
     // ---- each warp: take a cell, solve it, hand on its activations.  (A
     // warp that kept one of the neighbours it requested and ran it next,
@@ -1471,10 +1827,18 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32, (MODE == MODE_DF &
     // wave together.)
     for (;;) {
         int e = 0;
-        if (lane == 0) e = ring_pop(p, gctl, deadline);
-        e = __shfl_sync(FULL, e, 0);
-        if (e < 0) break;
-        if (p.hold_ns) {
+        unsigned my_ring = 0;  // ORD: the bucket ring this cell is counted under
+        if constexpr (ORD) {
+            e = bq_next(p, gctl, deadline, lane);
+            if (e < 0) break;
+            my_ring = (unsigned)e >> CELL_BITS;
+            e &= (int)CELL_MASK;
+        } else {
+            if (lane == 0) e = ring_pop(p, gctl, deadline);
+            e = __shfl_sync(FULL, e, 0);
+            if (e < 0) break;
+        }
+        if (!ORD && p.hold_ns) {
             // a cell requested less than hold_ns ago (0: no time recorded)
             // goes back to the ring's tail, still requested, and the warp
             // takes the next one: requests from several upstream neighbours
@@ -1504,20 +1868,52 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32, (MODE == MODE_DF &
         PROF_MARK(2);
         pacc[7] += 1;
         const int cg[1] = {c}, ig[1] = {ii};
-        const bool ok = visit_cells<MODE, K, false, VAR>(
+        const bool ok = visit_cells<MODE, K, ORD, VAR>(
             w, inst, gctl, deadline, c, ii, first, cg, ig, prof_on, pacc, pt,
-            [&](const InstDesc& dn, int nc, unsigned long long, unsigned long long, bool activate) {
-                if (activate && (atomicOr(&dn.qflag[nc], 1) & 3) == 0) {
-                    if (p.hold_ns) p.req_time[dn.cell_base + nc] = gtimer();
+            [&](const InstDesc& dn, int nc, unsigned long long kk, unsigned long long old, bool activate) {
+                if (!activate) return;
+                const int was = atomicOr(&dn.qflag[nc], 1) & 3;
+                if (was == 0) {
                     atomicAdd(&p.qctl[Q_PENDING], 1u);
-                    ring_push(p, gctl, (unsigned)(dn.cell_base + nc), deadline);
+                    if constexpr (ORD) {
+                        // filed by the value this side proposes (eq. cell_value):
+                        // the cell's own value, lowered by every earlier proposal,
+                        // would rank a cell visited before at its old value
+                        // (an activation always has a finite side, so a proposal)
+                        bq_request(p, gctl, (unsigned)(dn.cell_base + nc), kk, inv_delta, deadline);
+                    } else {
+                        if (p.hold_ns) p.req_time[dn.cell_base + nc] = gtimer();
+                        ring_push(p, gctl, (unsigned)(dn.cell_base + nc), deadline);
+                    }
+                } else if (ORD && (was & 2) && kk != KEY_UNSET) {
+                    // requested while it runs: its finish files it again, by
+                    // the lowest value proposed meanwhile (kept complemented,
+                    // 0 = none)
+                    atomicMax(&p.req_time[dn.cell_base + nc], ~kk);
                 }
             });
         // ---- finish: push again if a neighbour asked meanwhile
+        int adv = 0;
         if (lane == 0) {
             const int old = atomicAnd(&d.qflag[c], ~2);
-            if (old & 1) ring_push(p, gctl, (unsigned)e, deadline);
-            else atomicSub(&p.qctl[Q_PENDING], 1u);
+            if constexpr (ORD) {
+                if (old & 1) {
+                    const unsigned long long rk = atomicExch(&p.req_time[e], 0ull);
+                    bq_request(p, gctl, (unsigned)e, rk ? ~rk : ld_cg(&d.cval[c]), inv_delta, deadline);
+                } else {
+                    atomicSub(&p.qctl[Q_PENDING], 1u);
+                }
+                // the last cell of the front's bucket moves the front
+                const unsigned long long was = atomicAdd(bq_cw(p, my_ring), ~0ull);
+                adv = (was & 0xffffffffull) == 1ull && (ld_vol(&p.bq[BQ_FRONT]) & (NBQ - 1)) == my_ring;
+            } else {
+                if (old & 1) ring_push(p, gctl, (unsigned)e, deadline);
+                else atomicSub(&p.qctl[Q_PENDING], 1u);
+            }
+        }
+        if constexpr (ORD) {
+            if (__shfl_sync(FULL, adv, 0)) bq_advance(p, gctl, deadline, lane);
+            PROF_MARK(0);  // finish and front moves (profiles: "split")
         }
         __syncwarp();
         if (!ok) break;

@@ -9,26 +9,32 @@ namespace eik {
 // The Fast Heap-Cell variant and HCM with locking are built for FP64 only
 // (the only mode that offers them); the plain HCM kernels carry none of
 // their code.
+// sched: SCH_ROUNDS (k_solve), SCH_FIFO or SCH_ORDERED (k_solve_async,
+// one cell per warp; the value-ordered form is built for plain HCM only)
 template <int MODE, int K, int VAR>
-static const void* solver_fn_var(bool async) {
-    if constexpr (TileCfg<MODE, K>::CPW == 1)
-        if (async) return (const void*)k_solve_async<MODE, K, VAR>;
+static const void* solver_fn_var(int sched) {
+    if constexpr (TileCfg<MODE, K>::CPW == 1) {
+        if constexpr (VAR == VAR_HCM)
+            if (sched == SCH_ORDERED) return (const void*)k_solve_async<MODE, K, VAR, true>;
+        if (sched != SCH_ROUNDS) return (const void*)k_solve_async<MODE, K, VAR, false>;
+    }
     return (const void*)k_solve<MODE, K, VAR>;
 }
 
 template <int MODE, int K>
-static const void* solver_fn(bool async, int variant) {
+static const void* solver_fn(int sched, int variant) {
     if constexpr (MODE == MODE_F64) {
-        if (variant == VAR_FHCM) return solver_fn_var<MODE, K, VAR_FHCM>(async);
-        if (variant == VAR_LSM) return solver_fn_var<MODE, K, VAR_LSM>(async);
+        if (variant == VAR_FHCM) return solver_fn_var<MODE, K, VAR_FHCM>(sched);
+        if (variant == VAR_LSM) return solver_fn_var<MODE, K, VAR_LSM>(sched);
     }
-    return solver_fn_var<MODE, K, VAR_HCM>(async);
+    return solver_fn_var<MODE, K, VAR_HCM>(sched);
 }
 
 template <int MODE, int K>
-static void shape_of(int num_sms, int n_inst, int sm_cap, bool async, int variant, LaunchShape* s) {
+static void shape_of(int num_sms, int n_inst, int sm_cap, int sched, int variant, LaunchShape* s) {
     using C = TileCfg<MODE, K>;
-    const void* fn = solver_fn<MODE, K>(async, variant);
+    const void* fn = solver_fn<MODE, K>(sched, variant);
+    const bool async = sched != SCH_ROUNDS;
     s->threads = C::WPB * 32;
     s->smem = (size_t)C::WPB * C::WARP_BYTES + (size_t)C::lk_area(MODE == MODE_F64 ? variant : VAR_HCM) + 128 +
               (size_t)inst_state_bytes(n_inst);
@@ -55,37 +61,37 @@ static void shape_of(int num_sms, int n_inst, int sm_cap, bool async, int varian
 }
 
 template <int MODE>
-static int solver_shape_mode(int k, int num_sms, int n_inst, int sm_cap, bool async, int variant,
+static int solver_shape_mode(int k, int num_sms, int n_inst, int sm_cap, int sched, int variant,
                              LaunchShape* out) {
     out->blocks = 0;
     switch (k) {
-    case 4: shape_of<MODE, 4>(num_sms, n_inst, sm_cap, async, variant, out); break;
-    case 8: shape_of<MODE, 8>(num_sms, n_inst, sm_cap, async, variant, out); break;
-    case 16: shape_of<MODE, 16>(num_sms, n_inst, sm_cap, async, variant, out); break;
-    case 32: shape_of<MODE, 32>(num_sms, n_inst, sm_cap, async, variant, out); break;
-    case 64: shape_of<MODE, 64>(num_sms, n_inst, sm_cap, async, variant, out); break;
+    case 4: shape_of<MODE, 4>(num_sms, n_inst, sm_cap, sched, variant, out); break;
+    case 8: shape_of<MODE, 8>(num_sms, n_inst, sm_cap, sched, variant, out); break;
+    case 16: shape_of<MODE, 16>(num_sms, n_inst, sm_cap, sched, variant, out); break;
+    case 32: shape_of<MODE, 32>(num_sms, n_inst, sm_cap, sched, variant, out); break;
+    case 64: shape_of<MODE, 64>(num_sms, n_inst, sm_cap, sched, variant, out); break;
     default: return -1;
     }
     return out->blocks > 0 ? 0 : -1;
 }
 
 template <int MODE, int K>
-static cudaError_t launch_one(bool async, int variant, const SolveParams& p, const LaunchShape& s,
+static cudaError_t launch_one(int sched, int variant, const SolveParams& p, const LaunchShape& s,
                               cudaStream_t st) {
     void* args[] = {(void*)&p};
-    return cudaLaunchCooperativeKernel(solver_fn<MODE, K>(async, variant), dim3(s.blocks), dim3(s.threads), args,
+    return cudaLaunchCooperativeKernel(solver_fn<MODE, K>(sched, variant), dim3(s.blocks), dim3(s.threads), args,
                                        s.smem, st);
 }
 
 template <int MODE>
-static cudaError_t launch_solver_mode(int k, bool async, const SolveParams& p, const LaunchShape& s,
+static cudaError_t launch_solver_mode(int k, int sched, const SolveParams& p, const LaunchShape& s,
                                       cudaStream_t st) {
     switch (k) {
-    case 4: return launch_one<MODE, 4>(async, p.variant, p, s, st);
-    case 8: return launch_one<MODE, 8>(async, p.variant, p, s, st);
-    case 16: return launch_one<MODE, 16>(async, p.variant, p, s, st);
-    case 32: return launch_one<MODE, 32>(async, p.variant, p, s, st);
-    case 64: return launch_one<MODE, 64>(async, p.variant, p, s, st);
+    case 4: return launch_one<MODE, 4>(sched, p.variant, p, s, st);
+    case 8: return launch_one<MODE, 8>(sched, p.variant, p, s, st);
+    case 16: return launch_one<MODE, 16>(sched, p.variant, p, s, st);
+    case 32: return launch_one<MODE, 32>(sched, p.variant, p, s, st);
+    case 64: return launch_one<MODE, 64>(sched, p.variant, p, s, st);
     default: return cudaErrorInvalidValue;
     }
 }

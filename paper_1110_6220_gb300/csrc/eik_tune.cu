@@ -41,6 +41,8 @@ struct Entry {
     bool async_first = false, async_main = false;  // round-free schedule per pass
     bool one_pass = false;  // FP32_REFINE as one double-float pass
     unsigned hold_ns = 0;   // round-free: minimum request age before a cell runs
+    bool ordered = false;   // round-free main pass in value order (bucket rings)
+    int window = 31;        // ... taking cells from this many buckets above the front
 };
 
 std::mutex g_mu;
@@ -129,19 +131,26 @@ int load_file(const char* path) {
     if (!f) return EIK_EINVAL;
     char line[256];
     int rc = EIK_OK;
-    if (!std::fgets(line, sizeof line, f) || std::strncmp(line, "eik-tune 4", 10) != 0) {
+    // version 5 adds the value-ordered schedule and its window to each line;
+    // version 4 lines (no such fields) read as first in, first out
+    int version = 0;
+    if (std::fgets(line, sizeof line, f) && std::strncmp(line, "eik-tune 5", 10) == 0) version = 5;
+    else if (std::strncmp(line, "eik-tune 4", 10) == 0) version = 4;
+    if (!version) {
         rc = EIK_EINVAL;
     } else {
         std::map<Key, Entry> t;
         while (std::fgets(line, sizeof line, f)) {
             Key key;
             Entry e;
-            int af = 0, am = 0, op = 0;
+            int af = 0, am = 0, op = 0, ord = 0, win = 31;
             unsigned hold = 0;
-            if (std::sscanf(line, "%d %d %d %d %lf %lf %d %d %d %u %lf", &key.prec, &key.batch, &key.side, &e.k,
-                            &e.m_first, &e.m_main, &af, &am, &op, &hold, &e.ms) != 11 ||
+            const int want = version == 5 ? 13 : 11;
+            if (std::sscanf(line, "%d %d %d %d %lf %lf %d %d %d %u %lf %d %d", &key.prec, &key.batch, &key.side,
+                            &e.k, &e.m_first, &e.m_main, &af, &am, &op, &hold, &e.ms, &ord, &win) != want ||
                 (e.k != 4 && e.k != 8 && e.k != 16 && e.k != 32 && e.k != 64) || !(e.m_first > 0) ||
-                !(e.m_main > 0) || (af != 0 && af != 1) || (am != 0 && am != 1) || (op != 0 && op != 1)) {
+                !(e.m_main > 0) || (af != 0 && af != 1) || (am != 0 && am != 1) || (op != 0 && op != 1) ||
+                (ord != 0 && ord != 1) || win < 0 || win > NBQ - 1) {
                 rc = EIK_EINVAL;
                 break;
             }
@@ -149,6 +158,8 @@ int load_file(const char* path) {
             e.async_main = am;
             e.one_pass = op;
             e.hold_ns = hold;
+            e.ordered = ord;
+            e.window = win;
             t[key] = e;
         }
         if (!rc)
@@ -187,16 +198,27 @@ JobParams choose_params(const eik_plan_desc* d, int n) {
     P.async_main = e.async_main;
     // EIK_SCHED="<first>,<main>" with r (rounds) or a (async) overrides the
     // schedule of each pass (for measurements)
-    static const char* sched = std::getenv("EIK_SCHED");
+    const char* sched = std::getenv("EIK_SCHED");
     if (sched && std::strlen(sched) >= 3) {
         P.async_first = sched[0] == 'a';
         P.async_main = sched[2] == 'a';
     }
     P.one_pass = e.one_pass;
     P.hold_ns = e.hold_ns;
-    static const char* hold = std::getenv("EIK_HOLD_NS");  // measurements: overrides the table
+    P.ordered = e.ordered;
+    P.window = e.window;
+    // a schedule named in the descriptor wins for every persistent pass
+    if (d[0].schedule == EIK_SCHED_ROUNDS) {
+        P.async_first = P.async_main = P.ordered = false;
+    } else if (d[0].schedule == EIK_SCHED_FIFO || d[0].schedule == EIK_SCHED_ORDERED) {
+        P.async_first = P.async_main = true;
+        P.ordered = d[0].schedule == EIK_SCHED_ORDERED;
+        P.hold_ns = 0;
+    }
+    if (d[0].window > 0) P.window = d[0].window - 1;
+    const char* hold = std::getenv("EIK_HOLD_NS");  // measurements: overrides the table
     if (hold && hold[0]) P.hold_ns = (unsigned)std::strtoul(hold, nullptr, 10);
-    static const char* onep = std::getenv("EIK_ONE_PASS");
+    const char* onep = std::getenv("EIK_ONE_PASS");
     if (onep && onep[0]) P.one_pass = onep[0] == '1';
     return P;
 }
@@ -344,11 +366,12 @@ extern "C" int eik_tune_save(const char* path) {
     std::lock_guard<std::mutex> lock(g_mu);
     FILE* f = std::fopen(path, "w");
     if (!f) return EIK_EINVAL;
-    std::fprintf(f, "eik-tune 4\n");
+    std::fprintf(f, "eik-tune 5\n");
     for (auto& kv : g_table)
-        std::fprintf(f, "%d %d %d %d %.17g %.17g %d %d %d %u %.17g\n", kv.first.prec, kv.first.batch,
+        std::fprintf(f, "%d %d %d %d %.17g %.17g %d %d %d %u %.17g %d %d\n", kv.first.prec, kv.first.batch,
                      kv.first.side, kv.second.k, kv.second.m_first, kv.second.m_main, (int)kv.second.async_first,
-                     (int)kv.second.async_main, (int)kv.second.one_pass, kv.second.hold_ns, kv.second.ms);
+                     (int)kv.second.async_main, (int)kv.second.one_pass, kv.second.hold_ns, kv.second.ms,
+                     (int)kv.second.ordered, kv.second.window);
     return std::fclose(f) == 0 ? EIK_OK : EIK_EINVAL;
 }
 

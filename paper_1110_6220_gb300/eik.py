@@ -38,6 +38,10 @@ EIK_METHOD_HCM = 0
 EIK_METHOD_FHCM = 1
 EIK_METHOD_FMSM = 2
 EIK_METHOD_HCM_LSM = 3
+EIK_SCHED_AUTO = 0
+EIK_SCHED_ROUNDS = 1
+EIK_SCHED_FIFO = 2
+EIK_SCHED_ORDERED = 3
 EIK_NOALLOC_SCRATCH_BYTES = 32 << 20
 EIK_NOALLOC_MAX_SOURCES = 256
 
@@ -46,7 +50,8 @@ class eik_plan_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("h", ctypes.c_double),
                 ("cell_k", ctypes.c_int32), ("bucket_width", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("tol", ctypes.c_double),
-                ("deadline_ns", ctypes.c_int64), ("method", ctypes.c_int32)]
+                ("deadline_ns", ctypes.c_int64), ("method", ctypes.c_int32),
+                ("schedule", ctypes.c_int32), ("window", ctypes.c_int32)]
 
 
 class eik_instance(ctypes.Structure):
@@ -278,9 +283,10 @@ def _ptr(a, dtype):
 
 
 def make_desc(nx, ny, h, cell_k=8, precision=EIK_FP64, bucket_width=0.0, tol=0.0,
-              deadline_ns=0, method=0) -> eik_plan_desc:
+              deadline_ns=0, method=0, schedule=EIK_SCHED_AUTO, window=0) -> eik_plan_desc:
     return eik_plan_desc(int(nx), int(ny), float(h), int(cell_k), float(bucket_width),
-                         int(precision), float(tol), int(deadline_ns), int(method))
+                         int(precision), float(tol), int(deadline_ns), int(method), int(schedule),
+                         int(window))
 
 
 def make_instance(F, src_ij, src_q, U) -> eik_instance:
@@ -293,8 +299,9 @@ class Plan:
     """Owns an ``eik_plan`` for one grid shape."""
 
     def __init__(self, nx, ny, h, cell_k=8, precision=EIK_FP64, bucket_width=0.0, tol=0.0,
-                 deadline_ns=0, stream=None, method=EIK_METHOD_HCM):
-        self.desc = make_desc(nx, ny, h, cell_k, precision, bucket_width, tol, deadline_ns, method)
+                 deadline_ns=0, stream=None, method=EIK_METHOD_HCM, schedule=EIK_SCHED_AUTO, window=0):
+        self.desc = make_desc(nx, ny, h, cell_k, precision, bucket_width, tol, deadline_ns, method,
+                              schedule, window)
         self.handle = eik_plan_create(self.desc, stream)
 
     def solve(self, F, src_ij, src_q, U):
@@ -322,7 +329,7 @@ class Plan:
 
 
 def solve(F, h, si, sj, sq, cell_k=8, precision=EIK_FP64, bucket_width=0.0, tol=0.0,
-          deadline_ns=0, method=EIK_METHOD_HCM):
+          deadline_ns=0, method=EIK_METHOD_HCM, schedule=EIK_SCHED_AUTO, window=0):
     """Convenience: host arrays in, host U out, (U, stats); raises on error."""
     F = np.ascontiguousarray(F, dtype=np.float64)
     ny, nx = F.shape
@@ -330,7 +337,8 @@ def solve(F, h, si, sj, sq, cell_k=8, precision=EIK_FP64, bucket_width=0.0, tol=
                                   .reshape(-1), dtype=np.int32)
     sq = np.ascontiguousarray(np.atleast_1d(sq), dtype=np.float64)
     U = np.empty((ny, nx), dtype=np.float64)
-    with Plan(nx, ny, h, cell_k, precision, bucket_width, tol, deadline_ns, method=method) as p:
+    with Plan(nx, ny, h, cell_k, precision, bucket_width, tol, deadline_ns, method=method,
+              schedule=schedule, window=window) as p:
         rc, st = p.solve(F, src_ij, sq, U)
     if rc:
         raise EikError(rc, "eik_solve")

@@ -145,11 +145,30 @@ def test_tune_table_round_trip_and_use_without_gpu(tmp_path):
     g = tmp_path / "out.txt"
     assert eik.eik_tune_save(str(g)) == 0
     lines = g.read_text().splitlines()
-    assert lines[0] == "eik-tune 4"
-    assert [float(x) for x in lines[1].split()] == [0, 0, 10, 32, 8, 8, 0, 1, 0, 0, 1.5]
+    assert lines[0] == "eik-tune 5"
+    # a version-4 line reads as first in, first out with the full window
+    assert [float(x) for x in lines[1].split()] == [0, 0, 10, 32, 8, 8, 0, 1, 0, 0, 1.5, 0, 31]
+    # the saved table loads back as it was
+    assert eik.eik_tune_load(str(g)) == 0
+    assert eik.eik_plan_workspace_bytes(d0) == w32
+    # version 5: the value-ordered schedule takes its bucket rings (32 per
+    # cell, a power of two >= the job's cells) on top of the workspace
+    v5 = tmp_path / "v5.txt"
+    v5.write_text("eik-tune 5\n0 0 10 32 8 8 0 1 0 0 1.5 1 2\n")
+    assert eik.eik_tune_load(str(v5)) == 0
+    J = 33 * 33
+    assert eik.eik_plan_workspace_bytes(d0) == w32 + 32 * 2048 * 8 + 1024
+    assert J <= 2048
     bad = tmp_path / "bad.txt"
     bad.write_text("eik-tune 4\n1 0 10 12 8 8 0 0 0 0 1.0\n")  # k = 12 is not a cell size
     assert eik.eik_tune_load(str(bad)) == eik.EIK_EINVAL
+    bad.write_text("eik-tune 5\n1 0 10 16 8 8 0 1 0 0 1.0 1 32\n")  # windows are 0..31 in the table
+    assert eik.eik_tune_load(str(bad)) == eik.EIK_EINVAL
+    bad.write_text("eik-tune 5\n1 0 10 16 8 8 0 1 0 0 1.0\n")  # version 5 lines carry 13 fields
+    assert eik.eik_tune_load(str(bad)) == eik.EIK_EINVAL
+    assert eik.eik_tune_load(str(v5)) == 0
+    eik.eik_tune_reset()
+    assert eik.eik_tune_load(str(f)) == 0
     bad.write_text("something else\n")
     assert eik.eik_tune_load(str(bad)) == eik.EIK_EINVAL
     assert eik.eik_tune_load(str(tmp_path / "missing.txt")) == eik.EIK_EINVAL
@@ -179,3 +198,21 @@ def test_method_descriptor_rules_without_gpu():
     for k in (4, 8, 16, 32, 64):
         assert ws(k, F64, eik.EIK_METHOD_HCM_LSM) == ws(k, F64, eik.EIK_METHOD_HCM)
     assert ws(8, F64, 4) == 0
+
+
+def test_schedule_descriptor_rules_without_gpu():
+    """The descriptor's schedule and window: every EIK_SCHED_* and windows
+    0..32 are accepted, anything else refused; naming the value-ordered
+    schedule adds its bucket rings to the workspace (32 per cell, a power of
+    two >= the grid's cells), the other schedules do not."""
+    from paper_1110_6220_gb300 import eik
+    ws = lambda sched, win=0, k=8: eik.eik_plan_workspace_bytes(
+        eik.make_desc(257, 257, 1 / 256, k, eik.EIK_FP64, schedule=sched, window=win))
+    base = ws(eik.EIK_SCHED_FIFO)
+    assert base > 0 and ws(eik.EIK_SCHED_ROUNDS) == base
+    assert ws(eik.EIK_SCHED_ORDERED) == base + 32 * 2048 * 8 + 1024  # 33^2 cells -> rings of 2048
+    for w in (0, 1, 17, 32):
+        assert ws(eik.EIK_SCHED_ORDERED, w) > 0
+    assert ws(eik.EIK_SCHED_ORDERED, 33) == 0
+    assert ws(eik.EIK_SCHED_ORDERED, -1) == 0
+    assert ws(4) == 0 and ws(-1) == 0
