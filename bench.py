@@ -1,11 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of the two-scale Eikonal solver (one JSON line on rank 0).
 
-A step is one complete solve through the C ABI of the 1025 x 1025 grid with
-speed F = 1 + 0.5 sin(20 pi x) sin(20 pi y) and a point source at the centre
-(the paper's Tab. sinu_1 example at the single-GPU size): FP32 cell solves,
-the FP64 refinement pass and the FP64 residual certificate (precision
-"fp32ref", the default), or the plain FP64 solve (--precision fp64).
+A step is one complete solve through the C ABI of the largest single-grid
+workload: a 4097 x 4097 grid with a 64 x 64 checkerboard of speeds F in
+{1, 2} and a seeded maze of F = 0 walls one node thick with random gaps, 4
+seeded point sources (the paper's checkerboard and comb-maze examples at the
+single-GPU size): the double-float cell solves on the FP32 pipe and the FP64
+residual certificate (precision "fp32ref", the default), or the plain FP64
+solve (--precision fp64).  --workload sin1025 times the 1025 x 1025 grid with
+F = 1 + 0.5 sin(20 pi x) sin(20 pi y) and a centre source instead.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -33,8 +36,13 @@ import numpy as np  # noqa: E402
 
 METRIC = "converged Mpts/s at max|err| vs FP64 oracle"
 UNIT = "Mpts/s"
-N_GRID = 1025
 FALLBACK_HBM_GBS = 6800.0
+WORKLOADS = {
+    "checker_maze4097": "single solve FP32+FP64-refinement: 4097x4097 grid, piecewise-constant speed: 64x64 "
+                        "checkerboard of F in {1,2} plus seeded maze of axis-aligned barrier walls 1 gridpoint "
+                        "thick with F=0 leaving random gaps, 4 seeded random point sources",
+    "sin1025": "single solve, 1025x1025 grid on [0,1]^2, F=1+0.5 sin(20 pi x) sin(20 pi y), point source at centre",
+}
 
 
 def parse():
@@ -44,6 +52,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32ref", "fp64"], default="fp32ref")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="checker_maze4097")
     ap.add_argument("--k", type=int, default=0, help="cell size (0: the tuned default)")
     ap.add_argument("--bucket-width", type=float, default=0.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -65,18 +74,20 @@ def dist_env():
     return world, rank, local
 
 
-def workload():
+def workload(name="checker_maze4097"):
     from paper_1110_6220_gb300 import workloads as W
-    return W.sin_point(N_GRID, omega=20.0, amp=0.5)
+    if name == "sin1025":
+        return W.sin_point(1025, omega=20.0, amp=0.5)
+    return W.checker_maze(4097)
 
 
-def config_dict(args, k, precision):
-    return {"workload": f"single solve, {N_GRID}x{N_GRID} grid on [0,1]^2, "
-                        "F=1+0.5 sin(20 pi x) sin(20 pi y), point source at centre",
-            "grid": N_GRID, "precision": precision, "cell_k": k,
-            "bucket_width": "library choice per pass" if args.bucket_width == 0 else args.bucket_width,
-            "parallelism": "replicas (one independent grid per GPU)",
-            "l2": "flushed between timed steps (256 MiB write)"}
+def config_dict(args, k, precision, I=None):
+    d = {"workload": WORKLOADS[args.workload], "grid": f"{I.nx}x{I.ny}" if I is not None else None,
+         "precision": precision, "cell_k": k,
+         "bucket_width": "library choice per pass" if args.bucket_width == 0 else args.bucket_width,
+         "parallelism": "replicas (one independent grid per GPU)",
+         "l2": "flushed between timed steps (256 MiB write)"}
+    return d
 
 
 # ------------------------------------------------------------------ CPU side
@@ -138,7 +149,7 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    I = workload()
+    I = workload(args.workload)
     import oracle
     oracle.build()
     for _ in range(args.warmup):
@@ -153,7 +164,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(args, 0, "fp64 (CPU oracle)"),
+            "data": "synthetic", "config": config_dict(args, 0, "fp64 (CPU oracle)", I),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} full {I.nx}x{I.ny} FMM solves, 1 thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -240,9 +251,45 @@ def ncu_traffic(kernel, k):
     return e.get("dram_bytes_per_launch")
 
 
-def k_sweep(eik, torch, I, F, src, q, V, reps=3):
+def kernel_name(sched, prec, first):
+    """The persistent kernel a pass ran, from eik_stats.schedule (bit 0: FP32
+    pass round-free, bit 1: main pass round-free, bit 5: value order)."""
+    if first:
+        base, mode = ("k_solve_async" if sched & 1 else "k_solve"), "F32"
+    else:
+        base, mode = ("k_solve_async" if sched & 2 else "k_solve"), ("DF" if prec else "F64")
+    order = ",ordered" if (sched & 32) and base == "k_solve_async" else ""
+    return f"{base}<{mode}{order}>"
+
+
+def roofline(stats, k, prec, npts, p32, p64):
+    """Roofline of the dominant kernel (the longer persistent pass).
+    Algorithmic bytes per grid point (each point read and written once, plus
+    the halo of every cell): FP32 pass 4 B f + 2 x 4 B U, double-float and
+    FP64 passes 8 B f + 2 x 8 B U, each times (1 + 4/k).  The pass's device
+    time comes from events the library records around the launch on its
+    stream (eik_stats.pass_ms)."""
+    sched = stats[-1].schedule
+    if p32 > p64:
+        kname, kms, bpp = kernel_name(sched, prec, True), p32, 12.0 * (1 + 4.0 / k)
+    else:
+        kname, kms, bpp = kernel_name(sched, prec, False), p64, 24.0 * (1 + 4.0 / k)
+    peak, peak_src = measured_hbm()
+    achieved = bpp * npts / (kms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": ncu_traffic(kname, k), "peak_source": peak_src,
+            "kernel": kname, "cell_k": k, "kernel_ms": kms, "algorithmic_bytes_per_pt": bpp,
+            "algorithmic_bytes_per_launch": bpp * npts}
+
+
+def k_sweep(eik, torch, I, reps=3):
     """The single 1025^2 solve at every cell size, both precisions: device
     time of whole solves (median of reps) and the error against the oracle."""
+    import oracle
+    F = torch.from_numpy(I.F).cuda()
+    src = torch.from_numpy(I.src_ij).cuda()
+    q = torch.from_numpy(np.ascontiguousarray(I.sq)).cuda()
+    V = oracle.fmm(I.F, I.h, I.si, I.sj, I.sq)
     fin = np.isfinite(V)
     out = []
     for prec, pname in ((eik.EIK_FP64, "fp64"), (eik.EIK_FP32_REFINE, "fp32ref")):
@@ -261,7 +308,7 @@ def k_sweep(eik, torch, I, F, src, q, V, reps=3):
             med = statistics.median(ms)
             out.append({"precision": pname, "cell_k": k, "ms": med, "value": I.npts / med / 1e3,
                         "unit": UNIT, "max_rel_err": err, "rounds": st.rounds, "avhr": st.avhr,
-                        "pass_ms": list(st.pass_ms)})
+                        "pass_ms": list(st.pass_ms), "value_ordered": bool(st.schedule & 32)})
     return out
 
 
@@ -273,7 +320,7 @@ def config_measure(eik, torch, I, prec, steps=5, k=0):
     src = torch.from_numpy(I.src_ij).cuda()
     q = torch.from_numpy(np.ascontiguousarray(I.sq)).cuda()
     U = torch.empty_like(F)
-    ms = []
+    ms, sts = [], []
     with eik.Plan(I.nx, I.ny, I.h, k, prec) as p:
         for r in range(steps + 2):
             rc, st = p.solve(F, src, q, U)
@@ -281,6 +328,7 @@ def config_measure(eik, torch, I, prec, steps=5, k=0):
                 raise RuntimeError(f"eik_solve {I.name}: {eik.eik_strerror(rc)}")
             if r >= 2:
                 ms.append(st.ms)
+                sts.append(st)
     V = oracle.fmm(I.F, I.h, I.si, I.sj, I.sq)
     Ug = U.cpu().numpy()
     fin = np.isfinite(V)
@@ -289,7 +337,10 @@ def config_measure(eik, torch, I, prec, steps=5, k=0):
     out = {"grid": f"{I.nx}x{I.ny}", "precision": "fp64" if prec == eik.EIK_FP64 else "fp32ref",
            "cell_k": st.cell_k, "ms": med, "value": I.npts / med / 1e3, "unit": UNIT,
            "max_rel_err": err, "inf_pattern_exact": bool((np.isfinite(Ug) == fin).all()),
-           "err_bound": st.err_bound, "avhr": st.avhr, "schedule": st.schedule}
+           "err_bound": st.err_bound, "avhr": st.avhr, "avs": st.avs, "buckets": st.buckets,
+           "schedule": st.schedule, "value_ordered": bool(st.schedule & 32),
+           "roofline": roofline(sts, st.cell_k, prec, I.npts, statistics.mean(x.pass_ms[0] for x in sts),
+                                statistics.mean(x.pass_ms[1] for x in sts))}
     if prec == eik.EIK_FP64:
         # the FP64 pipe: three FP64 adds per node evaluation (the library's
         # count of evaluations, lock-step passes included) against GB300's
@@ -424,8 +475,21 @@ def batch_measure(eik, torch, steps=5, warmup=2, k=0, count=512, cpu_seconds=0.0
         if r:
             one_off.append(1e3 * (time.perf_counter() - t0))
     med = statistics.median(wall)
+    # the dominant kernel is the persistent pass over all grids: its time from
+    # the kernel's own start and end stamps (events do not time inside a
+    # replayed graph), its bytes those of every grid's points
+    pk = st[0].pass_ms[1]
+    kb = st[0].cell_k
+    bpp = 24.0 * (1 + 4.0 / kb)
+    peak, peak_src = measured_hbm()
+    kname = kernel_name(st[0].schedule, 1, False)
+    roof = {"bound": "hbm", "achieved": bpp * npts / (pk / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": bpp * npts / (pk / 1e3) / 1e9 / peak, "traffic": ncu_traffic(kname + "/batch", kb),
+            "peak_source": peak_src, "kernel": kname, "cell_k": kb, "kernel_ms": pk,
+            "algorithmic_bytes_per_pt": bpp, "algorithmic_bytes_per_launch": bpp * npts}
     out = {"workload": f"{count} grids, n log-uniform in [65, 1025], sin-product or random-block F, "
                        "1-8 sources, seed 1", "precision": "fp32ref", "cell_k_used": st[0].cell_k,
+           "roofline": roof,
            "points": npts, "ms_per_batch": med, "value": npts / (med / 1e3) / 1e6, "unit": UNIT,
            "timing": "wall clock per eik_batch_run (graph replay + read-back), median of 5",
            "device_ms": statistics.median(dms), "pass_ms": list(st[0].pass_ms),
@@ -579,7 +643,7 @@ def run_ours(args):
     build.build()
     from paper_1110_6220_gb300 import eik
 
-    I = workload()
+    I = workload(args.workload)
     prec = eik.EIK_FP32_REFINE if args.precision == "fp32ref" else eik.EIK_FP64
     k = args.k  # 0: the library's choice (tuned table or built-in)
     stream = torch.cuda.current_stream()
@@ -652,26 +716,13 @@ def run_ours(args):
         # and FP64 passes 8 B f + 2 x 8 B U, each times (1 + 4/k).
         p32 = statistics.mean(s.pass_ms[0] for s in stats)
         p64 = statistics.mean(s.pass_ms[1] for s in stats)
-        sched = stats[-1].schedule
-        if p32 > p64:
-            kname = "k_solve_async<F32>" if sched & 1 else "k_solve<F32>"
-            kms, bpp = p32, 12.0 * (1 + 4.0 / k)
-        else:
-            kname = ("k_solve_async" if sched & 2 else "k_solve") + ("<DF>" if prec else "<F64>")
-            kms, bpp = p64, 24.0 * (1 + 4.0 / k)
-        peak, peak_src = measured_hbm()
-        achieved = bpp * I.npts / (kms / 1e3) / 1e9
-        traffic = ncu_traffic(kname, k)
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                "kernel": kname, "kernel_ms": kms,
-                "algorithmic_bytes_per_pt": bpp}
+        roof = roofline(stats, k, prec, I.npts, p32, p64)
         s0 = stats[-1]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64" if prec else "f64", "data": "synthetic",
-                "config": config_dict(args, k, args.precision),
+                "config": config_dict(args, k, args.precision, I),
                 "max_rel_err": rel_err, "inf_pattern_exact": same_inf,
                 "err_bound": s0.err_bound, "status": eik.eik_strerror(s0.status),
                 "roofline": roof,
@@ -688,20 +739,26 @@ def run_ours(args):
         line["solver"]["bucket_width_main"] = s0.bucket_width
         line["solver"]["schedule"] = {"fp32_pass_round_free": bool(s0.schedule & 1),
                                       "main_pass_round_free": bool(s0.schedule & 2),
-                                      "one_double_float_pass": bool(s0.schedule & 4)}
+                                      "one_double_float_pass": bool(s0.schedule & 4),
+                                      "value_ordered": bool(s0.schedule & 32)}
+        from paper_1110_6220_gb300 import workloads as W
+        C2 = I if args.workload == "sin1025" else W.sin_point(1025)
         if not args.no_sweep:
-            line["k_sweep"] = k_sweep(eik, torch, I, F, src, q, V)
+            line["k_sweep"] = k_sweep(eik, torch, C2)
         if not args.no_configs:
-            from paper_1110_6220_gb300 import workloads as W
             line["configs"] = {
                 "c1_const129_fp64": config_measure(eik, torch, W.const_point(129), eik.EIK_FP64),
-                "c2_sin1025_fp64": config_measure(eik, torch, I, eik.EIK_FP64),
-                "c3_checker_maze4097_fp32ref": config_measure(eik, torch, W.checker_maze(4097), eik.EIK_FP32_REFINE),
+                "c2_sin1025_fp32ref": config_measure(eik, torch, C2, eik.EIK_FP32_REFINE),
+                "c2_sin1025_fp64": config_measure(eik, torch, C2, eik.EIK_FP64),
+                "c3_checker_maze4097_fp64": config_measure(eik, torch, W.checker_maze(4097), eik.EIK_FP64),
                 "q_boundary_sin1025_fp32ref": config_measure(eik, torch, W.sin_boundary(1025), eik.EIK_FP32_REFINE),
                 "q_boundary_sin1025_fp64": config_measure(eik, torch, W.sin_boundary(1025), eik.EIK_FP64),
             }
+            if args.workload == "sin1025":
+                line["configs"]["c3_checker_maze4097_fp32ref"] = config_measure(
+                    eik, torch, W.checker_maze(4097), eik.EIK_FP32_REFINE)
         if not args.no_configs:
-            line["fhcm"], line["fmsm"] = fhcm_measure(eik, torch, I)
+            line["fhcm"], line["fmsm"] = fhcm_measure(eik, torch, C2)
         if not args.no_batch:
             line["batch"] = batch_measure(eik, torch, count=args.batch_count,
                                           cpu_seconds=0.0 if args.no_cpu_baseline else 10.0)

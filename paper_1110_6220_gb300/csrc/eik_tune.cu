@@ -96,34 +96,46 @@ int side_class(const eik_plan_desc* d, int n) {
 //    against 179 / 588 ms round-free; sin20 at m = 16 51 / 130 ms against
 //    202 / 1448 ms.
 Entry builtin(int prec, bool batch, int side, bool fhcm) {
+    // the value-ordered round-free schedule (bucket rings of the proposed
+    // cell value, a front without barriers, a window of `w` buckets above it)
+    auto ordered = [](Entry e, double m, int w) {
+        e.async_first = e.async_main = true;
+        e.ordered = true;
+        e.m_first = e.m_main = m;
+        e.window = w;
+        e.hold_ns = 0;
+        return e;
+    };
     if (prec == EIK_FP32_REFINE) {
         // cells of 16 from ~4096^2 (4097^2 sin20: 18.3 vs 29.1 ms at k = 8;
         // checkerboard+maze 23.6 vs 25.3 ms); at ~2048^2 k = 8 and 16 split
         Entry e{batch || side >= 12 ? 16 : 8, 256.0, 16.0, 0.0, false, true};
         e.one_pass = true;
-        // holds (a young cell goes back to the ring): 4097^2 20 us (maze
-        // 21.9 -> 20.4 ms, sin20 17.3 -> 14.3 ms against 8 us), 2049^2 4 us
-        if (!batch) e.hold_ns = side >= 12 ? 20000 : side == 11 ? 4000 : 0;
-        if (!batch && side >= 13) {
-            e.m_main = 64.0;
-            e.async_main = false;
-            e.hold_ns = 0;
-        }
+        // holds (a young cell goes back to the ring): 2049^2 4 us
+        if (!batch) e.hold_ns = side == 11 ? 4000 : 0;
+        // single grids from ~4096^2 run in value order: buckets of 4 cell
+        // crossings, cells taken from the front's bucket and the w above it.
+        // 4097^2 checkerboard + maze 12.96 ms at w = 3 against 18.5 ms first
+        // in, first out (visits per cell 5.9 against 17.6), sin20 9.5-10.9 ms
+        // against 13.1-13.4; 8193^2 (w = 2) sin20 33.4 / maze 31.0 ms
+        // against 46 / 62 ms in rounds, 16385^2 116 / 100 against 120 / 192
+        if (!batch && side == 12) e = ordered(e, 4.0, 3);
+        if (!batch && side >= 13) e = ordered(e, 4.0, 2);
         return e;
     }
     if (batch || side <= 8) return Entry{8, 4.0, 4.0, 0.0, false, true};
-    // one FP64 grid: with a hold (a young cell goes back to the ring) the
-    // round-free schedule beats rounds from ~1024^2 (1025^2 sin20 3.68 ->
-    // 3.35 ms at 4 us; 2049^2 sin20 10.9 -> 9.3 ms and maze 14.0 -> 11.9 ms at
-    // 16 us; 4097^2 sin20 43.7 -> 36.7 ms, maze 40.9 -> 41.8 ms); at ~512^2 it
-    // splits (sin20 1.79 -> 1.66 ms, maze 5.33 -> 5.49 ms), rounds stay
     // FHCM's one-sweep visits gain less from merged requests: rounds
-    // (1025^2 sin20 2.72 ms, against 2.92 ms round-free with a 4 us hold)
-    if (side == 9 || fhcm) return Entry{8, 256.0, 256.0, 0.0};
-    if (side >= 13) return Entry{16, 32.0, 32.0, 0.0};
-    Entry e{8, 256.0, 256.0, 0.0, false, true};
-    e.hold_ns = side == 10 ? 4000 : 16000;
-    return e;
+    // (1025^2 sin20 2.72 ms, against 2.92 ms round-free with a 4 us hold);
+    // it has no value-ordered form
+    if (fhcm) return Entry{8, 256.0, 256.0, 0.0};
+    // one FP64 grid from ~512^2: value order, buckets of 4 crossings (FP64
+    // visits are the costly ones, so fewer of them pay most): 513^2 sin20 /
+    // maze 1.45 / 3.58 ms (w = 3) against 1.85 / 4.59 in rounds; 1025^2
+    // sin20 2.87 ms (w = 2) against 3.20 first in, first out with a 4 us
+    // hold; 2049^2 8.2 / 9.5 against 8.9 / 13.4; 4097^2 maze 24.0 against
+    // 41.1; 8193^2 at k = 16 46.6 / 55.5 against 55.1 / 158 in rounds
+    Entry e{side >= 13 ? 16 : 8, 4.0, 4.0, 0.0};
+    return ordered(e, 4.0, side <= 9 ? 3 : 2);
 }
 
 int load_file(const char* path) {

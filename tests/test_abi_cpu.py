@@ -114,51 +114,52 @@ def test_plan_create_rejects_bad_descriptors_before_touching_cuda():
 
 
 def test_tune_table_round_trip_and_use_without_gpu(tmp_path):
-    """A loaded table decides k for descriptors that leave it open (seen
-    through the workspace size, which needs no GPU); save writes back what
-    was loaded; malformed files merge nothing; reset restores the built-in
+    """A loaded table decides k and the schedule for descriptors that leave
+    them open (seen through the workspace size, which needs no GPU: the
+    value-ordered schedule adds its bucket rings); save writes back what was
+    loaded; malformed files merge nothing; reset restores the built-in
     choice."""
     from paper_1110_6220_gb300 import eik
     eik.eik_tune_reset()
-    d0 = eik.make_desc(1025, 1025, 1 / 1024, 0, eik.EIK_FP64)
-    w_auto = eik.eik_plan_workspace_bytes(d0)
-    w8 = eik.eik_plan_workspace_bytes(eik.make_desc(1025, 1025, 1 / 1024, 8, eik.EIK_FP64))
-    w32 = eik.eik_plan_workspace_bytes(eik.make_desc(1025, 1025, 1 / 1024, 32, eik.EIK_FP64))
-    assert w_auto == w8 and w32 != w8  # built-in: k = 8 for one FP64 grid
-    # FP32 + refinement: k = 8 for one grid up to ~2048^2, 16 from ~4096^2;
-    # FP64: 8 up to ~4096^2, 16 (bucketed rounds) from ~8192^2
-    R = eik.EIK_FP32_REFINE
-    for n, k in ((1025, 8), (2049, 8), (4097, 16), (8193, 16)):
-        assert eik.eik_plan_workspace_bytes(eik.make_desc(n, n, 1 / (n - 1), 0, R)) == \
-            eik.eik_plan_workspace_bytes(eik.make_desc(n, n, 1 / (n - 1), k, R)), n
-    for n, k in ((4097, 8), (8193, 16)):
-        assert eik.eik_plan_workspace_bytes(eik.make_desc(n, n, 1 / (n - 1), 0, eik.EIK_FP64)) == \
-            eik.eik_plan_workspace_bytes(eik.make_desc(n, n, 1 / (n - 1), k, eik.EIK_FP64)), n
+    F64, R = eik.EIK_FP64, eik.EIK_FP32_REFINE
+    FIFO, ORD = eik.EIK_SCHED_FIFO, eik.EIK_SCHED_ORDERED
+
+    def ws(n, k, prec, sched=0):
+        return eik.eik_plan_workspace_bytes(eik.make_desc(n, n, 1 / (n - 1), k, prec, schedule=sched))
+
+    d0 = eik.make_desc(1025, 1025, 1 / 1024, 0, F64)
+    w32_fifo, w32_ord = ws(1025, 32, F64, FIFO), ws(1025, 32, F64, ORD)
+    assert w32_ord == w32_fifo + 32 * 2048 * 8 + 1024  # 33^2 cells -> rings of 2048
+    # built in: one FP64 grid at k = 8 in value order from ~512^2 (k = 16
+    # from ~8192^2); FP32 + refinement k = 8 first in, first out up to
+    # ~2048^2, k = 16 in value order from ~4096^2
+    assert eik.eik_plan_workspace_bytes(d0) == ws(1025, 8, F64, ORD)
+    for n, k, sched in ((1025, 8, FIFO), (2049, 8, FIFO), (4097, 16, ORD), (8193, 16, ORD)):
+        assert ws(n, 0, R) == ws(n, k, R, sched), n
+    for n, k, sched in ((129, 8, FIFO), (513, 8, ORD), (4097, 8, ORD), (8193, 16, ORD)):
+        assert ws(n, 0, F64) == ws(n, k, F64, sched), n
     f = tmp_path / "tune.txt"
-    # class: FP64, single grid, side 2^10
+    # class: FP64, single grid, side 2^10 (a version-4 line: first in, first out)
     f.write_text("eik-tune 4\n0 0 10 32 8 8 0 1 0 0 1.5\n")
     assert eik.eik_tune_load(str(f)) == 0
-    assert eik.eik_plan_workspace_bytes(d0) == w32
+    assert eik.eik_plan_workspace_bytes(d0) == w32_fifo
     # another side class keeps the built-in choice
-    assert eik.eik_plan_workspace_bytes(eik.make_desc(129, 129, 1 / 128, 0, eik.EIK_FP64)) == \
-        eik.eik_plan_workspace_bytes(eik.make_desc(129, 129, 1 / 128, 8, eik.EIK_FP64))
+    assert ws(129, 0, F64) == ws(129, 8, F64, FIFO)
     g = tmp_path / "out.txt"
     assert eik.eik_tune_save(str(g)) == 0
     lines = g.read_text().splitlines()
     assert lines[0] == "eik-tune 5"
-    # a version-4 line reads as first in, first out with the full window
     assert [float(x) for x in lines[1].split()] == [0, 0, 10, 32, 8, 8, 0, 1, 0, 0, 1.5, 0, 31]
     # the saved table loads back as it was
     assert eik.eik_tune_load(str(g)) == 0
-    assert eik.eik_plan_workspace_bytes(d0) == w32
-    # version 5: the value-ordered schedule takes its bucket rings (32 per
-    # cell, a power of two >= the job's cells) on top of the workspace
+    assert eik.eik_plan_workspace_bytes(d0) == w32_fifo
+    # version 5: the value-ordered schedule, window 2
     v5 = tmp_path / "v5.txt"
     v5.write_text("eik-tune 5\n0 0 10 32 8 8 0 1 0 0 1.5 1 2\n")
     assert eik.eik_tune_load(str(v5)) == 0
-    J = 33 * 33
-    assert eik.eik_plan_workspace_bytes(d0) == w32 + 32 * 2048 * 8 + 1024
-    assert J <= 2048
+    assert eik.eik_plan_workspace_bytes(d0) == w32_ord
+    # a schedule named in the descriptor wins over the table
+    assert eik.eik_plan_workspace_bytes(eik.make_desc(1025, 1025, 1 / 1024, 0, F64, schedule=FIFO)) == w32_fifo
     bad = tmp_path / "bad.txt"
     bad.write_text("eik-tune 4\n1 0 10 12 8 8 0 0 0 0 1.0\n")  # k = 12 is not a cell size
     assert eik.eik_tune_load(str(bad)) == eik.EIK_EINVAL
@@ -166,15 +167,12 @@ def test_tune_table_round_trip_and_use_without_gpu(tmp_path):
     assert eik.eik_tune_load(str(bad)) == eik.EIK_EINVAL
     bad.write_text("eik-tune 5\n1 0 10 16 8 8 0 1 0 0 1.0\n")  # version 5 lines carry 13 fields
     assert eik.eik_tune_load(str(bad)) == eik.EIK_EINVAL
-    assert eik.eik_tune_load(str(v5)) == 0
-    eik.eik_tune_reset()
-    assert eik.eik_tune_load(str(f)) == 0
     bad.write_text("something else\n")
     assert eik.eik_tune_load(str(bad)) == eik.EIK_EINVAL
     assert eik.eik_tune_load(str(tmp_path / "missing.txt")) == eik.EIK_EINVAL
-    assert eik.eik_plan_workspace_bytes(d0) == w32
+    assert eik.eik_plan_workspace_bytes(d0) == w32_ord
     eik.eik_tune_reset()
-    assert eik.eik_plan_workspace_bytes(d0) == w8
+    assert eik.eik_plan_workspace_bytes(d0) == ws(1025, 8, F64, ORD)
 
 
 def test_method_descriptor_rules_without_gpu():

@@ -27,7 +27,7 @@ def test_reference_arm_prints_one_contract_line():
                            "d2h_bytes_per_step": 0}
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
-    assert "1025x1025" in line["config"]["workload"]
+    assert "4097x4097" in line["config"]["workload"]
 
 
 def test_reference_arm_other_ranks_exit_quietly():
