@@ -392,6 +392,82 @@ __device__ __forceinline__ bool node_candidate(const typename TileCfg<MODE, K>::
     return true;
 }
 
+// The same, for a lane that may have nothing to update (act false): every
+// input is loaded before anything is decided (the loads go out together,
+// and no update waits for f to come back first).  On the FP32 pipe the
+// update then runs without a branch -- a node that is not updated (a
+// source, an obstacle, the padding, an inactive lane) computes a value the
+// result masks; FP64 updates, at 1/64 of the FP32 rate on this part, are
+// skipped by a branch when the lane has none to make.
+template <int MODE, int K>
+__device__ __forceinline__ bool node_eval(const typename TileCfg<MODE, K>::T* tU,
+                                          const typename TileCfg<MODE, K>::FT* tF, const double* tG, int i,
+                                          int j, bool act, typename TileCfg<MODE, K>::T& cand,
+                                          typename TileCfg<MODE, K>::T& old) {
+    using C = TileCfg<MODE, K>;
+    const int q = (j + 1) * C::BW + (i + 1);
+    const auto fv = tF[q];
+    old = tU[q];
+    const auto W = tU[q - 1], E = tU[q + 1], S = tU[q - C::BW], N = tU[q + C::BW];
+    const bool upd = act && updatable(fv);
+    if constexpr (MODE == MODE_F64) {
+        const float2 fp = reinterpret_cast<const float2*>(tG)[j * K + i];
+        cand = old;
+        if (upd) cand = update_f64(W, E, S, N, fv, fp);
+    } else if constexpr (MODE == MODE_F32) {
+        cand = update_f32(W, E, S, N, fv);
+    } else {
+        cand = update_df(W, E, S, N, fv);
+    }
+    return upd;
+}
+
+// One anti-diagonal step of a direction's sweep for k >= 16: this lane's NS
+// slots (nodes u = rl, rl + LPD, ... of diagonal t2, which starts at row lo
+// and has len nodes) are independent, so their loads and updates form one
+// straight-line block and the warp waits for one update chain per step, not
+// one per slot.  Returns whether a node decreased (its flag set).
+template <int MODE, int K, int NS>
+__device__ __forceinline__ bool diag_step(typename TileCfg<MODE, K>::T* tU, const typename TileCfg<MODE, K>::FT* tF,
+                                          const double* tG, unsigned char* flags, int t2, int lo, int len, int rl,
+                                          bool sx, bool sy, bool on) {
+    using C = TileCfg<MODE, K>;
+    typename C::T cand[NS], old[NS];
+    bool ok[NS];
+    int qi[NS];
+#pragma unroll
+    for (int m = 0; m < NS; ++m) {
+        const int u = rl + C::LPD * m;
+        const bool a = on && u < len;
+        const int jj = lo + (a ? u : 0), ii2 = t2 - jj;  // a node of the diagonal either way
+        const int j = sy ? jj : K - 1 - jj, i = sx ? ii2 : K - 1 - ii2;
+        qi[m] = j * K + i;
+        ok[m] = node_eval<MODE, K>(tU, tF, tG, i, j, a, cand[m], old[m]);
+    }
+    bool changed = false;
+#pragma unroll
+    for (int m = 0; m < NS; ++m) {
+        if (ok[m] && lt(cand[m], old[m])) {
+            const int j = qi[m] / K, i = qi[m] - j * K;
+            tU[(j + 1) * C::BW + (i + 1)] = cand[m];
+            flags[qi[m]] = 1;
+            changed = true;
+        }
+    }
+    return changed;
+}
+// ns (the same for every lane) slots this step
+template <int MODE, int K, int NS = 1>
+__device__ __forceinline__ bool diag_step_n(int ns, typename TileCfg<MODE, K>::T* tU,
+                                            const typename TileCfg<MODE, K>::FT* tF, const double* tG,
+                                            unsigned char* flags, int t2, int lo, int len, int rl, bool sx, bool sy,
+                                            bool on) {
+    if constexpr (NS < TileCfg<MODE, K>::RPL) {
+        if (ns > NS) return diag_step_n<MODE, K, NS + 1>(ns, tU, tF, tG, flags, t2, lo, len, rl, sx, sy, on);
+    }
+    return diag_step<MODE, K, NS>(tU, tF, tG, flags, t2, lo, len, rl, sx, sy, on);
+}
+
 // Fixed-point check of a whole tile (this lane's share): true if some node
 // would still decrease.  It is equivalent to asking whether another pass
 // would change anything -- a pass changes nothing exactly when no node can
@@ -407,7 +483,8 @@ __device__ __forceinline__ bool tile_improvable(const typename TileCfg<MODE, K>:
     for (int e = dl; e < K * K; e += C::LPC) {
         const int j = e / K, i = e - j * K;
         typename C::T cand, old;
-        if (node_candidate<MODE, K>(tU, tF, tG, i, j, cand, old)) imp |= lt(cand, old);
+        const bool upd = node_eval<MODE, K>(tU, tF, tG, i, j, true, cand, old);
+        imp |= upd && lt(cand, old);
     }
     return imp;
 }
@@ -828,18 +905,31 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
                         }
                 }
             } else if constexpr (!DIAG) {
+                // this lane's row (node ii2 of it at this step, when in range):
+                // evaluated without a branch, stored when in range and lower
                 const unsigned ii2 = (unsigned)(t2 - jr);
-                if (lane_on && ii2 < (unsigned)K) {
-                    const int j = rl, i = sx ? (int)ii2 : K - 1 - (int)ii2;
-                    T cand, old;
-                    if (node_candidate<MODE, K>(tU, tF, tG, i, j, cand, old) && lt(cand, old)) {
-                        tU[(j + 1) * C::BW + (i + 1)] = cand;
-                        chg |= 1u << i;
-                        changed = true;
-                    }
+                const bool a = lane_on && ii2 < (unsigned)K;
+                const int ic = a ? (int)ii2 : 0;
+                const int j = rl, i = sx ? ic : K - 1 - ic;
+                T cand, old;
+                if (node_eval<MODE, K>(tU, tF, tG, i, j, a, cand, old) && lt(cand, old)) {
+                    tU[(j + 1) * C::BW + (i + 1)] = cand;
+                    chg |= 1u << i;
+                    changed = true;
                 }
+            } else if constexpr (MODE != MODE_F64) {
+                // anti-diagonal t2 (in sweep order): rows lo .. lo + len - 1,
+                // ceil(len / LPD) slots per lane, one straight-line block
+                const int lo = t2 < K ? 0 : t2 - (K - 1);
+                const int len = (t2 < K ? t2 : K - 1) - lo + 1;
+                const int ns = (len + C::LPD - 1) / C::LPD;
+                if (diag_step_n<MODE, K>(ns, tU, tF, tG, flags, t2, lo, len, rl, sx, sy, c >= 0 && (!FAST || dir_on)))
+                    changed = true;
             } else {
-                // anti-diagonal t2 (in sweep order): rows lo .. lo + len - 1
+                // FP64: the slots one after another (its updates are bound by
+                // the FP64 pipe, not by the chain's latency, and the straight-
+                // line block measured slower: k = 32 11.4 against 8.2 ms on
+                // the 1025^2 sin20 grid)
                 const int lo = t2 < K ? 0 : t2 - (K - 1);
                 const int len = (t2 < K ? t2 : K - 1) - lo + 1;
 #pragma unroll
@@ -1083,7 +1173,7 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
 // (key <= theta) or to the far list, and a grid barrier ends the round; when
 // an instance's near list runs dry its next bucket is split off the far list.
 template <int MODE, int K, int VAR>
-__global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32)
+__global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32, 2)
     k_solve(const __grid_constant__ SolveParams p) {
     using C = TileCfg<MODE, K>;
     constexpr unsigned FULL = 0xffffffffu;
@@ -1701,12 +1791,15 @@ __device__ __forceinline__ int bq_next(const SolveParams& p, Ctl* gctl, unsigned
 // spills, which measured slower (1025^2: 1.86 against 1.73 ms per pass; the
 // 512-grid batch 14.1 against 13.9 ms).  0 leaves the others to the compiler.
 // ORD: the value-ordered schedule (bucket rings, a front, a window) instead
-// of first-in first-out.  Left to itself the compiler squeezes the ordered
-// FP64 and FP32 kernels into 48-64 registers with spills; they get the
-// first-in first-out kernels' two blocks per SM instead.
+// of first-in first-out.  Left to itself the compiler squeezes several of
+// these kernels into 48-72 registers with spills; they are held to two
+// blocks per SM (up to 128 registers).  The first-in first-out double-float
+// kernels at k = 8 and 16 keep three (their whole warp budget waits on the
+// ring at once), the ordered one at k = 16 takes two and keeps the two
+// slots of each anti-diagonal step in registers (at three it spills).
 template <int MODE, int K, int VAR, bool ORD>
 __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32,
-                                  (MODE == MODE_DF && (K == 8 || K == 16)) ? 3 : (ORD ? 2 : 0))
+                                  (MODE == MODE_DF && (K == 8 || (K == 16 && !ORD))) ? 3 : 2)
     k_solve_async(const __grid_constant__ SolveParams p) {
     using C = TileCfg<MODE, K>;
     static_assert(C::CPW == 1, "one cell per warp");
