@@ -169,6 +169,8 @@ typedef struct {
                                coarse solve, then every cell once as its predecessors finish) */
     int32_t status;         /* EIK_OK or the error of this solve */
     double mono_pct;        /* FHCM: Monotonicity Checks that found the border monotone, % */
+    int64_t queue_left;     /* cells still requested or running after the solve: 0 whenever the
+                               status is EIK_OK (a check of the work queue's bookkeeping) */
 } eik_stats;
 
 typedef struct eik_plan_s* eik_plan;
@@ -332,18 +334,25 @@ void eik_server_destroy(eik_server s);
  * budget), or latency-critical loops that cannot afford the implicit device
  * synchronisation of an allocation.
  *
- * eik_solve_noalloc solves one FP64 instance (d->precision must be EIK_FP64)
- * like eik_plan_create + eik_solve + eik_plan_destroy, but allocates nothing,
- * on the device or on the host: the whole workspace lives in one fixed device
- * array of EIK_NOALLOC_SCRATCH_BYTES inside this library, which every GPU that
- * loads the library holds until the process exits.
- *   - in->F and in->U must be device pointers (EIK_EINVAL otherwise); the
- *     caller still owns and passes all inputs and outputs.
- *   - at most EIK_NOALLOC_MAX_SOURCES sources (host or device pointers).
+ * eik_solve_noalloc solves one FP64 instance (d->precision must be EIK_FP64,
+ * d->method EIK_METHOD_HCM) like eik_plan_create + eik_solve +
+ * eik_plan_destroy, but allocates nothing, on the device or on the host: the
+ * whole workspace lives in one fixed device array of
+ * EIK_NOALLOC_SCRATCH_BYTES inside this library, which every GPU that loads
+ * the library holds until the process exits.
+ *   - in->F and in->U must be device pointers of the current device
+ *     (EIK_EINVAL otherwise); the caller still owns and passes all inputs and
+ *     outputs.
+ *   - at most EIK_NOALLOC_MAX_SOURCES sources (host or device pointers; device
+ *     tables are read in cuda_stream's order).
  *   - a grid whose workspace does not fit the fixed array (about 1000 x 1000
  *     nodes at k = 8) is rejected with EIK_EINVAL.
- *   - the first call on a device looks up that device's copy of the array;
- *     make that first call before any stream capture.
+ *   - it always runs the bucketed-rounds schedule (the round-free schedules'
+ *     queues would need more scratch), in one wide bucket unless
+ *     d->bucket_width sets one; d->schedule is not used.
+ *   - the call copies through stack buffers and waits on its stream, so it
+ *     cannot be called while cuda_stream is being captured (EIK_EINVAL).
+ *   - the first call on a device looks up that device's copy of the array.
  *   - every call shares the one array: calls that overlap on a GPU (different
  *     streams or threads) race and corrupt each other; serialise them.
  *   - work is queued on cuda_stream (NULL: the legacy default stream); the

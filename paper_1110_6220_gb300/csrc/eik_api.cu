@@ -65,7 +65,17 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// EIK_ALLOC_LIMIT (bytes; unset: none): every workspace need above it fails
+// as cudaMalloc would on a device that small, whether or not a buffer kept
+// from an earlier call could serve it -- a host-side way to drive the
+// EIK_ENOMEM paths without exhausting the device.
+static size_t alloc_limit() {
+    const char* e = std::getenv("EIK_ALLOC_LIMIT");
+    return e && e[0] ? (size_t)std::strtoull(e, nullptr, 10) : ~(size_t)0;
+}
+
 int grow(DevBuf* b, size_t bytes) {
+    if (bytes > alloc_limit()) return EIK_ENOMEM;
     if (b->cap >= bytes) return EIK_OK;
     if (b->p) cudaFree(b->p);
     b->p = nullptr;

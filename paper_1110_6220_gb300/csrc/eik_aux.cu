@@ -265,6 +265,15 @@ __global__ void k_seed_cells(const AuxInst* A, const int* cell_pre, int n, int n
 // that evaluation and of f (over a hundred times the worst case of the dozen
 // pair operations involved).  +inf against a finite value counts as an
 // infinite residual.  Also the max finite V, and out = V + min q.
+// After a solve no cell may still be requested or running (every schedule
+// clears bits 0 and 1 of a cell's flag when it removes the cell and when
+// the removal ends): 1 if node (i, j) is its cell's first node and the cell
+// is flagged so.  FMSM marks its source cells for good and is left out.
+__device__ __forceinline__ unsigned queued_at(const AuxInst& p, int i, int j) {
+    if (!p.qflag || p.Fc || ((i | j) & (p.k - 1))) return 0u;
+    return (p.qflag[(j / p.k) * p.cxn + i / p.k] & 3) != 0;
+}
+
 __global__ void k_residual(const AuxInst* A, const int* blk_pre, int n) {
     const Where w = locate(A, blk_pre, n);
     const AuxInst& p = A[w.inst];
@@ -272,13 +281,14 @@ __global__ void k_residual(const AuxInst* A, const int* blk_pre, int n) {
     const int up = p.upitch;
     const float FINF = inf_of<float>();
     float r = 0.0f, rrel = 0.0f, umax = 0.0f;
-    unsigned long long bad = 0;
+    unsigned long long bad = 0, left = 0;
     const bool shifted = __double_as_longlong(p.shift) != 0;  // min q != 0: add it back
 #pragma unroll
     for (int s = 0; s < SPAN; ++s) {
         const int i = w.i + 32 * s;
         if (i >= p.nx || j >= p.ny) continue;
         const size_t q = (size_t)(j + 1) * up + (i + 1);
+        left += queued_at(p, i, j);
         const float2 V = p.Udf[q];
         const float2 fs = p.fdf[q];
         const float2 W = p.Udf[q - 1], E = p.Udf[q + 1], S = p.Udf[q - up], N = p.Udf[q + up];
@@ -327,8 +337,10 @@ __global__ void k_residual(const AuxInst* A, const int* blk_pre, int n) {
         eb = max(eb, __shfl_xor_sync(FULL, eb, o));
         ub = max(ub, __shfl_xor_sync(FULL, ub, o));
         bad += __shfl_xor_sync(FULL, bad, o);
+        left += __shfl_xor_sync(FULL, left, o);
     }
     if ((threadIdx.x & 31) == 0) {
+        if (left) atomicAdd(&p.res->n_left, left);
         const float rf = __uint_as_float(rb), ef = __uint_as_float(eb);
         atomicMax(&p.res->r_max, key_of(rf < FINF ? widen(rf) : inf_of<double>()));
         atomicMax(&p.res->r_rel, key_of(ef < FINF ? widen(ef) : inf_of<double>()));
@@ -342,10 +354,12 @@ __global__ void k_output(const AuxInst* A, const int* blk_pre, int n) {
     const Where w = locate(A, blk_pre, n);
     const AuxInst& p = A[w.inst];
     const int j = w.j;
+    unsigned long long left = 0;
 #pragma unroll
     for (int s = 0; s < SPAN; ++s) {
         const int i = w.i + 32 * s;
         if (i < p.nx && j < p.ny) {
+            left += queued_at(p, i, j);
             const size_t q = (size_t)(j + 1) * p.upitch + (i + 1);
             double v;
             if (p.U64) {
@@ -357,6 +371,9 @@ __global__ void k_output(const AuxInst* A, const int* blk_pre, int n) {
             p.out[(size_t)j * p.nx + i] = v + p.shift;
         }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) left += __shfl_xor_sync(FULL, left, o);
+    if ((threadIdx.x & 31) == 0 && left) atomicAdd(&p.res->n_left, left);
 }
 
 }  // namespace

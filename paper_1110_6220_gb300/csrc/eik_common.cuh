@@ -146,6 +146,12 @@ struct SolveParams {
     unsigned long long* bq_data;
     unsigned int bq_mask;
     int bq_window;
+    // checks of the failure paths and of the schedule's independence, set
+    // from the host (0: off): at most max_passes passes per removal (the
+    // cap that reports EIK_ENOTCONVERGED), and a pause of up to jitter_ns
+    // before each removal's tile load, drawn per removal
+    int max_passes;
+    unsigned jitter_ns;
 };
 constexpr int NBQ = 32;           // bucket rings of the value-ordered schedule (one lane of a warp each)
 constexpr int BQ_WORDS = 160;     // header words: pairs [0, 64), 64-bit counts [64, 128), front at 128
@@ -185,6 +191,7 @@ struct ResidualOut {              // reduced with atomics on ordered keys
     unsigned long long r_rel;     // max |V - T(V)| / f over the same nodes
     unsigned long long u_max;     // max finite V
     unsigned long long n_bad;     // finite/infinite mismatches
+    unsigned long long n_left;    // cells still requested or running after the solve (must be 0)
 };
 
 // Node-wise kernels (eik_aux.cu) map blocks of AUX_ROWS x AUX_COLS nodes

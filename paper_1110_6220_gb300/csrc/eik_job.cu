@@ -209,6 +209,14 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
     p.bq_data = j.bq_data;
     p.bq_mask = j.bq_mask;
     p.bq_window = j.window < 0 ? 0 : j.window > NBQ - 1 ? NBQ - 1 : j.window;
+    // host-set checks (0 / unset: off): EIK_MAX_PASSES caps the passes of a
+    // removal (a cap it hits reports EIK_ENOTCONVERGED), EIK_JITTER_NS
+    // pauses each removal by up to that many ns before its tile load
+    if (const char* e = std::getenv("EIK_MAX_PASSES")) p.max_passes = (int)std::strtol(e, nullptr, 10);
+    if (const char* e = std::getenv("EIK_JITTER_NS")) {
+        const long v = std::strtol(e, nullptr, 10);
+        p.jitter_ns = v > 0 ? (unsigned)(v < 1000000 ? v : 1000000) : 0u;
+    }
     const bool af = j.async_first && j.ring && j.k >= 8, am = j.async_main && j.ring && j.k >= 8;
     // the main pass's schedule (the value-ordered form for plain HCM only)
     const int sm = !am ? SCH_ROUNDS
@@ -389,6 +397,7 @@ void job_stats(const Layout& L, const eik_plan_desc* d, bool fp32, const Ctl* ic
     s.pass_ms[0] = fp32 ? span(g_first) : 0.0;
     s.pass_ms[1] = span(g_main);
     s.mono_pct = g_main->mono_n ? 100.0 * (double)g_main->mono_ok / (double)g_main->mono_n : 0.0;
+    s.queue_left = (int64_t)r->n_left;
     const double fmin = dval(ictl_main->fmin_f);
     s.bucket_width = bw_main > 0 ? bw_main : (bw_main < 0 ? -bw_main : 4.0) * L.k * fmin;
     if (fp32) {

@@ -65,7 +65,7 @@ struct StackSources {
     double q_min = 0.0;
 };
 
-int prepare_stack_sources(const Layout& L, const eik_instance* in, StackSources* s) {
+int prepare_stack_sources(const Layout& L, const eik_instance* in, cudaStream_t st, StackSources* s) {
     const int n = in->nsrc;
     if (n < 0 || n > MAX_SOURCES) return EIK_EINVAL;
     s->n = s->ncell = 0;
@@ -74,8 +74,11 @@ int prepare_stack_sources(const Layout& L, const eik_instance* in, StackSources*
     if (!in->src_ij || !in->src_q) return EIK_EINVAL;
     int32_t ij[2 * MAX_SOURCES];
     double q[MAX_SOURCES];
-    if (cudaMemcpy(ij, in->src_ij, (size_t)n * 8, cudaMemcpyDefault) != cudaSuccess ||
-        cudaMemcpy(q, in->src_q, (size_t)n * 8, cudaMemcpyDefault) != cudaSuccess) {
+    // read in the caller's stream order (a table written on that stream just
+    // before the call is read after the write), then wait for the copies
+    if (cudaMemcpyAsync(ij, in->src_ij, (size_t)n * 8, cudaMemcpyDefault, st) != cudaSuccess ||
+        cudaMemcpyAsync(q, in->src_q, (size_t)n * 8, cudaMemcpyDefault, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
         cudaGetLastError();
         return EIK_EINVAL;
     }
@@ -130,12 +133,31 @@ extern "C" int eik_solve_noalloc(const eik_plan_desc* d, const eik_instance* in,
     const auto t0 = std::chrono::steady_clock::now();
     if (!desc_valid(d) || !in || !in->F || !in->U) return EIK_EINVAL;
     if (d->precision != EIK_FP64 || d->method != EIK_METHOD_HCM) return EIK_EINVAL;
-    if (!is_device_ptr(in->F) || !is_device_ptr(in->U)) return EIK_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return EIK_ECUDA;
     }
+    // F and U must be device memory of the current device: the scratch
+    // used below is that device's copy
+    for (const void* ptr : {(const void*)in->F, (const void*)in->U}) {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, ptr) != cudaSuccess) {
+            cudaGetLastError();
+            return EIK_EINVAL;
+        }
+        if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) || pa.device != dev)
+            return EIK_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // the call copies through stack buffers and waits on its stream: not a
+    // sequence a stream under capture can hold
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return EIK_EINVAL;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return EIK_EINVAL;
     void* scratch = nullptr;
     int sms = 0;
     int rc = setup_device(dev, &scratch, &sms);
@@ -144,10 +166,12 @@ extern "C" int eik_solve_noalloc(const eik_plan_desc* d, const eik_instance* in,
     eik_plan_desc dd = *d;
     const JobParams P = choose_params(d, 1);
     dd.cell_k = P.k;
-    const double bw_main = d->bucket_width != 0.0 ? d->bucket_width : P.w_main;
+    // always bucketed rounds (the round-free schedules' rings would need
+    // more scratch), in one wide bucket unless the descriptor sets a width
+    const double bw_main = d->bucket_width != 0.0 ? d->bucket_width : -256.0;
     const Layout L = make_layout(d->nx, d->ny, dd.cell_k);
     StackSources ss;
-    rc = prepare_stack_sources(L, in, &ss);
+    rc = prepare_stack_sources(L, in, s, &ss);
     if (rc) return rc;
 
     // carve the scratch; grids that do not fit are rejected
@@ -209,7 +233,6 @@ extern "C" int eik_solve_noalloc(const eik_plan_desc* d, const eik_instance* in,
         tb.cell_inst[e] = 0;
     }
 
-    cudaStream_t s = (cudaStream_t)cuda_stream;
     // (the scratch holds the previous call's data: the init kernel rewrites
     // every element of the padded arrays, the +inf rings included)
     if (cudaMemcpyAsync(tdev, &tb, sizeof(tb), cudaMemcpyHostToDevice, s) != cudaSuccess ||

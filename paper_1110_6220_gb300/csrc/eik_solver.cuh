@@ -668,8 +668,10 @@ struct WarpState {
     int acc_inst;
     unsigned long long acc_visits, acc_sweeps, acc_lane, st_lane;
     unsigned long long mono_ok, mono_n;  // FHCM Monotonicity Checks
+    int cap;  // passes per removal before EIK_ENOTCONVERGED
 
-    __device__ __forceinline__ void init(unsigned char* smem) {
+    __device__ __forceinline__ void init(unsigned char* smem, int max_passes = 0) {
+        cap = max_passes > 0 && max_passes < C::MAX_PASSES ? max_passes : C::MAX_PASSES;
         lane = threadIdx.x & 31;
         const int warp = threadIdx.x >> 5;
         wbase = smem + warp * C::WARP_BYTES;
@@ -697,6 +699,20 @@ struct WarpState {
         }
     }
 };
+
+// A pause of up to jitter_ns before a removal's tile load (0: none), drawn
+// from the cell, the removal's start time and the warp: a host-set
+// perturbation of the schedule, whose result must not change (Theorem
+// convergence).  Bounded: __nanosleep's pause is at most about twice its
+// argument.
+__device__ __forceinline__ void jitter(unsigned jitter_ns, unsigned cell) {
+    if (!jitter_ns) return;
+    unsigned x = cell * 0x9E3779B1u ^ (unsigned)gtimer() ^ (threadIdx.x >> 5) * 0x85EBCA6Bu;
+    x ^= x >> 15;
+    x *= 0x2C1B3C6Du;
+    x ^= x >> 12;
+    __nanosleep(x % (jitter_ns + 1u));
+}
 
 // Solve the warp's cells cg[0..CPW) of instances ig[] (cell -1: none), which
 // the caller has already claimed (flag cleared, fences issued): TMA load of
@@ -843,7 +859,8 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
     int gsweeps = 0;
     bool gdone = c < 0;
     int s = 0;
-    for (; s < C::MAX_PASSES && __ballot_sync(FULL, !gdone) != 0u; ++s) {
+    const int cap = w.cap;
+    for (; s < cap && __ballot_sync(FULL, !gdone) != 0u; ++s) {
         bool changed = false;
         for (int t2 = 0; t2 < 2 * K - 1; ++t2) {
             if constexpr (LSM) {
@@ -987,12 +1004,12 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
             const unsigned long long now = __shfl_sync(FULL, gtimer(), 0);
             if (now > deadline) {
                 if (lane == 0) fail(gctl, EIK_ETIMEDOUT, 0x4000000ull);
-                s = C::MAX_PASSES + 1;
+                s = cap + 1;
                 break;
             }
         }
     }
-    if (s == C::MAX_PASSES && dl == 0 && c >= 0) {
+    if (s == cap && !gdone && dl == 0 && c >= 0) {
         atomicCAS(&ictl->status, 0, EIK_ENOTCONVERGED);
         fail(gctl, EIK_ENOTCONVERGED, (unsigned)c);
     }
@@ -1004,8 +1021,7 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
         // node evaluations executed for this cell (lock-step passes included;
         // with locking the local updates computed)
         const unsigned long long ev =
-            LSM ? (unsigned long long)nev
-                : (unsigned long long)(s < C::MAX_PASSES ? s + 1 : C::MAX_PASSES) * 4 * K * K;
+            LSM ? (unsigned long long)nev : (unsigned long long)(s < cap ? s + 1 : cap) * 4 * K * K;
         if (ii != w.acc_inst) {
             flush_counters(inst, w.acc_inst, w.acc_visits, w.acc_sweeps, w.acc_lane);
             w.acc_inst = ii;
@@ -1203,7 +1219,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32, 2)
     }
 
     WarpState<MODE, K> w;
-    w.init(smem);
+    w.init(smem, p.max_passes);
     const int lane = w.lane, g = w.g, dl = w.dl;
     const int warp = threadIdx.x >> 5;
     const int prof_on = p.profile;
@@ -1353,6 +1369,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32, 2)
             fence_acq_rel_gpu();
             fence_proxy_async_global();
             fence_proxy_async_shared();
+            jitter(p.jitter_ns, (unsigned)c);
             __syncwarp();
             PROF_MARK(2);
             pacc[7] += 1;
@@ -1815,7 +1832,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32,
     int* s_scr = s_pre + NI + 1;
 
     WarpState<MODE, K> w;
-    w.init(smem);
+    w.init(smem, p.max_passes);
     const int lane = w.lane;
     const int prof_on = p.profile;
     Ctl* gctl = p.gctl;
@@ -1957,6 +1974,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32,
         fence_acq_rel_gpu();
         fence_proxy_async_global();
         fence_proxy_async_shared();
+        jitter(p.jitter_ns, (unsigned)e);
         __syncwarp();
         PROF_MARK(2);
         pacc[7] += 1;

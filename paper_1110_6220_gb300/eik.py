@@ -68,7 +68,7 @@ class eik_stats(ctypes.Structure):
                 ("buckets", ctypes.c_int64), ("pass_ms", ctypes.c_double * 2),
                 ("launches", ctypes.c_int32), ("cell_k", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("mono_pct", ctypes.c_double)]
+                ("mono_pct", ctypes.c_double), ("queue_left", ctypes.c_int64)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
