@@ -326,6 +326,12 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
         boff += aux_blocks(L.nyp, L.nxp);
         blk_full_h[i] = bfull;
         bfull += aux_blocks(L.urows, L.upitch);
+        // the owner tables behind the prefixes (instance of each block); a
+        // job of one instance reads none
+        if (n > 1) {
+            for (int b = blk_pre_h[i]; b < boff; ++b) blk_pre_h[n + 1 + b] = i;
+            for (int b = blk_full_h[i]; b < bfull; ++b) blk_full_h[n + 1 + b] = i;
+        }
         cell_pre_h[i] = (int)coff;
         coff += (size_t)L.J;
         for (size_t e = 0; e < hs[i].node.size(); ++e, ++so) {

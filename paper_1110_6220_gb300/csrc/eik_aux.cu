@@ -44,8 +44,9 @@ struct Where {
 };
 __device__ __forceinline__ Where locate(const AuxInst* a, const int* blk_pre, int n) {
     const int b = blockIdx.x;
-    // blk_pre[n + 1 + b] holds the instance of block b (see k_block_owner)
-    const int lo = blk_pre[n + 1 + b];
+    // blk_pre[n + 1 + b] holds the instance of block b (written by the host;
+    // a single instance has no table)
+    const int lo = n == 1 ? 0 : blk_pre[n + 1 + b];
     const int local = b - blk_pre[lo];
     const int tx = (a[lo].nxp + AUX_COLS - 1) / AUX_COLS;
     Where w;
@@ -67,21 +68,16 @@ __device__ __forceinline__ bool speed_positive(double F) {
     return b > 0 && b < 0x7ff0000000000000ll;
 }
 
-// owner[b] = instance of block b, for the prefix pre[0..n]: one block per
-// instance fills its range
-__global__ void k_block_owner(const int* pre, int n, int* owner) {
-    const int i = blockIdx.x;
-    if (i >= n) return;
-    for (int b = pre[i] + threadIdx.x; b < pre[i + 1]; b += blockDim.x) owner[b] = i;
-}
-
 // Every element of the padded arrays (ring included): f = h/F on grid nodes,
 // +inf on obstacles, padding nodes and the ring; U = +inf.  Rejects F < 0,
 // NaN, +inf; reduces the smallest finite h/F into the instance's control
 // blocks.  Blocks map onto whole padded arrays (blk_full), 8 rows x 32 columns.
-__global__ void k_init_grid(const AuxInst* A, const int* blk_full, int n) {
+__device__ void init_sources_of_block(const AuxInst& p, int lo, int rb, int cb, const SourceTable& s);
+__device__ void init_source_cells(const AuxInst* A, const SourceTable& s);
+
+__global__ void k_init_grid(const AuxInst* A, const int* blk_full, int n, const SourceTable s) {
     const int b = blockIdx.x;
-    const int lo = blk_full[n + 1 + b];
+    const int lo = n == 1 ? 0 : blk_full[n + 1 + b];
     const AuxInst& p = A[lo];
     const int local = b - blk_full[lo];
     const int tx = (p.upitch + AUX_COLS - 1) / AUX_COLS;
@@ -147,16 +143,40 @@ __global__ void k_init_grid(const AuxInst* A, const int* blk_full, int n) {
         }
     }
     if (bad) atomicCAS(&p.ctl->status, 0, EIK_EINVAL);
+    // the sources that fall in this block's nodes, once its f and U are
+    // written; the source cells' queueing spread over the whole launch
+    if (s.n) {
+        __syncthreads();
+        init_sources_of_block(p, lo, (local / tx) * ROWS, (local % tx) * AUX_COLS, s);
+    }
+    if (s.ncell) init_source_cells(A, s);
 }
 
-// Sources: U = q (shifted) and f = -1 (fixed node); source cells get the cell
-// value max q (Sec. 4.2, HCM item 1) and start queued.
-__global__ void k_init_sources(const AuxInst* A, const SourceTable s) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < s.n) {
-        const AuxInst& p = A[s.node_inst[e]];
+// Sources: U = q (shifted) and f = -1 (fixed node).  The block of the
+// padded array at rows rb.., columns cb.. of instance lo finds the sources
+// of its rows by a binary search of the table (sorted by instance, then
+// node j nx + i) and writes the ones of its columns.
+__device__ void init_sources_of_block(const AuxInst& p, int lo, int rb, int cb, const SourceTable& s) {
+    __shared__ int s_first;
+    const int jlo = max(rb - 1, 0), jhi = min(rb - 1 + ROWS, p.ny);  // grid rows of the block
+    if (jlo >= jhi) return;
+    const long long key_lo = (long long)jlo * p.nx, key_hi = (long long)jhi * p.nx;
+    if (threadIdx.x == 0) {
+        int a = 0, z = s.n;  // first entry >= (lo, key_lo)
+        while (a < z) {
+            const int m = (a + z) >> 1;
+            const int mi = s.node_inst[m];
+            if (mi < lo || (mi == lo && (long long)s.node[m] < key_lo)) a = m + 1;
+            else z = m;
+        }
+        s_first = a;
+    }
+    __syncthreads();
+    for (int e = s_first + threadIdx.x; e < s.n; e += blockDim.x) {
+        if (s.node_inst[e] != lo || (long long)s.node[e] >= key_hi) break;
         const int node = s.node[e];
         const int i = node % p.nx, j = node / p.nx;
+        if (i + 1 < cb || i + 1 >= cb + AUX_COLS) continue;
         const double q = s.q[e];
         const size_t u = (size_t)(j + 1) * p.upitch + (i + 1);
         if (p.f64) p.f64[u] = -1.0;
@@ -167,11 +187,11 @@ __global__ void k_init_sources(const AuxInst* A, const SourceTable s) {
         if (p.Udf) p.Udf[u] = df_of(q);
     }
 }
-// one thread per instance: queue its source cells (their number per instance
-// is small; the far list is filled in order)
-__global__ void k_init_source_cells(const AuxInst* A, const SourceTable s) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < s.ncell) {
+// Source cells get the cell value max q (Sec. 4.2, HCM item 1) and start
+// queued, one thread of the launch each (they touch only the cell arrays,
+// which nothing else of the launch writes).
+__device__ void init_source_cells(const AuxInst* A, const SourceTable& s) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < s.ncell; e += gridDim.x * blockDim.x) {
         const AuxInst& p = A[s.cell_inst[e]];
         const int c = s.cell[e];
         p.cval[c] = s.cell_key[e];
@@ -182,16 +202,6 @@ __global__ void k_init_source_cells(const AuxInst* A, const SourceTable s) {
     }
 }
 
-__global__ void k_ctl_init(Ctl* ctl, int count) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < count) {
-        ctl[e].fmin[0] = KEY_UNSET;
-        ctl[e].fmin[1] = KEY_UNSET;
-        ctl[e].fmin_f = KEY_UNSET;
-        ctl[e].t_start = ~0ull;
-        ctl[e].qdelta = KEY_UNSET;
-    }
-}
 
 // Refinement start: V0 = (1 + beta) u32 just above the FP32 result (a
 // supersolution when the FP32 error is below beta; values are >= 0 after the
@@ -378,24 +388,9 @@ __global__ void k_output(const AuxInst* A, const int* blk_pre, int n) {
 
 }  // namespace
 
-cudaError_t launch_ctl_init(Ctl* ctl, int count, cudaStream_t st) {
-    k_ctl_init<<<(count + 255) / 256, 256, 0, st>>>(ctl, count);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_block_owner(const int* pre, int n, cudaStream_t st) {
-    k_block_owner<<<n, 256, 0, st>>>(pre, n, const_cast<int*>(pre) + n + 1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_init_grid(const AuxInst* a, const int* blk_pre, int n, int nblocks, cudaStream_t st) {
-    k_init_grid<<<nblocks, 32 * ROWS, 0, st>>>(a, blk_pre, n);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_init_sources(const AuxInst* a, const SourceTable& s, cudaStream_t st) {
-    if (s.n > 0) k_init_sources<<<(s.n + 255) / 256, 256, 0, st>>>(a, s);
-    if (s.ncell > 0) k_init_source_cells<<<(s.ncell + 255) / 256, 256, 0, st>>>(a, s);
+cudaError_t launch_init_grid(const AuxInst* a, const int* blk_full, int n, int nblocks, const SourceTable& s,
+                             cudaStream_t st) {
+    k_init_grid<<<nblocks, 32 * ROWS, 0, st>>>(a, blk_full, n, s);
     return cudaGetLastError();
 }
 

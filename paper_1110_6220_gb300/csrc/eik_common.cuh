@@ -41,14 +41,21 @@ __device__ inline double val_of(unsigned long long k) {
 // "far" lists (cells waiting for a later bucket), each of capacity J because a
 // cell is queued at most once at a time.
 struct Ctl {
+    // set to all ones before every solve (one 2-D memset over the control
+    // blocks, CTL_ONES_BYTES of each): keys reduced with atomicMin, unset
+    // = KEY_UNSET, and the first start stamp
+    unsigned long long fmin[2];   // min key over a far list (per split parity)
+    unsigned long long fmin_f;    // ordered key of min finite h/F (bucket width default)
+    unsigned long long qdelta;    // value order: ordered key of the launch's bucket width (the smallest
+                                  // of its instances')
+    unsigned long long t_start;   // launch-wide: first start of the persistent pass (%globaltimer, ns)
+    // set to zero before every solve
     unsigned int bar_count;       // grid barrier arrivals
     unsigned int bar_gen;         // grid barrier generation
     int cnt[3];                   // near-list lengths
     int fcnt[2];                  // far-list lengths
     int status;                   // EIK_* of this launch
     int abort;                    // set on any error: every block stops
-    unsigned long long fmin[2];   // min key over a far list (per split parity)
-    unsigned long long fmin_f;    // ordered key of min finite h/F (bucket width default)
     // counters (written once per warp at exit)
     unsigned long long visits;    // cell removals
     unsigned long long sweeps;    // sweeps, per cell until its own no-change sweep
@@ -56,14 +63,14 @@ struct Ctl {
     unsigned long long rounds;
     unsigned long long advances;  // bucket threshold moves
     unsigned long long err_info;  // first failing site (debugging aid)
-    // launch-wide control blocks: first start and last end of the persistent
-    // pass (%globaltimer, ns), kept where events cannot be (graph replay)
-    unsigned long long t_start, t_end;
+    // launch-wide control blocks: last end of the persistent pass
+    // (%globaltimer, ns; the start is above), kept where events cannot be
+    // (graph replay)
+    unsigned long long t_end;
     // FHCM Monotonicity Checks: monotone borders / checks made
     unsigned long long mono_ok, mono_n;
-    // value-ordered schedule: ordered key of the launch's bucket width (the
-    // smallest of its instances'), front moves, cells handed to idle warps
-    unsigned long long qdelta, fronts, handoffs;
+    // value-ordered schedule: front moves, cells handed to idle warps
+    unsigned long long fronts, handoffs;
     // value-ordered schedule, profiling only: 0 bucket claims, 1 tickets
     // taken, 2 cells received on a ticket, 3 gives, 4 requests filed again
     // (a front moved meanwhile), 5 bucket puts, 6 cells handed on by rare
@@ -106,6 +113,7 @@ struct __align__(64) InstDesc {
 };
 
 constexpr int MAX_BATCH = 2048;   // instances per persistent launch
+constexpr size_t CTL_ONES_BYTES = 5 * sizeof(unsigned long long);  // the fields of Ctl set to all ones
 
 // Variants of the persistent cell solver: HCM (Sec. 4.2, every removed cell
 // swept to convergence), FHCM (Sec. 4.3, one sweep per flagged direction)
@@ -228,13 +236,15 @@ struct SourceTable {
     const int* cell; const unsigned long long* cell_key; const int* cell_inst; int ncell;
 };
 
-cudaError_t launch_ctl_init(Ctl* ctl, int count, cudaStream_t st);  // count control blocks
 // A block prefix pre[0..n] is followed in memory by its owner table
-// (pre[n + 1 + b] = instance of block b), filled on the device by this:
-cudaError_t launch_block_owner(const int* pre, int n, cudaStream_t st);
-// f, U interiors; validation of F; min h/F per instance
-cudaError_t launch_init_grid(const AuxInst* a, const int* blk_pre, int n, int nblocks, cudaStream_t st);
-cudaError_t launch_init_sources(const AuxInst* a, const SourceTable& s, cudaStream_t st);
+// (pre[n + 1 + b] = instance of block b), filled by the host; a job of one
+// instance needs none (every block is instance 0's).
+// f and U over every element of the padded arrays, validation of F, min h/F
+// per instance; then, within the same launch, the sources (U = q, f = -1)
+// and the source cells (value max q, queued).  The source table is sorted by
+// (instance, node).
+cudaError_t launch_init_grid(const AuxInst* a, const int* blk_full, int n, int nblocks, const SourceTable& s,
+                             cudaStream_t st);
 // FP32 result -> double-float start values, cell keys; then queue the cells
 cudaError_t launch_seed_refine(const AuxInst* a, const int* blk_pre, int n, int nblocks,
                                const int* cell_pre, int ncells, float beta, cudaStream_t st);

@@ -181,18 +181,13 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
     const int n = j.n;
     cudaMemsetAsync(j.zero_base, 0, j.zero_bytes, st);
     cudaMemsetAsync(j.cval_all, 0xff, j.ncval * 8, st);
-    // the instances' control blocks and the two launch-wide ones behind them
-    if (launch_ctl_init(j.ictl, 2 * n + 2, st) != cudaSuccess) return EIK_ECUDA;
-    if (launch_block_owner(j.blk_pre, n, st) != cudaSuccess ||
-        launch_block_owner(j.blk_full, n, st) != cudaSuccess)
+    // the fields of the instances' control blocks and of the two launch-wide
+    // ones behind them that start at all ones
+    if (cudaMemset2DAsync(j.ictl, sizeof(Ctl), 0xff, CTL_ONES_BYTES, (size_t)(2 * n + 2), st) != cudaSuccess)
         return EIK_ECUDA;
-    nl += 2;
-    if (launch_init_grid(j.aux, j.blk_full, n, j.nblocks_full, st) != cudaSuccess) return EIK_ECUDA;
-    nl += 2;
-    if (j.nsrc_total) {
-        if (launch_init_sources(j.aux, j.src, st) != cudaSuccess) return EIK_ECUDA;
-        nl += 2;
-    }
+    // f, U, the sources and the source cells, in one launch
+    if (launch_init_grid(j.aux, j.blk_full, n, j.nblocks_full, j.src, st) != cudaSuccess) return EIK_ECUDA;
+    ++nl;
     SolveParams p{};
     p.n_inst = n;
     p.deadline_ns = j.deadline_ns > 0 ? j.deadline_ns : 20000000000ll;

@@ -97,6 +97,19 @@ int prepare_stack_sources(const Layout& L, const eik_instance* in, cudaStream_t 
             s->q[pos] = q[e];
         }
     }
+    // by node, as the device looks them up (insertion sort: at most
+    // MAX_SOURCES entries)
+    for (int a = 1; a < s->n; ++a) {
+        const int nd = s->node[a];
+        const double qv = s->q[a];
+        int b = a - 1;
+        for (; b >= 0 && s->node[b] > nd; --b) {
+            s->node[b + 1] = s->node[b];
+            s->q[b + 1] = s->q[b];
+        }
+        s->node[b + 1] = nd;
+        s->q[b + 1] = qv;
+    }
     s->q_min = std::numeric_limits<double>::infinity();
     for (int k = 0; k < s->n; ++k) s->q_min = std::fmin(s->q_min, s->q[k]);
     double cmax[MAX_SOURCES];
