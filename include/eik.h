@@ -256,10 +256,11 @@ void eik_batch_destroy(eik_batch b);
  *
  * eik_tune: time trial solves of the given instances, run as one job like
  * eik_solve_batch (n_inst = 1: like eik_solve), over k in {8, 16, 32}, rounds
- * with relative widths {2, 4, 16, 64, 256} and the round-free schedule,
+ * with relative widths {2, 4, 16, 64, 256}, the round-free schedule, and the
+ * value-ordered one with widths {2, 4, 8} and windows of 3 and 4 buckets,
  * timing each pass on its own; record
  * the fastest choice for the job's class (never one slower than the choice
- * in force before) and return it.  Blocks; about twenty solves.  Each U
+ * in force before) and return it.  Blocks; about forty solves.  Each U
  * receives a valid result.  All descriptors must have one precision and a
  * heap-cell method (EIK_METHOD_FMSM is refused with EIK_EINVAL);
  * their cell_k and bucket_width are ignored.  The table is per process and
@@ -279,6 +280,8 @@ typedef struct {
     double ms;             /* device time of the job with the chosen values */
     double ms_before;      /* device time with the choice in force before */
     int32_t trials;        /* solves run */
+    int32_t ordered;       /* 1: the round-free passes run in value order (EIK_SCHED_ORDERED) */
+    int32_t window;        /* ... taking cells from this many buckets (eik_plan_desc.window) */
 } eik_tune_result;
 
 int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t n_inst, void* cuda_stream,
@@ -295,11 +298,14 @@ void eik_tune_reset(void);
  * A request loop that keeps grids and cell queues on the device.  A server
  * thread takes submitted requests in arrival order and launches the oldest
  * ones of one (cell size, precision) class as a batched job (as
- * eik_solve_batch) on one of two job slots, each with its own stream and
+ * eik_solve_batch) on one of four job slots, each with its own stream and
  * device workspace.  A request is admitted when its device memory fits
- * hbm_budget_bytes together with the other running job, so requests that
- * arrive while a job runs start in the other slot as soon as memory and the
- * slot are free, and the two jobs share the GPU's SMs (continuous batching).
+ * hbm_budget_bytes together with the other running jobs, so requests that
+ * arrive while jobs run start in a free slot as soon as memory allows, and
+ * the jobs share the GPU's SMs (continuous batching): each takes as many
+ * blocks per SM as fit, in full, beside the running ones (their registers,
+ * threads and shared memory added up against the SM's limits; a job started
+ * alone leaves one block per SM for the next).
  * Results do not depend on the mix: each instance has its own queue and
  * arrays (Theorem convergence makes the result schedule-independent up to
  * rounding).

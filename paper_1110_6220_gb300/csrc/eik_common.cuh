@@ -171,7 +171,15 @@ struct LaunchShape {
     size_t smem;       // dynamic shared memory per block
     int blocks;        // co-resident blocks (cooperative launch)
     int per_sm;        // occupancy limit: blocks of this shape one SM holds
+    // what one block takes of an SM: registers (allocated per warp in units
+    // of 256) and shared memory (static + dynamic + the 1 KB the SM reserves
+    // per block)
+    int regs_block;
+    size_t smem_block;
 };
+// per-block resources of kernel fn launched with `threads` threads and
+// `dyn_smem` bytes of dynamic shared memory
+void block_resources(const void* fn, int threads, size_t dyn_smem, LaunchShape* s);
 
 // Schedules of a persistent pass: bucketed rounds (k_solve), or the
 // round-free kernel (k_solve_async, cell sizes >= 8) taking cells first in,

@@ -322,6 +322,7 @@ void shape_fmsm(int num_sms, int n_inst, int sm_cap, LaunchShape* s) {
     if (sm_cap > 0 && sm_cap < cap) cap = sm_cap;
     s->blocks = cap * num_sms;
     s->per_sm = per_sm;
+    block_resources(fn, s->threads, s->smem, s);
 }
 
 }  // namespace

@@ -298,31 +298,69 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
     return EIK_OK;
 }
 
-bool job_pairable(const JobDev& j, int num_sms) {
-    LaunchShape a{}, b{};
+void block_resources(const void* fn, int threads, size_t dyn_smem, LaunchShape* s) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        cudaGetLastError();
+        s->regs_block = 1 << 30;  // unknown: never shares an SM
+        s->smem_block = (size_t)1 << 40;
+        return;
+    }
+    const int warps = (threads + 31) / 32;
+    const int per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    s->regs_block = warps * per_warp;
+    s->smem_block = fa.sharedSizeBytes + dyn_smem + 1024;
+}
+
+JobDev probe_job(int n, int k, bool fp32, bool one_pass, bool async_first, bool async_main, bool ordered,
+                 int variant) {
+    static unsigned long long dummy_ring[1];
+    static unsigned dummy_bq[1];
+    JobDev j{};
+    j.n = n;
+    j.k = k;
+    j.fp32 = fp32;
+    j.one_pass = fp32 && one_pass;
+    j.async_first = async_first;
+    j.async_main = async_main;
+    j.ordered = ordered;
+    j.variant = variant;
+    j.ring = dummy_ring;  // the shapes only ask whether a ring exists
+    j.bq = ordered ? dummy_bq : nullptr;
+    return j;
+}
+
+bool job_footprint(const JobDev& j, int num_sms, Footprint* fp) {
+    if (j.fmsm) return false;
     const bool am = j.async_main && j.ring && j.k >= 8;
     const int sm = !am ? SCH_ROUNDS
                    : j.ordered && j.bq && j.variant == VAR_HCM ? SCH_ORDERED
-                                                                    : SCH_FIFO;
+                                                               : SCH_FIFO;
     const int sf = !(j.async_first && j.ring && j.k >= 8) ? SCH_ROUNDS
-                   : j.ordered && j.bq                ? SCH_ORDERED
-                                                           : SCH_FIFO;
-    if (j.fmsm) {
-        if (fmsm_shape(j.k, num_sms, j.n, 1, &a) || !j.coarse || !job_pairable(*j.coarse, num_sms)) return false;
-        return a.per_sm >= 2;
-    }
+                   : j.ordered && j.bq                    ? SCH_ORDERED
+                                                          : SCH_FIFO;
+    LaunchShape sh[2];
+    int m = 0;
     if (j.fp32 && j.one_pass) {
-        if (solver_shape_df(j.k, num_sms, j.n, 1, sm, VAR_HCM, &b)) return false;
-        return b.per_sm >= 2;
-    }
-    if (j.fp32) {
-        if (solver_shape_f32(j.k, num_sms, j.n, 1, sf, VAR_HCM, &a) ||
-            solver_shape_df(j.k, num_sms, j.n, 1, sm, VAR_HCM, &b))
+        if (solver_shape_df(j.k, num_sms, j.n, 1, sm, VAR_HCM, &sh[m++])) return false;
+    } else if (j.fp32) {
+        if (solver_shape_f32(j.k, num_sms, j.n, 1, sf, VAR_HCM, &sh[m++]) ||
+            solver_shape_df(j.k, num_sms, j.n, 1, sm, VAR_HCM, &sh[m++]))
             return false;
-        return a.per_sm >= 2 && b.per_sm >= 2;
+    } else {
+        if (solver_shape_f64(j.k, num_sms, j.n, 1, sm, j.variant, &sh[m++])) return false;
     }
-    if (solver_shape_f64(j.k, num_sms, j.n, 1, sm, j.variant, &a)) return false;
-    return a.per_sm >= 2;
+    Footprint f;
+    f.per_sm = 1 << 30;
+    for (int e = 0; e < m; ++e) {
+        f.threads = std::max(f.threads, sh[e].threads);
+        f.regs = std::max(f.regs, sh[e].regs_block);
+        f.smem = std::max(f.smem, sh[e].smem_block);
+        f.per_sm = std::min(f.per_sm, sh[e].per_sm);
+    }
+    if (f.per_sm < 1) return false;
+    *fp = f;
+    return true;
 }
 
 // ---------------------------------------------------------------- statistics

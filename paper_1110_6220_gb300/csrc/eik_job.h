@@ -100,10 +100,19 @@ void fill_inst_tables(const Layout& L, const InstArrays& a, bool fp32, double h,
 // and the main pass [2,3].
 int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, int* launches);
 
-// True when every solver launch of j, capped to one block per SM, takes at
-// most half of an SM's resources, so that two such jobs are co-resident in
-// full on separate streams (cooperative grids never wait on each other).
-bool job_pairable(const JobDev& j, int num_sms);
+// What the solver launches of a job take of one SM per block (the largest
+// over its passes, resource by resource) and the fewest blocks of them one
+// SM holds; false if a launch shape cannot be formed (FMSM jobs, whose
+// coarse job runs its own launches, report false: they run alone).
+struct Footprint {
+    int threads = 0, regs = 0, per_sm = 0;
+    size_t smem = 0;
+};
+bool job_footprint(const JobDev& j, int num_sms, Footprint* fp);
+// A job that only carries the schedule flags, for job_footprint before the
+// job is built.
+JobDev probe_job(int n, int k, bool fp32, bool one_pass, bool async_first, bool async_main, bool ordered,
+                 int variant);
 
 // Fill *st for instance i from the control blocks copied back to the host.
 void job_stats(const Layout& L, const eik_plan_desc* d, bool fp32, const Ctl* ictl_first,

@@ -6,10 +6,19 @@
 // each with its own stream, arena and events.  Whenever a slot is free it
 // takes the oldest waiting requests of one (cell size, precision) class that
 // fit the memory budget left by the other slots, and launches them as one
-// batched job (eik_job.h) capped to its share of the SMs, so that a job built
-// from requests that arrived while another job runs overlaps it on the
-// device.  Finished jobs are detected with events (no blocking), their
-// results copied out and their tickets completed.
+// batched job (eik_job.h) with as many blocks per SM as fit beside the jobs
+// already running, so that a job built from requests that arrived while
+// others run overlaps them on the device.  Finished jobs are detected with
+// events (no blocking), their results copied out and their tickets
+// completed.
+//
+// Co-residency: a persistent job's blocks wait for one another, so two of
+// them must never hold parts of the SMs the other needs.  Each job's
+// per-block resources (threads, registers as allocated per warp, shared
+// memory with the SM's per-block reserve) are added up against the SM's
+// limits over all running jobs, and a job takes only the blocks per SM that
+// fit in full (a job started alone leaves one block per SM free for the next
+// one).  A job whose resources are unknown runs alone.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -30,7 +39,7 @@ using namespace eik;
 
 namespace {
 
-constexpr int JOB_SLOTS = 2;
+constexpr int JOB_SLOTS = 4;
 
 struct Request {
     uint64_t ticket;
@@ -52,7 +61,8 @@ struct Slot {
     std::vector<eik_instance> insts;
     size_t bytes = 0;   // budget held while running
     bool busy = false;
-    bool shared = false;  // runs capped to one block per SM beside the other slot
+    Footprint fp;       // per-block resources of the job's persistent launches
+    int cap = 0;        // blocks per SM it holds; 0: alone at its full occupancy
 };
 
 }  // namespace
@@ -62,6 +72,9 @@ struct eik_server_s {
     int num_sms = 0;
     size_t budget = 0;
     int max_inflight = 64;
+    // one SM's limits, for the co-residency of jobs
+    int sm_threads = 0, sm_regs = 0, sm_blocks = 0;
+    size_t sm_smem = 0;
     cudaStream_t user_stream = nullptr;
     std::mutex mu;
     std::condition_variable cv;
@@ -162,19 +175,41 @@ bool launch_slot(eik_server_s* s, Slot& sl, size_t held_by_others) {
     }
     const JobParams P = choose_params(sl.descs.data(), (int)sl.descs.size());
     for (auto& dd : sl.descs) dd.cell_k = P.k;
-    // A job shares the SMs with the other slot's job only when both fit an
-    // SM side by side; otherwise it runs alone with full occupancy once the
-    // other slot is idle (two cooperative grids must never wait for each
-    // other's blocks to become resident).
-    JobDev probe{};
-    probe.n = (int)sl.reqs.size();
-    probe.k = P.k;
-    probe.fp32 = prec == EIK_FP32_REFINE;
-    sl.shared = job_pairable(probe, s->num_sms);
-    const Slot* other = nullptr;
-    for (const Slot& o : s->slots)
-        if (&o != &sl && o.busy) other = &o;
-    if (other && (!sl.shared || !other->shared)) {
+    // blocks per SM for this job beside the running ones (see the top of
+    // this file); -1: wait until they finish
+    const bool fp32 = prec == EIK_FP32_REFINE;
+    const int method = head->d.method;
+    const int variant = method == EIK_METHOD_FHCM ? VAR_FHCM : method == EIK_METHOD_HCM_LSM ? VAR_LSM : VAR_HCM;
+    Footprint fp;
+    const bool known = method != EIK_METHOD_FMSM &&
+                       job_footprint(probe_job((int)sl.reqs.size(), P.k, fp32, P.one_pass, P.async_first,
+                                               P.async_main, P.ordered && P.async_main && P.k >= 8, variant),
+                                     s->num_sms, &fp);
+    int used_threads = 0, used_regs = 0, used_blocks = 0;
+    size_t used_smem = 0;
+    bool any_other = false, other_alone = false;
+    for (const Slot& o : s->slots) {
+        if (&o == &sl || !o.busy) continue;
+        any_other = true;
+        if (o.cap <= 0) other_alone = true;
+        used_threads += o.cap * o.fp.threads;
+        used_regs += o.cap * o.fp.regs;
+        used_smem += (size_t)o.cap * o.fp.smem;
+        used_blocks += o.cap;
+    }
+    int cap = -1;
+    if (!known) {
+        cap = any_other ? -1 : 0;
+    } else if (!other_alone) {
+        int c = fp.per_sm;
+        for (; c >= 1; --c)
+            if (used_threads + c * fp.threads <= s->sm_threads && used_regs + c * fp.regs <= s->sm_regs &&
+                used_smem + (size_t)c * fp.smem <= s->sm_smem && used_blocks + c <= s->sm_blocks)
+                break;
+        cap = c >= 1 ? c : -1;
+        if (cap > 1 && !any_other && cap == fp.per_sm) cap -= 1;  // a block per SM for the next job
+    }
+    if (cap < 0) {
         // keep the requests at the head of the queue, in order
         for (auto it = sl.reqs.rbegin(); it != sl.reqs.rend(); ++it) {
             (*it)->state = 0;
@@ -189,7 +224,9 @@ bool launch_slot(eik_server_s* s, Slot& sl, size_t held_by_others) {
     int rc = build_job(&sl.job, (int)sl.reqs.size(), sl.descs.data(), sl.insts.data(), P,
                        prec == EIK_FP32_REFINE, head->d.deadline_ns, sl.stream);
     if (!rc) {
-        sl.job.j.sm_cap = sl.shared ? 1 : 0;
+        sl.job.j.sm_cap = cap;
+        sl.cap = cap;
+        sl.fp = fp;
         cudaEventRecord(sl.ev[0], sl.stream);
         int nl = 0;
         rc = enqueue_job(sl.job.j, s->num_sms, sl.stream, sl.ev + 2, &nl);
@@ -255,12 +292,18 @@ extern "C" int eik_server_create(eik_server* out, size_t hbm_budget_bytes, int32
     s->budget = hbm_budget_bytes;
     s->max_inflight = max_inflight > 0 ? max_inflight : 64;
     s->user_stream = (cudaStream_t)cuda_stream;
+    int smem = 0;
     if (cudaGetDevice(&s->device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
+        cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&s->sm_threads, cudaDevAttrMaxThreadsPerMultiProcessor, s->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&s->sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, s->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&s->sm_blocks, cudaDevAttrMaxBlocksPerMultiprocessor, s->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, s->device) != cudaSuccess) {
         cudaGetLastError();
         delete s;
         return EIK_ECUDA;
     }
+    s->sm_smem = (size_t)smem;
     for (Slot& sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();

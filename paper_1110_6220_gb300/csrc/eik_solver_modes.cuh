@@ -58,6 +58,7 @@ static void shape_of(int num_sms, int n_inst, int sm_cap, int sched, int variant
     if (sm_cap > 0 && sm_cap < cap) cap = sm_cap;  // leave room for other jobs
     s->blocks = (per_sm < cap ? per_sm : cap) * num_sms;
     s->per_sm = per_sm;
+    block_resources(fn, s->threads, s->smem, s);
 }
 
 template <int MODE>

@@ -280,6 +280,8 @@ extern "C" int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t 
         int k = 0;
         double mf = 0, mm = 0, est = 1e300;
         bool af = false, am = false, op = false;
+        bool ord = false;
+        int win = 31;
     } best;
     if (!rc) {
         for (int k : {8, 16, 32}) {
@@ -309,6 +311,23 @@ extern "C" int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t 
             const double est = (fp32 ? bf : 0.0) + bm + ov;
             if (!fp32) mf = mm, af = am;
             if (est < best.est) best = Best{k, mf, mm, est, af, am, false};
+            // the value-ordered schedule (FP32_REFINE as one double-float
+            // pass): buckets of 2, 4 and 8 cell crossings, windows of 2 and 3
+            // buckets above the front; whole-job times
+            for (double m : {2.0, 4.0, 8.0})
+                for (int w : {2, 3}) {
+                    JobParams O{k, -m, -m};
+                    O.async_first = O.async_main = true;
+                    O.ordered = true;
+                    O.window = w;
+                    O.one_pass = fp32;
+                    if (trial(O, t)) continue;
+                    if (t[0] < best.est) {
+                        best = Best{k, m, m, t[0], true, true, fp32};
+                        best.ord = true;
+                        best.win = w;
+                    }
+                }
             if (!fp32) continue;
             // FP32 + refinement as one double-float pass: rounds at every
             // width, then round-free
@@ -325,17 +344,23 @@ extern "C" int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t 
     Entry chosen{before.k, -before.w_first, -before.w_main, t_before[0], before.async_first, before.async_main};
     chosen.one_pass = before.one_pass;
     chosen.hold_ns = before.hold_ns;
+    chosen.ordered = before.ordered;
+    chosen.window = before.window;
     float t_new[3] = {0, 0, 0};
     JobParams B{best.k, -best.mf, -best.mm};
     B.async_first = best.af;
     B.async_main = best.am;
     B.one_pass = best.op;
+    B.ordered = best.ord;
+    B.window = best.win;
     if (!rc && best.k && trial(B, t_new) == EIK_OK && t_new[0] < t_before[0]) {
         chosen = Entry{best.k, best.mf, best.mm, t_new[0], best.af, best.am};
         chosen.one_pass = best.op;
+        chosen.ordered = best.ord;
+        chosen.window = best.win;
     }
-    // a round-free main pass: also try holding cells after their requests
-    if (!rc && chosen.async_main) {
+    // a first-in first-out main pass: also try holding cells after their requests
+    if (!rc && chosen.async_main && !chosen.ordered) {
         JobParams H{chosen.k, -chosen.m_first, -chosen.m_main};
         H.async_first = chosen.async_first;
         H.async_main = true;
@@ -366,6 +391,8 @@ extern "C" int eik_tune(const eik_plan_desc* d, const eik_instance* in, int32_t 
         out->async_main = chosen.async_main;
         out->one_pass = chosen.one_pass;
         out->hold_ns = (int32_t)chosen.hold_ns;
+        out->ordered = chosen.ordered;
+        out->window = chosen.ordered ? chosen.window + 1 : 0;
         out->ms = chosen.ms;
         out->ms_before = t_before[0];
         out->trials = trials;

@@ -81,7 +81,8 @@ class eik_tune_result(ctypes.Structure):
                 ("bucket_main", ctypes.c_double), ("async_first", ctypes.c_int32),
                 ("async_main", ctypes.c_int32), ("one_pass", ctypes.c_int32),
                 ("hold_ns", ctypes.c_int32), ("ms", ctypes.c_double),
-                ("ms_before", ctypes.c_double), ("trials", ctypes.c_int32)]
+                ("ms_before", ctypes.c_double), ("trials", ctypes.c_int32),
+                ("ordered", ctypes.c_int32), ("window", ctypes.c_int32)]
 
 
 eik_plan = ctypes.c_void_p

@@ -41,13 +41,15 @@ def test_tune_single_then_solve_uses_choice(eik, orc, prec):
     rc, r = eik.eik_tune([d], [eik.make_instance(I.F, src, I.sq, U)])
     assert rc == 0, eik.eik_strerror(rc)
     assert r.cell_k in (8, 16, 32) and r.trials >= 10
-    assert r.bucket_main in (2, 4, 16, 64, 256) or r.ms == r.ms_before
+    assert r.bucket_main in (2, 4, 8, 16, 64, 256) or r.ms == r.ms_before
     assert 0 < r.ms <= r.ms_before
+    assert r.ordered in (0, 1) and (r.window in (3, 4) if r.ordered else r.window == 0)
     V = orc.fmm(I.F, I.h, I.si, I.sj, I.sq)
     tol = TOL64 if prec == 0 else TOL32
     _check(U, V, tol, "last trial")
     U2, st = eik.solve(I.F, I.h, I.si, I.sj, I.sq, cell_k=0, precision=prec)
     assert st.cell_k == r.cell_k
+    assert bool(st.schedule & 32) == bool(r.ordered)  # the tuned schedule is the one that runs
     _check(U2, V, tol, "tuned solve")
 
 
