@@ -321,6 +321,7 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
         aux_h[i].Fc = fmsm ? (double*)fm_dev + coff : nullptr;
         aux_h[i].Uc = fmsm ? (double*)(fm_dev + a256(Jtot * 8)) + coff : nullptr;
         desc_main_h[i].cell_base = (int)coff;
+        desc_main_h[i].done = hj->done_dev ? hj->done_dev + i : nullptr;
         if (fp32) desc_f32_h[i].cell_base = (int)coff;
         blk_pre_h[i] = boff;
         boff += aux_blocks(L.nyp, L.nxp);
@@ -400,6 +401,9 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     j.ring = (unsigned long long*)(ring_dev + 384 + hist_bytes);
     j.ring_mask = (unsigned)(Q - 1);
     j.ordered = ordered;
+    // per-instance completion needs the main pass round-free in one launch:
+    // the one-pass FP32_REFINE form or FP64 HCM-family methods, cells >= 8
+    j.inst_done = hj->done_dev && P.async_main && k >= 8 && !fmsm && (!fp32 || P.one_pass);
     j.window = P.window;
     j.bq = ordered ? (unsigned*)(ring_dev + a256(384 + hist_bytes + Q * 8)) : nullptr;
     j.bq_data = ordered ? (unsigned long long*)((char*)j.bq + a256((size_t)BQ_WORDS * 4)) : nullptr;

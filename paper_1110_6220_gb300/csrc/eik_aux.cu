@@ -299,9 +299,12 @@ __global__ void k_residual(const AuxInst* A, const int* blk_pre, int n) {
         if (i >= p.nx || j >= p.ny) continue;
         const size_t q = (size_t)(j + 1) * up + (i + 1);
         left += queued_at(p, i, j);
-        const float2 V = p.Udf[q];
+        // U through L2: with per-instance completion this kernel runs while
+        // the persistent pass still works on other instances
+        const float2 V = __ldcg(p.Udf + q);
         const float2 fs = p.fdf[q];
-        const float2 W = p.Udf[q - 1], E = p.Udf[q + 1], S = p.Udf[q - up], N = p.Udf[q + up];
+        const float2 W = __ldcg(p.Udf + q - 1), E = __ldcg(p.Udf + q + 1), S = __ldcg(p.Udf + q - up),
+                     N = __ldcg(p.Udf + q + up);
         const bool vfin = V.x < FINF;
         if (vfin) umax = fmaxf(umax, V.x);
         double o = inf_of<double>();
@@ -373,9 +376,9 @@ __global__ void k_output(const AuxInst* A, const int* blk_pre, int n) {
             const size_t q = (size_t)(j + 1) * p.upitch + (i + 1);
             double v;
             if (p.U64) {
-                v = p.U64[q];
+                v = __ldcg(p.U64 + q);
             } else {
-                const float2 a = p.Udf[q];
+                const float2 a = __ldcg(p.Udf + q);
                 v = a.x < inf_of<float>() ? widen(a.x) + widen(a.y) : inf_of<double>();
             }
             p.out[(size_t)j * p.nx + i] = v + p.shift;

@@ -56,6 +56,7 @@ struct Ctl {
     int fcnt[2];                  // far-list lengths
     int status;                   // EIK_* of this launch
     int abort;                    // set on any error: every block stops
+    int left;                     // per-instance completion: the instance's cells requested or running
     // counters (written once per warp at exit)
     unsigned long long visits;    // cell removals
     unsigned long long sweeps;    // sweeps, per cell until its own no-change sweep
@@ -110,6 +111,8 @@ struct __align__(64) InstDesc {
     int cxn, cyn, J;
     double delta;                 // bucket width; < 0: |delta| k min f (from ctl->fmin_f); 0: 4 k min f
     int cell_base;                // index of this instance's first cell among the job's cells
+    unsigned* done;               // per-instance completion: a flag in mapped host memory, set to 1 when
+                                  // the instance's last requested cell finishes (null: not reported)
 };
 
 constexpr int MAX_BATCH = 2048;   // instances per persistent launch
@@ -160,6 +163,10 @@ struct SolveParams {
     // before each removal's tile load, drawn per removal
     int max_passes;
     unsigned jitter_ns;
+    // round-free schedules: count each instance's requested or running cells
+    // and flag the instance done when its count reaches zero (its result is
+    // final then, while the launch goes on with the others)
+    int inst_done;
 };
 constexpr int NBQ = 32;           // bucket rings of the value-ordered schedule (one lane of a warp each)
 constexpr int BQ_WORDS = 160;     // header words: pairs [0, 64), 64-bit counts [64, 128), front at 128

@@ -204,6 +204,7 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
     p.bq_data = j.bq_data;
     p.bq_mask = j.bq_mask;
     p.bq_window = j.window < 0 ? 0 : j.window > NBQ - 1 ? NBQ - 1 : j.window;
+    p.inst_done = j.inst_done ? 1 : 0;
     // host-set checks (0 / unset: off): EIK_MAX_PASSES caps the passes of a
     // removal (a cap it hits reports EIK_ENOTCONVERGED), EIK_JITTER_NS
     // pauses each removal by up to that many ns before its tile load
@@ -230,8 +231,10 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
         if (launch_solver_df(j.k, sm, p, shape, st) != cudaSuccess) return EIK_ECUDA;
         if (ev) cudaEventRecord(ev[3], st);
         ++nl;
-        if (launch_residual(j.aux, j.blk_pre, n, j.nblocks, st) != cudaSuccess) return EIK_ECUDA;
-        ++nl;
+        if (!j.inst_done) {
+            if (launch_residual(j.aux, j.blk_pre, n, j.nblocks, st) != cudaSuccess) return EIK_ECUDA;
+            ++nl;
+        }
     } else if (j.fp32) {
         if (solver_shape_f32(j.k, num_sms, n, j.sm_cap, sf, VAR_HCM, &shape)) return EIK_ECUDA;
         p.inst = j.desc_f32;
@@ -290,12 +293,22 @@ int enqueue_job(const JobDev& j, int num_sms, cudaStream_t st, cudaEvent_t* ev, 
         if (ev) cudaEventRecord(ev[3], st);
         ++nl;
     }
-    if (!j.fp32) {  // the pair modes' residual kernel writes the output
+    if (!j.fp32 && !j.inst_done) {  // the pair modes' residual kernel writes the output
         if (launch_output(j.aux, j.blk_pre, n, j.nblocks, st) != cudaSuccess) return EIK_ECUDA;
         ++nl;
     }
     if (launches) *launches = nl;
     return EIK_OK;
+}
+
+int finish_instance(const JobDev& j, int i, const Layout& L, cudaStream_t st) {
+    // a launch over one instance: its aux entry as entry 0, and the job's
+    // block prefix, whose first element is 0 (a single instance reads no
+    // owner table)
+    const int nb = aux_blocks(L.nyp, L.nxp);
+    const cudaError_t e = j.fp32 ? launch_residual(j.aux + i, j.blk_pre, 1, nb, st)
+                                 : launch_output(j.aux + i, j.blk_pre, 1, nb, st);
+    return e == cudaSuccess ? EIK_OK : EIK_ECUDA;
 }
 
 void block_resources(const void* fn, int threads, size_t dyn_smem, LaunchShape* s) {

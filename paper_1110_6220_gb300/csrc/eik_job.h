@@ -75,6 +75,11 @@ struct JobDev {
     unsigned* bq;
     unsigned long long* bq_data;
     unsigned bq_mask;
+    // per-instance completion (a round-free main pass in one launch): each
+    // instance's done flag is set by the launch, and the node-wise kernel
+    // that writes the output runs per instance (finish_instance), not after
+    // the pass
+    bool inst_done;
     // everything that enqueue_job zeroes before a solve: [zero_base, + zero_bytes)
     void* zero_base;
     size_t zero_bytes;
@@ -109,6 +114,11 @@ struct Footprint {
     size_t smem = 0;
 };
 bool job_footprint(const JobDev& j, int num_sms, Footprint* fp);
+
+// Per-instance completion: the node-wise kernel that certifies and writes
+// instance i's output (FP32_REFINE: the residual; FP64: the output), alone,
+// on st.  L: the instance's layout.
+int finish_instance(const JobDev& j, int i, const Layout& L, cudaStream_t st);
 // A job that only carries the schedule flags, for job_footprint before the
 // job is built.
 JobDev probe_job(int n, int k, bool fp32, bool one_pass, bool async_first, bool async_main, bool ordered,

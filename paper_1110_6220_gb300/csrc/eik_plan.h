@@ -71,6 +71,9 @@ struct HostJob {
     char* src_host = nullptr;    // pinned staging of the instances' sources
     size_t src_cap = 0;
     HostJob* coarse = nullptr;   // FMSM: the job of the coarse grids (owned)
+    // per-instance completion: device pointer of n done flags in mapped host
+    // memory (set by the caller before build_job; null: the job finishes as a whole)
+    unsigned* done_dev = nullptr;
 };
 
 // Lay out and upload a job of n instances (one k and precision); descs[i]

@@ -52,8 +52,13 @@ struct Request {
     int rc = EIK_EAGAIN;
 };
 
+// what a request's finishing work reads back: its instance's control block
+// of the main pass, its residual, and the launch-wide control block
+constexpr size_t FIN_REC = sizeof(Ctl) * 2 + sizeof(ResidualOut);
+
 struct Slot {
     cudaStream_t stream = nullptr;
+    cudaStream_t out = nullptr;  // per-request finishing work, beside the job's launches
     cudaEvent_t ev[6] = {};
     HostJob job;
     std::vector<Request*> reqs;
@@ -61,8 +66,17 @@ struct Slot {
     std::vector<eik_instance> insts;
     size_t bytes = 0;   // budget held while running
     bool busy = false;
+    bool main_done = false;  // the job's launches have finished
     Footprint fp;       // per-block resources of the job's persistent launches
     int cap = 0;        // blocks per SM it holds; 0: alone at its full occupancy
+    // per-instance completion: the job's done flags (mapped host memory), per
+    // request 0 running / 1 finishing / 2 complete, the finishing work's event
+    unsigned* done_h = nullptr;
+    unsigned* done_d = nullptr;
+    char* pin = nullptr;  // MAX_BATCH records of FIN_REC bytes (pinned)
+    std::vector<int> fin;
+    std::vector<cudaEvent_t> fev;
+    std::chrono::steady_clock::time_point t0;
 };
 
 }  // namespace
@@ -135,6 +149,85 @@ void complete_slot(eik_server_s* s, Slot& sl) {
     sl.bytes = 0;
 }
 
+// Per-instance completion: queue request e's finishing work on the slot's
+// second stream -- the node-wise kernel that certifies and writes its
+// output, the copy of a host U, and the read-back of its control block and
+// residual (and of the launch's, once the job's launches are over).
+void start_finish(Slot& sl, int e) {
+    HostJob& hj = sl.job;
+    const int n = hj.j.n;
+    char* rec = sl.pin + (size_t)e * FIN_REC;
+    int rc = finish_instance(hj.j, e, hj.L[e], sl.out);
+    if (!rc && hj.out_host[e] &&
+        cudaMemcpyAsync(hj.out_user[e], hj.arr[e].Ostage, (size_t)hj.L[e].nx * hj.L[e].ny * 8,
+                        cudaMemcpyDeviceToHost, sl.out) != cudaSuccess)
+        rc = EIK_ECUDA;
+    cudaMemcpyAsync(rec, hj.j.ictl + n + e, sizeof(Ctl), cudaMemcpyDeviceToHost, sl.out);
+    cudaMemcpyAsync(rec + sizeof(Ctl), hj.j.res + e, sizeof(ResidualOut), cudaMemcpyDeviceToHost, sl.out);
+    if (sl.main_done)
+        cudaMemcpyAsync(rec + sizeof(Ctl) + sizeof(ResidualOut), hj.j.gctl + 1, sizeof(Ctl), cudaMemcpyDeviceToHost,
+                        sl.out);
+    else
+        std::memset(rec + sizeof(Ctl) + sizeof(ResidualOut), 0, sizeof(Ctl));
+    if (rc) cudaGetLastError();
+    cudaEventRecord(sl.fev[e], sl.out);
+    sl.fin[e] = 1;
+}
+
+// Request e's finishing work is done: its statistics, its ticket.
+void complete_request(eik_server_s* s, Slot& sl, int e) {
+    HostJob& hj = sl.job;
+    const char* rec = sl.pin + (size_t)e * FIN_REC;
+    Ctl zero;
+    std::memset((void*)&zero, 0, sizeof(zero));
+    const Ctl* ic = (const Ctl*)rec;
+    const ResidualOut* r = (const ResidualOut*)(rec + sizeof(Ctl));
+    const Ctl* g = (const Ctl*)(rec + sizeof(Ctl) + sizeof(ResidualOut));
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - sl.t0).count();
+    eik_stats st;
+    job_stats(hj.L[e], &sl.descs[e], hj.j.fp32, &zero, ic, &zero, g, r, hj.shift[e], hj.bw_main[e], ms, &st);
+    st.schedule = (hj.j.async_main && hj.j.k >= 8 ? 2 : 0) | (hj.j.one_pass ? 4 : 0) |
+                  (hj.j.ordered && hj.j.variant == VAR_HCM ? 32 : 0);
+    st.pass_ms[0] = 0.0;
+    st.pass_ms[1] = ms;
+    Request* req = sl.reqs[e];
+    req->st = st;
+    req->rc = st.status;
+    req->state = 2;
+    --s->inflight;
+    sl.fin[e] = 2;
+}
+
+// Advance a busy slot whose job reports per-instance completion; true when
+// something happened.  The slot frees once every request is complete.
+bool advance_slot(eik_server_s* s, Slot& sl) {
+    bool progressed = false;
+    if (!sl.main_done && cudaEventQuery(sl.ev[1]) == cudaSuccess) {
+        sl.main_done = true;  // its SM blocks are free for other jobs
+        progressed = true;
+    }
+    const int n = (int)sl.reqs.size();
+    int complete = 0;
+    for (int e = 0; e < n; ++e) {
+        if (sl.fin[e] == 0 && (sl.main_done || *(volatile unsigned*)(sl.done_h + e))) {
+            start_finish(sl, e);
+            progressed = true;
+        }
+        if (sl.fin[e] == 1 && cudaEventQuery(sl.fev[e]) == cudaSuccess) {
+            complete_request(s, sl, e);
+            progressed = true;
+        }
+        complete += sl.fin[e] == 2;
+    }
+    if (complete == n && sl.main_done) {
+        sl.reqs.clear();
+        sl.busy = false;
+        sl.bytes = 0;
+        progressed = true;
+    }
+    return progressed;
+}
+
 // Launch the oldest admissible waiting requests on a free slot (lock held;
 // the CUDA calls happen with the lock released by the caller's structure:
 // build and enqueue are quick and non-blocking apart from small copies).
@@ -189,7 +282,7 @@ bool launch_slot(eik_server_s* s, Slot& sl, size_t held_by_others) {
     size_t used_smem = 0;
     bool any_other = false, other_alone = false;
     for (const Slot& o : s->slots) {
-        if (&o == &sl || !o.busy) continue;
+        if (&o == &sl || !o.busy || o.main_done) continue;  // only launches still on the SMs
         any_other = true;
         if (o.cap <= 0) other_alone = true;
         used_threads += o.cap * o.fp.threads;
@@ -221,8 +314,20 @@ bool launch_slot(eik_server_s* s, Slot& sl, size_t held_by_others) {
     }
     for (Request* r : sl.reqs)
         if (r->ready) cudaStreamWaitEvent(sl.stream, r->ready, 0);
-    int rc = build_job(&sl.job, (int)sl.reqs.size(), sl.descs.data(), sl.insts.data(), P,
-                       prec == EIK_FP32_REFINE, head->d.deadline_ns, sl.stream);
+    // per-instance completion: fresh flags (no launch of this slot runs now)
+    const int n = (int)sl.reqs.size();
+    std::memset(sl.done_h, 0, (size_t)n * sizeof(unsigned));
+    sl.job.done_dev = sl.done_d;
+    sl.fin.assign(n, 0);
+    sl.main_done = false;
+    while ((int)sl.fev.size() < n) {
+        cudaEvent_t e = nullptr;
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        sl.fev.push_back(e);
+    }
+    sl.t0 = std::chrono::steady_clock::now();
+    int rc = build_job(&sl.job, n, sl.descs.data(), sl.insts.data(), P, prec == EIK_FP32_REFINE,
+                       head->d.deadline_ns, sl.stream);
     if (!rc) {
         sl.job.j.sm_cap = cap;
         sl.cap = cap;
@@ -255,7 +360,10 @@ void server_loop(eik_server_s* s) {
     for (;;) {
         bool progressed = false;
         for (Slot& sl : s->slots) {
-            if (sl.busy && cudaEventQuery(sl.ev[1]) == cudaSuccess) {
+            if (!sl.busy) continue;
+            if (sl.job.j.inst_done) {
+                if (advance_slot(s, sl)) progressed = true;
+            } else if (cudaEventQuery(sl.ev[1]) == cudaSuccess) {
                 complete_slot(s, sl);
                 progressed = true;
             }
@@ -305,7 +413,11 @@ extern "C" int eik_server_create(eik_server* out, size_t hbm_budget_bytes, int32
     }
     s->sm_smem = (size_t)smem;
     for (Slot& sl : s->slots) {
-        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) {
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&sl.out, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaHostAlloc((void**)&sl.done_h, MAX_BATCH * sizeof(unsigned), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer((void**)&sl.done_d, sl.done_h, 0) != cudaSuccess ||
+            cudaMallocHost((void**)&sl.pin, MAX_BATCH * FIN_REC) != cudaSuccess) {
             cudaGetLastError();
             eik_server_destroy(s);
             return EIK_ECUDA;
@@ -389,10 +501,16 @@ extern "C" void eik_server_destroy(eik_server s) {
     if (s->worker.joinable()) s->worker.join();
     for (Slot& sl : s->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.out) cudaStreamSynchronize(sl.out);
         free_job(&sl.job);
         for (auto& e : sl.ev)
             if (e) cudaEventDestroy(e);
+        for (auto& e : sl.fev)
+            if (e) cudaEventDestroy(e);
         if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.out) cudaStreamDestroy(sl.out);
+        if (sl.done_h) cudaFreeHost(sl.done_h);
+        if (sl.pin) cudaFreeHost(sl.pin);
     }
     for (auto& kv : s->all) {
         if (kv.second->ready) cudaEventDestroy(kv.second->ready);

@@ -1803,6 +1803,13 @@ __device__ __forceinline__ int bq_next(const SolveParams& p, Ctl* gctl, unsigned
     }
 }
 
+// Per-instance completion: the instance's last requested cell has finished,
+// so its values are final -- publish them, then flag it in host memory.
+__device__ __forceinline__ void instance_done(const InstDesc& d) {
+    __threadfence_system();
+    *(volatile unsigned*)d.done = 1u;
+}
+
 // The double-float kernels at k = 8 and 16 are held to three blocks per SM:
 // left alone, the compiler fits them into 64 registers (four blocks) with
 // spills, which measured slower (1025^2: 1.86 against 1.73 ms per pass; the
@@ -1852,6 +1859,11 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32,
     // upstream neighbours, as the bucketed schedule would order them.
     for (int i = threadIdx.x; i < NI; i += blockDim.x) s_cnt[i] = min(ld_cg(&inst[i].ctl->fcnt[0]), inst[i].J);
     __syncthreads();
+    if (p.inst_done && blockIdx.x == 0)  // (before the prologue's grid barriers)
+        for (int i = threadIdx.x; i < NI; i += blockDim.x) {
+            inst[i].ctl->left = s_cnt[i];
+            if (s_cnt[i] == 0) instance_done(inst[i]);  // no source: final as it is
+        }
     const int total = block_exclusive_scan(s_cnt, s_pre, NI, s_scr);
     const unsigned Q = p.ring_mask + 1u;
     double inv_delta = 0.0;  // ORD: 1 / bucket width
@@ -1986,6 +1998,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32,
                 const int was = atomicOr(&dn.qflag[nc], 1) & 3;
                 if (was == 0) {
                     atomicAdd(&p.qctl[Q_PENDING], 1u);
+                    if (p.inst_done) atomicAdd(&dn.ctl->left, 1);
                     if constexpr (ORD) {
                         // filed by the value this side proposes (eq. cell_value):
                         // the cell's own value, lowered by every earlier proposal,
@@ -2005,8 +2018,11 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32,
             });
         // ---- finish: push again if a neighbour asked meanwhile
         int adv = 0;
+        if (p.inst_done && lane == 0)  // the instance's counters in place before it can be flagged done
+            flush_counters(inst, w.acc_inst, w.acc_visits, w.acc_sweeps, w.acc_lane);
         if (lane == 0) {
             const int old = atomicAnd(&d.qflag[c], ~2);
+            const bool last = !(old & 1) && p.inst_done && atomicSub(&d.ctl->left, 1) == 1;
             if constexpr (ORD) {
                 if (old & 1) {
                     const unsigned long long rk = atomicExch(&p.req_time[e], 0ull);
@@ -2021,6 +2037,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32,
                 if (old & 1) ring_push(p, gctl, (unsigned)e, deadline);
                 else atomicSub(&p.qctl[Q_PENDING], 1u);
             }
+            if (last) instance_done(d);
         }
         if constexpr (ORD) {
             if (__shfl_sync(FULL, adv, 0)) bq_advance(p, gctl, deadline, lane);
