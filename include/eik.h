@@ -306,6 +306,13 @@ void eik_tune_reset(void);
  * blocks per SM as fit, in full, beside the running ones (their registers,
  * threads and shared memory added up against the SM's limits; a job started
  * alone leaves one block per SM for the next).
+ * A request completes when its own grid has converged, not when its job's
+ * largest one has, wherever the job runs one round-free pass with cells of 8
+ * or more (the built-in form of every HCM and HCM_LSM job; not FHCM, FMSM,
+ * bucketed rounds or two-pass FP32_REFINE):
+ * the kernel flags each finished instance in host memory and the server
+ * writes that request's output and completes its ticket while the job goes
+ * on.  Other jobs complete all their requests together.
  * Results do not depend on the mix: each instance has its own queue and
  * arrays (Theorem convergence makes the result schedule-independent up to
  * rounding).
@@ -325,9 +332,11 @@ int eik_server_create(eik_server* out, size_t hbm_budget_bytes, int32_t max_infl
 int eik_submit(eik_server s, const eik_plan_desc* d, const eik_instance* in, uint64_t* ticket);
 
 /* Non-blocking: EIK_EAGAIN while the request is pending; otherwise its final
- * status (st, if not NULL, filled; st->ms is the device time of the job that
- * served it).  A ticket is polled to completion once; later polls and unknown
- * tickets return EIK_EINVAL. */
+ * status (st, if not NULL, filled; st->ms is the time from its job's launch
+ * to the request's completion: device time of the job where all requests
+ * complete together, host clock where each completes on its own).  A ticket
+ * is polled to completion once; later polls and unknown tickets return
+ * EIK_EINVAL. */
 int eik_poll(eik_server s, uint64_t ticket, eik_stats* st);
 
 /* Finish every queued request, then release the server.  NULL is ignored. */

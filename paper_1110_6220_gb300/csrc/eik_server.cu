@@ -8,9 +8,19 @@
 // fit the memory budget left by the other slots, and launches them as one
 // batched job (eik_job.h) with as many blocks per SM as fit beside the jobs
 // already running, so that a job built from requests that arrived while
-// others run overlaps them on the device.  Finished jobs are detected with
-// events (no blocking), their results copied out and their tickets
-// completed.
+// others run overlaps them on the device.
+//
+// Completion is per request where the job's persistent pass supports it
+// (round-free, cells of 8 or more, one pass): each instance counts its
+// requested and running cells, and the cell whose finish brings the count to
+// zero sets the instance's flag in mapped host memory.  The loop polls the
+// flags and, for each newly finished instance, queues its node-wise output
+// kernel, the copy of a host U and the read-back of its counters on the
+// slot's second stream; when that work's event has completed the ticket is
+// done, while the job's launch may still be running for its other requests.
+// A job's blocks leave the co-residency account as soon as its launches end.
+// Other jobs (rounds, FMSM, two passes) complete all their requests together
+// when the job's last event has completed.  Nothing blocks the loop.
 //
 // Co-residency: a persistent job's blocks wait for one another, so two of
 // them must never hold parts of the SMs the other needs.  Each job's

@@ -80,9 +80,10 @@ int side_class(const eik_plan_desc* d, int n) {
 //    checkerboard + maze from 39 visits per cell to 21, 33.8 ms to 23.7 ms);
 //    on 1025^2 and on the batch a hold saves nothing or costs time.
 //  - the tuner (eik_tune) on each class then moved three choices: FP64
-//    batches run round-free at k = 8 (46.2 ms instead of 75.8 ms on the
-//    512-grid mix), small FP64 grids too (129^2: 0.32 ms instead of 0.37
-//    ms), and ~2048^2 grids hold for 4 us (2049^2 maze: 6.3 ms for 6.8 ms).
+//    batches run round-free (46.2 ms instead of 75.8 ms on the 512-grid mix,
+//    k = 8; at k = 16 once its sweeps skipped empty slots, below), small
+//    FP64 grids too (129^2: 0.32 ms instead of 0.37 ms), and ~2048^2 grids
+//    hold for 4 us (2049^2 maze: 6.3 ms for 6.8 ms).
 //  - single grids of about 8192^2 and more go back to rounds, k = 16: on the
 //    round-free ring the visits per cell of the sin20 grid grow with the
 //    side (21 at 1025^2, 38 at 8193^2, 76 at 16385^2, 159 at 32769^2), while
@@ -123,6 +124,11 @@ Entry builtin(int prec, bool batch, int side, bool fhcm) {
         if (!batch && side >= 13) e = ordered(e, 4.0, 2);
         return e;
     }
+    // FP64 batches: first in, first out at k = 16 (the 512-grid mix 36.8 ms
+    // against 50.2 ms at k = 8; the 128-request serving mix, sides up to
+    // 2003, 60.0 against 74.1 ms; value order at k = 16 72-86 ms: its one
+    // bucket width, the finest instance's, is too narrow for the others)
+    if (batch && !fhcm) return Entry{16, 4.0, 4.0, 0.0, false, true};
     if (batch || side <= 8) return Entry{8, 4.0, 4.0, 0.0, false, true};
     // FHCM's one-sweep visits gain less from merged requests: rounds
     // (1025^2 sin20 2.72 ms, against 2.92 ms round-free with a 4 us hold);

@@ -155,3 +155,34 @@ def test_serving_admission_and_stream_order(eik, orc):
         assert rc == eik.EIK_EINVAL
     finally:
         eik.eik_server_destroy(srv)
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32ref"])
+def test_a_request_completes_when_its_own_grid_converges(eik, orc, prec):
+    """A small grid submitted together with a large one joins its job (one
+    launch) and completes long before it: the kernel flags each instance as
+    its last queued cell finishes, and the server finishes that request while
+    the launch goes on.  Both results match the oracle; a host U is written
+    by the request's own finishing copy."""
+    big = W.checker_maze(1537, seed=3, n_walls=12, n_src=2)
+    small = W.sin_point(129)
+    srv = eik.eik_server_create(8 << 30, 8)
+    try:
+        dbig = _device(big)
+        Us = np.full_like(small.F, -1.0)  # host U: staged, copied out per request
+        t_big = eik.eik_submit(srv, eik.make_desc(big.nx, big.ny, big.h, 16, prec),
+                               eik.make_instance(*dbig))[1]
+        t_small = eik.eik_submit(srv, eik.make_desc(small.nx, small.ny, small.h, 16, prec),
+                                 eik.make_instance(small.F, small.src_ij, small.sq, Us))[1]
+        rc_s, st_s = _wait(eik, srv, t_small)
+        rc_b, st_b = _wait(eik, srv, t_big)
+    finally:
+        eik.eik_server_destroy(srv)
+    assert rc_s == 0 and rc_b == 0
+    assert st_s.queue_left == 0 and st_b.queue_left == 0
+    assert st_s.ms < 0.5 * st_b.ms, (st_s.ms, st_b.ms)
+    tol = TOL64 if prec == 0 else TOL32
+    _check(Us, orc.fmm(small.F, small.h, small.si, small.sj, small.sq), tol, "small")
+    _check(dbig[3].cpu().numpy(), orc.fmm(big.F, big.h, big.si, big.sj, big.sq), tol, "big")
+    if prec == 1:
+        assert st_s.err_bound <= TOL32 and st_b.err_bound <= TOL32
