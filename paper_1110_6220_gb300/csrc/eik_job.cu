@@ -311,6 +311,12 @@ int finish_instance(const JobDev& j, int i, const Layout& L, cudaStream_t st) {
     return e == cudaSuccess ? EIK_OK : EIK_ECUDA;
 }
 
+int finish_instances(const JobDev& j, cudaStream_t st) {
+    const cudaError_t e = j.fp32 ? launch_residual(j.aux, j.blk_pre, j.n, j.nblocks, st)
+                                 : launch_output(j.aux, j.blk_pre, j.n, j.nblocks, st);
+    return e == cudaSuccess ? EIK_OK : EIK_ECUDA;
+}
+
 void block_resources(const void* fn, int threads, size_t dyn_smem, LaunchShape* s) {
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {

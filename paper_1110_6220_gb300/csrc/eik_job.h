@@ -119,6 +119,9 @@ bool job_footprint(const JobDev& j, int num_sms, Footprint* fp);
 // instance i's output (FP32_REFINE: the residual; FP64: the output), alone,
 // on st.  L: the instance's layout.
 int finish_instance(const JobDev& j, int i, const Layout& L, cudaStream_t st);
+// The same for every instance of the job in one launch (instances finished
+// alone before are written again with the same values).
+int finish_instances(const JobDev& j, cudaStream_t st);
 // A job that only carries the schedule flags, for job_footprint before the
 // job is built.
 JobDev probe_job(int n, int k, bool fp32, bool one_pass, bool async_first, bool async_main, bool ordered,

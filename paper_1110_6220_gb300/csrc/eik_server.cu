@@ -86,6 +86,10 @@ struct Slot {
     char* pin = nullptr;  // MAX_BATCH records of FIN_REC bytes (pinned)
     std::vector<int> fin;
     std::vector<cudaEvent_t> fev;
+    // the requests still open when the job's launches ended, finished
+    // together: their records come from the job's whole read-back
+    std::vector<char> in_all;
+    cudaEvent_t fev_all = nullptr;
     std::chrono::steady_clock::time_point t0;
 };
 
@@ -193,6 +197,14 @@ void complete_request(eik_server_s* s, Slot& sl, int e) {
     const Ctl* ic = (const Ctl*)rec;
     const ResidualOut* r = (const ResidualOut*)(rec + sizeof(Ctl));
     const Ctl* g = (const Ctl*)(rec + sizeof(Ctl) + sizeof(ResidualOut));
+    if (sl.in_all[e]) {
+        // the job's read-back: 2n instance blocks, 2 launch blocks, n residuals
+        const int n = hj.j.n;
+        const Ctl* base = (const Ctl*)hj.zero_host;
+        ic = base + n + e;
+        g = base + 2 * n + 1;
+        r = (const ResidualOut*)(base + 2 * n + 2) + e;
+    }
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - sl.t0).count();
     eik_stats st;
     job_stats(hj.L[e], &sl.descs[e], hj.j.fp32, &zero, ic, &zero, g, r, hj.shift[e], hj.bw_main[e], ms, &st);
@@ -217,13 +229,42 @@ bool advance_slot(eik_server_s* s, Slot& sl) {
         progressed = true;
     }
     const int n = (int)sl.reqs.size();
+    if (sl.main_done) {
+        // the requests not yet finished: one node-wise launch over the job
+        // and one read-back of its counters, after the single ones queued
+        // before on the same stream
+        HostJob& hj = sl.job;
+        int open = 0;
+        for (int e = 0; e < n; ++e) open += sl.fin[e] == 0;
+        if (open) {
+            int rc = finish_instances(hj.j, sl.out);
+            for (int e = 0; e < n; ++e) {
+                if (sl.fin[e] != 0) continue;
+                if (!rc && hj.out_host[e] &&
+                    cudaMemcpyAsync(hj.out_user[e], hj.arr[e].Ostage, (size_t)hj.L[e].nx * hj.L[e].ny * 8,
+                                    cudaMemcpyDeviceToHost, sl.out) != cudaSuccess)
+                    rc = EIK_ECUDA;
+            }
+            cudaMemcpyAsync(hj.zero_host, hj.j.zero_base,
+                            (size_t)(2 * n + 2) * sizeof(Ctl) + (size_t)n * sizeof(ResidualOut),
+                            cudaMemcpyDeviceToHost, sl.out);
+            if (rc) cudaGetLastError();
+            cudaEventRecord(sl.fev_all, sl.out);
+            for (int e = 0; e < n; ++e)
+                if (sl.fin[e] == 0) {
+                    sl.fin[e] = 1;
+                    sl.in_all[e] = 1;
+                }
+            progressed = true;
+        }
+    }
     int complete = 0;
     for (int e = 0; e < n; ++e) {
-        if (sl.fin[e] == 0 && (sl.main_done || *(volatile unsigned*)(sl.done_h + e))) {
+        if (sl.fin[e] == 0 && *(volatile unsigned*)(sl.done_h + e)) {
             start_finish(sl, e);
             progressed = true;
         }
-        if (sl.fin[e] == 1 && cudaEventQuery(sl.fev[e]) == cudaSuccess) {
+        if (sl.fin[e] == 1 && cudaEventQuery(sl.in_all[e] ? sl.fev_all : sl.fev[e]) == cudaSuccess) {
             complete_request(s, sl, e);
             progressed = true;
         }
@@ -329,6 +370,7 @@ bool launch_slot(eik_server_s* s, Slot& sl, size_t held_by_others) {
     std::memset(sl.done_h, 0, (size_t)n * sizeof(unsigned));
     sl.job.done_dev = sl.done_d;
     sl.fin.assign(n, 0);
+    sl.in_all.assign(n, 0);
     sl.main_done = false;
     while ((int)sl.fev.size() < n) {
         cudaEvent_t e = nullptr;
@@ -433,6 +475,7 @@ extern "C" int eik_server_create(eik_server* out, size_t hbm_budget_bytes, int32
             return EIK_ECUDA;
         }
         for (auto& e : sl.ev) cudaEventCreate(&e);
+        cudaEventCreateWithFlags(&sl.fev_all, cudaEventDisableTiming);
     }
     try {
         s->worker = std::thread(server_loop, s);
@@ -517,6 +560,7 @@ extern "C" void eik_server_destroy(eik_server s) {
             if (e) cudaEventDestroy(e);
         for (auto& e : sl.fev)
             if (e) cudaEventDestroy(e);
+        if (sl.fev_all) cudaEventDestroy(sl.fev_all);
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.out) cudaStreamDestroy(sl.out);
         if (sl.done_h) cudaFreeHost(sl.done_h);
