@@ -141,7 +141,7 @@ def test_largest_grids_by_properties(eik, orc, n, prec):
     """The largest grids in this suite: 32769^2 in FP32_REFINE (1.07 G nodes,
     about half the 2^31-node limit, every array past 8 GB), 16385^2 in FP64
     and 8193^2 in FP32_REFINE, the sin20 speed with a centre source; all
-    three run the bucketed schedule the library picks for such grids.  The
+    three run the value-ordered schedule the library picks for such grids.  The
     oracle cannot solve them in seconds, so they are checked by properties
     that hold at any size: the source keeps q, every node is finite (no obstacles), and at
     20,000 sampled nodes the oracle's local update of eq. Eik_discr, applied
