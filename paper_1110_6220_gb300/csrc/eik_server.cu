@@ -90,6 +90,11 @@ struct Slot {
     // together: their records come from the job's whole read-back
     std::vector<char> in_all;
     cudaEvent_t fev_all = nullptr;
+    // the requests in the order their finishing work was queued on `out`:
+    // their events complete in that order, so the loop queries only the
+    // oldest one still pending
+    std::vector<int> fin_order;
+    size_t fin_head = 0;
     std::chrono::steady_clock::time_point t0;
 };
 
@@ -186,6 +191,7 @@ void start_finish(Slot& sl, int e) {
     if (rc) cudaGetLastError();
     cudaEventRecord(sl.fev[e], sl.out);
     sl.fin[e] = 1;
+    sl.fin_order.push_back(e);
 }
 
 // Request e's finishing work is done: its statistics, its ticket.
@@ -254,23 +260,25 @@ bool advance_slot(eik_server_s* s, Slot& sl) {
                 if (sl.fin[e] == 0) {
                     sl.fin[e] = 1;
                     sl.in_all[e] = 1;
+                    sl.fin_order.push_back(e);
                 }
             progressed = true;
         }
     }
-    int complete = 0;
-    for (int e = 0; e < n; ++e) {
-        if (sl.fin[e] == 0 && *(volatile unsigned*)(sl.done_h + e)) {
-            start_finish(sl, e);
-            progressed = true;
-        }
-        if (sl.fin[e] == 1 && cudaEventQuery(sl.in_all[e] ? sl.fev_all : sl.fev[e]) == cudaSuccess) {
-            complete_request(s, sl, e);
-            progressed = true;
-        }
-        complete += sl.fin[e] == 2;
+    if (!sl.main_done)
+        for (int e = 0; e < n; ++e)
+            if (sl.fin[e] == 0 && *(volatile unsigned*)(sl.done_h + e)) {
+                start_finish(sl, e);
+                progressed = true;
+            }
+    while (sl.fin_head < sl.fin_order.size()) {
+        const int e = sl.fin_order[sl.fin_head];
+        if (cudaEventQuery(sl.in_all[e] ? sl.fev_all : sl.fev[e]) != cudaSuccess) break;
+        complete_request(s, sl, e);
+        ++sl.fin_head;
+        progressed = true;
     }
-    if (complete == n && sl.main_done) {
+    if (sl.fin_head == (size_t)n && sl.main_done) {
         sl.reqs.clear();
         sl.busy = false;
         sl.bytes = 0;
@@ -371,6 +379,8 @@ bool launch_slot(eik_server_s* s, Slot& sl, size_t held_by_others) {
     sl.job.done_dev = sl.done_d;
     sl.fin.assign(n, 0);
     sl.in_all.assign(n, 0);
+    sl.fin_order.clear();
+    sl.fin_head = 0;
     sl.main_done = false;
     while ((int)sl.fev.size() < n) {
         cudaEvent_t e = nullptr;
