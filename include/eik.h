@@ -25,8 +25,11 @@
  * (i, j) at index j*nx + i, x_i = i*h, y_j = j*h.
  *
  * Pointers: every data pointer (F, sources, U) may be a host pointer or a
- * CUDA device pointer; the library detects which.  Host buffers are copied
- * through the plan's workspace; pinned host memory makes those copies faster.
+ * CUDA device pointer; the library detects which.  Pinned host F and U
+ * (cudaMallocHost, cudaHostAlloc, cudaHostRegister) are read and written in
+ * place by the kernels across the host link; pageable host buffers are copied
+ * through the plan's workspace.  Host source tables are always read by the
+ * host.
  * The caller owns all buffers; they must stay valid until the call that uses
  * them has returned (eik_solve, eik_solve_batch) or until eik_poll reports
  * EIK_OK (eik_submit).

@@ -65,6 +65,21 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// A host buffer the kernels can address in place -- pinned memory
+// (cudaMallocHost, cudaHostAlloc, cudaHostRegister) -- has a device address
+// for the current device: the init kernel then reads F, and the output kernel
+// writes U, across the host link with no staging copy.  Null for device and
+// pageable memory.
+const void* host_mapped(const void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // EIK_ALLOC_LIMIT (bytes; unset: none): every workspace need above it fails
 // as cudaMalloc would on a device that small, whether or not a buffer kept
 // from an earlier call could serve it -- a host-side way to drive the
@@ -152,6 +167,8 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
     hj->bw_main.resize(n);
     std::vector<HostSources> hs((size_t)n);
     std::vector<char> stageF((size_t)n);
+    std::vector<const double*> mapF((size_t)n, nullptr);  // pinned host F, U: their device addresses
+    std::vector<double*> mapU((size_t)n, nullptr);
     hj->L.resize(n);
     hj->arr.resize(n);
     hj->shift.resize(n);
@@ -214,8 +231,11 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
         const int rc = prepare_sources_host(hj->L[i], in[i].nsrc, (const int32_t*)sp,
                                             (const double*)(sp + (size_t)in[i].nsrc * 8), &hs[i]);
         if (rc) return rc;
-        stageF[i] = !is_device_ptr(in[i].F);
-        hj->out_host[i] = !is_device_ptr(in[i].U);
+        const bool dF = is_device_ptr(in[i].F), dU = is_device_ptr(in[i].U);
+        mapF[i] = dF ? nullptr : (const double*)host_mapped(in[i].F);
+        mapU[i] = dU ? nullptr : (double*)host_mapped(in[i].U);
+        stageF[i] = !dF && !mapF[i];
+        hj->out_host[i] = !dU && !mapU[i];
         hj->out_user[i] = in[i].U;
         hj->shift[i] = hs[i].node.empty() ? 0.0 : hs[i].q_min;
         nsrc += hs[i].node.size();
@@ -303,8 +323,8 @@ int build_job(HostJob* hj, int n, const eik_plan_desc* descs, const eik_instance
         a.visits = visits_all + coff;
         a.dflags = dflags_all + coff;
         hj->arr[i] = a;
-        const double* F = stageF[i] ? a.Fstage : in[i].F;
-        double* out = hj->out_host[i] ? a.Ostage : in[i].U;
+        const double* F = stageF[i] ? a.Fstage : mapF[i] ? mapF[i] : in[i].F;
+        double* out = hj->out_host[i] ? a.Ostage : mapU[i] ? mapU[i] : in[i].U;
         const double bw = descs[i].bucket_width;
         hj->bw_main[i] = bw != 0.0 ? bw : P.w_main;
         fill_inst_tables(L, a, fp32, descs[i].h, bw != 0.0 ? bw : P.w_first, hj->bw_main[i], &ictl_dev[i],

@@ -162,6 +162,71 @@ def test_device_pointers_match_host_pointers(eik, orc):
     compare(Uh, V, TOL64, "host pointers")
 
 
+def test_pinned_host_buffers_in_place(eik, orc):
+    """Pinned host F and U are read and written by the kernels in place (no
+    staging copy): single grids in both precisions, a batch mixing pinned,
+    pageable and device buffers, a fixed batch replayed with new speeds in the
+    same pinned buffer, and a served request -- each against the oracle."""
+    import time
+    import torch
+    I = W.checker_maze(300, seed=5, n_walls=4, n_src=2)
+    V = oracle_U(orc, I)
+    Fp = torch.from_numpy(I.F).pin_memory()
+    for prec, tol in ((eik.EIK_FP64, TOL64), (eik.EIK_FP32_REFINE, TOL32)):
+        Up = torch.full(I.F.shape, -1.0, dtype=torch.float64).pin_memory()
+        with eik.Plan(I.nx, I.ny, I.h, 8, prec) as p:
+            rc, st = p.solve(Fp, I.src_ij, I.sq, Up)
+        assert rc == 0, eik.eik_strerror(rc)
+        compare(Up.numpy(), V, tol, f"pinned F and U, precision {prec}")
+    # a batch: pinned, pageable and device buffers side by side
+    J = W.sin_point(129)
+    VJ = oracle_U(orc, J)
+    Ud = torch.empty(J.F.shape, dtype=torch.float64, device="cuda")
+    Upg = np.full_like(J.F, -1.0)
+    Upn = torch.full(I.F.shape, -1.0, dtype=torch.float64).pin_memory()
+    Fd = torch.from_numpy(J.F).cuda()
+    descs = [eik.make_desc(I.nx, I.ny, I.h, 16, eik.EIK_FP64), eik.make_desc(J.nx, J.ny, J.h, 16, eik.EIK_FP64),
+             eik.make_desc(J.nx, J.ny, J.h, 16, eik.EIK_FP64)]
+    insts = [eik.make_instance(Fp, I.src_ij, I.sq, Upn), eik.make_instance(J.F, J.src_ij, J.sq, Upg),
+             eik.make_instance(Fd, J.src_ij, J.sq, Ud)]
+    rc, sts = eik.eik_solve_batch(descs, insts)
+    assert rc == 0
+    compare(Upn.numpy(), V, TOL64, "batch, pinned")
+    compare(Upg, VJ, TOL64, "batch, pageable")
+    compare(Ud.cpu().numpy(), VJ, TOL64, "batch, device")
+    # a fixed batch replayed with new speeds written into the same pinned F
+    F2 = np.ascontiguousarray(I.F * 1.5)
+    b = eik.eik_batch_create([descs[0]], [insts[0]])
+    try:
+        assert eik.eik_batch_run(b)[0] == 0
+        compare(Upn.numpy(), V, TOL64, "fixed batch, pinned")
+        Fp.numpy()[...] = F2
+        assert eik.eik_batch_run(b)[0] == 0
+        Vs = orc.fmm(F2, I.h, I.si, I.sj, I.sq)
+        compare(Upn.numpy(), Vs, TOL64, "fixed batch, pinned, new speeds")
+    finally:
+        eik.eik_batch_destroy(b)
+    # a served request with pinned buffers
+    Fp.numpy()[...] = I.F
+    Ups = torch.full(I.F.shape, -1.0, dtype=torch.float64).pin_memory()
+    srv = eik.eik_server_create(1 << 30, 4)
+    try:
+        rc, t = eik.eik_submit(srv, eik.make_desc(I.nx, I.ny, I.h, 16, eik.EIK_FP32_REFINE),
+                               eik.make_instance(Fp, I.src_ij, I.sq, Ups))
+        assert rc == 0
+        t0 = time.perf_counter()
+        while True:
+            rc, st = eik.eik_poll(srv, t)
+            if rc != eik.EIK_EAGAIN:
+                break
+            assert time.perf_counter() - t0 < 60
+            time.sleep(2e-4)
+        assert rc == 0
+    finally:
+        eik.eik_server_destroy(srv)
+    compare(Ups.numpy(), V, TOL32, "served, pinned")
+
+
 def test_invalid_inputs_rejected(eik):
     I = W.const_point(33)
     F = I.F.copy()
