@@ -468,6 +468,87 @@ __device__ __forceinline__ bool diag_step_n(int ns, typename TileCfg<MODE, K>::T
     return diag_step<MODE, K, NS>(tU, tF, tG, flags, t2, lo, len, rl, sx, sy, on);
 }
 
+// Linear addressing of the anti-diagonal slots (k >= 16, FP32 and
+// double-float modes).  In sweep coordinates node u of diagonal t2 is
+// (jj, ii2) = (u, t2 - u) for t2 < k and (t2 - (k-1) + u, k-1-u) after; its
+// tile index (j+1) BW + i + 1 and flag index j k + i are therefore a base per
+// half plus u times a per-direction delta plus t2 times a per-half delta.
+// Computed once per visit, they leave one multiply-add per slot on the step's
+// dependent chain instead of the index arithmetic a fresh step would redo
+// after each warp barrier (measured: a step of a 16-node cell 468 -> 359
+// cycles for a warp alone, 925 -> 824 with three blocks per SM).
+struct DiagLin {
+    int qz0, qz1, fz0, fz1;  // node u = 0 at t2 = 0 of each half (the second extrapolated)
+    int dq0, dq1, df0, df1;  // per step, each half
+    int dqu, dfu;            // per unit of u
+};
+template <int K, int BW>
+__device__ __forceinline__ DiagLin diag_lin(bool sx, bool sy) {
+    DiagLin L;
+    const int sgx = sx ? 1 : -1, sgy = sy ? 1 : -1;
+    const int j0 = sy ? 0 : K - 1, i0 = sx ? 0 : K - 1;
+    L.qz0 = (j0 + 1) * BW + (i0 + 1);
+    L.fz0 = j0 * K + i0;
+    const int j1 = sy ? -(K - 1) : 2 * K - 2, i1 = sx ? K - 1 : 0;
+    L.qz1 = (j1 + 1) * BW + (i1 + 1);
+    L.fz1 = j1 * K + i1;
+    L.dq0 = sgx;
+    L.df0 = sgx;
+    L.dq1 = sgy * BW;
+    L.df1 = sgy * K;
+    L.dqu = sgy * BW - sgx;
+    L.dfu = sgy * K - sgx;
+    return L;
+}
+// One step with linear addresses: this lane's NS slots of diagonal t2 (len
+// nodes), loads first, then the branch-free updates, then the stores.
+template <int MODE, int K, int NS>
+__device__ __forceinline__ bool diag_step_lin(typename TileCfg<MODE, K>::T* tU,
+                                              const typename TileCfg<MODE, K>::FT* tF, unsigned char* flags, int t2,
+                                              int len, int rl, const DiagLin& L, bool on) {
+    using C = TileCfg<MODE, K>;
+    typename C::T cand[NS], old[NS];
+    bool ok[NS];
+    int qq[NS], ff[NS];
+    const bool first = t2 < K;
+    const int qb = first ? L.qz0 + L.dq0 * t2 : L.qz1 + L.dq1 * t2;
+    const int fb = first ? L.fz0 + L.df0 * t2 : L.fz1 + L.df1 * t2;
+#pragma unroll
+    for (int m = 0; m < NS; ++m) {
+        const int u = rl + C::LPD * m;
+        const bool a = on && u < len;
+        const int uu = a ? u : 0;  // an idle slot reads the diagonal's first node
+        const int q = qb + uu * L.dqu;
+        qq[m] = q;
+        ff[m] = fb + uu * L.dfu;
+        const auto fv = tF[q];
+        old[m] = tU[q];
+        const auto W = tU[q - 1], E = tU[q + 1], S = tU[q - C::BW], N = tU[q + C::BW];
+        ok[m] = a && updatable(fv);
+        if constexpr (MODE == MODE_F32) cand[m] = update_f32(W, E, S, N, fv);
+        else cand[m] = update_df(W, E, S, N, fv);
+    }
+    bool changed = false;
+#pragma unroll
+    for (int m = 0; m < NS; ++m) {
+        if (ok[m] && lt(cand[m], old[m])) {
+            tU[qq[m]] = cand[m];
+            flags[ff[m]] = 1;
+            changed = true;
+        }
+    }
+    return changed;
+}
+template <int MODE, int K, int NS = 1>
+__device__ __forceinline__ bool diag_step_lin_n(int ns, typename TileCfg<MODE, K>::T* tU,
+                                                const typename TileCfg<MODE, K>::FT* tF, unsigned char* flags,
+                                                int t2, int len, int rl, const DiagLin& L, bool on) {
+    if constexpr (NS < TileCfg<MODE, K>::RPL) {
+        if (ns > NS) return diag_step_lin_n<MODE, K, NS + 1>(ns, tU, tF, flags, t2, len, rl, L, on);
+    }
+    return diag_step_lin<MODE, K, NS>(tU, tF, flags, t2, len, rl, L, on);
+}
+
 // Fixed-point check of a whole tile (this lane's share): true if some node
 // would still decrease.  It is equivalent to asking whether another pass
 // would change anything -- a pass changes nothing exactly when no node can
@@ -860,6 +941,7 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
     bool gdone = c < 0;
     int s = 0;
     const int cap = w.cap;
+    [[maybe_unused]] const DiagLin dlin = diag_lin<K, C::BW>(sx, sy);
     for (; s < cap && __ballot_sync(FULL, !gdone) != 0u; ++s) {
         bool changed = false;
         for (int t2 = 0; t2 < 2 * K - 1; ++t2) {
@@ -940,27 +1022,42 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
                 const int lo = t2 < K ? 0 : t2 - (K - 1);
                 const int len = (t2 < K ? t2 : K - 1) - lo + 1;
                 const int ns = (len + C::LPD - 1) / C::LPD;
-                if (diag_step_n<MODE, K>(ns, tU, tF, tG, flags, t2, lo, len, rl, sx, sy, c >= 0 && (!FAST || dir_on)))
-                    changed = true;
+                const bool on = c >= 0 && (!FAST || dir_on);
+                // linear addresses where they measured faster: the value-
+                // ordered and bucketed kernels (the 4097^2 pass 10.47 ->
+                // 9.83 ms); the first-in first-out kernel at three blocks per
+                // SM keeps the indices per step (its 512-grid batch 14.46
+                // against 14.78 ms with linear addresses)
+                if constexpr (CVAL) {
+                    if (diag_step_lin_n<MODE, K>(ns, tU, tF, flags, t2, len, rl, dlin, on)) changed = true;
+                } else {
+                    if (diag_step_n<MODE, K>(ns, tU, tF, tG, flags, t2, lo, len, rl, sx, sy, on)) changed = true;
+                }
             } else {
                 // FP64: the slots one after another (its updates are bound by
                 // the FP64 pipe, not by the chain's latency, and the straight-
                 // line block measured slower: k = 32 11.4 against 8.2 ms on
                 // the 1025^2 sin20 grid)
-                const int lo = t2 < K ? 0 : t2 - (K - 1);
-                const int len = (t2 < K ? t2 : K - 1) - lo + 1;
+                const int len = t2 < K ? t2 + 1 : 2 * K - 1 - t2;
+                const bool first = t2 < K;  // linear addresses, as above
+                const int qb = first ? dlin.qz0 + dlin.dq0 * t2 : dlin.qz1 + dlin.dq1 * t2;
+                const int fb = first ? dlin.fz0 + dlin.df0 * t2 : dlin.fz1 + dlin.df1 * t2;
 #pragma unroll
                 for (int m = 0; m < C::RPL; ++m) {
                     if (m * C::LPD < len) {  // the same for every lane
                         const int u = rl + C::LPD * m;
                         if (u < len && c >= 0 && (!FAST || dir_on)) {
-                            const int jj = lo + u, ii2 = t2 - jj;
-                            const int j = sy ? jj : K - 1 - jj, i = sx ? ii2 : K - 1 - ii2;
-                            T cand, old;
-                            if (node_candidate<MODE, K>(tU, tF, tG, i, j, cand, old) && lt(cand, old)) {
-                                tU[(j + 1) * C::BW + (i + 1)] = cand;
-                                flags[j * K + i] = 1;
-                                changed = true;
+                            const int q = qb + u * dlin.dqu, fi = fb + u * dlin.dfu;
+                            const auto fv = tF[q];
+                            if (updatable(fv)) {
+                                const T old = tU[q];
+                                const T cand = update_f64(tU[q - 1], tU[q + 1], tU[q - C::BW], tU[q + C::BW], fv,
+                                                          reinterpret_cast<const float2*>(tG)[fi]);
+                                if (lt(cand, old)) {
+                                    tU[q] = cand;
+                                    flags[fi] = 1;
+                                    changed = true;
+                                }
                             }
                         }
                     }
