@@ -473,17 +473,19 @@ __device__ __forceinline__ bool diag_step_n(int ns, typename TileCfg<MODE, K>::T
 // (jj, ii2) = (u, t2 - u) for t2 < k and (t2 - (k-1) + u, k-1-u) after; its
 // tile index (j+1) BW + i + 1 and flag index j k + i are therefore a base per
 // half plus u times a per-direction delta plus t2 times a per-half delta.
-// Computed once per visit, they leave one multiply-add per slot on the step's
+// Computed once per visit, they leave an add per slot on the step's
 // dependent chain instead of the index arithmetic a fresh step would redo
-// after each warp barrier (measured: a step of a 16-node cell 468 -> 359
-// cycles for a warp alone, 925 -> 824 with three blocks per SM).
+// after each warp barrier (a step of a 16-node cell alone: 468 -> 359 cycles
+// for a warp, 925 -> 824 with three blocks per SM; the 4097^2 pass 10.47 ->
+// 9.59 ms, its sweeps ~29 K -> ~19 K cycles per visit).
 struct DiagLin {
     int qz0, qz1, fz0, fz1;  // node u = 0 at t2 = 0 of each half (the second extrapolated)
     int dq0, dq1, df0, df1;  // per step, each half
     int dqu, dfu;            // per unit of u
+    int qrl, frl, qsl, fsl;  // this lane's first slot (u = rl) and the slot stride (u += LPD)
 };
 template <int K, int BW>
-__device__ __forceinline__ DiagLin diag_lin(bool sx, bool sy) {
+__device__ __forceinline__ DiagLin diag_lin(bool sx, bool sy, int rl = 0, int lpd = 8) {
     DiagLin L;
     const int sgx = sx ? 1 : -1, sgy = sy ? 1 : -1;
     const int j0 = sy ? 0 : K - 1, i0 = sx ? 0 : K - 1;
@@ -498,6 +500,10 @@ __device__ __forceinline__ DiagLin diag_lin(bool sx, bool sy) {
     L.df1 = sgy * K;
     L.dqu = sgy * BW - sgx;
     L.dfu = sgy * K - sgx;
+    L.qrl = rl * L.dqu;
+    L.frl = rl * L.dfu;
+    L.qsl = lpd * L.dqu;
+    L.fsl = lpd * L.dfu;
     return L;
 }
 // One step with linear addresses: this lane's NS slots of diagonal t2 (len
@@ -517,10 +523,10 @@ __device__ __forceinline__ bool diag_step_lin(typename TileCfg<MODE, K>::T* tU,
     for (int m = 0; m < NS; ++m) {
         const int u = rl + C::LPD * m;
         const bool a = on && u < len;
-        const int uu = a ? u : 0;  // an idle slot reads the diagonal's first node
-        const int q = qb + uu * L.dqu;
+        // an idle slot reads the diagonal's first node
+        const int q = a ? qb + L.qrl + m * L.qsl : qb;
         qq[m] = q;
-        ff[m] = fb + uu * L.dfu;
+        ff[m] = a ? fb + L.frl + m * L.fsl : fb;
         const auto fv = tF[q];
         old[m] = tU[q];
         const auto W = tU[q - 1], E = tU[q + 1], S = tU[q - C::BW], N = tU[q + C::BW];
@@ -547,6 +553,42 @@ __device__ __forceinline__ bool diag_step_lin_n(int ns, typename TileCfg<MODE, K
         if (ns > NS) return diag_step_lin_n<MODE, K, NS + 1>(ns, tU, tF, flags, t2, len, rl, L, on);
     }
     return diag_step_lin<MODE, K, NS>(tU, tF, flags, t2, len, rl, L, on);
+}
+
+// A whole pass (2k-1 steps) as loops of a fixed slot count: diagonal t2
+// holds len = t2 + 1 nodes while rising and 2k-1-t2 after, so ns =
+// ceil(len / LPD) steps up from 1 to RPL over t2 < LPD (RPL - 1) and back
+// down over the last LPD (RPL - 1) steps; each loop's steps compile without
+// a dispatch on ns (a 16-node cell's step alone: 429 -> 359 cycles for a
+// warp, 703 -> 645 at two blocks per SM; the 4097^2 pass: 9.59 -> 9.56 ms,
+// whose visits now spend ~19 K of ~33 K cycles in sweeps).
+template <int MODE, int K, int NS = 1>
+__device__ __forceinline__ bool diag_pass_lin(typename TileCfg<MODE, K>::T* tU,
+                                              const typename TileCfg<MODE, K>::FT* tF, unsigned char* flags, int rl,
+                                              const DiagLin& L, bool on) {
+    using C = TileCfg<MODE, K>;
+    constexpr int P = C::LPD;
+    bool changed = false;
+    if constexpr (NS < C::RPL) {
+        // rising: t2 in [P (NS - 1), P NS); then the phases above; then falling
+        for (int t2 = P * (NS - 1); t2 < P * NS; ++t2) {
+            changed |= diag_step_lin<MODE, K, NS>(tU, tF, flags, t2, t2 + 1, rl, L, on);
+            __syncwarp();
+        }
+        changed |= diag_pass_lin<MODE, K, NS + 1>(tU, tF, flags, rl, L, on);
+        for (int t2 = 2 * K - 1 - P * NS; t2 < 2 * K - 1 - P * (NS - 1); ++t2) {
+            changed |= diag_step_lin<MODE, K, NS>(tU, tF, flags, t2, 2 * K - 1 - t2, rl, L, on);
+            __syncwarp();
+        }
+    } else {
+        // the middle: every diagonal of RPL slots
+        for (int t2 = P * (NS - 1); t2 < 2 * K - 1 - P * (NS - 1); ++t2) {
+            const int len = t2 < K ? t2 + 1 : 2 * K - 1 - t2;
+            changed |= diag_step_lin<MODE, K, NS>(tU, tF, flags, t2, len, rl, L, on);
+            __syncwarp();
+        }
+    }
+    return changed;
 }
 
 // Fixed-point check of a whole tile (this lane's share): true if some node
@@ -941,10 +983,15 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
     bool gdone = c < 0;
     int s = 0;
     const int cap = w.cap;
-    [[maybe_unused]] const DiagLin dlin = diag_lin<K, C::BW>(sx, sy);
+    [[maybe_unused]] const DiagLin dlin = diag_lin<K, C::BW>(sx, sy, rl, C::LPD);
     for (; s < cap && __ballot_sync(FULL, !gdone) != 0u; ++s) {
         bool changed = false;
-        for (int t2 = 0; t2 < 2 * K - 1; ++t2) {
+        // the value-ordered and bucketed kernels' pass in FP32 and double-
+        // float modes, k >= 16: loops of a fixed slot count, linear addresses
+        constexpr bool PHASED = DIAG && !LSM && CVAL && MODE != MODE_F64;
+        if constexpr (PHASED)
+            changed = diag_pass_lin<MODE, K>(tU, tF, flags, rl, dlin, c >= 0 && (!FAST || dir_on));
+        for (int t2 = 0; t2 < (PHASED ? 0 : 2 * K - 1); ++t2) {
             if constexpr (LSM) {
                 if constexpr (!DIAG) {
                     const unsigned ii2 = (unsigned)(t2 - jr);
