@@ -1201,7 +1201,24 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
         }
     }
     __syncwarp();
-    // ---- write back the nodes that changed (coalesced across lanes)
+    // ---- write back the nodes that changed (coalesced across lanes).  One
+    // cell per warp: the descriptor is read and the cell's origin formed once,
+    // before the stores (which the compiler must assume may alias it).
+    if constexpr (C::CPW == 1) {
+        if (cg[0] >= 0) {
+            const InstDesc& dc = inst[ig[0]];
+            const int cxn0 = dc.cxn;
+            const size_t up = dc.upitch;
+            T* const gbase = reinterpret_cast<T*>(dc.U) + (size_t)((cg[0] / cxn0) * K + 1) * up +
+                             (size_t)((cg[0] % cxn0) * K + 1);
+            const T* gU = reinterpret_cast<const T*>(wbase);
+#pragma unroll 8
+            for (int e = lane; e < K * K; e += 32) {
+                const int j = e / K, i = e - (e / K) * K;
+                if ((masks[j] >> i) & 1ull) gbase[(size_t)j * up + i] = gU[(j + 1) * C::BW + (i + 1)];
+            }
+        }
+    } else
     for (int e = lane; e < C::CPW * K * K; e += 32) {
         const int gg = e / (K * K);
         const int rem = e - gg * K * K;
@@ -1739,20 +1756,28 @@ __device__ __forceinline__ int bq_read(const SolveParams& p, Ctl* gctl, unsigned
 }
 // Request a cell (global index e) whose activation proposes cell-value key
 // `key`: count it under its bucket, then hand it to a parked warp (within
-// the window) or file it.
+// the window) or file it.  f and waiters: the front and the parked warps as
+// the caller read them, before its own atomics (their loads then overlap the
+// caller's round trips; a stale front only sends the count round once more).
+// A cell handed on takes its ticket of the parking ring together with its
+// count: a cell within the window stays within it when the front moves up,
+// since its bucket rises to the new front at most.
 __device__ __forceinline__ bool bq_request(const SolveParams& p, Ctl* gctl, unsigned e, unsigned long long key,
-                                           double inv_delta, unsigned long long deadline) {
-    unsigned f = ld_vol(&p.bq[BQ_FRONT]);
-    int waiters = ring_waiters(p);
+                                           double inv_delta, unsigned long long deadline, unsigned f, int waiters) {
     const double v = key == KEY_UNSET ? inf_of<double>() : val_of(key) * inv_delta;
     const unsigned a0 = v < 1073741824.0 ? (unsigned)v : 1073741824u;
-    unsigned a, s;
-    for (unsigned tries = 1;; ++tries) {
-        a = a0 < f ? f : a0;
-        a = a > f + NBQ - 1 ? f + NBQ - 1 : a;
-        s = a & (NBQ - 1);
-        const unsigned long long old = atomicAdd(bq_cw(p, s), 1ull);
-        if ((old & CW_CLOSED) == 0 && (old >> 33) == (unsigned long long)(a / NBQ)) break;
+    unsigned a = a0 < f ? f : a0;
+    a = a > f + NBQ - 1 ? f + NBQ - 1 : a;
+    const bool hand = a <= f + (unsigned)p.bq_window && waiters > 0;
+    unsigned t = 0;
+    if (hand) {
+        QEV(3);
+        t = atomicAdd(&p.qctl[Q_TAIL], 1u);
+    }
+    unsigned s = a & (NBQ - 1);
+    unsigned long long old = atomicAdd(bq_cw(p, s), 1ull);
+    bool moved = false;
+    for (unsigned tries = 1; (old & CW_CLOSED) != 0 || (old >> 33) != (unsigned long long)(a / NBQ); ++tries) {
         // the front moved past this bucket: file the cell under the new front
         atomicAdd(bq_cw(p, s), ~0ull);
         QEV(4);
@@ -1760,12 +1785,21 @@ __device__ __forceinline__ bool bq_request(const SolveParams& p, Ctl* gctl, unsi
             fail(gctl, EIK_ETIMEDOUT, 0x6500000ull);
             return false;
         }
+        moved = true;
         f = ld_vol(&p.bq[BQ_FRONT]);
-        waiters = ring_waiters(p);
+        a = a0 < f ? f : a0;
+        a = a > f + NBQ - 1 ? f + NBQ - 1 : a;
+        s = a & (NBQ - 1);
+        old = atomicAdd(bq_cw(p, s), 1ull);
     }
     const unsigned ent = e | (s << CELL_BITS);
-    if (a <= f + (unsigned)p.bq_window && waiters > 0) return give(p, gctl, ent, deadline);
+    if (hand) return ring_fill(p, gctl, t, ent, deadline);
+    if (moved && a <= f + (unsigned)p.bq_window && ring_waiters(p) > 0) return give(p, gctl, ent, deadline);
     return bq_put(p, gctl, s, ent, deadline);
+}
+__device__ __forceinline__ bool bq_request(const SolveParams& p, Ctl* gctl, unsigned e, unsigned long long key,
+                                           double inv_delta, unsigned long long deadline) {
+    return bq_request(p, gctl, e, key, inv_delta, deadline, ld_vol(&p.bq[BQ_FRONT]), ring_waiters(p));
 }
 // Warp-wide scan of the bucket rings in one round trip (lane L reads ring
 // L's head and tail, lane 0 the front too): the mask of rings, rotated so
@@ -2139,6 +2173,14 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32,
             w, inst, gctl, deadline, c, ii, first, cg, ig, prof_on, pacc, pt,
             [&](const InstDesc& dn, int nc, unsigned long long kk, unsigned long long old, bool activate) {
                 if (!activate) return;
+                // ORD: the front and the parked warps, read while the flag's
+                // atomic is on its way
+                unsigned f_pre = 0u;
+                int w_pre = 0;
+                if constexpr (ORD) {
+                    f_pre = ld_vol(&p.bq[BQ_FRONT]);
+                    w_pre = ring_waiters(p);
+                }
                 const int was = atomicOr(&dn.qflag[nc], 1) & 3;
                 if (was == 0) {
                     atomicAdd(&p.qctl[Q_PENDING], 1u);
@@ -2148,7 +2190,7 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32,
                         // the cell's own value, lowered by every earlier proposal,
                         // would rank a cell visited before at its old value
                         // (an activation always has a finite side, so a proposal)
-                        bq_request(p, gctl, (unsigned)(dn.cell_base + nc), kk, inv_delta, deadline);
+                        bq_request(p, gctl, (unsigned)(dn.cell_base + nc), kk, inv_delta, deadline, f_pre, w_pre);
                     } else {
                         if (p.hold_ns) p.req_time[dn.cell_base + nc] = gtimer();
                         ring_push(p, gctl, (unsigned)(dn.cell_base + nc), deadline);
@@ -2169,8 +2211,13 @@ __global__ void __launch_bounds__(TileCfg<MODE, K>::WPB * 32,
             const bool last = !(old & 1) && p.inst_done && atomicSub(&d.ctl->left, 1) == 1;
             if constexpr (ORD) {
                 if (old & 1) {
+                    // requested again while it ran: filed by the lowest value
+                    // proposed meanwhile (its reads all in flight at once)
+                    const unsigned f_pre = ld_vol(&p.bq[BQ_FRONT]);
+                    const int w_pre = ring_waiters(p);
+                    const unsigned long long cv = ld_cg(&d.cval[c]);
                     const unsigned long long rk = atomicExch(&p.req_time[e], 0ull);
-                    bq_request(p, gctl, (unsigned)e, rk ? ~rk : ld_cg(&d.cval[c]), inv_delta, deadline);
+                    bq_request(p, gctl, (unsigned)e, rk ? ~rk : cv, inv_delta, deadline, f_pre, w_pre);
                 } else {
                     atomicSub(&p.qctl[Q_PENDING], 1u);
                 }
