@@ -422,52 +422,6 @@ __device__ __forceinline__ bool node_eval(const typename TileCfg<MODE, K>::T* tU
     return upd;
 }
 
-// One anti-diagonal step of a direction's sweep for k >= 16: this lane's NS
-// slots (nodes u = rl, rl + LPD, ... of diagonal t2, which starts at row lo
-// and has len nodes) are independent, so their loads and updates form one
-// straight-line block and the warp waits for one update chain per step, not
-// one per slot.  Returns whether a node decreased (its flag set).
-template <int MODE, int K, int NS>
-__device__ __forceinline__ bool diag_step(typename TileCfg<MODE, K>::T* tU, const typename TileCfg<MODE, K>::FT* tF,
-                                          const double* tG, unsigned char* flags, int t2, int lo, int len, int rl,
-                                          bool sx, bool sy, bool on) {
-    using C = TileCfg<MODE, K>;
-    typename C::T cand[NS], old[NS];
-    bool ok[NS];
-    int qi[NS];
-#pragma unroll
-    for (int m = 0; m < NS; ++m) {
-        const int u = rl + C::LPD * m;
-        const bool a = on && u < len;
-        const int jj = lo + (a ? u : 0), ii2 = t2 - jj;  // a node of the diagonal either way
-        const int j = sy ? jj : K - 1 - jj, i = sx ? ii2 : K - 1 - ii2;
-        qi[m] = j * K + i;
-        ok[m] = node_eval<MODE, K>(tU, tF, tG, i, j, a, cand[m], old[m]);
-    }
-    bool changed = false;
-#pragma unroll
-    for (int m = 0; m < NS; ++m) {
-        if (ok[m] && lt(cand[m], old[m])) {
-            const int j = qi[m] / K, i = qi[m] - j * K;
-            tU[(j + 1) * C::BW + (i + 1)] = cand[m];
-            flags[qi[m]] = 1;
-            changed = true;
-        }
-    }
-    return changed;
-}
-// ns (the same for every lane) slots this step
-template <int MODE, int K, int NS = 1>
-__device__ __forceinline__ bool diag_step_n(int ns, typename TileCfg<MODE, K>::T* tU,
-                                            const typename TileCfg<MODE, K>::FT* tF, const double* tG,
-                                            unsigned char* flags, int t2, int lo, int len, int rl, bool sx, bool sy,
-                                            bool on) {
-    if constexpr (NS < TileCfg<MODE, K>::RPL) {
-        if (ns > NS) return diag_step_n<MODE, K, NS + 1>(ns, tU, tF, tG, flags, t2, lo, len, rl, sx, sy, on);
-    }
-    return diag_step<MODE, K, NS>(tU, tF, tG, flags, t2, lo, len, rl, sx, sy, on);
-}
-
 // Linear addressing of the anti-diagonal slots (k >= 16, FP32 and
 // double-float modes).  In sweep coordinates node u of diagonal t2 is
 // (jj, ii2) = (u, t2 - u) for t2 < k and (t2 - (k-1) + u, k-1-u) after; its
@@ -477,7 +431,8 @@ __device__ __forceinline__ bool diag_step_n(int ns, typename TileCfg<MODE, K>::T
 // dependent chain instead of the index arithmetic a fresh step would redo
 // after each warp barrier (a step of a 16-node cell alone: 468 -> 359 cycles
 // for a warp, 925 -> 824 with three blocks per SM; the 4097^2 pass 10.47 ->
-// 9.59 ms, its sweeps ~29 K -> ~19 K cycles per visit).
+// 9.59 ms, its sweeps ~29 K -> ~19 K cycles per visit; with the loops of a
+// fixed slot count below, the 512-grid batch's pass 11.6 -> 11.1 ms).
 struct DiagLin {
     int qz0, qz1, fz0, fz1;  // node u = 0 at t2 = 0 of each half (the second extrapolated)
     int dq0, dq1, df0, df1;  // per step, each half
@@ -545,16 +500,6 @@ __device__ __forceinline__ bool diag_step_lin(typename TileCfg<MODE, K>::T* tU,
     }
     return changed;
 }
-template <int MODE, int K, int NS = 1>
-__device__ __forceinline__ bool diag_step_lin_n(int ns, typename TileCfg<MODE, K>::T* tU,
-                                                const typename TileCfg<MODE, K>::FT* tF, unsigned char* flags,
-                                                int t2, int len, int rl, const DiagLin& L, bool on) {
-    if constexpr (NS < TileCfg<MODE, K>::RPL) {
-        if (ns > NS) return diag_step_lin_n<MODE, K, NS + 1>(ns, tU, tF, flags, t2, len, rl, L, on);
-    }
-    return diag_step_lin<MODE, K, NS>(tU, tF, flags, t2, len, rl, L, on);
-}
-
 // A whole pass (2k-1 steps) as loops of a fixed slot count: diagonal t2
 // holds len = t2 + 1 nodes while rising and 2k-1-t2 after, so ns =
 // ceil(len / LPD) steps up from 1 to RPL over t2 < LPD (RPL - 1) and back
@@ -986,9 +931,9 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
     [[maybe_unused]] const DiagLin dlin = diag_lin<K, C::BW>(sx, sy, rl, C::LPD);
     for (; s < cap && __ballot_sync(FULL, !gdone) != 0u; ++s) {
         bool changed = false;
-        // the value-ordered and bucketed kernels' pass in FP32 and double-
-        // float modes, k >= 16: loops of a fixed slot count, linear addresses
-        constexpr bool PHASED = DIAG && !LSM && CVAL && MODE != MODE_F64;
+        // FP32 and double-float passes with k >= 16: loops of a fixed slot
+        // count with linear addresses (the t2 loop below then runs no step)
+        constexpr bool PHASED = DIAG && !LSM && MODE != MODE_F64;
         if constexpr (PHASED)
             changed = diag_pass_lin<MODE, K>(tU, tF, flags, rl, dlin, c >= 0 && (!FAST || dir_on));
         for (int t2 = 0; t2 < (PHASED ? 0 : 2 * K - 1); ++t2) {
@@ -1063,24 +1008,7 @@ __device__ __forceinline__ bool visit_cells(WarpState<MODE, K>& w, const InstDes
                     chg |= 1u << i;
                     changed = true;
                 }
-            } else if constexpr (MODE != MODE_F64) {
-                // anti-diagonal t2 (in sweep order): rows lo .. lo + len - 1,
-                // ceil(len / LPD) slots per lane, one straight-line block
-                const int lo = t2 < K ? 0 : t2 - (K - 1);
-                const int len = (t2 < K ? t2 : K - 1) - lo + 1;
-                const int ns = (len + C::LPD - 1) / C::LPD;
-                const bool on = c >= 0 && (!FAST || dir_on);
-                // linear addresses where they measured faster: the value-
-                // ordered and bucketed kernels (the 4097^2 pass 10.47 ->
-                // 9.83 ms); the first-in first-out kernel at three blocks per
-                // SM keeps the indices per step (its 512-grid batch 14.46
-                // against 14.78 ms with linear addresses)
-                if constexpr (CVAL) {
-                    if (diag_step_lin_n<MODE, K>(ns, tU, tF, flags, t2, len, rl, dlin, on)) changed = true;
-                } else {
-                    if (diag_step_n<MODE, K>(ns, tU, tF, tG, flags, t2, lo, len, rl, sx, sy, on)) changed = true;
-                }
-            } else {
+            } else if constexpr (MODE == MODE_F64) {
                 // FP64: the slots one after another (its updates are bound by
                 // the FP64 pipe, not by the chain's latency, and the straight-
                 // line block measured slower: k = 32 11.4 against 8.2 ms on
