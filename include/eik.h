@@ -246,16 +246,16 @@ void eik_batch_destroy(eik_batch b);
  * built-in choices measured on GB300.  Plans take the choice at
  * eik_plan_create; batches and served jobs at each call.
  *
- * Each pass runs either in bucketed rounds (a grid barrier per round) or
- * round-free: warps take cells from a device-side ring as they come, in
- * first-in first-out order, with no buckets.  FP32_REFINE runs either as an
- * FP32 pass followed by a double-float refinement pass seeded from it, or as
- * one double-float pass from the sources; both take every update on the FP32
- * pipe and end with the same FP64 residual certificate.  Built in, single
- * grids up to about 4096^2 run round-free and larger ones in bucketed rounds
- * of 16-node cells: on the ring a smooth field's cells are revisited more
- * often the larger the grid, while buckets keep the visits per cell near
- * constant.
+ * Each pass runs on one of the schedules above (EIK_SCHED_*).  FP32_REFINE
+ * runs either as an FP32 pass followed by a double-float refinement pass
+ * seeded from it, or as one double-float pass from the sources; both take
+ * every update on the FP32 pipe and end with the same FP64 residual
+ * certificate.  Built in: single FP64 grids from about 512^2, and single
+ * FP32_REFINE grids from about 4096^2 (cells of 16), run in value order,
+ * which keeps the visits per cell low where a first-in first-out queue's grow
+ * with the grid; smaller single grids and all batches run first in, first
+ * out (batches with cells of 16), where the value order's queue costs more
+ * than the visits it saves.
  *
  * eik_tune: time trial solves of the given instances, run as one job like
  * eik_solve_batch (n_inst = 1: like eik_solve), over k in {8, 16, 32}, rounds
