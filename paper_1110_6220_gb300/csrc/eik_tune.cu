@@ -1,6 +1,7 @@
-// eik_tune.cu -- the cell size k and the bucket width of each pass, per
-// class of job, and the autotuner that fills that table by timing trial
-// solves (eik_tune / eik_tune_save / eik_tune_load / eik_tune_reset).
+// eik_tune.cu -- the cell size k, the schedule and bucket width of each pass
+// (and the value order's window), per class of job, and the autotuner that
+// fills that table by timing trial solves (eik_tune / eik_tune_save /
+// eik_tune_load / eik_tune_reset).
 //
 // The paper leaves k to the user (Sec. 4's HCM/FHCM tables sweep it) and the
 // bucket width of Dial's method (Sec. 2) is a free parameter of the bucketed
@@ -56,46 +57,32 @@ int side_class(const eik_plan_desc* d, int n) {
     return (int)std::lround(0.5 * std::log2(std::max(pts, 1.0)));
 }
 
-// Built-in choices, from sweeps on GB300 over k in {8, 16, 32} and relative
-// widths 2..256 (single 1025^2 sin-product grid in both precisions, 4097^2
-// checkerboard + maze, 512 uneven grids):
-//  - single grid, FP64: k = 8 with one wide bucket (pure label correcting in
-//    rounds) was fastest, 1.7x the time of 4-cell buckets;
-//  - single grid, FP32 + refinement: k = 8, FP32 pass at 256, refinement at 16;
-//  - batches: k = 16, FP32 pass at 64, refinement (and FP64) at 4.
-//  - FP32 + refinement runs as one double-float pass from the sources on the
-//    round-free schedule (k_solve_async): 2.10 ms on the 1025^2 grid against
-//    4.89 ms for an FP32 pass plus a refinement pass, 8.2 ms against 21.6 ms
-//    on a 2049^2 checkerboard + maze, 28.7 ms against 56.6 ms on the batch.
-//    A double-float visit costs about a quarter of an FP64 one (the FP64 pipe
-//    is slow), and a pass from the sources visits each cell a few times where
-//    a refinement pass seeded everywhere revisits it on every upstream change;
-//  - FP64 first stayed on rounds: round-free, it visits each cell 4-5x as
-//    often, and FP64 visits are the costly ones; once a hold could merge
-//    requests without idling warps, round-free won from ~1024^2 (below).
-//  - single grids of about 4096^2 and more hold each round-free cell: a
-//    cell requested less than the hold ago goes back to the ring, so the
-//    requests of several upstream neighbours merge into one visit (first
-//    measured with the warp waiting instead: 8 us took the 4097^2
-//    checkerboard + maze from 39 visits per cell to 21, 33.8 ms to 23.7 ms);
-//    on 1025^2 and on the batch a hold saves nothing or costs time.
-//  - the tuner (eik_tune) on each class then moved three choices: FP64
-//    batches run round-free (46.2 ms instead of 75.8 ms on the 512-grid mix,
-//    k = 8; at k = 16 once its sweeps skipped empty slots, below), small
-//    FP64 grids too (129^2: 0.32 ms instead of 0.37 ms), and ~2048^2 grids
-//    hold for 4 us (2049^2 maze: 6.3 ms for 6.8 ms).
-//  - single grids of about 8192^2 and more go back to rounds, k = 16: on the
-//    round-free ring the visits per cell of the sin20 grid grow with the
-//    side (21 at 1025^2, 38 at 8193^2, 76 at 16385^2, 159 at 32769^2), while
-//    value-ordered buckets keep them at 3-5.  Double-float, sin20: 34 / 92 /
-//    274 ms at m = 16 against 76 / 558 / 4669 ms round-free; the 4097^2 tie
-//    (13.5 against 13.0 ms) keeps it round-free there.  A checkerboard +
-//    maze keeps ~21 visits per cell round-free at any size and needs more
-//    buckets (its values are longer detours), so m = 64, which costs it
-//    64 / 190 ms against 46 / 167 ms round-free at 8193^2 / 16385^2 and
-//    gives sin20 45 / 122 / 404 ms.  FP64 at m = 32: the maze 158 / 468 ms
-//    against 179 / 588 ms round-free; sin20 at m = 16 51 / 130 ms against
-//    202 / 1448 ms.
+// Built-in choices, from sweeps on GB300 over k in {8, 16, 32}, relative
+// widths 2..256 and the three schedules (single 1025^2 sin-product grids in
+// both precisions, 4097^2 checkerboard + maze, 8193^2 and larger sin20
+// grids, 512 uneven grids).  The measurements that set each one stand beside
+// it in builtin() below; the history, in brief:
+//  - FP32 + refinement runs as one double-float pass from the sources: 2.10
+//    ms on the 1025^2 grid against 4.89 ms for an FP32 pass plus a
+//    refinement pass, 8.2 against 21.6 ms on a 2049^2 checkerboard + maze,
+//    28.7 against 56.6 ms on the batch.  A double-float visit costs about a
+//    quarter of an FP64 one (the FP64 pipe is slow), and a pass from the
+//    sources visits each cell a few times where a refinement pass seeded
+//    everywhere revisits it on every upstream change.
+//  - Bucketed rounds pay a grid barrier per round (~19 us however few cells
+//    it holds); the first-in first-out ring pays revisits that grow with the
+//    grid side (21 visits per cell at 1025^2, 38 at 8193^2, 159 at 32769^2
+//    on sin20).  The value-ordered schedule keeps the buckets and drops the
+//    rounds, and wins for single grids from ~512^2 in FP64 and ~4096^2 in
+//    FP32_REFINE; below that (and on every batch, where its queue costs more
+//    than the visits it saves) first in, first out stays.
+//  - A hold on the first-in first-out ring (a cell requested less than the
+//    hold ago goes back to the ring, so the requests of several upstream
+//    neighbours merge into one visit) pays at ~2048^2 only.
+//  - The tuner (eik_tune) on each class moved some choices: FP64 batches run
+//    round-free (46.2 ms instead of 75.8 ms on the 512-grid mix in rounds),
+//    small FP64 grids too (129^2: 0.32 ms instead of 0.37 ms), ~2048^2
+//    grids hold for 4 us (2049^2 maze: 6.3 ms for 6.8 ms).
 Entry builtin(int prec, bool batch, int side, bool fhcm) {
     // the value-ordered round-free schedule (bucket rings of the proposed
     // cell value, a front without barriers, a window of `w` buckets above it)
