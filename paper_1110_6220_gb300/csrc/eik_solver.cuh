@@ -1,19 +1,22 @@
-// eik_solver.cuh -- the persistent, bucketed cell solver, templated on the
-// arithmetic mode and the cell size K.  Instantiated by eik_solver_*.cu.
+// eik_solver.cuh -- the persistent cell solvers, templated on the arithmetic
+// mode and the cell size K.  Instantiated by eik_solver_*.cu.
 //
 // What one launch computes (Chacon & Vladimirsky, Sec. 4.2):
 //   Alg. generic_LC_cells with the HCM refinements -- cells carry cell values
-//   (eq. cell_value) and four directional flags (Remark HCM_preferred_sweeps);
-//   a removed cell is swept to convergence with its preferred directions first
-//   and the Alg. FSM_order cycle afterwards; a changed boundary value V_i with
-//   V_i < V_j (x_j across the boundary, not in Q) activates the neighbour.
-// GPU recast: instead of popping the single smallest cell from a heap, every
-// queued cell whose value lies within `delta` of the smallest one is released
-// at once (one "bucket"), and the bucket's cells are processed concurrently
-// by all warps.  Re-activations that fall inside the current bucket are
-// processed in the next round; the others wait in a far list.  Theorem
-// convergence (any removal order, exact per-cell solves) makes the result the
-// exact solution of eq. Eik_discr regardless of this schedule.
+//   (eq. cell_value); a removed cell is swept to convergence in the four
+//   directions of Alg. FSM_order (here all four at once, one warp per cell);
+//   a changed boundary value V_i with V_i < V_j (x_j across the boundary, not
+//   in Q) activates the neighbour.
+// GPU recast: no heap.  Three orders of removal, each exact by Theorem
+// convergence (any removal order, exact per-cell solves):
+//   - k_solve, bucketed rounds: every queued cell whose value lies within
+//     `delta` of the smallest is released at once and processed by all
+//     warps; re-activations run in the next round, after a grid barrier;
+//   - k_solve_async, first in first out: each warp takes the next requested
+//     cell from a device ring as soon as it is free;
+//   - k_solve_async with ORD, value order: Dial's buckets without rounds
+//     (bucket rings, a front that moves up as its bucket empties, a window
+//     of buckets above it that warps take cells from).
 //
 // All stored values are >= +0 (the host shifts q by its minimum), so the
 // bit patterns of doubles and floats order like the values: min and compare
