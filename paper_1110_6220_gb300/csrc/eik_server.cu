@@ -171,7 +171,9 @@ void complete_slot(eik_server_s* s, Slot& sl) {
 // Per-instance completion: queue request e's finishing work on the slot's
 // second stream -- the node-wise kernel that certifies and writes its
 // output, the copy of a host U, and the read-back of its control block and
-// residual (and of the launch's, once the job's launches are over).
+// residual.  Called only while the job's launches run (requests still open
+// when they end are finished together, in advance_slot), so the launch-wide
+// block's record stays zero.
 void start_finish(Slot& sl, int e) {
     HostJob& hj = sl.job;
     const int n = hj.j.n;
@@ -183,11 +185,7 @@ void start_finish(Slot& sl, int e) {
         rc = EIK_ECUDA;
     cudaMemcpyAsync(rec, hj.j.ictl + n + e, sizeof(Ctl), cudaMemcpyDeviceToHost, sl.out);
     cudaMemcpyAsync(rec + sizeof(Ctl), hj.j.res + e, sizeof(ResidualOut), cudaMemcpyDeviceToHost, sl.out);
-    if (sl.main_done)
-        cudaMemcpyAsync(rec + sizeof(Ctl) + sizeof(ResidualOut), hj.j.gctl + 1, sizeof(Ctl), cudaMemcpyDeviceToHost,
-                        sl.out);
-    else
-        std::memset(rec + sizeof(Ctl) + sizeof(ResidualOut), 0, sizeof(Ctl));
+    std::memset(rec + sizeof(Ctl) + sizeof(ResidualOut), 0, sizeof(Ctl));
     if (rc) cudaGetLastError();
     cudaEventRecord(sl.fev[e], sl.out);
     sl.fin[e] = 1;
